@@ -1,0 +1,138 @@
+"""Least squares through the QR factors, its backward error, and
+augmented-system iterative refinement (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+The paper names applying Q and forming Q as the natural follow-ups of the
+tiled factorization (Section 5); least squares is their first user:
+    min ||A x - b||,  A = Q [R; 0]  =>  x = R[:n, :n]^{-1} (Q^T b)[:n].
+
+Backward error (the paper is silent; normwise reading recorded with the
+design notes):
+    eta(x) = ||A^T r||_2 / (||A||_F (||A||_F ||x||_2 + ||b||_2)),  r = b - A x.
+
+Refinement (the paper is silent): Bjorck's iterative refinement of the
+augmented system
+    [ I   A ] [r]   [b]
+    [ A^T 0 ] [x] = [0]
+with residuals in float64 and each correction solved through a QR
+factorization (possibly of lower accuracy):
+    f = b - r - A x,  g = -A^T r
+    h  = R^{-T} g,  d = Q^T f = [d1; d2]
+    dx = R^{-1} (d1 - h),  dr = Q [h; d2]
+    x += dx, r += dr.
+"""
+
+import numpy as np
+
+from .householder import geqr2, apply_qt as _apply_qt_unblocked, apply_q as _apply_q_unblocked
+
+
+def back_substitution(R, C):
+    """Solve R X = C for upper triangular n x n R, one row at a time from the
+    bottom (plain loop)."""
+    R = np.asarray(R, dtype=np.float64)
+    X = np.array(C, dtype=np.float64, copy=True)
+    if X.ndim == 1:
+        X = X[:, None]
+    n = R.shape[0]
+    for i in reversed(range(n)):
+        if i + 1 < n:
+            X[i, :] -= R[i, i + 1:n] @ X[i + 1:n, :]
+        X[i, :] /= R[i, i]
+    return X
+
+
+def forward_substitution_rt(R, G):
+    """Solve R^T H = G for upper triangular R (so R^T is lower), top down."""
+    R = np.asarray(R, dtype=np.float64)
+    H = np.array(G, dtype=np.float64, copy=True)
+    if H.ndim == 1:
+        H = H[:, None]
+    n = R.shape[0]
+    for i in range(n):
+        if i > 0:
+            H[i, :] -= R[:i, i] @ H[:i, :]
+        H[i, :] /= R[i, i]
+    return H
+
+
+class QRSolver:
+    """Least-squares solves from one unblocked QR factorization (m >= n)."""
+
+    def __init__(self, A):
+        A = np.asarray(A, dtype=np.float64)
+        self.m, self.n = A.shape
+        assert self.m >= self.n
+        self.F, self.tau = geqr2(A)
+        self.R = np.triu(self.F[:self.n, :self.n])
+
+    def qt(self, B):
+        return _apply_qt_unblocked(self.F, self.tau, B)
+
+    def q(self, B):
+        return _apply_q_unblocked(self.F, self.tau, B)
+
+    def solve(self, B):
+        B = np.asarray(B, dtype=np.float64)
+        vec = B.ndim == 1
+        C = self.qt(B[:, None] if vec else B)
+        X = back_substitution(self.R, C[:self.n])
+        return X[:, 0] if vec else X
+
+
+def lstsq(A, B):
+    """x = argmin ||A x - b|| for full-rank m x n A, m >= n."""
+    return QRSolver(A).solve(B)
+
+
+def backward_error(A, x, b):
+    """Normwise backward error of an LS solution (columnwise for several
+    right-hand sides: returns the max over columns)."""
+    A = np.asarray(A, dtype=np.float64)
+    x = np.asarray(x, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64)
+    if x.ndim == 1:
+        x = x[:, None]
+        b = b[:, None]
+    nA = np.linalg.norm(A, "fro")
+    worst = 0.0
+    for c in range(x.shape[1]):
+        r = b[:, c] - A @ x[:, c]
+        eta = np.linalg.norm(A.T @ r) / (nA * (nA * np.linalg.norm(x[:, c]) + np.linalg.norm(b[:, c])))
+        worst = max(worst, eta)
+    return worst
+
+
+def augmented_refinement(A, b, solver, tol=1e-12, maxit=30, x0=None):
+    """Bjorck's refinement of the augmented system with float64 residuals.
+
+    ``solver`` is a QRSolver-like object (methods qt, q and attribute R) of a
+    possibly perturbed or lower-accuracy factorization of A.  Returns
+    (x, r, iterations, backward errors per iteration).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64).ravel()
+    m, n = A.shape
+    R = np.asarray(solver.R, dtype=np.float64)
+    if x0 is None:
+        c = np.asarray(solver.qt(b[:, None]), dtype=np.float64)[:, 0]
+        x = back_substitution(R, c[:n])[:, 0]
+    else:
+        x = np.array(x0, dtype=np.float64)
+    r = b - A @ x
+    history = [backward_error(A, x, b)]
+    it = 0
+    while history[-1] > tol and it < maxit:
+        f = b - r - A @ x
+        g = -(A.T @ r)
+        h = forward_substitution_rt(R, g)[:, 0]
+        d = np.asarray(solver.qt(f[:, None]), dtype=np.float64)[:, 0]
+        dx = back_substitution(R, (d[:n] - h)[:, None])[:, 0]
+        y = np.concatenate([h, d[n:]])
+        dr = np.asarray(solver.q(y[:, None]), dtype=np.float64)[:, 0]
+        x = x + dx
+        r = r + dr
+        it += 1
+        history.append(backward_error(A, x, b))
+    return x, r, it, history

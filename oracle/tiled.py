@@ -1,0 +1,246 @@
+"""Tile kernels and Algorithm 1 (oracle).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__``).
+
+Paper, Section 3.1: four elementary operations on b x b tiles
+  GEQRT  (DGEQT2)  A_kk -> V_kk, R_kk and T_kk
+  LARFB  (DLARFB)  A_kj <- (I - V_kk T_kk V_kk^T)^T A_kj
+  TSQRT  (DTSQT2)  [R_kk; A_ik] -> [I; V_ik], R~_kk and T_ik
+  SSRFB  (DSSRFB)  [A_kj; A_ij] <- (I - [I; V_ik] T_ik [I; V_ik]^T)^T [A_kj; A_ij]
+and Algorithm 1, the loop nest k / j / i / j that drives them.
+
+Readings of the paper used here (each listed with the design notes):
+* The update formulas print (I - V T V^T); with T from the forward recurrence
+  that is H_0...H_{b-1} = Q, so the factorization must apply its transpose
+  (I - V T^T V^T).  A wrong orientation fails A = QR.
+* Inner blocking: the paper's kernels are unblocked (ib = b).  With ib < b the
+  b columns of a tile are handled in b/ib blocks; block l has its own ib x ib
+  T_l, stored side by side as an ib x b array per tile.  Within a block the
+  columns are factored one by one (as DGEQR2); the block's reflectors are then
+  applied to the tile's trailing columns at once.  Block l of a TSQRT touches
+  rows l*ib .. (l+1)*ib-1 of the top triangle and every row of the bottom tile.
+  LARFB / SSRFB apply blocks l = 0, 1, ... (Q^T) or in reverse (Q).
+  ib = b reproduces the paper's unblocked kernels exactly.
+* Edge tiles: A is zero-padded to p*b x q*b.  Zero rows stay zero under the
+  reflectors and zero columns get tau = 0, so R[:m, :n] is unchanged.
+* The second loop of Algorithm 1 prints "i = k+1, k+1, ..."; read k+1, k+2, ...
+"""
+
+import math
+
+import numpy as np
+
+from .householder import householder, geqr2, unit_lower, larft
+
+
+def _stacked_v(V2, l0, ib, nb):
+    """Explicit [I; V2] for block l of a TSQRT: 2b x ib, with the identity's
+    ones in rows l0 .. l0+ib-1 of the top tile (Section 3.1, DTSQT2)."""
+    Vfull = np.zeros((2 * nb, ib))
+    for c in range(ib):
+        Vfull[l0 + c, c] = 1.0
+    Vfull[nb:, :] = V2
+    return Vfull
+
+
+def geqrt(Akk, ib):
+    """DGEQT2 with inner blocking ib.  Section 3.1.
+
+    Returns (F, T): F holds R_kk on/above the diagonal and V_kk below it;
+    T is ib x b, block l in columns l*ib .. (l+1)*ib-1.
+    """
+    F = np.array(Akk, dtype=np.float64, copy=True)
+    nb = F.shape[0]
+    assert F.shape == (nb, nb) and nb % ib == 0
+    T = np.zeros((ib, nb))
+    for l0 in range(0, nb, ib):
+        l1 = l0 + ib
+        panel, tau = geqr2(F[l0:, l0:l1])         # DGEQR2 on the ib-wide panel
+        F[l0:, l0:l1] = panel
+        V = unit_lower(panel, ib)
+        Tl = larft(V, tau)
+        T[:, l0:l1] = Tl
+        C = F[l0:, l1:]
+        F[l0:, l1:] = C - V @ (Tl.T @ (V.T @ C))  # (I - V T_l^T V^T) on the rest
+    return F, T
+
+
+def larfb(C, Fkk, Tkk, ib, trans=True):
+    """DLARFB: apply the reflectors of a GEQRT'ed diagonal tile to C (b x w).
+
+    trans=True applies Q_kk^T = product over blocks l = 0, 1, ... of
+    (I - V_l T_l^T V_l^T); trans=False applies Q_kk (blocks in reverse, T_l).
+    """
+    C = np.array(C, dtype=np.float64, copy=True)
+    nb = Fkk.shape[0]
+    blocks = list(range(0, nb, ib))
+    if not trans:
+        blocks.reverse()
+    for l0 in blocks:
+        l1 = l0 + ib
+        V = unit_lower(Fkk[l0:, l0:l1], ib)
+        Tl = Tkk[:, l0:l1]
+        op = Tl.T if trans else Tl
+        C[l0:, :] -= V @ (op @ (V.T @ C[l0:, :]))
+    return C
+
+
+def tsqrt(Rkk, Aik, ib):
+    """DTSQT2 with inner blocking ib: QR of the triangle R_kk stacked on A_ik.
+
+    Returns (R, V, T): R is Rkk with its upper triangle replaced by R~_kk (its
+    strictly lower part, which holds V_kk, is left as it was); V overwrites
+    A_ik; T is ib x b.  Section 3.1.
+    """
+    R = np.array(Rkk, dtype=np.float64, copy=True)
+    A = np.array(Aik, dtype=np.float64, copy=True)
+    nb = R.shape[0]
+    assert R.shape == (nb, nb) and A.shape == (nb, nb) and nb % ib == 0
+    T = np.zeros((ib, nb))
+    for l0 in range(0, nb, ib):
+        l1 = l0 + ib
+        tau = np.zeros(ib)
+        for c in range(l0, l1):
+            # the reflector's top part is e_c: rows above c were annihilated
+            # earlier and rows below c of the triangle are zero
+            t, v2, beta = householder(R[c, c], A[:, c])
+            R[c, c] = beta
+            A[:, c] = v2
+            tau[c - l0] = t
+            if t != 0.0 and c + 1 < l1:
+                w = R[c, c + 1:l1] + v2 @ A[:, c + 1:l1]
+                R[c, c + 1:l1] -= t * w
+                A[:, c + 1:l1] -= t * np.outer(v2, w)
+        Vfull = _stacked_v(A[:, l0:l1], l0, ib, nb)
+        Tl = larft(Vfull, tau)
+        T[:, l0:l1] = Tl
+        if l1 < nb:
+            C = np.vstack([R[:, l1:], A[:, l1:]])
+            C -= Vfull @ (Tl.T @ (Vfull.T @ C))
+            R[l0:l1, l1:] = C[l0:l1, :]        # only the block's rows change
+            A[:, l1:] = C[nb:, :]
+    return R, A, T
+
+
+def ssrfb(Akj, Aij, Vik, Tik, ib, trans=True):
+    """DSSRFB: apply the reflectors [I; V_ik], T_ik of a TSQRT to the stacked
+    pair [A_kj; A_ij] (each b x w).  Section 3.1.
+
+    trans=True applies Q^T (blocks l = 0, 1, ..., T_l^T); trans=False Q.
+    """
+    nb = Vik.shape[0]
+    C = np.vstack([np.asarray(Akj, dtype=np.float64),
+                   np.asarray(Aij, dtype=np.float64)])
+    blocks = list(range(0, nb, ib))
+    if not trans:
+        blocks.reverse()
+    for l0 in blocks:
+        l1 = l0 + ib
+        Vfull = _stacked_v(Vik[:, l0:l1], l0, ib, nb)
+        Tl = Tik[:, l0:l1]
+        op = Tl.T if trans else Tl
+        C -= Vfull @ (op @ (Vfull.T @ C))
+    return C[:nb, :].copy(), C[nb:, :].copy()
+
+
+class TiledFactors:
+    """Result of Algorithm 1: the padded p*b x q*b array holding R and the
+    tiled V, and the T blocks keyed by (i, k)."""
+
+    def __init__(self, m, n, nb, ib, Ap, T):
+        self.m, self.n, self.nb, self.ib = m, n, nb, ib
+        self.p = Ap.shape[0] // nb
+        self.q = Ap.shape[1] // nb
+        self.Ap = Ap
+        self.T = T
+
+    def tile(self, i, j):
+        nb = self.nb
+        return self.Ap[i * nb:(i + 1) * nb, j * nb:(j + 1) * nb]
+
+    @property
+    def F(self):
+        """m x n array with R on/above the diagonal and the tiled V below."""
+        return self.Ap[:self.m, :self.n].copy()
+
+    @property
+    def R(self):
+        return np.triu(self.Ap[:self.m, :self.n])
+
+
+def grid(m, n, nb):
+    """Tile counts p = ceil(m/b), q = ceil(n/b)."""
+    return max(1, math.ceil(m / nb)), max(1, math.ceil(n / nb))
+
+
+def tiled_qr(A, nb, ib):
+    """Algorithm 1 of the paper on the zero-padded tile grid."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    p, q = grid(m, n, nb)
+    Ap = np.zeros((p * nb, q * nb))
+    Ap[:m, :n] = A
+    f = TiledFactors(m, n, nb, ib, Ap, {})
+    tile = f.tile
+    for k in range(min(p, q)):
+        Fkk, Tkk = geqrt(tile(k, k), ib)
+        tile(k, k)[:] = Fkk
+        f.T[(k, k)] = Tkk
+        for j in range(k + 1, q):
+            tile(k, j)[:] = larfb(tile(k, j), tile(k, k), Tkk, ib, trans=True)
+        for i in range(k + 1, p):
+            R, V, Tik = tsqrt(tile(k, k), tile(i, k), ib)
+            tile(k, k)[:] = R
+            tile(i, k)[:] = V
+            f.T[(i, k)] = Tik
+            for j in range(k + 1, q):
+                top, bot = ssrfb(tile(k, j), tile(i, j), V, Tik, ib, trans=True)
+                tile(k, j)[:] = top
+                tile(i, j)[:] = bot
+    return f
+
+
+def _padded_rows(f, B):
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    assert B.shape[0] == f.m
+    Bp = np.zeros((f.p * f.nb, B.shape[1]))
+    Bp[:f.m] = B
+    return Bp
+
+
+def apply_qt(f, B):
+    """Q^T B from the tiled factors, replaying Algorithm 1's order: LARFB on
+    row block k, then SSRFB on the pairs (k, i)."""
+    Bp = _padded_rows(f, B)
+    nb = f.nb
+    rows = lambda i: slice(i * nb, (i + 1) * nb)
+    for k in range(min(f.p, f.q)):
+        Bp[rows(k)] = larfb(Bp[rows(k)], f.tile(k, k), f.T[(k, k)], f.ib, trans=True)
+        for i in range(k + 1, f.p):
+            top, bot = ssrfb(Bp[rows(k)], Bp[rows(i)], f.tile(i, k), f.T[(i, k)],
+                             f.ib, trans=True)
+            Bp[rows(k)], Bp[rows(i)] = top, bot
+    return Bp[:f.m]
+
+
+def apply_q(f, B):
+    """Q B: the transposes of apply_qt's steps in reverse order."""
+    Bp = _padded_rows(f, B)
+    nb = f.nb
+    rows = lambda i: slice(i * nb, (i + 1) * nb)
+    for k in reversed(range(min(f.p, f.q))):
+        for i in reversed(range(k + 1, f.p)):
+            top, bot = ssrfb(Bp[rows(k)], Bp[rows(i)], f.tile(i, k), f.T[(i, k)],
+                             f.ib, trans=False)
+            Bp[rows(k)], Bp[rows(i)] = top, bot
+        Bp[rows(k)] = larfb(Bp[rows(k)], f.tile(k, k), f.T[(k, k)], f.ib, trans=False)
+    return Bp[:f.m]
+
+
+def form_q(f, ncols=None):
+    """Explicit Q (m x ncols, default m x m) = Q applied to the identity."""
+    if ncols is None:
+        ncols = f.m
+    return apply_q(f, np.eye(f.m, ncols))
