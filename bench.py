@@ -1,0 +1,355 @@
+#!/usr/bin/env python
+"""Benchmark of the GB300 tiled Householder QR (libtqr).
+
+Default workload: one 8192 x 8192 FP64 factorization, entries N(0,1) from
+NumPy PCG64 seed 0, tile nb = 128, inner block ib = 32 -- one point of the
+square-size sweep of the plain-FP64 tiled QR.  A step restores the matrix
+from a pristine device copy and calls tqr_factor (pack to Block Data Layout,
+the persistent task kernel, unpack).  The 512 MiB input is larger than L2.
+
+Metric: TFLOP/s counting 2 m n^2 - 2 n^3 / 3 per factorization, and its
+fraction of this GPU's FP64 FMA peak (measured in the run by a DFMA probe).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--workload NAME]
+    python bench.py --impl reference ...   (the CPU oracle on host cores)
+
+With N > 1 (torchrun) every rank factors its own matrix (independent
+replicas, no collective: a single factorization does not shard); value is
+the total over ranks divided by the slowest rank's time.
+"""
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+WORKLOADS = {
+    "qr8192": dict(m=8192, n=8192, nb=128, ib=32),
+    "qr16384": dict(m=16384, n=16384, nb=128, ib=32),
+    "qr4096": dict(m=4096, n=4096, nb=128, ib=32),
+    "qr2048": dict(m=2048, n=2048, nb=128, ib=32),
+    "ts65536x2048": dict(m=65536, n=2048, nb=128, ib=32),
+}
+METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs FP64 peak"
+
+
+def qr_flops(m, n):
+    k = min(m, n)
+    if m >= n:
+        return 2.0 * m * n * n - 2.0 * n ** 3 / 3.0
+    return 2.0 * n * m * m - 2.0 * m ** 3 / 3.0 if k else 0.0
+
+
+def workload_name(w):
+    return "tiled QR %dx%d FP64, N(0,1) seed 0, nb=%d ib=%d" % (w["m"], w["n"], w["nb"], w["ib"])
+
+
+# ---------------------------------------------------------------- CPU oracle sample
+_ORACLE_SNIPPET = r"""
+import json, os, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle import householder as H
+from paper_0707_3548_gb300 import inputs
+m, n, target, steps = %(m)d, %(n)d, %(target)f, %(steps)d
+FULL = inputs.normal_matrix(m, n, 0)   # the workload matrix (same generator, same seed)
+def panel(c):
+    return np.asfortranarray(FULL[:, :c])
+# calibrate t(c) = a c + b c^2 (per-column overhead + rank-1 updates) at two widths
+ts = []
+for c in (48, 96):
+    t0 = time.perf_counter(); H.geqr2(panel(c)); ts.append(time.perf_counter() - t0)
+b = max((ts[1] / 96 - ts[0] / 48) / 48, 1e-12)
+a = max(ts[0] / 48 - b * 48, 0.0)
+c = (-a + (a * a + 4 * b * target) ** 0.5) / (2 * b)
+c = int(max(32, min(n, c)))
+P = panel(c)
+times = []
+for _ in range(steps):
+    t0 = time.perf_counter(); H.geqr2(P); times.append(time.perf_counter() - t0)
+flops = 2.0 * m * c * c - 2.0 * c ** 3 / 3.0
+print(json.dumps({"c": c, "times": times, "flops": flops}))
+"""
+
+
+def oracle_sample(m, n, target_s, steps):
+    """Times the oracle's unblocked Householder QR (DGEQR2 equivalent) on the
+    first c columns of the workload matrix, c sized for ~target_s seconds, in
+    a single-threaded subprocess.  Returns (TFLOP/s per step, c, times)."""
+    code = _ORACLE_SNIPPET % dict(root=ROOT, m=m, n=n, target=target_s, steps=steps)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    rates = [r["flops"] / t / 1e12 for t in r["times"]]
+    return rates, r["c"], r["times"]
+
+
+def run_reference(args, w):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    per_step = max(2.0, min(10.0, 120.0 / max(1, args.steps + args.warmup)))
+    rates, c, times = oracle_sample(w["m"], w["n"], per_step, args.warmup + args.steps)
+    timed = times[args.warmup:]
+    rates = rates[args.warmup:]
+    value = statistics.mean(rates)
+    sample = ("unblocked Householder QR (oracle, NumPy fp64) of the first %d columns of the %dx%d workload "
+              "matrix per step" % (c, w["m"], w["n"]))
+    line = {
+        "impl": "reference", "metric": METRIC, "value": value, "unit": "TFLOP/s",
+        "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": 1e3 * statistics.mean(timed), "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic: N(0,1), NumPy PCG64 seed 0",
+        "config": {"workload": workload_name(w), "m": w["m"], "n": w["n"], "nb": w["nb"], "ib": w["ib"]},
+        "cpu_baseline": {"value": value, "unit": "TFLOP/s", "cores": 1, "kind": "oracle", "sample": sample},
+        "e2e": {"value": value, "unit": "TFLOP/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- clocks
+_SMI_FIELDS = ("clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+               "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+               "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+
+class ClockSampler:
+    def __init__(self, bus_id):
+        self.bus_id = bus_id
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        cmd = ["nvidia-smi", "--query-gpu=" + _SMI_FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["-i", self.bus_id]
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(cmd, stdout=self.fh, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.proc = None
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+            self.fh.close()
+
+    def summary(self):
+        if self.proc is None or not self.path:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        rows = []
+        with open(self.path) as fh:
+            for line in fh:
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) >= 8:
+                    rows.append(parts)
+        os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["no samples"]}
+        def num(x):
+            try:
+                return float(x)
+            except ValueError:
+                return None
+        sm = [num(r[0]) for r in rows if num(r[0]) is not None]
+        mx = [num(r[1]) for r in rows if num(r[1]) is not None]
+        pw = [num(r[2]) for r in rows if num(r[2]) is not None]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if r[4 + k].lower() == "active"})
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(mx) if mx else None,
+                "power_w_max": max(pw) if pw else None, "samples": len(rows), "reasons": reasons}
+
+
+def engine_sha():
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_0707_3548_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        if f.startswith("tqr_engine") or f == "tqr_graph.h":
+            with open(os.path.join(csrc, f), "rb") as fh:
+                h.update(fh.read())
+    return h.hexdigest()[:16]
+
+
+def measured_traffic(workload):
+    """DRAM bytes per launch of the task kernel from the committed ncu summary,
+    only while the kernel sources still match the capture."""
+    path = os.path.join(ROOT, "profiles", "task_kernel_traffic.json")
+    if not os.path.exists(path):
+        return None
+    try:
+        d = json.load(open(path))
+    except ValueError:
+        return None
+    if d.get("engine_sha") != engine_sha():
+        return None
+    return d.get("traffic_bytes_per_launch", {}).get(workload)
+
+
+# ---------------------------------------------------------------- main arm
+def run_ours(args, w):
+    import numpy as np
+    import torch
+
+    from paper_0707_3548_gb300 import build as B
+    from paper_0707_3548_gb300 import inputs, tqr
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    tqr.lib()
+    m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
+    A = inputs.normal_matrix(m, n, 0)
+    dev = torch.device("cuda", local)
+    dA0 = tqr.colmajor(torch.from_numpy(A).to(dev))
+    dA = tqr.colmajor(torch.empty((m, n), dtype=torch.float64, device=dev))
+    T = tqr.new_t(m, n, nb, ib, dA)
+    stream = torch.cuda.current_stream()
+
+    def step():
+        dA.copy_(dA0)
+        tqr.tqr_factor(dA, nb, ib, T)
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert tqr.tqr_stream_status() == tqr.TQR_OK
+    if dist is not None:
+        dist.barrier()
+    props = torch.cuda.get_device_properties(dev)
+    bus = None
+    try:
+        bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except AttributeError:
+        bus = None
+    tqr.tqr_debug_timing(1)
+    tqr.tqr_debug_timing_read()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(bus) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    kern_ms, launches = tqr.tqr_debug_timing_read()
+    tqr.tqr_debug_timing(0)
+    status = tqr.tqr_stream_status()
+    elapsed_ms = e0.elapsed_time(e1)
+    if dist is not None:
+        t = torch.tensor([elapsed_ms], device=dev)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        elapsed_ms = float(t.item())
+    flops = qr_flops(m, n)
+    value = flops * args.steps * world / (elapsed_ms * 1e-3) / 1e12
+
+    # end to end through the C ABI with pinned host buffers
+    hA_t = torch.empty((n, m), dtype=torch.float64).pin_memory()
+    hA = hA_t.numpy().T                       # column-major m x n view
+    hT_t = torch.empty(T.numel(), dtype=torch.float64).pin_memory()
+    hT = hT_t.numpy()
+    e2e_times = []
+    for it in range(args.warmup + args.steps):
+        np.copyto(hA, A)
+        t0 = time.perf_counter()
+        tqr.tqr_factor(hA, nb, ib, hT)
+        t1 = time.perf_counter()
+        if it >= args.warmup:
+            e2e_times.append(t1 - t0)
+    e2e_s = statistics.mean(e2e_times)
+    if dist is not None:
+        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+    e2e = {"value": flops * world / e2e_s / 1e12, "unit": "TFLOP/s",
+           "h2d_bytes_per_step": 8 * m * n, "d2h_bytes_per_step": 8 * m * n + 8 * T.numel(),
+           "ms_per_step": e2e_s * 1e3}
+
+    peak = tqr.tqr_debug_fp64_peak()
+    kern_avg_ms = kern_ms / max(1, launches)
+    achieved = flops / (kern_avg_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": measured_traffic(args.workload),
+                "kernel": "tqr::run_tasks_kernel<double> (persistent task scheduler)",
+                "peak_source": "FP64 DFMA probe measured in this run (tqr_debug_fp64_peak); "
+                               "nominal GB300 FP64 1.25 TFLOP/s",
+                "kernel_ms_per_launch": kern_avg_ms}
+
+    if rank != 0:
+        if dist is not None:
+            dist.barrier()
+            dist.destroy_process_group()
+        return
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        rates, c, times = oracle_sample(m, n, 6.0, 2)
+        cpu = {"value": max(rates), "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": "unblocked Householder QR (oracle, NumPy fp64, 1 thread) of the first %d columns of the "
+                         "%dx%d workload matrix, best of 2 (%.1f s)" % (c, m, n, min(times))}
+    line = {
+        "metric": METRIC, "value": value, "unit": "TFLOP/s", "n_gpus": world, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic: N(0,1) entries, NumPy PCG64 seed 0",
+        "config": {"workload": workload_name(w), "m": m, "n": n, "nb": nb, "ib": ib,
+                   "l2": "input 8*m*n bytes > 129 MB L2, restored from a device copy each step",
+                   "parallelism": "replicas" if world > 1 else "single GPU"},
+        "fp64_peak_fraction": value / world / peak,
+        "roofline": roofline,
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": 3 * args.steps,
+        "clocks": clk.summary(),
+        "status": status,
+    }
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="qr8192", choices=sorted(WORKLOADS))
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    w = WORKLOADS[args.workload]
+    if args.impl == "reference":
+        run_reference(args, w)
+    else:
+        run_ours(args, w)
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,167 @@
+/*
+ * tqr.h -- C ABI of libtqr, a GB300 (sm_103a) tiled Householder QR and
+ * least-squares library.
+ *
+ * Method: the tiled QR factorization of Buttari, Langou, Kurzak and Dongarra,
+ * "Parallel Tiled QR Factorization for Multicore Architectures": the matrix is
+ * cut into nb x nb tiles held in Block Data Layout (Section 3.4) and factored
+ * by the four tile kernels GEQRT, LARFB, TSQRT and SSRFB (Section 3.1) in the
+ * order of Algorithm 1, executed out of order over the task dependency DAG
+ * (Section 3.3).  The kernels use inner blocking ib: each tile's nb columns
+ * are handled as nb/ib blocks with one ib x ib compact-WY factor T_l each.
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ * - Matrices are column-major with a leading dimension (LAPACK style).
+ * - Pointers may be DEVICE pointers (cudaMalloc / PyTorch CUDA tensors) or
+ *   HOST pointers (pageable or pinned).  The library asks CUDA which one it
+ *   is given.  Device pointers: the call is asynchronous on `stream` and
+ *   returns once the work is enqueued.  Host pointers: the library copies
+ *   the data to the device, runs, copies results back and synchronizes the
+ *   stream before returning.  All pointers of one call must be of one kind.
+ * - `stream` is a cudaStream_t passed as void* (NULL = legacy default).
+ * - The caller owns every buffer it passes.  Scratch memory the library needs
+ *   is allocated stream-ordered (cudaMallocAsync) and released on the same
+ *   stream, unless the *_ws variant is used with a caller-provided workspace.
+ * - Return value: 0 on success; -i if argument i (1-based) is invalid, in
+ *   which case nothing is enqueued; a positive TQR_ERR_* code otherwise.
+ *   Errors never abort the process and never trap the GPU.  A device-side
+ *   failure of an asynchronous call (TQR_ERR_TIMEOUT) is reported by
+ *   tqr_stream_status().
+ * - Supported tile sizes: 8 <= nb <= 256, nb % 8 == 0; ib divides nb and
+ *   ib <= 64.
+ */
+#ifndef TQR_H
+#define TQR_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  TQR_OK = 0,
+  TQR_ERR_CUDA = 1,        /* a CUDA runtime call failed */
+  TQR_ERR_NOMEM = 2,       /* device or pinned memory could not be allocated */
+  TQR_ERR_TIMEOUT = 3,     /* a dependency wait in the device scheduler ran out */
+  TQR_ERR_RANK = 4,        /* least squares: |r_ii| <= n * eps * max|r_jj| */
+  TQR_ERR_NOCONV = 5,      /* least squares: refinement did not reach tol */
+  TQR_ERR_BUSY = 6,        /* batch / server: no free slot right now */
+  TQR_ERR_UNSUPPORTED = 7  /* valid arguments outside what this build supports */
+};
+
+enum { TQR_PREC_FP64 = 0, TQR_PREC_FP32 = 1 };
+
+/*
+ * Version string of the library ("tqr <major>.<minor> sm_103a").
+ */
+const char* tqr_version(void);
+
+/*
+ * Bytes needed for the T array of an m x n factorization with tile nb and
+ * inner block ib.  Section 3.1: every GEQRT(k) and every TSQRT(k, i) produces
+ * a T_ik; here each is an ib x nb array (block l's ib x ib upper triangular
+ * T_l in columns l*ib .. l*ib+ib-1, column-major, leading dimension ib).
+ * With p = ceil(m/nb), q = ceil(n/nb), kt = min(p, q), the blocks are stored
+ * for k = 0..kt-1 and i = k..p-1 in that order:
+ *     offset(i, k) = (k*p - k*(k-1)/2 + (i - k)) * ib * nb  elements.
+ * Returns 0 for invalid sizes.
+ */
+size_t tqr_t_size(int64_t m, int64_t n, int nb, int ib);
+
+/*
+ * Bytes of device scratch tqr_factor_ws needs for these sizes (the tile
+ * buffer in Block Data Layout, dependency counters and the task list).
+ */
+size_t tqr_work_size(int64_t m, int64_t n, int nb, int ib);
+
+/*
+ * Tiled QR factorization, Algorithm 1 of the paper (Sections 3.1-3.4).
+ *   m, n   (args 1, 2)  matrix size, m >= 0, n >= 0
+ *   A      (arg 3)      m x n, column-major; on exit R is on and above the
+ *                       diagonal, V_kk strictly below the diagonal of each
+ *                       diagonal tile and V_ik in every tile below it
+ *   lda    (arg 4)      >= max(1, m)
+ *   nb, ib (args 5, 6)  tile size and inner block size
+ *   T      (arg 7)      tqr_t_size(m, n, nb, ib) bytes of doubles, written
+ *   stream (arg 8)
+ * The result can only be used with the same nb, ib and T.  Rank-deficient
+ * input is factored (zero columns give tau = 0).  The factorization is
+ * deterministic: the task order on the GPU does not change a single bit.
+ */
+int tqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib,
+               double* T, void* stream);
+
+/*
+ * As tqr_factor, with caller-provided device scratch `work` of at least
+ * tqr_work_size(m, n, nb, ib) bytes (256-byte aligned) at args 8-9.
+ */
+int tqr_factor_ws(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib,
+                  double* T, void* work, size_t work_bytes, void* stream);
+
+/*
+ * Apply Q or Q^T from a tqr_factor result to B (m x nrhs), in place
+ * (the DORMQR analogue named in Section 5 of the paper).
+ *   trans  (arg 1)  'T': B <- Q^T B (Algorithm 1's order: LARFB on row block
+ *                   k, then SSRFB on the pairs (k, i));  'N': B <- Q B
+ *                   (the same steps transposed, in reverse order)
+ *   m, n   (args 2, 3), nrhs (arg 4) >= 0
+ *   A, lda (args 5, 6)  factored matrix from tqr_factor
+ *   nb, ib (args 7, 8), T (arg 9) as passed to tqr_factor
+ *   B, ldb (args 10, 11) m x nrhs, ldb >= max(1, m)
+ * Forming Q explicitly is trans = 'N' applied to the identity.
+ */
+int tqr_apply_qt(char trans, int64_t m, int64_t n, int64_t nrhs,
+                 const double* A, int64_t lda, int nb, int ib, const double* T,
+                 double* B, int64_t ldb, void* stream);
+
+/*
+ * Least squares  min ||A x - b||_2  for full-rank A, m >= n, through the
+ * tiled QR: x = R[0:n,0:n]^{-1} (Q^T b)[0:n].  The factorization, Q^T B and
+ * the back substitution run as one task graph on the device.
+ *   m, n, nrhs (args 1-3)   m >= n >= 1, nrhs >= 1
+ *   A, lda     (args 4, 5)  m x n, NOT modified (the library factors a copy)
+ *   B, ldb     (args 6, 7)  m x nrhs right-hand sides
+ *   X, ldx     (args 8, 9)  n x nrhs solutions, ldx >= n
+ *   prec       (arg 10)     TQR_PREC_FP64: plain FP64.  TQR_PREC_FP32: the
+ *                           factorization in FP32 (norms and tau in FP64),
+ *                           then iterative refinement of the augmented
+ *                           system with FP64 residuals until the backward
+ *                           error is <= tol
+ *   tol        (arg 11)     backward-error target for refinement (e.g. 1e-12)
+ *   maxit      (arg 12)     refinement iteration limit
+ *   iters      (arg 13)     out (may be NULL): refinement steps taken
+ *   berr       (arg 14)     out (may be NULL): final normwise backward error
+ *                           max_c ||A^T r_c|| / (||A||_F (||A||_F ||x_c|| + ||b_c||))
+ *   nb, ib     (args 15-16) tile and inner block size (0, 0 = library choice)
+ *   stream     (arg 17)
+ * Synchronizes the stream (the refinement loop needs the backward error on
+ * the host).  Returns TQR_ERR_RANK for a numerically rank-deficient R and
+ * TQR_ERR_NOCONV when refinement stalls above tol.
+ */
+int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                 const double* B, int64_t ldb, double* X, int64_t ldx, int prec,
+                 double tol, int maxit, int* iters, double* berr, int nb, int ib,
+                 void* stream);
+
+/*
+ * Device status of the asynchronous calls made on `stream`: synchronizes the
+ * stream and returns TQR_OK, TQR_ERR_TIMEOUT (a scheduler wait ran out; the
+ * affected output is undefined) or TQR_ERR_CUDA.  Clears the recorded status.
+ */
+int tqr_stream_status(void* stream);
+
+/*
+ * Dependency-wait limit of the device scheduler in milliseconds (default
+ * 20000).  A wait that exceeds it makes every CTA of that launch stop and
+ * the call report TQR_ERR_TIMEOUT.  Returns the previous value.
+ */
+int64_t tqr_set_wait_limit_ms(int64_t ms);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TQR_H */

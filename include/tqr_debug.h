@@ -1,0 +1,92 @@
+/*
+ * tqr_debug.h -- host-only introspection of libtqr's task plans.
+ *
+ * These calls need no GPU: they build the task list of one launch on the
+ * host (the same code path the device launches use) so that tests can check
+ * the scheduling rules without running kernels.
+ */
+#ifndef TQR_DEBUG_H
+#define TQR_DEBUG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/*
+ * Builds the ordered task list of one launch.
+ *   mode     (arg 1)  0 factor, 1 apply Q^T, 2 apply Q, 3 back substitution,
+ *                     4 forward substitution with R^T
+ *   m, n     (args 2, 3), nb, ib (args 4, 5) as for tqr_factor
+ *   cs       (arg 6)  slab width (columns) of the column-slab tasks; must
+ *                     divide nb
+ *   nrhs     (arg 7)  right-hand-side columns (0: none)
+ *   trsm     (arg 8)  factor mode: append the back substitution (1) or not
+ *   workers  (arg 9)  CTAs assumed by the list-scheduling simulation
+ *   policy   (arg 10) -1 best of both, 0 paper priorities, 1 bottom level
+ *   out      (arg 11) int32[8 * cap]: per task kind, s, inst, k, i, j, l, 0
+ *                     (may be NULL to query the count)
+ *   cap      (arg 12) capacity of `out` in tasks
+ *   stats    (arg 13) double[6] or NULL: chosen makespan, other makespan,
+ *                     policy, edges, critical path, total work (seconds of
+ *                     the cost model)
+ * Returns the number of tasks (>= 0), or -i for invalid argument i, or
+ * -100 if the rules contradict the sequential order (message via
+ * tqr_debug_last_error).
+ */
+int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int workers,
+                       int policy, int32_t* out, int64_t cap, double* stats);
+
+/*
+ * The version waits and signals the device scheduler derives for one task
+ * (kind, k, i, j, s, l as in tqr_debug_plan) of a launch described by
+ * (mode, m, n, nb, ib, cs, nrhs).  waits: int32[4*3] (counter, count,
+ * version), signals: int32[2*2] (counter, count).  Returns
+ * nwaits + 16 * nsignals.
+ */
+int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, const int32_t* task,
+                    int32_t* waits, int32_t* signals);
+
+/*
+ * Overrides the scheduling of later launches (for tests): policy -1 (best of
+ * both, default), 0 (paper priorities) or 1 (bottom level); max_ctas > 0
+ * caps the persistent grid (0: no cap).  The result of a factorization does
+ * not depend on either.  Returns 0, or -1 / -2 for an invalid argument.
+ */
+int tqr_debug_set_schedule(int policy, int max_ctas);
+
+/*
+ * Launches the device scheduler on a task whose input is never produced
+ * (a TSQRT whose GEQRT is missing), with the given wait limit in
+ * milliseconds, and returns the status the launch reports: TQR_ERR_TIMEOUT
+ * when the bounded wait gives up as designed.  Uses the current device.
+ */
+int tqr_debug_stalled_launch(int64_t limit_ms, void* stream);
+
+/*
+ * Kernel timing for benchmarks.  While enabled (enable = 1), every launch of
+ * the persistent task kernel is bracketed by CUDA events on its stream.
+ * tqr_debug_timing_read synchronizes those events and returns the summed
+ * milliseconds and the number of launches since the last read (or since
+ * enabling), then clears them.  Returns 0 or TQR_ERR_CUDA.
+ */
+int tqr_debug_timing(int enable);
+int tqr_debug_timing_read(double* ms, int64_t* launches);
+
+/*
+ * Measures this GPU's FP64 FMA throughput with a register-resident DFMA loop
+ * (every SM, 8 independent chains per thread).  Writes TFLOP/s to *tflops.
+ * Returns 0 or TQR_ERR_CUDA.
+ */
+int tqr_debug_fp64_peak(double* tflops, void* stream);
+
+/* Last error message of this thread ("" if none). */
+const char* tqr_debug_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* TQR_DEBUG_H */

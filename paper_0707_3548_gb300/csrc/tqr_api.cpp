@@ -1,0 +1,519 @@
+// tqr_api.cpp -- the C ABI of libtqr (declared in include/tqr.h).
+//
+// Host-side orchestration only: argument checks, workspace layout, the plan
+// cache, host/device pointer staging and kernel launches.  All arithmetic of
+// the factorization runs in the kernels of tqr_engine.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <list>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "tqr.h"
+#include "tqr_api_internal.h"
+#include "tqr_engine.h"
+#include "tqr_plan.h"
+
+namespace tqr {
+
+static long long g_wait_limit_ms = 20000;
+static int g_policy = -1;
+static int g_max_ctas = 0;
+static std::mutex g_mu;
+
+void set_schedule(int policy, int max_ctas) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_policy = policy;
+  g_max_ctas = max_ctas;
+}
+static thread_local std::string g_last_error;
+
+void set_last_error(const std::string& s) { g_last_error = s; }
+const char* last_error() { return g_last_error.c_str(); }
+
+int device_sms() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 0;
+  static std::map<int, int> cache;
+  std::lock_guard<std::mutex> lk(g_mu);
+  auto it = cache.find(dev);
+  if (it != cache.end()) return it->second;
+  int sms = 0;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 0;
+  cache[dev] = sms;
+  return sms;
+}
+
+long long wait_limit_ns() { return g_wait_limit_ms * 1000000LL; }
+
+// Tile shape choice: the widest slab (32, 16 or 8 columns dividing nb) that
+// keeps the most CTAs per SM (up to 2: 128 registers x 256 threads).
+bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem) {
+  const int kSmemPerSM = 233472, kSmemPerBlock = 232448, kReserved = 1024;
+  int best_cs = 0, best_occ = 0, best_smem = 0;
+  for (int c : {32, 16, 8}) {
+    if (c > nb || nb % c != 0) continue;
+    if (ib * c > kThreads * kMaxOutPerThread) continue;
+    const SmemLayout L = smem_layout(nb, ib, c, esize);
+    if (L.bytes > kSmemPerBlock) continue;
+    int occ = kSmemPerSM / (L.bytes + kReserved);
+    if (occ > 2) occ = 2;
+    if (occ > best_occ) {
+      best_occ = occ;
+      best_cs = c;
+      best_smem = L.bytes;
+    }
+  }
+  if (best_occ == 0) return false;
+  *cs = best_cs;
+  *ctas_per_sm = best_occ;
+  *smem = best_smem;
+  return true;
+}
+
+Inst make_inst(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm) {
+  Inst I = {};
+  I.m = static_cast<int>(m);
+  I.n = static_cast<int>(n);
+  I.p = static_cast<int>(std::max<int64_t>(1, (m + nb - 1) / nb));
+  I.q = static_cast<int>(std::max<int64_t>(1, (n + nb - 1) / nb));
+  I.kt = std::min(I.p, I.q);
+  I.nrhs = nrhs;
+  I.qb = nrhs > 0 ? (nrhs + nb - 1) / nb : 0;
+  I.nb = nb;
+  I.ib = ib;
+  I.cs = cs;
+  I.NS = nb / cs;
+  I.mode = mode;
+  I.trsm = trsm;
+  return I;
+}
+
+// ---------------------------------------------------------------- plan cache
+struct DevPlan {
+  TaskX* d_tasks = nullptr;
+  int ntasks = 0;
+  int grid = 0;
+  PlanStats stats;
+  int device = -1;
+  ~DevPlan() {
+    if (d_tasks) {
+      int cur = -1;
+      cudaGetDevice(&cur);
+      if (device >= 0 && device != cur) cudaSetDevice(device);
+      cudaFree(d_tasks);
+      if (device >= 0 && device != cur) cudaSetDevice(cur);
+    }
+  }
+};
+
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int> PlanKey;
+
+static std::list<std::pair<PlanKey, std::shared_ptr<DevPlan>>> g_plans;
+static const size_t kMaxPlans = 24;
+
+static PlanKey key_of(const Inst& I, int esize, int grid, int dev, int policy) {
+  return PlanKey(I.mode, I.m, I.n, I.nb, I.ib, I.cs, I.nrhs, I.trsm, esize, grid, dev, policy);
+}
+
+std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int* status) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const int sms = device_sms();
+  std::vector<TaskX> seq;
+  int policy, max_ctas;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    policy = g_policy;
+    max_ctas = g_max_ctas;
+  }
+  // grid: at most ctas_per_sm CTAs per SM (and the debug cap)
+  int max_grid = sms * ctas_per_sm;
+  if (max_ctas > 0 && max_ctas < max_grid) max_grid = max_ctas;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
+      const PlanKey& k = it->first;
+      if (std::get<0>(k) == I.mode && std::get<1>(k) == I.m && std::get<2>(k) == I.n && std::get<3>(k) == I.nb &&
+          std::get<4>(k) == I.ib && std::get<5>(k) == I.cs && std::get<6>(k) == I.nrhs && std::get<7>(k) == I.trsm &&
+          std::get<8>(k) == esize && std::get<10>(k) == dev && std::get<11>(k) == policy &&
+          std::get<9>(k) == max_grid) {
+        auto p = it->second;
+        g_plans.splice(g_plans.begin(), g_plans, it);
+        return p;
+      }
+    }
+  }
+  seq_tasks(I, 0, seq);
+  auto plan = std::make_shared<DevPlan>();
+  plan->device = dev;
+  plan->ntasks = static_cast<int>(seq.size());
+  plan->grid = std::max(1, std::min<int>(max_grid, plan->ntasks));
+  if (!seq.empty()) {
+    std::vector<TaskX> ordered;
+    std::string err;
+    std::vector<Inst> insts(1, I);
+    if (!order_tasks(insts, seq, plan->grid, esize, ctas_per_sm, policy, ordered, &plan->stats, &err)) {
+      set_last_error(err);
+      *status = TQR_ERR_UNSUPPORTED;
+      return nullptr;
+    }
+    if (cudaMalloc(&plan->d_tasks, sizeof(TaskX) * ordered.size()) != cudaSuccess) {
+      *status = TQR_ERR_NOMEM;
+      return nullptr;
+    }
+    if (cudaMemcpy(plan->d_tasks, ordered.data(), sizeof(TaskX) * ordered.size(), cudaMemcpyHostToDevice) !=
+        cudaSuccess) {
+      *status = TQR_ERR_CUDA;
+      return nullptr;
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_plans.emplace_front(key_of(I, esize, max_grid, dev, policy), plan);
+  while (g_plans.size() > kMaxPlans) g_plans.pop_back();
+  return plan;
+}
+
+// ---------------------------------------------------------------- timing
+struct TimingState {
+  bool on = false;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pending;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> pool;
+};
+static TimingState g_timing;
+
+static std::pair<cudaEvent_t, cudaEvent_t> timing_pair() {
+  std::pair<cudaEvent_t, cudaEvent_t> p(nullptr, nullptr);
+  if (!g_timing.pool.empty()) {
+    p = g_timing.pool.back();
+    g_timing.pool.pop_back();
+    return p;
+  }
+  cudaEventCreate(&p.first);
+  cudaEventCreate(&p.second);
+  return p;
+}
+
+int timing_enable(int on) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_timing.on = on != 0;
+  return 0;
+}
+
+int timing_read(double* ms, int64_t* launches) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  double total = 0;
+  int64_t cnt = 0;
+  int rc = 0;
+  for (auto& p : g_timing.pending) {
+    float t = 0;
+    if (cudaEventSynchronize(p.second) != cudaSuccess || cudaEventElapsedTime(&t, p.first, p.second) != cudaSuccess)
+      rc = 1;
+    total += t;
+    ++cnt;
+    g_timing.pool.push_back(p);
+  }
+  g_timing.pending.clear();
+  if (ms) *ms = total;
+  if (launches) *launches = cnt;
+  return rc;
+}
+
+void clear_plans() {
+  std::lock_guard<std::mutex> lk(g_mu);
+  g_plans.clear();
+}
+
+// ---------------------------------------------------------------- workspace
+static size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+WsLayout ws_layout(const Inst& I, int esize, bool with_t) {
+  WsLayout W;
+  const size_t nb2 = static_cast<size_t>(I.nb) * I.nb;
+  size_t o = 0;
+  W.oA = o;
+  o += al256(nb2 * I.p * I.q * esize);
+  W.oB = o;
+  o += al256(nb2 * I.p * I.qb * esize);
+  W.oT = o;
+  if (with_t) o += al256(static_cast<size_t>(t_elems(I.p, I.q, I.nb, I.ib)) * esize);
+  W.oVer = o;
+  o += al256(sizeof(int) * static_cast<size_t>(I.p) * (I.q + I.qb) * I.NS);
+  W.oInst = o;
+  o += al256(sizeof(Inst));
+  W.oCtl = o;
+  o += al256(ctl_bytes());
+  W.bytes = o;
+  return W;
+}
+
+// Clears the counters and control block, uploads the instance and runs the
+// plan.  `I` must already hold the device pointers.
+template <typename real>
+int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st) {
+  int status = TQR_OK;
+  std::shared_ptr<DevPlan> plan = get_plan(I, sizeof(real), ctas_per_sm, &status);
+  if (!plan) return status;
+  if (plan->ntasks == 0) return TQR_OK;
+  if (cudaMemsetAsync(ws + W.oVer, 0, W.oCtl + ctl_bytes() - W.oVer, st) != cudaSuccess) return TQR_ERR_CUDA;
+  if (cudaMemcpyAsync(ws + W.oInst, &I, sizeof(Inst), cudaMemcpyHostToDevice, st) != cudaSuccess) return TQR_ERR_CUDA;
+  std::pair<cudaEvent_t, cudaEvent_t> ev(nullptr, nullptr);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_timing.on) {
+      ev = timing_pair();
+      cudaEventRecord(ev.first, st);
+    }
+  }
+  cudaError_t e = launch_run<real>(plan->d_tasks, plan->ntasks, reinterpret_cast<const Inst*>(ws + W.oInst),
+                                   ws + W.oCtl, wait_limit_ns(), plan->grid, smem, st);
+  if (ev.first) {
+    cudaEventRecord(ev.second, st);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_timing.pending.push_back(ev);
+  }
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return TQR_ERR_CUDA;
+  }
+  return TQR_OK;
+}
+
+template int run_plan<double>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t);
+template int run_plan<float>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t);
+
+// ---------------------------------------------------------------- pointers
+int ptr_kind(const void* p) {
+  if (p == nullptr) return PTR_NULL;
+  cudaPointerAttributes a;
+  cudaError_t e = cudaPointerGetAttributes(&a, p);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return PTR_HOST;
+  }
+  if (a.type == cudaMemoryTypeDevice || a.type == cudaMemoryTypeManaged) return PTR_DEVICE;
+  return PTR_HOST;
+}
+
+int check_tiles(int nb, int ib, int arg_nb, int arg_ib) {
+  if (nb < 8 || nb > 256 || nb % 8 != 0) return -arg_nb;
+  if (ib < 1 || ib > 64 || nb % ib != 0) return -arg_ib;
+  return 0;
+}
+
+}  // namespace tqr
+
+using namespace tqr;
+
+// ---------------------------------------------------------------- factor
+template <typename real>
+static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, real* T, void* work,
+                         size_t work_bytes, cudaStream_t st) {
+  int cs, occ, smem;
+  if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
+  Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
+  const WsLayout W = ws_layout(I, sizeof(real), false);
+  char* ws = static_cast<char*>(work);
+  bool own = false;
+  if (ws == nullptr) {
+    if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
+      cudaGetLastError();
+      return TQR_ERR_NOMEM;
+    }
+    own = true;
+  } else if (work_bytes < W.bytes) {
+    return -10;
+  }
+  I.A = ws + W.oA;
+  I.B = nullptr;
+  I.T = T;
+  I.ver = reinterpret_cast<int*>(ws + W.oVer);
+  const int sms = device_sms();
+  int status = TQR_OK;
+  if (launch_pack<real>(A, lda, static_cast<int>(m), static_cast<int>(n), static_cast<real*>(I.A), I.p, I.q, nb, sms,
+                        st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  if (status == TQR_OK) status = run_plan<real>(I, ws, W, occ, smem, st);
+  if (status == TQR_OK &&
+      launch_unpack<real>(static_cast<real*>(I.A), I.p, nb, A, lda, static_cast<int>(m), static_cast<int>(n), sms, st) !=
+          cudaSuccess)
+    status = TQR_ERR_CUDA;
+  if (own) cudaFreeAsync(ws, st);
+  return status;
+}
+
+static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* work,
+                         size_t work_bytes, void* stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (m > (1LL << 30) || n > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
+  if (lda < std::max<int64_t>(1, m)) return -4;
+  int c = check_tiles(nb, ib, 5, 6);
+  if (c) return c;
+  if (m == 0 || n == 0) return TQR_OK;
+  if (A == nullptr) return -3;
+  if (T == nullptr) return -7;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ka = ptr_kind(A), kt = ptr_kind(T);
+  if (ka != kt) return -7;
+  if (ka == PTR_DEVICE) return factor_device<double>(m, n, A, lda, nb, ib, T, work, work_bytes, st);
+  // host buffers: stage through the device, synchronously
+  const size_t tbytes = tqr_t_size(m, n, nb, ib);
+  double *dA = nullptr, *dT = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dT), tbytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (dA) cudaFreeAsync(dA, st);
+    return TQR_ERR_NOMEM;
+  }
+  int status = TQR_OK;
+  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  if (status == TQR_OK) status = factor_device<double>(m, n, dA, m, nb, ib, dT, work, work_bytes, st);
+  if (status == TQR_OK &&
+      (cudaMemcpy2DAsync(A, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
+                         cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+       cudaMemcpyAsync(T, dT, tbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess))
+    status = TQR_ERR_CUDA;
+  cudaFreeAsync(dA, st);
+  cudaFreeAsync(dT, st);
+  int dev_status = TQR_OK;
+  if (read_status(&dev_status, st) != cudaSuccess) return TQR_ERR_CUDA;
+  if (status == TQR_OK) status = dev_status;
+  return status;
+}
+
+// ---------------------------------------------------------------- apply
+template <typename real>
+static int apply_device(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb,
+                        int ib, const real* T, double* B, int64_t ldb, cudaStream_t st) {
+  int cs, occ, smem;
+  if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
+  Inst I = make_inst(trans == 'T' ? M_APPLY_QT : M_APPLY_Q, m, n, nb, ib, cs, static_cast<int>(nrhs), 0);
+  const WsLayout W = ws_layout(I, sizeof(real), false);
+  char* ws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return TQR_ERR_NOMEM;
+  }
+  I.A = ws + W.oA;
+  I.B = ws + W.oB;
+  I.T = const_cast<real*>(T);
+  I.ver = reinterpret_cast<int*>(ws + W.oVer);
+  const int sms = device_sms();
+  int status = TQR_OK;
+  if (launch_pack<real>(A, lda, static_cast<int>(m), static_cast<int>(n), static_cast<real*>(I.A), I.p, I.q, nb, sms,
+                        st) != cudaSuccess ||
+      launch_pack<real>(B, ldb, static_cast<int>(m), static_cast<int>(nrhs), static_cast<real*>(I.B), I.p, I.qb, nb,
+                        sms, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  if (status == TQR_OK) status = run_plan<real>(I, ws, W, occ, smem, st);
+  if (status == TQR_OK && launch_unpack<real>(static_cast<real*>(I.B), I.p, nb, B, ldb, static_cast<int>(m),
+                                              static_cast<int>(nrhs), sms, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  cudaFreeAsync(ws, st);
+  return status;
+}
+
+extern "C" {
+
+const char* tqr_version(void) { return "tqr 0.1 sm_103a"; }
+
+size_t tqr_t_size(int64_t m, int64_t n, int nb, int ib) {
+  if (m < 0 || n < 0 || check_tiles(nb, ib, 1, 2) != 0) return 0;
+  const int p = static_cast<int>(std::max<int64_t>(1, (m + nb - 1) / nb));
+  const int q = static_cast<int>(std::max<int64_t>(1, (n + nb - 1) / nb));
+  return sizeof(double) * static_cast<size_t>(t_elems(p, q, nb, ib));
+}
+
+size_t tqr_work_size(int64_t m, int64_t n, int nb, int ib) {
+  if (m < 0 || n < 0 || check_tiles(nb, ib, 1, 2) != 0) return 0;
+  int cs, occ, smem;
+  if (!choose_shape(nb, ib, sizeof(double), &cs, &occ, &smem)) return 0;
+  const Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
+  return ws_layout(I, sizeof(double), false).bytes;
+}
+
+int tqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* stream) {
+  return factor_common(m, n, A, lda, nb, ib, T, nullptr, 0, stream);
+}
+
+int tqr_factor_ws(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* work,
+                  size_t work_bytes, void* stream) {
+  if (work == nullptr) return -8;
+  if (ptr_kind(work) != PTR_DEVICE) return -8;
+  if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -8;
+  return factor_common(m, n, A, lda, nb, ib, T, work, work_bytes, stream);
+}
+
+int tqr_apply_qt(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
+                 const double* T, double* B, int64_t ldb, void* stream) {
+  if (trans != 'T' && trans != 'N' && trans != 't' && trans != 'n') return -1;
+  trans = (trans == 't' || trans == 'T') ? 'T' : 'N';
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (nrhs < 0) return -4;
+  if (m > (1LL << 30) || n > (1LL << 30) || nrhs > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
+  if (lda < std::max<int64_t>(1, m)) return -6;
+  int c = check_tiles(nb, ib, 7, 8);
+  if (c) return c;
+  if (ldb < std::max<int64_t>(1, m)) return -11;
+  if (m == 0 || n == 0 || nrhs == 0) return TQR_OK;
+  if (A == nullptr) return -5;
+  if (T == nullptr) return -9;
+  if (B == nullptr) return -10;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ka = ptr_kind(A);
+  if (ptr_kind(T) != ka) return -9;
+  if (ptr_kind(B) != ka) return -10;
+  if (ka == PTR_DEVICE) return apply_device<double>(trans, m, n, nrhs, A, lda, nb, ib, T, B, ldb, st);
+  const size_t tbytes = tqr_t_size(m, n, nb, ib);
+  double *dA = nullptr, *dT = nullptr, *dB = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dT), tbytes, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (dA) cudaFreeAsync(dA, st);
+    if (dT) cudaFreeAsync(dT, st);
+    return TQR_ERR_NOMEM;
+  }
+  int status = TQR_OK;
+  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dT, T, tbytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  if (status == TQR_OK) status = apply_device<double>(trans, m, n, nrhs, dA, m, nb, ib, dT, dB, m, st);
+  if (status == TQR_OK && cudaMemcpy2DAsync(B, sizeof(double) * ldb, dB, sizeof(double) * m, sizeof(double) * m,
+                                            nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  cudaFreeAsync(dA, st);
+  cudaFreeAsync(dT, st);
+  cudaFreeAsync(dB, st);
+  int dev_status = TQR_OK;
+  if (read_status(&dev_status, st) != cudaSuccess) return TQR_ERR_CUDA;
+  if (status == TQR_OK) status = dev_status;
+  return status;
+}
+
+int tqr_stream_status(void* stream) {
+  int s = TQR_OK;
+  if (read_status(&s, static_cast<cudaStream_t>(stream)) != cudaSuccess) return TQR_ERR_CUDA;
+  return s;
+}
+
+int64_t tqr_set_wait_limit_ms(int64_t ms) {
+  const int64_t old = g_wait_limit_ms;
+  if (ms > 0) g_wait_limit_ms = ms;
+  return old;
+}
+
+}  // extern "C"

@@ -1,0 +1,36 @@
+// tqr_api_internal.h -- helpers shared by the C ABI translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include <memory>
+#include <string>
+
+#include "tqr_graph.h"
+
+namespace tqr {
+
+enum { PTR_NULL = 0, PTR_HOST = 1, PTR_DEVICE = 2 };
+
+struct WsLayout {
+  size_t oA, oB, oT, oVer, oInst, oCtl, bytes;
+};
+
+void set_last_error(const std::string& s);
+const char* last_error();
+int device_sms();
+long long wait_limit_ns();
+bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem);
+Inst make_inst(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm);
+WsLayout ws_layout(const Inst& I, int esize, bool with_t);
+template <typename real>
+int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st);
+int ptr_kind(const void* p);
+int check_tiles(int nb, int ib, int arg_nb, int arg_ib);
+void clear_plans();
+void set_schedule(int policy, int max_ctas);
+int timing_enable(int on);
+int timing_read(double* ms, int64_t* launches);
+
+}  // namespace tqr

@@ -1,0 +1,999 @@
+// tqr_engine.cu -- device side of libtqr: the tile kernels of the tiled QR
+// (Section 3.1 of Buttari, Langou, Kurzak, Dongarra), the persistent task
+// scheduler that runs them over the tile DAG (Section 3.3), and the Block
+// Data Layout pack/unpack kernels (Section 3.4).
+//
+// One CTA executes one task at a time.  Tasks come from a list ordered by
+// priority; a CTA takes the next task with one atomic ticket, waits (bounded)
+// until the version counters of the task's operands say its inputs are final,
+// runs the tile kernel in shared memory and then bumps the counters of what it
+// wrote.  Since tickets are handed out in list order and the list is a
+// topological order of the DAG, the oldest unfinished task always has its
+// inputs ready, so the scheme cannot deadlock and needs no co-residency.
+//
+// Arithmetic: FP64 tiles use DFMA (the FP64 tensor path measured slower on
+// this part); FP32 tiles compute in FP32 while column norms, beta and tau are
+// computed in FP64.
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "tqr_graph.h"
+#include "tqr_engine.h"
+
+namespace tqr {
+
+// ---------------------------------------------------------------- primitives
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ int ld_acquire(const int* p) {
+  int v;
+  asm volatile("ld.acquire.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ int ld_relaxed(const int* p) {
+  int v;
+  asm volatile("ld.relaxed.gpu.global.s32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void mbar_init(uint32_t bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t done;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(done)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return done != 0;
+}
+
+// 1-D bulk copy (TMA engine) global -> shared, completing on an mbarrier.
+__device__ __forceinline__ void bulk_g2s(uint32_t dst, const void* src, uint32_t bytes, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(dst),
+      "l"(src), "r"(bytes), "r"(bar)
+      : "memory");
+}
+
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.global;" ::: "memory");
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+template <typename real>
+__device__ __forceinline__ real ldg_cg(const real* p) {
+  return __ldcg(p);
+}
+
+template <typename real>
+__device__ __forceinline__ real warp_sum(real v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned long long warp_max_u64(unsigned long long v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    unsigned long long w = __shfl_xor_sync(0xffffffffu, v, o);
+    v = w > v ? w : v;
+  }
+  return v;
+}
+
+template <typename real>
+__device__ __forceinline__ unsigned long long abs_bits(real x);
+template <>
+__device__ __forceinline__ unsigned long long abs_bits<double>(double x) {
+  return static_cast<unsigned long long>(__double_as_longlong(x)) & 0x7fffffffffffffffull;
+}
+template <>
+__device__ __forceinline__ unsigned long long abs_bits<float>(float x) {
+  return static_cast<unsigned long long>(__double_as_longlong(static_cast<double>(x))) &
+         0x7fffffffffffffffull;
+}
+
+// ---------------------------------------------------------------- context
+struct Ctl {
+  int next;       // next ticket
+  int error;      // 0, or TQR_ERR_TIMEOUT
+  int err_task;   // task index whose wait ran out
+  int err_where;  // 1: dependency wait, 2: bulk-copy wait
+};
+
+__device__ int g_status;  // sticky device status of asynchronous launches
+
+template <typename real>
+struct Ctx {
+  real *P, *T, *S, *Top, *W, *Rb;
+  double* red;       // reduction scratch (>= 2*kThreads + 160 doubles)
+  uint32_t bar;
+  uint32_t phase;
+  int nb, ib, cs;
+  int ldP, ldT, ldS;
+  Ctl* ctl;
+  long long limit_ns;
+  int task;
+};
+
+template <typename real>
+__device__ void set_error(Ctx<real>& cx, int where) {
+  if (atomicCAS(&cx.ctl->error, 0, 3 /* TQR_ERR_TIMEOUT */) == 0) {
+    cx.ctl->err_task = cx.task;
+    cx.ctl->err_where = where;
+  }
+  atomicCAS(&g_status, 0, 3);
+}
+
+// Wait for the current bulk-copy phase; bounded by the wait limit.
+template <typename real>
+__device__ void bulk_wait(Ctx<real>& cx) {
+  if (!mbar_try_wait(cx.bar, cx.phase)) {
+    const unsigned long long t0 = gtimer();
+    int it = 0;
+    while (!mbar_try_wait(cx.bar, cx.phase)) {
+      if ((++it & 63) == 0) {
+        if (ld_relaxed(&cx.ctl->error) != 0) break;
+        if ((long long)(gtimer() - t0) > cx.limit_ns) {
+          set_error(cx, 2);
+          break;
+        }
+      }
+    }
+  }
+  cx.phase ^= 1u;
+}
+
+// Copy ncols full columns (rows elements each, contiguous in global memory
+// with stride gld) into shared memory (stride sld) with the bulk-copy engine.
+// rows * sizeof(real) and every address must be 16-byte multiples.
+template <typename real>
+__device__ void bulk_cols(Ctx<real>& cx, real* dst, int sld, const real* src, long long gld, int rows,
+                          int ncols) {
+  const uint32_t bytes = static_cast<uint32_t>(rows) * sizeof(real);
+  if (threadIdx.x < 32) {
+    const int lane = threadIdx.x;
+    if (lane == 0) {
+      fence_proxy_async();
+      mbar_arrive_expect_tx(cx.bar, bytes * ncols);
+    }
+    __syncwarp();
+    for (int c = lane; c < ncols; c += 32)
+      bulk_g2s(smem_u32(dst + c * sld), src + c * gld, bytes, cx.bar);
+  }
+  bulk_wait(cx);
+}
+
+// Plain strided copies (L2 only; data may come from other SMs).
+template <typename real>
+__device__ void load_block(real* dst, int sld, const real* src, long long gld, int rows, int ncols) {
+  for (int e = threadIdx.x; e < rows * ncols; e += kThreads) {
+    int r = e % rows, c = e / rows;
+    dst[r + c * sld] = ldg_cg(src + r + c * gld);
+  }
+}
+
+template <typename real>
+__device__ void store_block(real* dst, long long gld, const real* src, int sld, int rows, int ncols) {
+  for (int e = threadIdx.x; e < rows * ncols; e += kThreads) {
+    int r = e % rows, c = e / rows;
+    dst[r + c * gld] = src[r + c * sld];
+  }
+}
+
+// ---------------------------------------------------------------- tile ops
+// One block reflector applied to a column slab (Section 3.1, DLARFB/DSSRFB
+// with compact WY):
+//   W    = L^T Top + V^T S          (L = identity when L == nullptr)
+//   W    = T^T W (trans) or T W
+//   Top -= L W,   S -= V W
+// V is nv x ib (ldv), L the unit lower ib x ib block (read below its
+// diagonal only), Top ib x w (ldt), S nv x w (lds), T ib x ib (ldT).
+template <typename real>
+__device__ void apply_block(const real* __restrict__ V, int ldv, int nv, const real* __restrict__ L, int ldl,
+                            real* Top, int ldt, real* S, int lds, const real* __restrict__ Tm, int ldT,
+                            int ib, int w, real* W, bool trans) {
+  const int tid = threadIdx.x;
+  const int nout = ib * w;
+  for (int o = tid; o < nout; o += kThreads) {
+    const int r = o % ib, c = o / ib;
+    const real* vr = V + r * ldv;
+    const real* sc = S + c * lds;
+    real a0 = Top[r + c * ldt], a1 = real(0);
+    if (L != nullptr)
+      for (int t = r + 1; t < ib; ++t) a1 += L[t + r * ldl] * Top[t + c * ldt];
+    int t = 0;
+    for (; t + 3 < nv; t += 4) {
+      a0 += vr[t] * sc[t];
+      a1 += vr[t + 1] * sc[t + 1];
+      a0 += vr[t + 2] * sc[t + 2];
+      a1 += vr[t + 3] * sc[t + 3];
+    }
+    for (; t < nv; ++t) a0 += vr[t] * sc[t];
+    W[o] = a0 + a1;
+  }
+  __syncthreads();
+  real tmp[kMaxOutPerThread];
+  {
+    int cnt = 0;
+    for (int o = tid; o < nout; o += kThreads, ++cnt) {
+      const int r = o % ib, c = o / ib;
+      const real* wc = W + c * ib;
+      real a = real(0);
+      if (trans) {
+        for (int s = 0; s <= r; ++s) a += Tm[s + r * ldT] * wc[s];
+      } else {
+        for (int s = r; s < ib; ++s) a += Tm[r + s * ldT] * wc[s];
+      }
+      tmp[cnt] = a;
+    }
+  }
+  __syncthreads();
+  {
+    int cnt = 0;
+    for (int o = tid; o < nout; o += kThreads, ++cnt) W[o] = tmp[cnt];
+  }
+  __syncthreads();
+  for (int o = tid; o < nout; o += kThreads) {
+    const int r = o % ib, c = o / ib;
+    const real* wc = W + c * ib;
+    real a = wc[r];
+    if (L != nullptr)
+      for (int t = 0; t < r; ++t) a += L[r + t * ldl] * wc[t];
+    Top[r + c * ldt] -= a;
+  }
+  const int nS = nv * w;
+  for (int o = tid; o < nS; o += kThreads) {
+    const int t = o % nv, c = o / nv;
+    const real* wc = W + c * ib;
+    real a0 = real(0), a1 = real(0);
+    int r = 0;
+    for (; r + 1 < ib; r += 2) {
+      a0 += V[t + r * ldv] * wc[r];
+      a1 += V[t + (r + 1) * ldv] * wc[r + 1];
+    }
+    if (r < ib) a0 += V[t + r * ldv] * wc[r];
+    S[t + c * lds] -= a0 + a1;
+  }
+  __syncthreads();
+}
+
+// Householder reflector for column c of a panel (LAPACK convention; FP64):
+// warp 0 computes ||x2|| over x2[0..len) (stride 1), then lane 0 derives
+// beta = -sign(alpha) ||[alpha; x2]||, tau = (beta - alpha)/beta and the scale
+// 1/(alpha - beta) of v, and stores them in red[0..2] (tau also in taus[c]).
+// The sum of squares is taken directly when max|x| lies in [2^-500, 2^500]
+// (no intermediate can overflow or lose the result to underflow there);
+// otherwise it is recomputed on x scaled by an exact power of two.
+template <typename real>
+__device__ void reflector(const real* x2, int len, real alpha_r, double* red, double* taus, int c) {
+  if (threadIdx.x >= 32) return;
+  const int lane = threadIdx.x;
+  double ssq = 0.0;
+  unsigned long long mx = 0;
+  for (int r = lane; r < len; r += 32) {
+    const double x = static_cast<double>(x2[r]);
+    ssq = fma(x, x, ssq);
+    const unsigned long long b = abs_bits(x2[r]);
+    mx = b > mx ? b : mx;
+  }
+  ssq = warp_sum(ssq);
+  mx = warp_max_u64(mx);
+  const double amax = __longlong_as_double(static_cast<long long>(mx));
+  double xnorm;
+  if (amax != 0.0 && isfinite(amax) && (amax < 0x1p-500 || amax > 0x1p500)) {
+    const int e = ilogb(amax);
+    const double sc = scalbn(1.0, -e);
+    double s2 = 0.0;
+    for (int r = lane; r < len; r += 32) {
+      const double x = static_cast<double>(x2[r]) * sc;
+      s2 = fma(x, x, s2);
+    }
+    s2 = warp_sum(s2);
+    xnorm = scalbn(sqrt(s2), e);
+  } else {
+    xnorm = sqrt(ssq);
+  }
+  if (lane == 0) {
+    const double alpha = static_cast<double>(alpha_r);
+    double tau, beta, scal;
+    if (xnorm == 0.0) {
+      tau = 0.0;
+      beta = alpha;
+      scal = 0.0;
+    } else {
+      const double h = hypot(alpha, xnorm);
+      beta = (alpha >= 0.0) ? -h : h;  // sign(0) = +1, also for -0.0
+      tau = (beta - alpha) / beta;
+      scal = 1.0 / (alpha - beta);
+    }
+    red[0] = tau;
+    red[1] = beta;
+    red[2] = scal;
+    taus[c] = tau;
+  }
+}
+
+// Unblocked QR of an ib-wide panel (DGEQR2 on the panel, Section 2).
+//   TS == false (GEQRT): P is nr x ib; reflector c has v = [1; P(c+1:nr, c)].
+//   TS == true  (TSQRT): the top is the ib x ib triangle R (ld ldr) and P is
+//                        nr x ib below it; reflector c has v = [e_c; P(:, c)].
+template <typename real, bool TS>
+__device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, double* red, double* taus) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  constexpr int nwarps = kThreads / 32;
+  for (int c = 0; c < ib; ++c) {
+    real* pc = P + c * ldP;
+    if constexpr (TS)
+      reflector<real>(pc, nr, R[c + c * ldr], red, taus, c);
+    else
+      reflector<real>(pc + c + 1, nr - c - 1, pc[c], red, taus, c);
+    __syncthreads();
+    const real tau = static_cast<real>(red[0]);
+    const real beta = static_cast<real>(red[1]);
+    const real scal = static_cast<real>(red[2]);
+    const int r0 = TS ? 0 : c + 1;
+    for (int r = r0 + tid; r < nr; r += kThreads) pc[r] *= scal;
+    __syncthreads();
+    if (tid == 0) {
+      if constexpr (TS)
+        R[c + c * ldr] = beta;
+      else
+        pc[c] = beta;
+    }
+    if (tau != real(0)) {
+      for (int d = c + 1 + wid; d < ib; d += nwarps) {
+        real* pd = P + d * ldP;
+        real acc = real(0);
+        for (int r = r0 + lane; r < nr; r += 32) acc += pc[r] * pd[r];
+        acc = warp_sum(acc);
+        real top;
+        if constexpr (TS)
+          top = R[c + d * ldr];
+        else
+          top = pd[c];
+        const real wv = tau * (top + acc);
+        for (int r = r0 + lane; r < nr; r += 32) pd[r] -= wv * pc[r];
+        if (lane == 0) {
+          if constexpr (TS)
+            R[c + d * ldr] = top - wv;
+          else
+            pd[c] = top - wv;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Compact-WY T of the panel's reflectors (DLARFT, forward, columnwise):
+//   T(c,c) = tau_c,  T(0:c, c) = -tau_c T(0:c, 0:c) (V(:,0:c)^T v_c).
+// The Gram products Y(a,b) = v_a^T v_b (a < b) go to Y (ib x ib, ld ib); the
+// recurrence runs one row of T per lane (rows are independent).
+template <typename real, bool TS>
+__device__ void form_t(const real* P, int ldP, int nr, int ib, const double* taus, real* Y, real* Tm,
+                       int ldT) {
+  const int tid = threadIdx.x;
+  const int npairs = ib * ib;
+  for (int e = tid; e < npairs; e += kThreads) {
+    const int a = e % ib, b = e / ib;
+    if (a >= b) continue;
+    const real* pa = P + a * ldP;
+    const real* pb = P + b * ldP;
+    real acc = real(0);
+    if (!TS) {
+      // v_a = [0..0, 1 at a, P(a+1:, a)], v_b = [0..0, 1 at b, P(b+1:, b)]
+      acc = pa[b];
+      for (int r = b + 1; r < nr; ++r) acc += pa[r] * pb[r];
+    } else {
+      for (int r = 0; r < nr; ++r) acc += pa[r] * pb[r];
+    }
+    Y[a + b * ib] = acc;
+  }
+  __syncthreads();
+  if (tid < 32) {
+    for (int r = tid; r < ib; r += 32) {
+      for (int c = 0; c < ib; ++c) {
+        real v;
+        if (c < r) {
+          v = real(0);
+        } else if (c == r) {
+          v = static_cast<real>(taus[c]);
+        } else {
+          real acc = real(0);
+          for (int s = r; s < c; ++s) acc += Tm[r + s * ldT] * Y[s + c * ib];
+          v = -static_cast<real>(taus[c]) * acc;
+        }
+        Tm[r + c * ldT] = v;
+      }
+    }
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- tasks
+template <typename real>
+__device__ __forceinline__ real* tile_ptr(const Inst& I, int i, int j) {
+  const long long nb2 = static_cast<long long>(I.nb) * I.nb;
+  if (j < I.q) return static_cast<real*>(I.A) + (static_cast<long long>(i) + static_cast<long long>(j) * I.p) * nb2;
+  return static_cast<real*>(I.B) + (static_cast<long long>(i) + static_cast<long long>(j - I.q) * I.p) * nb2;
+}
+
+template <typename real>
+__device__ __forceinline__ real* t_ptr(const Inst& I, int i, int k) {
+  return static_cast<real*>(I.T) + t_offset(I.p, I.nb, I.ib, i, k);
+}
+
+// Width of slab s of tile column j.
+__device__ __forceinline__ int slab_width(const Inst& I, int j, int s) {
+  int w = I.cs;
+  if (j >= I.q) {
+    const int c0 = (j - I.q) * I.nb + s * I.cs;
+    int rem = I.nrhs - c0;
+    if (rem < w) w = rem;
+  }
+  return w;
+}
+
+// GEQRT(k): Section 3.1 DGEQT2 with inner blocking.
+template <typename real>
+__device__ void exec_geqrt(Ctx<real>& cx, const Inst& I, int k) {
+  const int nb = I.nb, ib = I.ib, cs = I.cs;
+  real* A = tile_ptr<real>(I, k, k);
+  real* Tg = t_ptr<real>(I, k, k);
+  double* taus = cx.red + 2 * kThreads;
+  for (int l0 = 0; l0 < nb; l0 += ib) {
+    const int nr = nb - l0;
+    load_block(cx.P, cx.ldP, A + l0 + static_cast<long long>(l0) * nb, nb, nr, ib);
+    __syncthreads();
+    panel_qr<real, false>(cx.P, cx.ldP, nr, ib, nullptr, 0, cx.red, taus);
+    store_block(A + l0 + static_cast<long long>(l0) * nb, nb, cx.P, cx.ldP, nr, ib);
+    form_t<real, false>(cx.P, cx.ldP, nr, ib, taus, cx.Rb, cx.T, cx.ldT);
+    store_block(Tg + static_cast<long long>(l0) * ib, ib, cx.T, cx.ldT, ib, ib);
+    for (int c0 = l0 + ib; c0 < nb; c0 += cs) {
+      const int w = nb - c0 < cs ? nb - c0 : cs;
+      load_block(cx.S, cx.ldS, A + l0 + static_cast<long long>(c0) * nb, nb, nr, w);
+      __syncthreads();
+      apply_block<real>(cx.P + ib, cx.ldP, nr - ib, cx.P, cx.ldP, cx.S, cx.ldS, cx.S + ib, cx.ldS, cx.T, cx.ldT,
+                        ib, w, cx.W, true);
+      store_block(A + l0 + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nr, w);
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// TSQRT(k, i): Section 3.1 DTSQT2 with inner blocking.
+template <typename real>
+__device__ void exec_tsqrt(Ctx<real>& cx, const Inst& I, int k, int i) {
+  const int nb = I.nb, ib = I.ib, cs = I.cs;
+  real* Rt = tile_ptr<real>(I, k, k);
+  real* Ai = tile_ptr<real>(I, i, k);
+  real* Tg = t_ptr<real>(I, i, k);
+  double* taus = cx.red + 2 * kThreads;
+  real* Rb = cx.Rb;  // ib x ib triangle, ld ib
+  for (int l0 = 0; l0 < nb; l0 += ib) {
+    // the triangle's block (upper part only; its lower part holds V_kk)
+    for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+      const int r = e % ib, c = e / ib;
+      Rb[r + c * ib] = (r <= c) ? ldg_cg(Rt + (l0 + r) + static_cast<long long>(l0 + c) * nb) : real(0);
+    }
+    bulk_cols(cx, cx.P, cx.ldP, Ai + static_cast<long long>(l0) * nb, nb, nb, ib);
+    __syncthreads();
+    panel_qr<real, true>(cx.P, cx.ldP, nb, ib, Rb, ib, cx.red, taus);
+    for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+      const int r = e % ib, c = e / ib;
+      if (r <= c) Rt[(l0 + r) + static_cast<long long>(l0 + c) * nb] = Rb[r + c * ib];
+    }
+    store_block(Ai + static_cast<long long>(l0) * nb, nb, cx.P, cx.ldP, nb, ib);
+    __syncthreads();
+    form_t<real, true>(cx.P, cx.ldP, nb, ib, taus, cx.Rb, cx.T, cx.ldT);
+    store_block(Tg + static_cast<long long>(l0) * ib, ib, cx.T, cx.ldT, ib, ib);
+    for (int c0 = l0 + ib; c0 < nb; c0 += cs) {
+      const int w = nb - c0 < cs ? nb - c0 : cs;
+      load_block(cx.Top, ib, Rt + l0 + static_cast<long long>(c0) * nb, nb, ib, w);
+      bulk_cols(cx, cx.S, cx.ldS, Ai + static_cast<long long>(c0) * nb, nb, nb, w);
+      __syncthreads();
+      apply_block<real>(cx.P, cx.ldP, nb, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, true);
+      store_block(Rt + l0 + static_cast<long long>(c0) * nb, nb, cx.Top, ib, ib, w);
+      store_block(Ai + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nb, w);
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// LARFB(k, j, s): slab s of tile (k, j) <- Q_kk^T (or Q_kk) times it.
+template <typename real>
+__device__ void exec_larfb(Ctx<real>& cx, const Inst& I, int k, int j, int s, bool trans) {
+  const int nb = I.nb, ib = I.ib;
+  const real* Vt = tile_ptr<real>(I, k, k);
+  const real* Tg = t_ptr<real>(I, k, k);
+  real* C = tile_ptr<real>(I, k, j) + static_cast<long long>(s) * I.cs * nb;
+  const int w = slab_width(I, j, s);
+  bulk_cols(cx, cx.S, cx.ldS, C, nb, nb, w);
+  const int nblk = nb / ib;
+  for (int bb = 0; bb < nblk; ++bb) {
+    const int l = trans ? bb : nblk - 1 - bb;
+    const int l0 = l * ib, nr = nb - l0;
+    // V_l: unit lower block; read only below the diagonal (the triangle above
+    // may be rewritten concurrently by TSQRT of the same step)
+    for (int e = threadIdx.x; e < nr * ib; e += kThreads) {
+      const int r = e % nr, c = e / nr;
+      if (r > c) cx.P[r + c * cx.ldP] = ldg_cg(Vt + (l0 + r) + static_cast<long long>(l0 + c) * nb);
+    }
+    load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
+    __syncthreads();
+    apply_block<real>(cx.P + ib, cx.ldP, nr - ib, cx.P, cx.ldP, cx.S + l0, cx.ldS, cx.S + l0 + ib, cx.ldS, cx.T,
+                      cx.ldT, ib, w, cx.W, trans);
+  }
+  store_block(C, nb, cx.S, cx.ldS, nb, w);
+  __syncthreads();
+}
+
+// SSRFB(k, i, j, s): slab s of [(k, j); (i, j)] <- Q_ik^T (or Q_ik) times it.
+template <typename real>
+__device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int i, int j, int s, bool trans) {
+  const int nb = I.nb, ib = I.ib;
+  const real* Vt = tile_ptr<real>(I, i, k);
+  const real* Tg = t_ptr<real>(I, i, k);
+  const long long soff = static_cast<long long>(s) * I.cs * nb;
+  real* Ct = tile_ptr<real>(I, k, j) + soff;
+  real* Cb = tile_ptr<real>(I, i, j) + soff;
+  const int w = slab_width(I, j, s);
+  const int nblk = nb / ib;
+  bulk_cols(cx, cx.S, cx.ldS, Cb, nb, nb, w);
+  for (int bb = 0; bb < nblk; ++bb) {
+    const int l = trans ? bb : nblk - 1 - bb;
+    const int l0 = l * ib;
+    load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
+    load_block(cx.Top, ib, Ct + l0, nb, ib, w);
+    bulk_cols(cx, cx.P, cx.ldP, Vt + static_cast<long long>(l0) * nb, nb, nb, ib);
+    __syncthreads();
+    apply_block<real>(cx.P, cx.ldP, nb, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, trans);
+    store_block(Ct + l0, nb, cx.Top, ib, ib, w);
+    __syncthreads();
+  }
+  store_block(Cb, nb, cx.S, cx.ldS, nb, w);
+  __syncthreads();
+}
+
+// S(0:nv, 0:w) -= V(0:nv, 0:kk) X(0:kk, 0:w)   (V ld ldv, X ld ldx)
+template <typename real>
+__device__ void gemm_sub(real* S, int lds, int nv, int w, const real* V, int ldv, const real* X, int ldx, int kk) {
+  for (int o = threadIdx.x; o < nv * w; o += kThreads) {
+    const int t = o % nv, c = o / nv;
+    const real* xc = X + c * ldx;
+    real a0 = real(0), a1 = real(0);
+    int r = 0;
+    for (; r + 1 < kk; r += 2) {
+      a0 += V[t + r * ldv] * xc[r];
+      a1 += V[t + (r + 1) * ldv] * xc[r + 1];
+    }
+    if (r < kk) a0 += V[t + r * ldv] * xc[r];
+    S[t + c * lds] -= a0 + a1;
+  }
+}
+
+// TRSM_UPD(k, l, j, s): C_k -= R_kl X_l on slab s of right-hand-side column j.
+template <typename real>
+__device__ void exec_trsm_upd(Ctx<real>& cx, const Inst& I, int k, int l, int j, int s) {
+  const int nb = I.nb, ib = I.ib;
+  const long long soff = static_cast<long long>(s) * I.cs * nb;
+  real* C = tile_ptr<real>(I, k, j) + soff;
+  const real* X = tile_ptr<real>(I, l, j) + soff;
+  const real* R = tile_ptr<real>(I, k, l);
+  const int w = slab_width(I, j, s);
+  bulk_cols(cx, cx.S, cx.ldS, C, nb, nb, w);
+  for (int c0 = 0; c0 < nb; c0 += ib) {
+    bulk_cols(cx, cx.P, cx.ldP, R + static_cast<long long>(c0) * nb, nb, nb, ib);
+    load_block(cx.W, ib, X + c0, nb, ib, w);
+    __syncthreads();
+    gemm_sub(cx.S, cx.ldS, nb, w, cx.P, cx.ldP, cx.W, ib, ib);
+    __syncthreads();
+  }
+  store_block(C, nb, cx.S, cx.ldS, nb, w);
+  __syncthreads();
+}
+
+// TRSM_SOLVE(k, j, s): X_k = R_kk^{-1} C_k (upper triangular, blocked by ib
+// from the bottom).  Rows past n (zero padding) get x = 0.
+template <typename real>
+__device__ void exec_trsm_solve(Ctx<real>& cx, const Inst& I, int k, int j, int s) {
+  const int nb = I.nb, ib = I.ib;
+  const long long soff = static_cast<long long>(s) * I.cs * nb;
+  real* C = tile_ptr<real>(I, k, j) + soff;
+  const real* R = tile_ptr<real>(I, k, k);
+  const int w = slab_width(I, j, s);
+  const int nvalid = I.n - k * nb;  // rows of this tile inside the matrix
+  bulk_cols(cx, cx.S, cx.ldS, C, nb, nb, w);
+  for (int b0 = nb - ib; b0 >= 0; b0 -= ib) {
+    for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+      const int r = e % ib, c = e / ib;
+      cx.T[r + c * cx.ldT] = (r <= c) ? ldg_cg(R + (b0 + r) + static_cast<long long>(b0 + c) * nb) : real(0);
+    }
+    __syncthreads();
+    if (threadIdx.x < w) {
+      real* x = cx.S + threadIdx.x * cx.ldS + b0;
+      for (int r = ib - 1; r >= 0; --r) {
+        real v = x[r];
+        for (int t = r + 1; t < ib; ++t) v -= cx.T[r + t * cx.ldT] * x[t];
+        x[r] = (b0 + r < nvalid) ? v / cx.T[r + r * cx.ldT] : real(0);
+      }
+    }
+    __syncthreads();
+    if (b0 > 0) {
+      load_block(cx.P, cx.ldP, R + static_cast<long long>(b0) * nb, nb, b0, ib);
+      __syncthreads();
+      gemm_sub(cx.S, cx.ldS, b0, w, cx.P, cx.ldP, cx.S + b0, cx.ldS, ib);
+      __syncthreads();
+    }
+  }
+  store_block(C, nb, cx.S, cx.ldS, nb, w);
+  __syncthreads();
+}
+
+// TRSMT_UPD(k, l, j, s): C_k -= R_lk^T X_l  (l < k).
+template <typename real>
+__device__ void exec_trsmt_upd(Ctx<real>& cx, const Inst& I, int k, int l, int j, int s) {
+  const int nb = I.nb, ib = I.ib;
+  const long long soff = static_cast<long long>(s) * I.cs * nb;
+  real* C = tile_ptr<real>(I, k, j) + soff;
+  const real* X = tile_ptr<real>(I, l, j) + soff;
+  const real* R = tile_ptr<real>(I, l, k);
+  const int w = slab_width(I, j, s);
+  bulk_cols(cx, cx.S, cx.ldS, X, nb, nb, w);
+  for (int r0 = 0; r0 < nb; r0 += ib) {
+    bulk_cols(cx, cx.P, cx.ldP, R + static_cast<long long>(r0) * nb, nb, nb, ib);
+    load_block(cx.Top, ib, C + r0, nb, ib, w);
+    __syncthreads();
+    for (int o = threadIdx.x; o < ib * w; o += kThreads) {
+      const int r = o % ib, c = o / ib;
+      const real* pr = cx.P + r * cx.ldP;
+      const real* xc = cx.S + c * cx.ldS;
+      real a0 = real(0), a1 = real(0);
+      int t = 0;
+      for (; t + 1 < nb; t += 2) {
+        a0 += pr[t] * xc[t];
+        a1 += pr[t + 1] * xc[t + 1];
+      }
+      if (t < nb) a0 += pr[t] * xc[t];
+      cx.Top[r + c * ib] -= a0 + a1;
+    }
+    __syncthreads();
+    store_block(C + r0, nb, cx.Top, ib, ib, w);
+    __syncthreads();
+  }
+}
+
+// TRSMT_SOLVE(k, j, s): X_k = R_kk^{-T} C_k (forward substitution by ib blocks).
+template <typename real>
+__device__ void exec_trsmt_solve(Ctx<real>& cx, const Inst& I, int k, int j, int s) {
+  const int nb = I.nb, ib = I.ib;
+  const long long soff = static_cast<long long>(s) * I.cs * nb;
+  real* C = tile_ptr<real>(I, k, j) + soff;
+  const real* R = tile_ptr<real>(I, k, k);
+  const int w = slab_width(I, j, s);
+  const int nvalid = I.n - k * nb;
+  bulk_cols(cx, cx.S, cx.ldS, C, nb, nb, w);
+  for (int b0 = 0; b0 < nb; b0 += ib) {
+    for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+      const int r = e % ib, c = e / ib;
+      cx.T[r + c * cx.ldT] = (r <= c) ? ldg_cg(R + (b0 + r) + static_cast<long long>(b0 + c) * nb) : real(0);
+    }
+    __syncthreads();
+    if (threadIdx.x < w) {
+      real* x = cx.S + threadIdx.x * cx.ldS + b0;
+      for (int r = 0; r < ib; ++r) {
+        real v = x[r];
+        for (int t = 0; t < r; ++t) v -= cx.T[t + r * cx.ldT] * x[t];
+        x[r] = (b0 + r < nvalid) ? v / cx.T[r + r * cx.ldT] : real(0);
+      }
+    }
+    __syncthreads();
+    const int nbelow = nb - b0 - ib;
+    if (nbelow > 0) {
+      // P(r', t) = R(b0 + t, b0 + ib + r'): the block row to the right, transposed
+      for (int e = threadIdx.x; e < nbelow * ib; e += kThreads) {
+        const int rr = e % nbelow, t = e / nbelow;
+        cx.P[rr + t * cx.ldP] = ldg_cg(R + (b0 + t) + static_cast<long long>(b0 + ib + rr) * nb);
+      }
+      __syncthreads();
+      gemm_sub(cx.S + b0 + ib, cx.ldS, nbelow, w, cx.P, cx.ldP, cx.S + b0, cx.ldS, ib);
+      __syncthreads();
+    }
+  }
+  store_block(C, nb, cx.S, cx.ldS, nb, w);
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------- scheduler
+// Thread 0 waits until every counter of every wait has reached its version.
+template <typename real>
+__device__ bool wait_deps(Ctx<real>& cx, const Inst& I, const TaskX& t) {
+  Wait w[4];
+  Signal sg[2];
+  int nsig;
+  const int nw = task_rules(I, t, w, sg, &nsig);
+  unsigned long long t0 = 0;
+  for (int a = 0; a < nw; ++a) {
+    for (int c = 0; c < w[a].cnt; ++c) {
+      const int* ctr = I.ver + w[a].ctr + c;
+      if (ld_acquire(ctr) >= w[a].ver) continue;
+      if (t0 == 0) t0 = gtimer();
+      unsigned ns = 32;
+      while (ld_acquire(ctr) < w[a].ver) {
+        __nanosleep(ns);
+        if (ns < 512) ns <<= 1;
+        if (ld_relaxed(&cx.ctl->error) != 0) return false;
+        if ((long long)(gtimer() - t0) > cx.limit_ns) {
+          set_error(cx, 1);
+          return false;
+        }
+      }
+    }
+  }
+  return true;
+}
+
+__device__ void signal_done(const Inst& I, const TaskX& t) {
+  Wait w[4];
+  Signal sg[2];
+  int nsig;
+  task_rules(I, t, w, sg, &nsig);
+  __threadfence();
+  for (int a = 0; a < nsig; ++a)
+    for (int c = 0; c < sg[a].cnt; ++c) atomicAdd(I.ver + sg[a].ctr + c, 1);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
+                                                             const Inst* __restrict__ insts, Ctl* ctl,
+                                                             long long limit_ns) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  __shared__ TaskX s_task;
+  __shared__ Inst s_inst;
+  __shared__ int s_go;
+
+  Ctx<real> cx;
+  cx.task = 0;
+  cx.ctl = ctl;
+  cx.limit_ns = limit_ns;
+  cx.phase = 0;
+  int cur_nb = -1, cur_ib = -1, cur_cs = -1;
+  if (threadIdx.x == 0) {
+    // the barrier sits at the end of the largest layout; its offset is passed
+    // through the kernel's dynamic size
+    uint32_t dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    mbar_init(smem_u32(smem + dyn - 16), 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  {
+    uint32_t dyn;
+    asm volatile("mov.u32 %0, %%dynamic_smem_size;" : "=r"(dyn));
+    cx.bar = smem_u32(smem + dyn - 16);
+  }
+  __syncthreads();
+
+  while (true) {
+    if (threadIdx.x == 0) {
+      int go = 0;
+      if (ld_relaxed(&ctl->error) == 0) {
+        const int t = atomicAdd(&ctl->next, 1);
+        if (t < ntasks) {
+          s_task = tasks[t];
+          s_inst = insts[s_task.inst];
+          cx.task = t;
+          go = wait_deps(cx, s_inst, s_task) ? 1 : 0;
+        }
+      }
+      s_go = go;
+    }
+    __syncthreads();
+    if (!s_go) break;
+    const TaskX t = s_task;
+    const Inst& I = s_inst;
+    if (I.nb != cur_nb || I.ib != cur_ib || I.cs != cur_cs) {
+      const SmemLayout L = smem_layout(I.nb, I.ib, I.cs, sizeof(real));
+      cx.P = reinterpret_cast<real*>(smem + L.oP);
+      cx.T = reinterpret_cast<real*>(smem + L.oT);
+      cx.S = reinterpret_cast<real*>(smem + L.oS);
+      cx.Top = reinterpret_cast<real*>(smem + L.oTop);
+      cx.W = reinterpret_cast<real*>(smem + L.oW);
+      cx.red = reinterpret_cast<double*>(smem + L.oRed);
+      cx.Rb = L.r_in_s ? cx.S : cx.Top;
+      cx.nb = I.nb;
+      cx.ib = I.ib;
+      cx.cs = I.cs;
+      cx.ldP = ld_pad(I.nb, sizeof(real));
+      cx.ldS = ld_pad(I.nb, sizeof(real));
+      cx.ldT = I.ib + 1;
+      cur_nb = I.nb;
+      cur_ib = I.ib;
+      cur_cs = I.cs;
+    }
+    switch (t.kind) {
+      case K_GEQRT: exec_geqrt(cx, I, t.k); break;
+      case K_TSQRT: exec_tsqrt(cx, I, t.k, t.i); break;
+      case K_LARFB: exec_larfb(cx, I, t.k, t.j, t.s, true); break;
+      case K_LARFB_N: exec_larfb(cx, I, t.k, t.j, t.s, false); break;
+      case K_SSRFB: exec_ssrfb(cx, I, t.k, t.i, t.j, t.s, true); break;
+      case K_SSRFB_N: exec_ssrfb(cx, I, t.k, t.i, t.j, t.s, false); break;
+      case K_TRSM_UPD: exec_trsm_upd(cx, I, t.k, t.l, t.j, t.s); break;
+      case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
+      case K_TRSMT_UPD: exec_trsmt_upd(cx, I, t.k, t.l, t.j, t.s); break;
+      case K_TRSMT_SOLVE: exec_trsmt_solve(cx, I, t.k, t.j, t.s); break;
+      default: break;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) signal_done(I, t);
+  }
+}
+
+// ---------------------------------------------------------------- BDL
+// Column-major (ld) -> Block Data Layout tiles (Section 3.4), zero padded.
+// One thread per tile element, consecutive threads on consecutive rows.
+template <typename S, typename D>
+__global__ void pack_kernel(const S* __restrict__ A, long long lda, int m, int n, D* __restrict__ Ab, int p,
+                            int q, int nb) {
+  const long long nb2 = static_cast<long long>(nb) * nb;
+  const long long total = nb2 * p * q;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long tile = e / nb2;
+    const int rem = static_cast<int>(e - tile * nb2);
+    const int r = rem % nb, c = rem / nb;
+    const int ti = static_cast<int>(tile % p), tj = static_cast<int>(tile / p);
+    const long long gi = static_cast<long long>(ti) * nb + r, gj = static_cast<long long>(tj) * nb + c;
+    D v = D(0);
+    if (gi < m && gj < n) v = static_cast<D>(A[gi + gj * lda]);
+    Ab[e] = v;
+  }
+}
+
+template <typename S, typename D>
+__global__ void unpack_kernel(const S* __restrict__ Ab, int p, int nb, D* __restrict__ A, long long lda, int m,
+                              int n) {
+  const long long total = static_cast<long long>(m) * n;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int gi = static_cast<int>(e % m);
+    const int gj = static_cast<int>(e / m);
+    const int ti = gi / nb, r = gi - ti * nb;
+    const int tj = gj / nb, c = gj - tj * nb;
+    A[gi + static_cast<long long>(gj) * lda] =
+        static_cast<D>(Ab[(static_cast<long long>(ti) + static_cast<long long>(tj) * p) * nb * nb +
+                          static_cast<long long>(c) * nb + r]);
+  }
+}
+
+__global__ void status_reset_kernel() { g_status = 0; }
+
+// ---------------------------------------------------------------- host launchers
+static int grid_for(long long work, int sms) {
+  long long g = (work + 255) / 256;
+  long long cap = static_cast<long long>(sms) * 8;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
+template <typename real>
+cudaError_t launch_pack(const double* A, long long lda, int m, int n, real* Ab, int p, int q, int nb, int sms,
+                        cudaStream_t st) {
+  const long long total = static_cast<long long>(nb) * nb * p * q;
+  pack_kernel<double, real><<<grid_for(total, sms), 256, 0, st>>>(A, lda, m, n, Ab, p, q, nb);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_unpack(const real* Ab, int p, int nb, double* A, long long lda, int m, int n, int sms,
+                          cudaStream_t st) {
+  if (static_cast<long long>(m) * n == 0) return cudaSuccess;
+  unpack_kernel<real, double><<<grid_for(static_cast<long long>(m) * n, sms), 256, 0, st>>>(Ab, p, nb, A, lda, m, n);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
+                       int smem_bytes, cudaStream_t st) {
+  cudaError_t e = cudaFuncSetAttribute(run_tasks_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_bytes);
+  if (e != cudaSuccess) return e;
+  run_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl), limit_ns);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t occupancy(int smem_bytes, int* blocks_per_sm) {
+  cudaError_t e = cudaFuncSetAttribute(run_tasks_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       smem_bytes);
+  if (e != cudaSuccess) return e;
+  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, run_tasks_kernel<real>, kThreads, smem_bytes);
+}
+
+cudaError_t read_status(int* status, cudaStream_t st) {
+  cudaError_t e = cudaMemcpyFromSymbolAsync(status, g_status, sizeof(int), 0, cudaMemcpyDeviceToHost, st);
+  if (e != cudaSuccess) return e;
+  e = cudaStreamSynchronize(st);
+  if (e != cudaSuccess) return e;
+  status_reset_kernel<<<1, 1, 0, st>>>();
+  return cudaGetLastError();
+}
+
+size_t ctl_bytes() { return sizeof(Ctl); }
+
+// Register-resident DFMA chains: 8 independent FMAs per iteration per thread.
+__global__ void dfma_probe_kernel(double* out, int iters, double a, double b) {
+  double x0 = threadIdx.x, x1 = x0 + 1, x2 = x0 + 2, x3 = x0 + 3, x4 = x0 + 4, x5 = x0 + 5, x6 = x0 + 6, x7 = x0 + 7;
+  for (int i = 0; i < iters; ++i) {
+    x0 = fma(x0, a, b); x1 = fma(x1, a, b); x2 = fma(x2, a, b); x3 = fma(x3, a, b);
+    x4 = fma(x4, a, b); x5 = fma(x5, a, b); x6 = fma(x6, a, b); x7 = fma(x7, a, b);
+  }
+  out[blockIdx.x * blockDim.x + threadIdx.x] = x0 + x1 + x2 + x3 + x4 + x5 + x6 + x7;
+}
+
+cudaError_t fp64_peak(double* tflops, cudaStream_t st) {
+  int dev = 0, sms = 0;
+  cudaGetDevice(&dev);
+  cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  const int threads = 256, blocks = sms * 4, iters = 4000;
+  double* out = nullptr;
+  cudaError_t e = cudaMallocAsync(reinterpret_cast<void**>(&out), sizeof(double) * threads * blocks, st);
+  if (e != cudaSuccess) return e;
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  dfma_probe_kernel<<<blocks, threads, 0, st>>>(out, 100, 0.999, 1e-3);
+  float best = 1e30f;
+  for (int rep = 0; rep < 3; ++rep) {
+    cudaEventRecord(e0, st);
+    dfma_probe_kernel<<<blocks, threads, 0, st>>>(out, iters, 0.999, 1e-3);
+    cudaEventRecord(e1, st);
+    cudaEventSynchronize(e1);
+    float ms = 0;
+    cudaEventElapsedTime(&ms, e0, e1);
+    if (ms < best) best = ms;
+  }
+  e = cudaGetLastError();
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(out, st);
+  cudaStreamSynchronize(st);
+  *tflops = 2.0 * 8.0 * iters * static_cast<double>(blocks) * threads / (best * 1e-3) / 1e12;
+  return e;
+}
+
+template cudaError_t launch_pack<double>(const double*, long long, int, int, double*, int, int, int, int,
+                                         cudaStream_t);
+template cudaError_t launch_pack<float>(const double*, long long, int, int, float*, int, int, int, int,
+                                        cudaStream_t);
+template cudaError_t launch_unpack<double>(const double*, int, int, double*, long long, int, int, int,
+                                           cudaStream_t);
+template cudaError_t launch_unpack<float>(const float*, int, int, double*, long long, int, int, int, cudaStream_t);
+template cudaError_t launch_run<double>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t);
+template cudaError_t launch_run<float>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t);
+template cudaError_t occupancy<double>(int, int*);
+template cudaError_t occupancy<float>(int, int*);
+
+}  // namespace tqr

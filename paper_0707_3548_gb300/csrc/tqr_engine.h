@@ -1,0 +1,29 @@
+// tqr_engine.h -- host-side entry points of the device engine (tqr_engine.cu).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "tqr_graph.h"
+
+namespace tqr {
+
+template <typename real>
+cudaError_t launch_pack(const double* A, long long lda, int m, int n, real* Ab, int p, int q, int nb, int sms,
+                        cudaStream_t st);
+template <typename real>
+cudaError_t launch_unpack(const real* Ab, int p, int nb, double* A, long long lda, int m, int n, int sms,
+                          cudaStream_t st);
+template <typename real>
+cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
+                       int smem_bytes, cudaStream_t st);
+template <typename real>
+cudaError_t occupancy(int smem_bytes, int* blocks_per_sm);
+
+// Copies the sticky device status to *status (synchronizing st) and clears it.
+cudaError_t read_status(int* status, cudaStream_t st);
+size_t ctl_bytes();
+// FP64 FMA throughput probe (TFLOP/s).
+cudaError_t fp64_peak(double* tflops, cudaStream_t st);
+
+}  // namespace tqr

@@ -1,0 +1,231 @@
+// tqr_graph.h -- task descriptors and the data-flow rules of the tile DAG.
+//
+// Shared by the host plan builder and the device scheduler (both compile it).
+//
+// The paper (Section 3.3) runs Algorithm 1 as a DAG of tile tasks whose edges
+// are the data dependencies between them.  Here the DAG is never stored: each
+// tile column slab (i, j, s) owns a version counter that counts the tasks that
+// have written it, and every task knows, from its indices alone, which version
+// of each operand it needs.  A task may start once every counter it waits on
+// has reached the required version; when it ends it increments the counters of
+// what it wrote.  Because every writer of a slab also waits for that slab's
+// previous version, the writers of each slab run in exactly the order of the
+// sequential algorithm, so the result does not depend on the schedule.
+//
+// Operand versions below are counts of earlier writers of the slab in the
+// sequential order of the mode:
+//   FACTOR  (Algorithm 1; optional right-hand-side tile columns j >= q are
+//            updated like trailing columns, i.e. Q^T B; optional back
+//            substitution X = R^-1 (Q^T B)[0:n] appended)
+//   APPLY_QT (factors final: LARFB/SSRFB on B only, Algorithm 1's order)
+//   APPLY_Q  (factors final: the transposed steps in reverse order)
+//   TRSM     (factors final: back substitution on B only)
+//   TRSMT    (factors final: forward substitution R^T X = B)
+#pragma once
+
+#include <stdint.h>
+
+#if defined(__CUDACC__)
+#define TQR_HD __host__ __device__ __forceinline__
+#else
+#define TQR_HD inline
+#endif
+
+namespace tqr {
+
+enum Kind : int {
+  K_GEQRT = 0,       // Section 3.1 DGEQT2 on tile (k,k)
+  K_TSQRT = 1,       // Section 3.1 DTSQT2 on (k,k) upper triangle + (i,k)
+  K_LARFB = 2,       // Section 3.1 DLARFB: slab s of (k,j) <- Q_kk^T (k,j)
+  K_SSRFB = 3,       // Section 3.1 DSSRFB: slab s of [(k,j); (i,j)] <- Q_ik^T [.]
+  K_LARFB_N = 4,     // (k,j) slab <- Q_kk (k,j)            (apply Q)
+  K_SSRFB_N = 5,     // [(k,j); (i,j)] slab <- Q_ik [.]     (apply Q)
+  K_TRSM_UPD = 6,    // C_k <- C_k - R_kl X_l   (l > k), slab s of column j
+  K_TRSM_SOLVE = 7,  // X_k <- R_kk^-1 C_k
+  K_TRSMT_UPD = 8,   // C_k <- C_k - R_lk^T X_l (l < k)
+  K_TRSMT_SOLVE = 9, // X_k <- R_kk^-T C_k
+  K_NKINDS = 10
+};
+
+enum Mode : int { M_FACTOR = 0, M_APPLY_QT = 1, M_APPLY_Q = 2, M_TRSM = 3, M_TRSMT = 4 };
+
+// One task (32 bytes, two vector loads on the device).  k: elimination step;
+// i: row tile; j: column tile (A columns < q, right-hand-side columns >= q);
+// s: column slab of tile column j; l: the second tile index of TRSM updates.
+struct TaskX {
+  int32_t kind, s, inst, k, i, j, l, pad;
+};
+
+// Per-problem description (device copy lives in global memory).
+struct Inst {
+  void* A;          // BDL tiles of A: tile (i,j) at ((i + j*p) * nb * nb) elements
+  void* B;          // BDL tiles of the right-hand sides: tile (i, q+jb) at
+                    // ((i + jb*p) * nb * nb) elements
+  void* T;          // T blocks (element type of A), see t_offset
+  int32_t* ver;     // version counters, (j*p + i)*NS + s for j in [0, q+qb)
+  int32_t m, n, p, q, kt, qb, nrhs;
+  int32_t nb, ib, cs, NS;   // NS = nb/cs slabs per full tile column
+  int32_t mode;
+  int32_t trsm;             // FACTOR mode: back substitution appended (1) or not (0)
+  int32_t pad0, pad1;
+};
+
+// Number of slabs of tile column j (A columns: NS; right-hand-side columns:
+// enough slabs to cover the real columns of that tile column).
+TQR_HD int slabs_of_col(const Inst& I, int j) {
+  if (j < I.q) return I.NS;
+  int c0 = (j - I.q) * I.nb;
+  int w = I.nrhs - c0;
+  if (w > I.nb) w = I.nb;
+  if (w <= 0) return 0;
+  return (w + I.cs - 1) / I.cs;
+}
+
+TQR_HD int ctr_index(const Inst& I, int i, int j, int s) { return (j * I.p + i) * I.NS + s; }
+
+// A wait: counters ctr .. ctr+cnt-1 must all be >= ver.
+struct Wait { int ctr, cnt, ver; };
+// A signal: counters ctr .. ctr+cnt-1 are incremented.
+struct Signal { int ctr, cnt; };
+
+// Fills up to 4 waits and 2 signals; returns the number of waits, writes the
+// number of signals to *nsig.  `a_final` (APPLY/TRSM modes): A's tiles were
+// factored by an earlier launch, so waits on them are dropped.
+TQR_HD int task_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* nsig) {
+  const int p = I.p, kt = I.kt, NS = I.NS;
+  const int k = t.k, i = t.i, j = t.j, s = t.s, l = t.l;
+  const bool a_final = I.mode != M_FACTOR;
+  int nw = 0;
+  *nsig = 0;
+  switch (t.kind) {
+    case K_GEQRT:
+      w[nw++] = {ctr_index(I, k, k, 0), NS, k};
+      sg[(*nsig)++] = {ctr_index(I, k, k, 0), NS};
+      break;
+    case K_TSQRT:
+      w[nw++] = {ctr_index(I, k, k, 0), NS, i};
+      w[nw++] = {ctr_index(I, i, k, 0), NS, k};
+      sg[(*nsig)++] = {ctr_index(I, k, k, 0), NS};
+      sg[(*nsig)++] = {ctr_index(I, i, k, 0), NS};
+      break;
+    case K_LARFB:
+      if (!a_final) w[nw++] = {ctr_index(I, k, k, 0), NS, k + 1};
+      w[nw++] = {ctr_index(I, k, j, s), 1, k};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    case K_SSRFB:
+      if (!a_final) w[nw++] = {ctr_index(I, i, k, 0), NS, k + 1};
+      w[nw++] = {ctr_index(I, k, j, s), 1, i};
+      w[nw++] = {ctr_index(I, i, j, s), 1, k};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      sg[(*nsig)++] = {ctr_index(I, i, j, s), 1};
+      break;
+    case K_SSRFB_N: {
+      // sequential order: for k = kt-1..0 { for i = p-1..k+1 SSRFB_N(k,i); LARFB_N(k) }
+      int mi = i < kt ? i : kt;
+      int bot = (i < kt ? (p - i) : 0) + (mi - 1 - k);
+      w[nw++] = {ctr_index(I, k, j, s), 1, p - 1 - i};
+      w[nw++] = {ctr_index(I, i, j, s), 1, bot};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      sg[(*nsig)++] = {ctr_index(I, i, j, s), 1};
+      break;
+    }
+    case K_LARFB_N:
+      w[nw++] = {ctr_index(I, k, j, s), 1, p - 1 - k};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    case K_TRSM_UPD: {
+      // C_k -= R_kl X_l, l = kt-1 .. k+1, then SOLVE(k).  In FACTOR mode the
+      // right-hand sides first received p (rows < kt) writes from the
+      // factorization and R's tiles (k, l), k <= l < q, end at version p.
+      int base = a_final ? 0 : p;
+      if (!a_final) w[nw++] = {ctr_index(I, k, l, 0), NS, p};
+      w[nw++] = {ctr_index(I, l, j, s), 1, base + (kt - l)};
+      w[nw++] = {ctr_index(I, k, j, s), 1, base + (kt - 1 - l)};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    }
+    case K_TRSM_SOLVE: {
+      int base = a_final ? 0 : p;
+      if (!a_final) w[nw++] = {ctr_index(I, k, k, 0), NS, p};
+      w[nw++] = {ctr_index(I, k, j, s), 1, base + (kt - 1 - k)};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    }
+    case K_TRSMT_UPD:
+      // forward substitution: C_k -= R_lk^T X_l for l = 0 .. k-1, then SOLVE
+      w[nw++] = {ctr_index(I, l, j, s), 1, l + 1};
+      w[nw++] = {ctr_index(I, k, j, s), 1, l};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    case K_TRSMT_SOLVE:
+      w[nw++] = {ctr_index(I, k, j, s), 1, k};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    default:
+      break;
+  }
+  return nw;
+}
+
+// Offset (in elements) of T block (i, k), i >= k, each ib x nb.
+TQR_HD int64_t t_offset(int p, int nb, int ib, int i, int k) {
+  int64_t idx = (int64_t)k * p - (int64_t)k * (k - 1) / 2 + (i - k);
+  return idx * (int64_t)ib * nb;
+}
+
+TQR_HD int64_t t_elems(int p, int q, int nb, int ib) {
+  int kt = p < q ? p : q;
+  return t_offset(p, nb, ib, kt, kt);  // first index past the last block
+}
+
+}  // namespace tqr
+
+namespace tqr {
+
+// Threads per CTA of the persistent task kernel.
+constexpr int kThreads = 256;
+// Largest ib * cs (outputs of one W block) handled per thread batch.
+constexpr int kMaxOutPerThread = 8;
+
+// Shared-memory layout of the task kernel (byte offsets, 16-byte aligned):
+//   P   nb x ib    panel being factored / reflector block V_l
+//   T   ib x ib    T_l
+//   S   nb x cs    column slab being updated (bottom tile or whole slab);
+//                  also holds TSQRT's ib x ib triangle when it fits
+//   Top ib x cs    top rows of a TSQRT/SSRFB update (ib x ib if it must hold
+//                  TSQRT's triangle)
+//   W   ib x cs    W = V^T S products
+//   Red doubles    reduction scratch and per-column scalars
+//   Bar 8 bytes    mbarrier for the bulk (TMA) copies
+struct SmemLayout {
+  int oP, oT, oS, oTop, oW, oRed, oBar, bytes;
+  bool r_in_s;
+};
+
+TQR_HD int align16(int x) { return (x + 15) & ~15; }
+
+// Leading dimension of the nb-row panels and slabs in shared memory: padded
+// by 16 bytes so columns stay 16-byte aligned for the bulk copies while
+// lanes that walk along a row do not all hit one bank.
+TQR_HD int ld_pad(int nb, int esize) { return nb + 16 / esize; }
+
+TQR_HD SmemLayout smem_layout(int nb, int ib, int cs, int esize) {
+  SmemLayout L;
+  const int ld = ld_pad(nb, esize);
+  L.r_in_s = (ld * cs >= ib * ib);
+  int top_elems = ib * cs;
+  if (!L.r_in_s && ib * ib > top_elems) top_elems = ib * ib;
+  int o = 0;
+  L.oP = o;   o += align16(ld * ib * esize);
+  L.oT = o;   o += align16(ib * (ib + 1) * esize);
+  L.oS = o;   o += align16(ld * cs * esize);
+  L.oTop = o; o += align16(top_elems * esize);
+  L.oW = o;   o += align16(ib * cs * esize);
+  L.oRed = o; o += align16((2 * kThreads + 2 * 64 + 32) * 8);
+  L.oBar = o; o += 16;
+  L.bytes = o;
+  return L;
+}
+
+}  // namespace tqr

@@ -1,0 +1,481 @@
+// tqr_ls.cu -- least squares on top of the tiled QR (tqr_solve_ls).
+//
+// FP64: one task graph factors A, applies Q^T to the right-hand sides (they
+// ride along as extra tile columns of Algorithm 1) and back-substitutes with
+// R (Section 5 of the paper names applying Q as the factorization's natural
+// companion).
+//
+// FP32 + refinement: the same graph in FP32 (column norms and tau in FP64)
+// gives x0; then Bjorck's iterative refinement of the augmented system
+//     [I A; A^T 0] [r; x] = [b; 0]
+// runs with FP64 residuals  f = b - r - A x,  g = -A^T r  and corrections from
+// the FP32 factors:  h = R^-T g,  d = Q^T f,  dx = R^-1 (d1 - h),
+// dr = Q [h; d2],  until the normwise backward error
+//     max_c ||A^T (b_c - A x_c)|| / (||A||_F (||A||_F ||x_c|| + ||b_c||))
+// is at most tol.  The FP64 work (residuals, A^T products, norms) runs in the
+// kernels below; they are bound by the FP64 pipe or by HBM.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "tqr.h"
+#include "tqr_api_internal.h"
+#include "tqr_engine.h"
+
+namespace tqr {
+
+constexpr int kLsThreads = 256;
+constexpr int kRhsChunk = 8;
+
+// Y(r, c) = Z(r, c) - sum_{j in split} A(r, j) X(j, c), written per split
+// into P[split] (m x nrhs, ld m); a second kernel sums the splits in order.
+__global__ void __launch_bounds__(kLsThreads) gemm_nn_partial(const double* __restrict__ A, long long lda, int m,
+                                                              int n, const double* __restrict__ X, long long ldx,
+                                                              int nrhs, int split_len,
+                                                              double* __restrict__ P) {
+  __shared__ double xs[64][kRhsChunk];
+  const int r = blockIdx.x * kLsThreads + threadIdx.x;
+  const int j0 = blockIdx.y * split_len;
+  const int j1 = min(n, j0 + split_len);
+  for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
+    const int cw = min(kRhsChunk, nrhs - c0);
+    double acc[kRhsChunk];
+#pragma unroll
+    for (int c = 0; c < kRhsChunk; ++c) acc[c] = 0.0;
+    for (int jb = j0; jb < j1; jb += 64) {
+      const int jw = min(64, j1 - jb);
+      __syncthreads();
+      for (int e = threadIdx.x; e < 64 * kRhsChunk; e += kLsThreads) {
+        const int jj = e % 64, c = e / 64;
+        xs[jj][c] = (jj < jw && c < cw) ? X[(jb + jj) + static_cast<long long>(c0 + c) * ldx] : 0.0;
+      }
+      __syncthreads();
+      if (r < m) {
+        for (int jj = 0; jj < jw; ++jj) {
+          const double a = A[r + static_cast<long long>(jb + jj) * lda];
+#pragma unroll
+          for (int c = 0; c < kRhsChunk; ++c) acc[c] = fma(a, xs[jj][c], acc[c]);
+        }
+      }
+    }
+    if (r < m)
+      for (int c = 0; c < cw; ++c)
+        P[(static_cast<long long>(blockIdx.y) * nrhs + c0 + c) * m + r] = acc[c];
+  }
+}
+
+// Y = alpha * Z + beta * W - sum_s P[s]   (all m x nrhs; Z, W may be null)
+__global__ void combine_partials(const double* __restrict__ P, int nsplit, int m, int nrhs,
+                                 const double* __restrict__ Z, long long ldz, double alpha,
+                                 const double* __restrict__ Wm, long long ldw, double beta, double* __restrict__ Y,
+                                 long long ldy) {
+  const long long total = static_cast<long long>(m) * nrhs;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(e % m), c = static_cast<int>(e / m);
+    double v = 0.0;
+    if (Z) v = alpha * Z[r + c * ldz];
+    if (Wm) v += beta * Wm[r + c * ldw];
+    for (int s = 0; s < nsplit; ++s) v -= P[(static_cast<long long>(s) * nrhs + c) * m + r];
+    Y[r + c * ldy] = v;
+  }
+}
+
+// G(j, c) = alpha * sum_r A(r, j) R(r, c): one warp per column j.
+__global__ void __launch_bounds__(kLsThreads) gemm_tn(const double* __restrict__ A, long long lda, int m, int n,
+                                                      const double* __restrict__ R, long long ldr, int nrhs,
+                                                      double alpha, double* __restrict__ G, long long ldg) {
+  const int lane = threadIdx.x & 31;
+  const int j = blockIdx.x * (kLsThreads / 32) + (threadIdx.x >> 5);
+  if (j >= n) return;
+  const double* a = A + static_cast<long long>(j) * lda;
+  for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
+    const int cw = min(kRhsChunk, nrhs - c0);
+    double acc[kRhsChunk];
+#pragma unroll
+    for (int c = 0; c < kRhsChunk; ++c) acc[c] = 0.0;
+    for (int r = lane; r < m; r += 32) {
+      const double av = a[r];
+#pragma unroll
+      for (int c = 0; c < kRhsChunk; ++c)
+        if (c < cw) acc[c] = fma(av, R[r + static_cast<long long>(c0 + c) * ldr], acc[c]);
+    }
+#pragma unroll
+    for (int c = 0; c < kRhsChunk; ++c) {
+      double v = acc[c];
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+      if (lane == 0 && c < cw) G[j + static_cast<long long>(c0 + c) * ldg] = alpha * v;
+    }
+  }
+}
+
+// Per-column sums of squares of an m x ncols column-major matrix into
+// out[c] (deterministic: one block per column, fixed reduction tree).
+__global__ void __launch_bounds__(kLsThreads) col_sumsq(const double* __restrict__ X, long long ldx, int m,
+                                                        double* __restrict__ out) {
+  __shared__ double red[kLsThreads / 32];
+  const int c = blockIdx.x;
+  double s = 0.0;
+  for (int r = threadIdx.x; r < m; r += kLsThreads) {
+    const double v = X[r + static_cast<long long>(c) * ldx];
+    s = fma(v, v, s);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kLsThreads / 32; ++w) t += red[w];
+    out[c] = t;
+  }
+}
+
+// min and max |R(i, i)| over i < n of the tiled factor (diagonal tiles).
+template <typename real>
+__global__ void diag_minmax(const real* __restrict__ Ab, int p, int nb, int n, double* __restrict__ out) {
+  __shared__ double smin[kLsThreads], smax[kLsThreads];
+  double mn = INFINITY, mx = 0.0;
+  for (int i = threadIdx.x; i < n; i += kLsThreads) {
+    const int t = i / nb, r = i - t * nb;
+    const double v = fabs(static_cast<double>(
+        Ab[(static_cast<long long>(t) + static_cast<long long>(t) * p) * nb * nb + static_cast<long long>(r) * nb + r]));
+    mn = fmin(mn, v);
+    mx = fmax(mx, v);
+  }
+  smin[threadIdx.x] = mn;
+  smax[threadIdx.x] = mx;
+  __syncthreads();
+  for (int s = kLsThreads / 2; s > 0; s >>= 1) {
+    if (threadIdx.x < s) {
+      smin[threadIdx.x] = fmin(smin[threadIdx.x], smin[threadIdx.x + s]);
+      smax[threadIdx.x] = fmax(smax[threadIdx.x], smax[threadIdx.x + s]);
+    }
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) {
+    out[0] = smin[0];
+    out[1] = smax[0];
+  }
+}
+
+// Y(0:rows, :) = alpha X1 + beta X2 (column-major, any of X1/X2 null = 0).
+// (Y may alias X1 or X2: every element is read and written by one thread.)
+__global__ void axpby(int rows, int cols, double alpha, const double* X1, long long ld1, double beta,
+                      const double* X2, long long ld2, double* Y, long long ldy) {
+  const long long total = static_cast<long long>(rows) * cols;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int r = static_cast<int>(e % rows), c = static_cast<int>(e / rows);
+    double v = 0.0;
+    if (X1) v = alpha * X1[r + c * ld1];
+    if (X2) v += beta * X2[r + c * ld2];
+    Y[r + c * ldy] = v;
+  }
+}
+
+static int ew_grid(long long total) {
+  const int sms = device_sms();
+  long long g = (total + 255) / 256;
+  return static_cast<int>(std::max<long long>(1, std::min<long long>(g, static_cast<long long>(sms) * 8)));
+}
+
+// FP64 helpers on the stream -------------------------------------------------
+struct LsScratch {
+  double* part;    // nsplit * m * nrhs
+  int nsplit;
+  int split_len;
+};
+
+static LsScratch ls_scratch_shape(int m, int n, int nrhs) {
+  const int sms = device_sms();
+  const int row_blocks = (m + kLsThreads - 1) / kLsThreads;
+  int nsplit = std::max(1, std::min(n, (4 * sms + row_blocks - 1) / row_blocks));
+  nsplit = std::min(nsplit, 64);
+  LsScratch s;
+  s.part = nullptr;
+  s.nsplit = nsplit;
+  s.split_len = (n + nsplit - 1) / nsplit;
+  s.nsplit = (n + s.split_len - 1) / s.split_len;
+  (void)nrhs;
+  return s;
+}
+
+// Y = alpha Z + beta W - A X
+static cudaError_t resid(const LsScratch& sc, const double* A, long long lda, int m, int n, const double* X,
+                         long long ldx, int nrhs, const double* Z, long long ldz, double alpha, const double* Wm,
+                         long long ldw, double beta, double* Y, long long ldy, cudaStream_t st) {
+  dim3 grid((m + kLsThreads - 1) / kLsThreads, sc.nsplit);
+  gemm_nn_partial<<<grid, kLsThreads, 0, st>>>(A, lda, m, n, X, ldx, nrhs, sc.split_len, sc.part);
+  combine_partials<<<ew_grid(static_cast<long long>(m) * nrhs), 256, 0, st>>>(sc.part, sc.nsplit, m, nrhs, Z, ldz,
+                                                                            alpha, Wm, ldw, beta, Y, ldy);
+  return cudaGetLastError();
+}
+
+static cudaError_t atr(const double* A, long long lda, int m, int n, const double* R, long long ldr, int nrhs,
+                       double alpha, double* G, long long ldg, cudaStream_t st) {
+  const int wpb = kLsThreads / 32;
+  gemm_tn<<<(n + wpb - 1) / wpb, kLsThreads, 0, st>>>(A, lda, m, n, R, ldr, nrhs, alpha, G, ldg);
+  return cudaGetLastError();
+}
+
+// Backward error of (x, b): needs e = b - A x already in E.  Writes the
+// per-column norms squared of A^T e, x, b and ||A||_F^2 into nrm.
+struct BerrBufs {
+  double* G;     // n x nrhs
+  double* nrm;   // 3 * nrhs
+};
+
+static cudaError_t berr_terms(const double* A, long long lda, int m, int n, const double* E, const double* Xv,
+                              long long ldx, const double* Bv, long long ldb, int nrhs, const BerrBufs& bb,
+                              cudaStream_t st) {
+  cudaError_t e = atr(A, lda, m, n, E, m, nrhs, 1.0, bb.G, n, st);
+  if (e != cudaSuccess) return e;
+  col_sumsq<<<nrhs, kLsThreads, 0, st>>>(bb.G, n, n, bb.nrm);
+  col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Xv, ldx, n, bb.nrm + nrhs);
+  col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Bv, ldb, m, bb.nrm + 2 * nrhs);
+  return cudaGetLastError();
+}
+
+static double berr_host(const std::vector<double>& h, int nrhs, double nA2) {
+  const double nA = std::sqrt(nA2);
+  double worst = 0.0;
+  for (int c = 0; c < nrhs; ++c) {
+    const double num = std::sqrt(h[c]);
+    const double den = nA * (nA * std::sqrt(h[nrhs + c]) + std::sqrt(h[2 * nrhs + c]));
+    const double eta = den > 0 ? num / den : (num > 0 ? INFINITY : 0.0);
+    if (!(eta <= worst)) worst = eta;  // NaN-propagating max
+  }
+  return worst;
+}
+
+static size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// ---------------------------------------------------------------------------
+static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* A, int64_t lda, const double* B,
+                        int64_t ldb, double* X, int64_t ldx, int prec, double tol, int maxit, int* iters_out,
+                        double* berr_out, int nb, int ib, cudaStream_t st) {
+  const int m = static_cast<int>(m64), n = static_cast<int>(n64), nrhs = static_cast<int>(nrhs64);
+  const int esize = prec == TQR_PREC_FP64 ? 8 : 4;
+  int cs, occ, smem;
+  if (!choose_shape(nb, ib, esize, &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
+  Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, nrhs, 1);
+  const WsLayout W = ws_layout(I, esize, true);
+  LsScratch sc = ls_scratch_shape(m, n, nrhs);
+  const size_t mr = static_cast<size_t>(m) * nrhs, nr = static_cast<size_t>(n) * nrhs;
+  // FP64 vectors
+  size_t o = al(W.bytes);
+  const size_t o_part = o;  o += al(sizeof(double) * sc.nsplit * mr);
+  const size_t o_e = o;     o += al(sizeof(double) * mr);
+  const size_t o_r = o;     o += al(sizeof(double) * mr);
+  const size_t o_f = o;     o += al(sizeof(double) * mr);
+  const size_t o_d = o;     o += al(sizeof(double) * mr);
+  const size_t o_g = o;     o += al(sizeof(double) * nr);
+  const size_t o_h = o;     o += al(sizeof(double) * nr);
+  const size_t o_x = o;     o += al(sizeof(double) * nr);
+  const size_t o_G = o;     o += al(sizeof(double) * nr);
+  const size_t o_nrm = o;   o += al(sizeof(double) * (3 * nrhs + 4));
+  const size_t total = o;
+  char* ws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), total, st) != cudaSuccess) {
+    cudaGetLastError();
+    return TQR_ERR_NOMEM;
+  }
+  sc.part = reinterpret_cast<double*>(ws + o_part);
+  double* E = reinterpret_cast<double*>(ws + o_e);
+  double* Rr = reinterpret_cast<double*>(ws + o_r);
+  double* F = reinterpret_cast<double*>(ws + o_f);
+  double* D = reinterpret_cast<double*>(ws + o_d);
+  double* Gv = reinterpret_cast<double*>(ws + o_g);
+  double* H = reinterpret_cast<double*>(ws + o_h);
+  double* Xw = reinterpret_cast<double*>(ws + o_x);
+  BerrBufs bb;
+  bb.G = reinterpret_cast<double*>(ws + o_G);
+  bb.nrm = reinterpret_cast<double*>(ws + o_nrm);
+  double* nA2 = bb.nrm + 3 * nrhs;       // ||A||_F^2
+  double* dmm = bb.nrm + 3 * nrhs + 2;   // min, max |r_ii|
+  I.A = ws + W.oA;
+  I.B = ws + W.oB;
+  I.T = ws + W.oT;
+  I.ver = reinterpret_cast<int*>(ws + W.oVer);
+  const int sms = device_sms();
+  int status = TQR_OK;
+  int iters = 0;
+  double berr = INFINITY;
+  std::vector<double> hn(3 * nrhs + 4);
+  auto fail = [&](int s) {
+    if (status == TQR_OK) status = s;
+  };
+  auto pack_rhs = [&](const double* src, long long lds, int rows) {
+    cudaError_t e = esize == 8 ? launch_pack<double>(src, lds, rows, nrhs, static_cast<double*>(I.B), I.p, I.qb, nb,
+                                                      sms, st)
+                               : launch_pack<float>(src, lds, rows, nrhs, static_cast<float*>(I.B), I.p, I.qb, nb, sms,
+                                                    st);
+    if (e != cudaSuccess) fail(TQR_ERR_CUDA);
+  };
+  auto unpack_rhs = [&](double* dst, long long ldd, int rows) {
+    cudaError_t e = esize == 8 ? launch_unpack<double>(static_cast<double*>(I.B), I.p, nb, dst, ldd, rows, nrhs, sms, st)
+                               : launch_unpack<float>(static_cast<float*>(I.B), I.p, nb, dst, ldd, rows, nrhs, sms, st);
+    if (e != cudaSuccess) fail(TQR_ERR_CUDA);
+  };
+  auto run = [&](int mode, int trsm) {
+    if (status != TQR_OK) return;
+    I.mode = mode;
+    I.trsm = trsm;
+    const int s = esize == 8 ? run_plan<double>(I, ws, W, occ, smem, st) : run_plan<float>(I, ws, W, occ, smem, st);
+    fail(s);
+  };
+  auto read_back = [&]() {
+    if (cudaMemcpyAsync(hn.data(), bb.nrm, sizeof(double) * hn.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      fail(TQR_ERR_CUDA);
+  };
+  // factor + Q^T B + back substitution, one graph
+  {
+    cudaError_t e = esize == 8 ? launch_pack<double>(A, lda, m, n, static_cast<double*>(I.A), I.p, I.q, nb, sms, st)
+                               : launch_pack<float>(A, lda, m, n, static_cast<float*>(I.A), I.p, I.q, nb, sms, st);
+    if (e != cudaSuccess) fail(TQR_ERR_CUDA);
+  }
+  pack_rhs(B, ldb, m);
+  run(M_FACTOR, 1);
+  unpack_rhs(Xw, n, n);
+  if (status == TQR_OK) {
+    if (esize == 8)
+      diag_minmax<double><<<1, kLsThreads, 0, st>>>(static_cast<double*>(I.A), I.p, nb, n, dmm);
+    else
+      diag_minmax<float><<<1, kLsThreads, 0, st>>>(static_cast<float*>(I.A), I.p, nb, n, dmm);
+  }
+  // ||A||_F^2 as the sum of column sums of squares (A may have lda > m)
+  if (status == TQR_OK) {
+    double* colsq = Gv;  // n entries (nrhs >= 1 so Gv holds at least n)
+    col_sumsq<<<n, kLsThreads, 0, st>>>(A, lda, m, colsq);
+    col_sumsq<<<1, kLsThreads, 0, st>>>(colsq, n, n, nA2);
+    if (cudaGetLastError() != cudaSuccess) fail(TQR_ERR_CUDA);
+  }
+  if (status == TQR_OK) {
+    // e = b - A x, backward-error terms
+    if (resid(sc, A, lda, m, n, Xw, n, nrhs, B, ldb, 1.0, nullptr, 0, 0.0, E, m, st) != cudaSuccess ||
+        berr_terms(A, lda, m, n, E, Xw, n, B, ldb, nrhs, bb, st) != cudaSuccess)
+      fail(TQR_ERR_CUDA);
+    read_back();
+  }
+  if (status == TQR_OK) {
+    const double eps = esize == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+    if (!(hn[3 * nrhs + 2] > n * eps * hn[3 * nrhs + 3])) status = TQR_ERR_RANK;
+    berr = berr_host(hn, nrhs, hn[3 * nrhs]);
+  }
+  if (status == TQR_OK && esize == 4) {
+    // augmented-system refinement; r starts as the residual of x0
+    if (cudaMemcpyAsync(Rr, E, sizeof(double) * mr, cudaMemcpyDeviceToDevice, st) != cudaSuccess) fail(TQR_ERR_CUDA);
+    double prev = berr;
+    int stall = 0;
+    while (status == TQR_OK && berr > tol && iters < maxit) {
+      // f = b - r - A x = e - r;  g = -A^T r
+      axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, E, m, -1.0, Rr, m, F, m);
+      if (atr(A, lda, m, n, Rr, m, nrhs, -1.0, Gv, n, st) != cudaSuccess) fail(TQR_ERR_CUDA);
+      // h = R^-T g
+      pack_rhs(Gv, n, n);
+      run(M_TRSMT, 0);
+      unpack_rhs(H, n, n);
+      // d = Q^T f
+      pack_rhs(F, m, m);
+      run(M_APPLY_QT, 0);
+      unpack_rhs(D, m, m);
+      // dx = R^-1 (d1 - h)
+      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, D, m, -1.0, H, n, Gv, n);
+      pack_rhs(Gv, n, n);
+      run(M_TRSM, 0);
+      unpack_rhs(Gv, n, n);
+      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0, Gv, n, Xw, n);
+      // dr = Q [h; d2]
+      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, H, n, 0.0, nullptr, 0, D, m);
+      pack_rhs(D, m, m);
+      run(M_APPLY_Q, 0);
+      unpack_rhs(D, m, m);
+      axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, Rr, m, 1.0, D, m, Rr, m);
+      ++iters;
+      if (resid(sc, A, lda, m, n, Xw, n, nrhs, B, ldb, 1.0, nullptr, 0, 0.0, E, m, st) != cudaSuccess ||
+          berr_terms(A, lda, m, n, E, Xw, n, B, ldb, nrhs, bb, st) != cudaSuccess)
+        fail(TQR_ERR_CUDA);
+      read_back();
+      if (status != TQR_OK) break;
+      berr = berr_host(hn, nrhs, hn[3 * nrhs]);
+      if (!(berr < 0.5 * prev)) {
+        if (++stall >= 3) break;
+      } else {
+        stall = 0;
+      }
+      prev = std::min(prev, berr);
+    }
+    if (status == TQR_OK && !(berr <= tol)) status = TQR_ERR_NOCONV;
+  }
+  // X = x (also on NOCONV / RANK: the best available solution)
+  if (cudaMemcpy2DAsync(X, sizeof(double) * ldx, Xw, sizeof(double) * n, sizeof(double) * n, nrhs,
+                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    fail(TQR_ERR_CUDA);
+  cudaFreeAsync(ws, st);
+  int dev_status = TQR_OK;
+  if (read_status(&dev_status, st) != cudaSuccess) fail(TQR_ERR_CUDA);
+  if (dev_status != TQR_OK) status = dev_status;
+  if (iters_out) *iters_out = iters;
+  if (berr_out) *berr_out = berr;
+  return status;
+}
+
+}  // namespace tqr
+
+using namespace tqr;
+
+extern "C" int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, const double* B,
+                            int64_t ldb, double* X, int64_t ldx, int prec, double tol, int maxit, int* iters,
+                            double* berr, int nb, int ib, void* stream) {
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (nrhs < 1) return -3;
+  if (m > (1LL << 30) || nrhs > (1LL << 20)) return TQR_ERR_UNSUPPORTED;
+  if (A == nullptr) return -4;
+  if (lda < m) return -5;
+  if (B == nullptr) return -6;
+  if (ldb < m) return -7;
+  if (X == nullptr) return -8;
+  if (ldx < n) return -9;
+  if (prec != TQR_PREC_FP64 && prec != TQR_PREC_FP32) return -10;
+  if (!(tol >= 0)) return -11;
+  if (maxit < 0) return -12;
+  if (nb == 0) nb = n >= 1024 ? 128 : 64;
+  if (ib == 0) ib = std::min(32, nb);
+  const int c = check_tiles(nb, ib, 15, 16);
+  if (c) return c;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ka = ptr_kind(A);
+  if (ptr_kind(B) != ka) return -6;
+  if (ptr_kind(X) != ka) return -8;
+  if (ka == PTR_DEVICE)
+    return solve_device(m, n, nrhs, A, lda, B, ldb, X, ldx, prec, tol, maxit, iters, berr, nb, ib, st);
+  double *dA = nullptr, *dB = nullptr, *dX = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dX), sizeof(double) * n * nrhs, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (dA) cudaFreeAsync(dA, st);
+    if (dB) cudaFreeAsync(dB, st);
+    return TQR_ERR_NOMEM;
+  }
+  int status = TQR_OK;
+  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  if (status == TQR_OK) status = solve_device(m, n, nrhs, dA, m, dB, m, dX, n, prec, tol, maxit, iters, berr, nb, ib, st);
+  if ((status == TQR_OK || status == TQR_ERR_NOCONV || status == TQR_ERR_RANK) &&
+      cudaMemcpy2DAsync(X, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n, nrhs,
+                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  cudaFreeAsync(dA, st);
+  cudaFreeAsync(dB, st);
+  cudaFreeAsync(dX, st);
+  if (cudaStreamSynchronize(st) != cudaSuccess) return TQR_ERR_CUDA;
+  return status;
+}

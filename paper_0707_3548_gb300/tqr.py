@@ -1,0 +1,277 @@
+"""Thin ctypes binding of libtqr (include/tqr.h, include/tqr_debug.h).
+
+Argument marshalling only: every step of the computation runs in the CUDA
+library.  Functions keep the C names.  Matrix arguments may be
+
+* torch tensors on a CUDA device (the call is asynchronous on the current
+  torch stream),
+* torch CPU tensors or NumPy arrays (the library stages them through the GPU
+  and synchronizes),
+
+and must be float64 and column-major (``x.stride(0) == 1``; the leading
+dimension is taken from ``x.stride(1)``).  ``colmajor(x)`` makes such a copy.
+
+The library is loaded on first use; if it is missing the call raises
+RuntimeError (there is no fallback).
+"""
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libtqr.so")
+
+TQR_OK = 0
+TQR_ERR_CUDA = 1
+TQR_ERR_NOMEM = 2
+TQR_ERR_TIMEOUT = 3
+TQR_ERR_RANK = 4
+TQR_ERR_NOCONV = 5
+TQR_ERR_BUSY = 6
+TQR_ERR_UNSUPPORTED = 7
+TQR_PREC_FP64 = 0
+TQR_PREC_FP32 = 1
+
+_ERRNAMES = {1: "TQR_ERR_CUDA", 2: "TQR_ERR_NOMEM", 3: "TQR_ERR_TIMEOUT", 4: "TQR_ERR_RANK",
+             5: "TQR_ERR_NOCONV", 6: "TQR_ERR_BUSY", 7: "TQR_ERR_UNSUPPORTED"}
+
+_lib = None
+
+_i64 = ctypes.c_int64
+_int = ctypes.c_int
+_vp = ctypes.c_void_p
+_dbl = ctypes.c_double
+_size = ctypes.c_size_t
+
+# name -> (restype, argtypes); every declaration of include/*.h
+SIGNATURES = {
+    "tqr_version": (ctypes.c_char_p, []),
+    "tqr_t_size": (_size, [_i64, _i64, _int, _int]),
+    "tqr_work_size": (_size, [_i64, _i64, _int, _int]),
+    "tqr_factor": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp]),
+    "tqr_factor_ws": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _size, _vp]),
+    "tqr_apply_qt": (_int, [ctypes.c_char, _i64, _i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _i64, _vp]),
+    "tqr_solve_ls": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int,
+                            ctypes.POINTER(_int), ctypes.POINTER(_dbl), _int, _int, _vp]),
+    "tqr_stream_status": (_int, [_vp]),
+    "tqr_set_wait_limit_ms": (_i64, [_i64]),
+    "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
+    "tqr_debug_rules": (_int, [_int, _i64, _i64, _int, _int, _int, _int, _vp, _vp, _vp]),
+    "tqr_debug_set_schedule": (_int, [_int, _int]),
+    "tqr_debug_stalled_launch": (_int, [_i64, _vp]),
+    "tqr_debug_timing": (_int, [_int]),
+    "tqr_debug_timing_read": (_int, [ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
+    "tqr_debug_fp64_peak": (_int, [ctypes.POINTER(_dbl), _vp]),
+    "tqr_debug_last_error": (ctypes.c_char_p, []),
+}
+
+
+class TqrError(RuntimeError):
+    def __init__(self, fn, code):
+        self.code = code
+        name = _ERRNAMES.get(code, "invalid argument %d" % -code if code < 0 else str(code))
+        super().__init__("%s failed: %s (%d)" % (fn, name, code))
+
+
+def lib():
+    """The loaded libtqr (ctypes.CDLL); raises if it has not been built."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("libtqr.so is not built (run paper_0707_3548_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        for name, (res, args) in SIGNATURES.items():
+            f = getattr(L, name)
+            f.restype = res
+            f.argtypes = args
+        _lib = L
+    return _lib
+
+
+# ------------------------------------------------------------------ marshalling
+def _torch():
+    import torch
+    return torch
+
+
+def colmajor(x):
+    """Column-major float64 copy of a 2-D torch tensor or array (same device)."""
+    if isinstance(x, np.ndarray):
+        return np.asfortranarray(x, dtype=np.float64)
+    torch = _torch()
+    x = x.to(torch.float64)
+    if x.dim() == 1:
+        x = x[:, None]
+    return x.t().contiguous().t()
+
+
+def _mat(x, name):
+    """(pointer, rows, cols, ld, is_cuda) of a column-major float64 matrix."""
+    if isinstance(x, np.ndarray):
+        if x.dtype != np.float64:
+            raise TypeError("%s must be float64" % name)
+        if x.ndim == 1:
+            return x.ctypes.data, x.shape[0], 1, max(1, x.shape[0]), False
+        if not x.flags.f_contiguous and x.shape[1] > 1:
+            raise ValueError("%s must be column-major (np.asfortranarray)" % name)
+        return x.ctypes.data, x.shape[0], x.shape[1], max(1, x.shape[0]), False
+    torch = _torch()
+    if x.dtype != torch.float64:
+        raise TypeError("%s must be float64" % name)
+    if x.dim() == 1:
+        return x.data_ptr(), x.shape[0], 1, max(1, x.shape[0]), x.is_cuda
+    if x.shape[0] > 1 and x.stride(0) != 1:
+        raise ValueError("%s must be column-major (use tqr.colmajor)" % name)
+    ld = x.stride(1) if x.shape[1] > 1 else max(1, x.shape[0])
+    return x.data_ptr(), x.shape[0], x.shape[1], ld, x.is_cuda
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if isinstance(x, np.ndarray):
+        return x.ctypes.data
+    return x.data_ptr()
+
+
+def _stream(is_cuda, stream=None):
+    if stream is not None:
+        return stream
+    if not is_cuda:
+        return None
+    return _torch().cuda.current_stream().cuda_stream
+
+
+def _check(fn, code):
+    if code != TQR_OK:
+        raise TqrError(fn, code)
+    return code
+
+
+# ------------------------------------------------------------------ API
+def tqr_version():
+    return lib().tqr_version().decode()
+
+
+def tqr_t_size(m, n, nb, ib):
+    return lib().tqr_t_size(m, n, nb, ib)
+
+
+def tqr_work_size(m, n, nb, ib):
+    return lib().tqr_work_size(m, n, nb, ib)
+
+
+def new_t(m, n, nb, ib, like):
+    """A T buffer (float64, flat) for tqr_factor on the device/host of `like`."""
+    cnt = tqr_t_size(m, n, nb, ib) // 8
+    if isinstance(like, np.ndarray):
+        return np.zeros(cnt)
+    return _torch().zeros(cnt, dtype=_torch().float64, device=like.device)
+
+
+def tqr_factor(A, nb, ib, T=None, stream=None, check=True):
+    """Factors column-major A in place; returns T (allocated if not given)."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    if T is None:
+        T = new_t(m, n, nb, ib, A)
+    rc = lib().tqr_factor(m, n, pa, lda, nb, ib, _ptr(T), _stream(cuda, stream))
+    if check:
+        _check("tqr_factor", rc)
+    return T if check else (T, rc)
+
+
+def tqr_factor_ws(A, nb, ib, T, work, stream=None):
+    pa, m, n, lda, cuda = _mat(A, "A")
+    nbytes = work.numel() * work.element_size()
+    _check("tqr_factor_ws", lib().tqr_factor_ws(m, n, pa, lda, nb, ib, _ptr(T), _ptr(work), nbytes,
+                                                 _stream(cuda, stream)))
+    return T
+
+
+def tqr_apply_qt(trans, A, nb, ib, T, B, stream=None):
+    """B <- Q^T B ('T') or Q B ('N') in place, from tqr_factor's A and T."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    pb, mb, nrhs, ldb, _ = _mat(B, "B")
+    if mb != m:
+        raise ValueError("B must have m rows")
+    _check("tqr_apply_qt", lib().tqr_apply_qt(trans.encode() if isinstance(trans, str) else trans, m, n, nrhs,
+                                               pa, lda, nb, ib, _ptr(T), pb, ldb, _stream(cuda, stream)))
+    return B
+
+
+def tqr_solve_ls(A, B, X=None, prec=TQR_PREC_FP64, tol=1e-12, maxit=30, nb=0, ib=0, stream=None, check=True):
+    """Least squares min ||A x - b|| per column of B; returns (X, iters, berr, status)."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    pb, mb, nrhs, ldb, _ = _mat(B, "B")
+    if X is None:
+        if isinstance(A, np.ndarray):
+            X = np.zeros((n, nrhs), order="F")
+        else:
+            X = colmajor(_torch().zeros((n, nrhs), dtype=_torch().float64, device=A.device))
+    px, _, _, ldx, _ = _mat(X, "X")
+    iters = _int(0)
+    berr = _dbl(0.0)
+    rc = lib().tqr_solve_ls(m, n, nrhs, pa, lda, pb, ldb, px, ldx, prec, tol, maxit, ctypes.byref(iters),
+                            ctypes.byref(berr), nb, ib, _stream(cuda, stream))
+    if check and rc not in (TQR_OK,):
+        raise TqrError("tqr_solve_ls", rc)
+    return X, iters.value, berr.value, rc
+
+
+def tqr_stream_status(stream=None):
+    return lib().tqr_stream_status(_stream(True, stream))
+
+
+def tqr_set_wait_limit_ms(ms):
+    return lib().tqr_set_wait_limit_ms(ms)
+
+
+# ------------------------------------------------------------------ host-only introspection
+def tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs=0, trsm=0, workers=8, policy=-1):
+    """(tasks int32[N, 8], stats float64[6]) of the ordered plan of one launch."""
+    L = lib()
+    cnt = L.tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs, trsm, workers, policy, None, 0, None)
+    if cnt < 0:
+        raise RuntimeError("tqr_debug_plan: %d %s" % (cnt, L.tqr_debug_last_error().decode()))
+    out = np.zeros((cnt, 8), dtype=np.int32)
+    stats = np.zeros(6)
+    L.tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs, trsm, workers, policy, out.ctypes.data, cnt,
+                     stats.ctypes.data)
+    return out, stats
+
+
+def tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, task):
+    """(waits [(ctr, cnt, ver)], signals [(ctr, cnt)]) of one task."""
+    t = np.asarray(list(task) + [0] * (8 - len(task)), dtype=np.int32)
+    w = np.zeros(12, dtype=np.int32)
+    s = np.zeros(4, dtype=np.int32)
+    r = lib().tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, t.ctypes.data, w.ctypes.data, s.ctypes.data)
+    nw, ns = r % 16, r // 16
+    return [tuple(w[3 * a:3 * a + 3]) for a in range(nw)], [tuple(s[2 * a:2 * a + 2]) for a in range(ns)]
+
+
+def tqr_debug_set_schedule(policy=-1, max_ctas=0):
+    return lib().tqr_debug_set_schedule(policy, max_ctas)
+
+
+def tqr_debug_stalled_launch(limit_ms, stream=None):
+    return lib().tqr_debug_stalled_launch(limit_ms, _stream(True, stream))
+
+
+def tqr_debug_timing(enable):
+    return lib().tqr_debug_timing(1 if enable else 0)
+
+
+def tqr_debug_timing_read():
+    """(milliseconds, launches) of the persistent kernel since the last read."""
+    ms = _dbl(0)
+    n = _i64(0)
+    _check("tqr_debug_timing_read", lib().tqr_debug_timing_read(ctypes.byref(ms), ctypes.byref(n)))
+    return ms.value, n.value
+
+
+def tqr_debug_fp64_peak(stream=None):
+    t = _dbl(0)
+    _check("tqr_debug_fp64_peak", lib().tqr_debug_fp64_peak(ctypes.byref(t), _stream(True, stream)))
+    return t.value

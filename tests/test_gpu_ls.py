@@ -1,0 +1,53 @@
+"""GPU least squares (tqr_solve_ls) against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import lstsq as LS
+from paper_0707_3548_gb300 import inputs, tqr
+from tests.gpu_util import to_dev, to_host, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("m,n,nrhs,nb,ib", [(700, 300, 1, 128, 32), (500, 500, 3, 64, 16), (1000, 130, 17, 64, 32)])
+def test_solve_fp64_matches_oracle(m, n, nrhs, nb, ib):
+    torch_cuda()
+    A = inputs.normal_matrix(m, n, 31)
+    B = inputs.normal_matrix(m, nrhs, 32)
+    X, it, berr, rc = tqr.tqr_solve_ls(to_dev(A), to_dev(B), nb=nb, ib=ib)
+    assert rc == tqr.TQR_OK and it == 0
+    Xo = LS.lstsq(A, B)
+    assert np.max(np.abs(to_host(X) - Xo)) <= 1e-10 * max(1.0, np.abs(Xo).max())
+    assert berr <= 1e-14
+    assert abs(berr - LS.backward_error(A, to_host(X), B)) <= 1e-15 + 0.05 * berr
+
+
+@pytest.mark.parametrize("kappa", [1e2, 1e5])
+def test_solve_fp32_refined_reaches_fp64_accuracy(kappa):
+    torch_cuda()
+    A, b, _ = inputs.conditioned_ls_problem(2000, 500, kappa, seed=1)
+    X, it, berr, rc = tqr.tqr_solve_ls(to_dev(A), to_dev(b[:, None]), prec=tqr.TQR_PREC_FP32, tol=1e-12,
+                                       maxit=30, nb=64, ib=16)
+    assert rc == tqr.TQR_OK, (rc, it, berr)
+    assert berr <= 1e-12 and it >= 1
+    xo = LS.lstsq(A, b)
+    assert np.linalg.norm(to_host(X)[:, 0] - xo) / np.linalg.norm(xo) <= 1e-13 * kappa
+    assert LS.backward_error(A, to_host(X)[:, 0], b) <= 1e-12
+
+
+def test_solve_host_buffers():
+    torch_cuda()
+    A = inputs.normal_matrix(300, 100, 3)
+    B = inputs.normal_matrix(300, 2, 4)
+    X, it, berr, rc = tqr.tqr_solve_ls(A, B, nb=64, ib=16)
+    assert rc == 0
+    assert np.allclose(X, LS.lstsq(A, B), atol=1e-11)
+
+
+def test_rank_deficient_reports_rank():
+    torch_cuda()
+    A = inputs.normal_matrix(200, 50, 5)
+    A[:, 10] = A[:, 3]
+    B = inputs.normal_matrix(200, 1, 6)
+    X, it, berr, rc = tqr.tqr_solve_ls(to_dev(A), to_dev(B), nb=32, ib=8, check=False)
+    assert rc == tqr.TQR_ERR_RANK
