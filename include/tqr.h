@@ -129,7 +129,8 @@ int tqr_apply_qt(char trans, int64_t m, int64_t n, int64_t nrhs,
  *                           factorization in FP32 (norms and tau in FP64),
  *                           then iterative refinement of the augmented
  *                           system with FP64 residuals until the backward
- *                           error is <= tol
+ *                           error is <= tol and the last correction changes
+ *                           x by at most 2^-50 ||x|| (FP64 accuracy)
  *   tol        (arg 11)     backward-error target for refinement (e.g. 1e-12)
  *   maxit      (arg 12)     refinement iteration limit
  *   iters      (arg 13)     out (may be NULL): refinement steps taken
@@ -139,7 +140,9 @@ int tqr_apply_qt(char trans, int64_t m, int64_t n, int64_t nrhs,
  *   stream     (arg 17)
  * Synchronizes the stream (the refinement loop needs the backward error on
  * the host).  Returns TQR_ERR_RANK for a numerically rank-deficient R and
- * TQR_ERR_NOCONV when refinement stalls above tol.
+ * TQR_ERR_NOCONV when refinement stalls (neither the backward error nor the
+ * correction halves in 3 steps) or reaches maxit with the backward error
+ * above tol; X then holds the best iterate.
  */
 int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda,
                  const double* B, int64_t ldb, double* X, int64_t ldx, int prec,

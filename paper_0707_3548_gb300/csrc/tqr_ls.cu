@@ -275,7 +275,7 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
   const size_t o_h = o;     o += al(sizeof(double) * nr);
   const size_t o_x = o;     o += al(sizeof(double) * nr);
   const size_t o_G = o;     o += al(sizeof(double) * nr);
-  const size_t o_nrm = o;   o += al(sizeof(double) * (3 * nrhs + 4));
+  const size_t o_nrm = o;   o += al(sizeof(double) * (4 * nrhs + 4));
   const size_t total = o;
   char* ws = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&ws), total, st) != cudaSuccess) {
@@ -303,7 +303,8 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
   int status = TQR_OK;
   int iters = 0;
   double berr = INFINITY;
-  std::vector<double> hn(3 * nrhs + 4);
+  std::vector<double> hn(4 * nrhs + 4);
+  double* dx2 = bb.nrm + 3 * nrhs + 4;   // ||dx_c||^2 of the last correction
   auto fail = [&](int s) {
     if (status == TQR_OK) status = s;
   };
@@ -368,9 +369,13 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
   if (status == TQR_OK && esize == 4) {
     // augmented-system refinement; r starts as the residual of x0
     if (cudaMemcpyAsync(Rr, E, sizeof(double) * mr, cudaMemcpyDeviceToDevice, st) != cudaSuccess) fail(TQR_ERR_CUDA);
-    double prev = berr;
+    // Refine until the backward error meets tol AND the last correction no
+    // longer moves x beyond FP64 rounding (||dx|| <= 2^-50 ||x||), so the
+    // answer matches an FP64 solve; stop early on stagnation (neither the
+    // backward error nor the correction halves for 3 steps) or at maxit.
+    double prev = berr, prev_dx = INFINITY, dxrel = INFINITY;
     int stall = 0;
-    while (status == TQR_OK && berr > tol && iters < maxit) {
+    while (status == TQR_OK && (berr > tol || dxrel > 0x1p-50) && iters < maxit) {
       // f = b - r - A x = e - r;  g = -A^T r
       axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, E, m, -1.0, Rr, m, F, m);
       if (atr(A, lda, m, n, Rr, m, nrhs, -1.0, Gv, n, st) != cudaSuccess) fail(TQR_ERR_CUDA);
@@ -387,6 +392,7 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
       pack_rhs(Gv, n, n);
       run(M_TRSM, 0);
       unpack_rhs(Gv, n, n);
+      col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0, Gv, n, Xw, n);
       // dr = Q [h; d2]
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, H, n, 0.0, nullptr, 0, D, m);
@@ -401,12 +407,20 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
       read_back();
       if (status != TQR_OK) break;
       berr = berr_host(hn, nrhs, hn[3 * nrhs]);
-      if (!(berr < 0.5 * prev)) {
+      dxrel = 0.0;
+      for (int c = 0; c < nrhs; ++c) {
+        const double xr = std::sqrt(hn[nrhs + c]);
+        const double d = std::sqrt(hn[3 * nrhs + 4 + c]);
+        const double rel = xr > 0 ? d / xr : d;
+        if (!(rel <= dxrel)) dxrel = rel;
+      }
+      if (!(berr < 0.5 * prev) && !(dxrel < 0.5 * prev_dx)) {
         if (++stall >= 3) break;
       } else {
         stall = 0;
       }
       prev = std::min(prev, berr);
+      prev_dx = std::min(prev_dx, dxrel);
     }
     if (status == TQR_OK && !(berr <= tol)) status = TQR_ERR_NOCONV;
   }

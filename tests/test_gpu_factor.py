@@ -124,7 +124,8 @@ def test_empty_and_tiny():
     T = torch.zeros(1, dtype=torch.float64, device="cuda")
     assert tqr.lib().tqr_factor(0, 5, z.data_ptr(), 1, 8, 4, T.data_ptr(), None) == 0
     F, _ = _factor(np.array([[-3.0]]), 8, 8)
-    assert F[0, 0] == 3.0   # beta = -sign(alpha) |alpha|
+    assert F[0, 0] == -3.0   # nothing below alpha: tau = 0, beta = alpha (as the oracle)
+    assert TL.tiled_qr(np.array([[-3.0]]), 8, 8).F[0, 0] == -3.0
 
 
 def test_exact_zero_column_and_padding():
