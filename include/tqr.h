@@ -49,7 +49,8 @@ enum {
   TQR_ERR_RANK = 4,        /* least squares: |r_ii| <= n * eps * max|r_jj| */
   TQR_ERR_NOCONV = 5,      /* least squares: refinement did not reach tol */
   TQR_ERR_BUSY = 6,        /* batch / server: no free slot right now */
-  TQR_ERR_UNSUPPORTED = 7  /* valid arguments outside what this build supports */
+  TQR_ERR_UNSUPPORTED = 7, /* valid arguments outside what this build supports */
+  TQR_ERR_TOO_LARGE = 8    /* tqr_factor_noalloc: problem exceeds its static scratch */
 };
 
 enum { TQR_PREC_FP64 = 0, TQR_PREC_FP32 = 1 };
@@ -148,6 +149,46 @@ int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t ld
                  const double* B, int64_t ldb, double* X, int64_t ldx, int prec,
                  double tol, int maxit, int* iters, double* berr, int nb, int ib,
                  void* stream);
+
+/*
+ * tqr_factor without any memory allocation.  (The paper has no counterpart:
+ * this is a deployment variant of Algorithm 1.)
+ *
+ * Some callers cannot allocate device memory at the point where they need a
+ * factorization: a process whose device memory has all been handed to another
+ * allocator up front (a framework's caching allocator or a serving process
+ * that reserves HBM at start-up), or latency-critical code that may not risk
+ * an allocation's delay or failure.  This entry point allocates nothing: no
+ * cudaMalloc, cudaMallocAsync, cudaFree or other allocating routine, on the
+ * device or on the host.  Its scratch -- the Block Data Layout tiles, the
+ * dependency counters, the task list and the control words -- lives in one
+ * file-scope static device array of about 31 MiB that every GPU which loads
+ * libtqr holds until the process exits.
+ *
+ * Arguments, result and T layout are those of tqr_factor; A and T must be
+ * device pointers (host buffers would need staging memory; -3 / -7).
+ * Limits: the zero-padded matrix may hold at most TQR_NOALLOC_MAX_TILE_ELEMS
+ * doubles (ceil(m/nb) * ceil(n/nb) * nb^2, e.g. 1536 x 2048 with nb = 128),
+ * at most TQR_NOALLOC_MAX_COUNTERS slab counters and TQR_NOALLOC_MAX_TASKS
+ * tasks; larger problems return TQR_ERR_TOO_LARGE and enqueue nothing.
+ * Tasks run in Algorithm 1's sequential order (no schedule simulation); the
+ * result is bit-identical to tqr_factor's.
+ *
+ * Set-up: the first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress) with that device current; make that first call
+ * before any stream capture.  Every call, on every stream, shares the one
+ * array per device and it keeps the previous call's contents: the call
+ * clears the counters and control words it needs zeroed and overwrites the
+ * tiles.  Calls whose GPU work overlaps (on different streams, or from
+ * different host threads) race on the array and give undefined results;
+ * serialize them, e.g. on one stream.  Asynchronous on `stream`; device-side
+ * wait timeouts are reported by tqr_stream_status().
+ */
+#define TQR_NOALLOC_MAX_TILE_ELEMS (3 * 1024 * 1024)
+#define TQR_NOALLOC_MAX_COUNTERS (1024 * 1024)
+#define TQR_NOALLOC_MAX_TASKS 65536
+int tqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib,
+                       double* T, void* stream);
 
 /*
  * Device status of the asynchronous calls made on `stream`: synchronizes the

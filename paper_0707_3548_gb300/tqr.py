@@ -30,11 +30,12 @@ TQR_ERR_RANK = 4
 TQR_ERR_NOCONV = 5
 TQR_ERR_BUSY = 6
 TQR_ERR_UNSUPPORTED = 7
+TQR_ERR_TOO_LARGE = 8
 TQR_PREC_FP64 = 0
 TQR_PREC_FP32 = 1
 
 _ERRNAMES = {1: "TQR_ERR_CUDA", 2: "TQR_ERR_NOMEM", 3: "TQR_ERR_TIMEOUT", 4: "TQR_ERR_RANK",
-             5: "TQR_ERR_NOCONV", 6: "TQR_ERR_BUSY", 7: "TQR_ERR_UNSUPPORTED"}
+             5: "TQR_ERR_NOCONV", 6: "TQR_ERR_BUSY", 7: "TQR_ERR_UNSUPPORTED", 8: "TQR_ERR_TOO_LARGE"}
 
 _lib = None
 
@@ -54,6 +55,7 @@ SIGNATURES = {
     "tqr_apply_qt": (_int, [ctypes.c_char, _i64, _i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _i64, _vp]),
     "tqr_solve_ls": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int,
                             ctypes.POINTER(_int), ctypes.POINTER(_dbl), _int, _int, _vp]),
+    "tqr_factor_noalloc": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp]),
     "tqr_stream_status": (_int, [_vp]),
     "tqr_set_wait_limit_ms": (_i64, [_i64]),
     "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
@@ -179,6 +181,16 @@ def tqr_factor(A, nb, ib, T=None, stream=None, check=True):
     if check:
         _check("tqr_factor", rc)
     return T if check else (T, rc)
+
+
+def tqr_factor_noalloc(A, nb, ib, T, stream=None, check=True):
+    """tqr_factor with no allocation at all (static device scratch).  A (in
+    place) and T must be CUDA tensors; returns the status code."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    rc = lib().tqr_factor_noalloc(m, n, pa, lda, nb, ib, _ptr(T), _stream(cuda, stream))
+    if check:
+        _check("tqr_factor_noalloc", rc)
+    return rc
 
 
 def tqr_factor_ws(A, nb, ib, T, work, stream=None):
