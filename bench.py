@@ -2,8 +2,9 @@
 """Benchmark of the GB300 tiled Householder QR (libtqr).
 
 Default workload: one 8192 x 8192 FP64 factorization, entries N(0,1) from
-NumPy PCG64 seed 0, tile nb = 128, inner block ib = 32 -- one point of the
-square-size sweep of the plain-FP64 tiled QR.  A step restores the matrix
+NumPy PCG64 seed 0, tile nb = 128, inner block ib = 16 -- one point of the
+square-size sweep of the plain-FP64 tiled QR (the fastest (nb, ib) of the
+nb in {128, 192, 256} x ib in {16, 32, 64} sweep at this size).  A step restores the matrix
 from a pristine device copy and calls tqr_factor (pack to Block Data Layout,
 the persistent task kernel, unpack).  The 512 MiB input is larger than L2.
 
@@ -32,11 +33,17 @@ if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
 WORKLOADS = {
-    "qr8192": dict(m=8192, n=8192, nb=128, ib=32),
-    "qr16384": dict(m=16384, n=16384, nb=128, ib=32),
-    "qr4096": dict(m=4096, n=4096, nb=128, ib=32),
-    "qr2048": dict(m=2048, n=2048, nb=128, ib=32),
-    "ts65536x2048": dict(m=65536, n=2048, nb=128, ib=32),
+    "qr8192": dict(m=8192, n=8192, nb=128, ib=16),
+    "qr16384": dict(m=16384, n=16384, nb=128, ib=16),
+    "qr4096": dict(m=4096, n=4096, nb=128, ib=16),
+    "qr2048": dict(m=2048, n=2048, nb=128, ib=16),
+    "ts65536x2048": dict(m=65536, n=2048, nb=128, ib=16),
+    # least squares A = U diag(sigma) V^T, kappa 1e2 / 1e5 / 1e8: plain FP64
+    # against FP32 factorization + FP64-residual refinement
+    "ls16384x4096k1e2": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e2, ls=True),
+    "ls16384x4096k1e5": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e5, ls=True),
+    "ls16384x4096k1e8": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e8, ls=True),
+    "ls4096x1024k1e2": dict(m=4096, n=1024, nb=128, ib=32, kappa=1e2, ls=True),
 }
 METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs FP64 peak"
 
@@ -276,15 +283,15 @@ def run_ours(args, w):
     hT_t = torch.empty(T.numel(), dtype=torch.float64).pin_memory()
     hT = hT_t.numpy()
     e2e_times = []
-    for it in range(args.warmup + args.steps):
+    for it in range(0 if args.no_e2e else args.warmup + args.steps):
         np.copyto(hA, A)
         t0 = time.perf_counter()
         tqr.tqr_factor(hA, nb, ib, hT)
         t1 = time.perf_counter()
         if it >= args.warmup:
             e2e_times.append(t1 - t0)
-    e2e_s = statistics.mean(e2e_times)
-    if dist is not None:
+    e2e_s = statistics.mean(e2e_times) if e2e_times else float("nan")
+    if dist is not None and e2e_times:
         t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
@@ -335,6 +342,52 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
+def run_ls(args, w):
+    """Least-squares solves/s, plain FP64 vs FP32 + refinement, same problem,
+    same backward-error target (1e-12)."""
+    import numpy as np
+    import torch
+
+    from paper_0707_3548_gb300 import build as B
+    from paper_0707_3548_gb300 import inputs, tqr
+
+    torch.cuda.set_device(0)
+    B.build()
+    m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
+    A, b, x_true = inputs.conditioned_ls_problem(m, n, w["kappa"], seed=0)
+    dA = tqr.colmajor(torch.from_numpy(A).cuda())
+    db = tqr.colmajor(torch.from_numpy(b[:, None]).cuda())
+    out = {}
+    xs = {}
+    for name, prec in (("fp64", tqr.TQR_PREC_FP64), ("fp32_refined", tqr.TQR_PREC_FP32)):
+        times, its, berrs, rcs = [], [], [], []
+        for step in range(args.warmup + args.steps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            X, it, berr, rc = tqr.tqr_solve_ls(dA, db, prec=prec, tol=1e-12, maxit=40, nb=nb, ib=ib, check=False)
+            torch.cuda.synchronize()
+            t1 = time.perf_counter()
+            if step >= args.warmup:
+                times.append(t1 - t0)
+                its.append(it)
+                berrs.append(berr)
+                rcs.append(rc)
+        xs[name] = X.cpu().numpy()[:, 0]
+        lat = sorted(times)
+        out[name] = {"solves_per_s": 1.0 / statistics.mean(times), "p50_ms": 1e3 * lat[len(lat) // 2],
+                     "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], "iters": its[-1],
+                     "berr": max(berrs), "status": rcs[-1]}
+    ref = xs["fp64"]
+    out["fp32_refined"]["rel_diff_vs_fp64"] = float(np.linalg.norm(xs["fp32_refined"] - ref) / np.linalg.norm(ref))
+    line = {"metric": "LS solves/s, plain FP64 vs FP32+refinement at backward error <= 1e-12",
+            "value": out["fp32_refined"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
+            "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic: A = U diag(sigma) V^T, seed 0",
+            "config": {"workload": "least squares %dx%d kappa=%g, nrhs=1, nb=%d ib=%d" % (m, n, w["kappa"], nb, ib)},
+            "ls": out, "speedup_vs_fp64": out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"]}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -343,10 +396,19 @@ def main():
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="qr8192", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--nb", type=int, default=0, help="override the workload's tile size")
+    ap.add_argument("--ib", type=int, default=0, help="override the workload's inner block size")
     args = ap.parse_args()
-    w = WORKLOADS[args.workload]
+    w = dict(WORKLOADS[args.workload])
+    if args.nb:
+        w["nb"] = args.nb
+    if args.ib:
+        w["ib"] = args.ib
     if args.impl == "reference":
         run_reference(args, w)
+    elif w.get("ls"):
+        run_ls(args, w)
     else:
         run_ours(args, w)
 

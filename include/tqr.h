@@ -151,6 +151,56 @@ int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t ld
                  void* stream);
 
 /*
+ * One matrix of a batch (tqr_batch_submit).
+ *   m, n    size (>= 1 each)
+ *   A, lda  device pointer, column-major, overwritten as by tqr_factor
+ *   T       device pointer, tqr_t_size(m, n, nb, ib) bytes, written
+ *   nb, ib  tile sizes; nb = ib = 0 takes tqr_autotune's choice (size T
+ *           with tqr_autotune's nb and ib first)
+ */
+typedef struct tqr_desc {
+  int64_t m, n;
+  double* A;
+  int64_t lda;
+  double* T;
+  int32_t nb, ib;
+} tqr_desc;
+
+/*
+ * Tile sizes for one m x n factorization inside a batch, from a table of
+ * half-octave size classes filled on first use by a model of the scheduler's
+ * costs (padded work plus a small weight on the critical path; candidates
+ * nb in {16..256}, ib in {16, 32}).  Writes *nb, *ib.  Returns 0 or -i.
+ */
+int tqr_autotune(int64_t m, int64_t n, int* nb, int* ib);
+
+/*
+ * Factor `count` independent matrices in ONE persistent launch whose global
+ * task DAG interleaves the tiles of all of them (Algorithm 1 per matrix;
+ * tasks ordered by decreasing longest remaining path).  Every descriptor's A
+ * and T must be device memory.  The batch's device work is captured in a
+ * CUDA graph the first time a batch of these exact shapes is submitted and
+ * replayed afterwards.  Asynchronous on `stream`; *ticket identifies the
+ * batch for tqr_batch_poll / tqr_batch_wait.  Returns 0, -i for invalid
+ * argument i (-2: some descriptor is invalid), TQR_ERR_BUSY if a batch of
+ * the same shapes is still running (poll it first), or another TQR_ERR_*.
+ * Results are identical to factoring each matrix alone with the same nb, ib.
+ */
+int tqr_batch_submit(int count, const tqr_desc* descs, uint64_t* ticket, void* stream);
+
+/*
+ * Non-blocking completion check.  *done = 1 when the batch has finished;
+ * then status_per_item (may be NULL, else `count` ints) receives each
+ * matrix's status and the ticket is consumed.  Returns the batch status
+ * (0, TQR_ERR_TIMEOUT, TQR_ERR_CUDA) once done, 0 while running, -1 for an
+ * unknown ticket.
+ */
+int tqr_batch_poll(uint64_t ticket, int* done, int* status_per_item);
+
+/* Blocking form of tqr_batch_poll. */
+int tqr_batch_wait(uint64_t ticket, int* status_per_item);
+
+/*
  * tqr_factor without any memory allocation.  (The paper has no counterpart:
  * this is a deployment variant of Algorithm 1.)
  *

@@ -29,6 +29,7 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
 int ptr_kind(const void* p);
 int check_tiles(int nb, int ib, int arg_nb, int arg_ib);
 void clear_plans();
+void autotune(int64_t m, int64_t n, int* nb, int* ib);
 void set_schedule(int policy, int max_ctas);
 int timing_enable(int on);
 int timing_read(double* ms, int64_t* launches);

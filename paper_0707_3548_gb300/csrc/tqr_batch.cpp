@@ -1,0 +1,360 @@
+// tqr_batch.cpp -- many independent factorizations in one persistent launch
+// (tqr_batch_submit / tqr_batch_poll / tqr_batch_wait) and the tile-size
+// autotuner (tqr_autotune).
+//
+// A batch is one global task list over all its matrices: every matrix keeps
+// its own tiles, T, version counters and (nb, ib), and its tasks are merged
+// into a single priority order (decreasing longest remaining path), so the
+// tiles of all instances interleave on the SMs of one persistent kernel.
+// The batch's device work -- descriptor upload, counter reset, batched pack,
+// the task kernel, batched unpack and the status read-back -- is captured once
+// per batch shape in a CUDA graph; resubmitting a batch of the same shapes
+// (any matrices) refills a pinned descriptor buffer and relaunches the graph.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <tuple>
+#include <vector>
+
+#include "tqr.h"
+#include "tqr_api_internal.h"
+#include "tqr_engine.h"
+#include "tqr_plan.h"
+
+namespace tqr {
+
+// ---------------------------------------------------------------- autotuner
+// Model-based choice of (nb, ib) for one m x n factorization in a batch:
+// the padded task set's cost under the scheduler's cost model (work in CTA
+// seconds, which sets batch throughput) plus a small weight on its critical
+// path (its latency).  Candidates keep two CTAs per SM; ib is 16 or 32.
+static double model_score(int64_t m, int64_t n, int nb, int ib) {
+  int cs, occ, smem;
+  if (!choose_shape(nb, ib, 8, &cs, &occ, &smem) || occ < 2) return INFINITY;
+  Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
+  TaskX t = {};
+  t.j = 0;
+  auto cost = [&](int kind) {
+    t.kind = kind;
+    return task_cost(I, t, 8, 2);
+  };
+  const double cg = cost(K_GEQRT), ct = cost(K_TSQRT), cl = cost(K_LARFB), cs_ = cost(K_SSRFB);
+  double work = 0, cp = 0;
+  for (int k = 0; k < I.kt; ++k) {
+    const double rows = I.p - k - 1, cols = I.q - k - 1;
+    work += cg + cols * I.NS * cl + rows * ct + rows * cols * I.NS * cs_;
+    cp += cg + (rows > 0 ? ct : 0) + (cols > 0 ? cs_ : 0);
+  }
+  cp += std::max(0, I.p - I.kt) * ct;
+  return work + 0.25 * cp;
+}
+
+static std::mutex g_tune_mu;
+static std::map<std::pair<int, int>, std::pair<int, int>> g_tune;
+
+static int size_class(int64_t x) {
+  // half-octave classes: 64, 90, 128, 181, 256, ...
+  if (x <= 1) return 0;
+  return static_cast<int>(std::floor(2.0 * std::log2(static_cast<double>(x)) + 0.5));
+}
+
+void autotune(int64_t m, int64_t n, int* nb_out, int* ib_out) {
+  const std::pair<int, int> key(size_class(m), size_class(n));
+  {
+    std::lock_guard<std::mutex> lk(g_tune_mu);
+    auto it = g_tune.find(key);
+    if (it != g_tune.end()) {
+      *nb_out = it->second.first;
+      *ib_out = it->second.second;
+      return;
+    }
+  }
+  // evaluate at the class's representative size
+  const int64_t mr = std::max<int64_t>(1, std::llround(std::pow(2.0, key.first / 2.0)));
+  const int64_t nr = std::max<int64_t>(1, std::llround(std::pow(2.0, key.second / 2.0)));
+  int best_nb = 64, best_ib = 16;
+  double best = INFINITY;
+  for (int nb : {16, 32, 48, 64, 96, 128, 192, 256}) {
+    for (int ib : {16, 32}) {
+      if (ib > nb || nb % ib) continue;
+      const double sc = model_score(mr, nr, nb, ib);
+      if (sc < best) {
+        best = sc;
+        best_nb = nb;
+        best_ib = ib;
+      }
+    }
+  }
+  std::lock_guard<std::mutex> lk(g_tune_mu);
+  g_tune[key] = std::make_pair(best_nb, best_ib);
+  *nb_out = best_nb;
+  *ib_out = best_ib;
+}
+
+// ---------------------------------------------------------------- plans
+struct BatchPlan {
+  std::vector<std::tuple<int64_t, int64_t, int, int>> shape;  // (m, n, nb, ib) per item
+  int count = 0;
+  int device = -1;
+  int smem = 0, grid = 0, ntasks = 0;
+  PlanStats stats;
+  char* ws = nullptr;          // tiles + counters + control, device
+  size_t ws_bytes = 0, ver_off = 0, ver_bytes = 0, ctl_off = 0;
+  Inst* d_insts = nullptr;     // device
+  PackDesc* d_pack = nullptr;  // device
+  TaskX* d_tasks = nullptr;    // device
+  Inst* h_insts = nullptr;     // pinned
+  PackDesc* h_pack = nullptr;  // pinned
+  int* h_status = nullptr;     // pinned
+  std::vector<size_t> tile_off, ctr_off;
+  cudaGraphExec_t exec = nullptr;
+  cudaEvent_t done = nullptr;
+  bool busy = false;
+  ~BatchPlan() {
+    if (exec) cudaGraphExecDestroy(exec);
+    if (done) cudaEventDestroy(done);
+    if (ws) cudaFree(ws);
+    if (d_insts) cudaFree(d_insts);
+    if (d_pack) cudaFree(d_pack);
+    if (d_tasks) cudaFree(d_tasks);
+    if (h_insts) cudaFreeHost(h_insts);
+    if (h_pack) cudaFreeHost(h_pack);
+    if (h_status) cudaFreeHost(h_status);
+  }
+};
+
+static std::mutex g_bmu;
+static std::vector<std::shared_ptr<BatchPlan>> g_bplans;  // most recent first
+static const size_t kMaxBatchPlans = 4;
+struct Ticket {
+  std::shared_ptr<BatchPlan> plan;
+  int count;
+  bool finished;
+  int status;
+};
+static std::map<uint64_t, Ticket> g_tickets;
+static uint64_t g_next_ticket = 1;
+
+static size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+static int build_batch_plan(const std::vector<std::tuple<int64_t, int64_t, int, int>>& shape,
+                            std::shared_ptr<BatchPlan>* out) {
+  auto P = std::make_shared<BatchPlan>();
+  P->shape = shape;
+  P->count = static_cast<int>(shape.size());
+  cudaGetDevice(&P->device);
+  std::vector<Inst> insts(shape.size());
+  size_t off = 0;
+  P->tile_off.resize(shape.size());
+  P->ctr_off.resize(shape.size());
+  int max_smem = 0, min_occ = 2;
+  for (size_t a = 0; a < shape.size(); ++a) {
+    const int64_t m = std::get<0>(shape[a]), n = std::get<1>(shape[a]);
+    const int nb = std::get<2>(shape[a]), ib = std::get<3>(shape[a]);
+    int cs, occ, smem;
+    if (!choose_shape(nb, ib, 8, &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
+    max_smem = std::max(max_smem, smem);
+    min_occ = std::min(min_occ, occ);
+    insts[a] = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
+    P->tile_off[a] = off;
+    off += al256(sizeof(double) * static_cast<size_t>(insts[a].p) * insts[a].q * nb * nb);
+  }
+  P->ver_off = off;
+  for (size_t a = 0; a < shape.size(); ++a) {
+    P->ctr_off[a] = off;
+    off += al256(sizeof(int) * static_cast<size_t>(insts[a].p) * insts[a].q * insts[a].NS);
+  }
+  P->ctl_off = off;
+  P->ver_bytes = off - P->ver_off + al256(ctl_bytes());
+  off += al256(ctl_bytes());
+  P->ws_bytes = off;
+  // global task list
+  std::vector<TaskX> seq, ordered;
+  for (size_t a = 0; a < shape.size(); ++a) seq_tasks(insts[a], static_cast<int>(a), seq);
+  P->ntasks = static_cast<int>(seq.size());
+  const int sms = device_sms();
+  P->grid = std::max(1, std::min(sms * min_occ, P->ntasks));
+  P->smem = max_smem;
+  std::string err;
+  if (!order_bottom_level(insts, seq, 8, min_occ, P->grid, ordered, &P->stats, &err)) {
+    set_last_error(err);
+    return TQR_ERR_UNSUPPORTED;
+  }
+  if (cudaMalloc(&P->ws, P->ws_bytes) != cudaSuccess ||
+      cudaMalloc(&P->d_insts, sizeof(Inst) * shape.size()) != cudaSuccess ||
+      cudaMalloc(&P->d_pack, sizeof(PackDesc) * shape.size()) != cudaSuccess ||
+      cudaMalloc(&P->d_tasks, sizeof(TaskX) * std::max<size_t>(1, ordered.size())) != cudaSuccess ||
+      cudaMallocHost(&P->h_insts, sizeof(Inst) * shape.size()) != cudaSuccess ||
+      cudaMallocHost(&P->h_pack, sizeof(PackDesc) * shape.size()) != cudaSuccess ||
+      cudaMallocHost(&P->h_status, sizeof(int) * 4) != cudaSuccess) {
+    cudaGetLastError();
+    return TQR_ERR_NOMEM;
+  }
+  if (!ordered.empty() &&
+      cudaMemcpy(P->d_tasks, ordered.data(), sizeof(TaskX) * ordered.size(), cudaMemcpyHostToDevice) != cudaSuccess)
+    return TQR_ERR_CUDA;
+  for (size_t a = 0; a < shape.size(); ++a) {
+    Inst I = insts[a];
+    I.A = P->ws + P->tile_off[a];
+    I.B = nullptr;
+    I.T = nullptr;  // per submit
+    I.ver = reinterpret_cast<int*>(P->ws + P->ctr_off[a]);
+    P->h_insts[a] = I;
+    PackDesc& d = P->h_pack[a];
+    d.A = nullptr;
+    d.lda = 0;
+    d.Ab = I.A;
+    d.m = I.m;
+    d.n = I.n;
+    d.p = I.p;
+    d.q = I.q;
+    d.nb = I.nb;
+    d.pad = 0;
+  }
+  if (cudaEventCreateWithFlags(&P->done, cudaEventDisableTiming) != cudaSuccess) return TQR_ERR_CUDA;
+  // capture the batch's device work once
+  int occ_dummy = 0;
+  if (occupancy<double>(P->smem, &occ_dummy) != cudaSuccess) return TQR_ERR_CUDA;
+  cudaStream_t cap;
+  if (cudaStreamCreateWithFlags(&cap, cudaStreamNonBlocking) != cudaSuccess) return TQR_ERR_CUDA;
+  cudaGraph_t graph = nullptr;
+  int status = TQR_OK;
+  if (cudaStreamBeginCapture(cap, cudaStreamCaptureModeRelaxed) != cudaSuccess) status = TQR_ERR_CUDA;
+  if (status == TQR_OK) {
+    const size_t n = shape.size();
+    if (cudaMemcpyAsync(P->d_insts, P->h_insts, sizeof(Inst) * n, cudaMemcpyHostToDevice, cap) != cudaSuccess ||
+        cudaMemcpyAsync(P->d_pack, P->h_pack, sizeof(PackDesc) * n, cudaMemcpyHostToDevice, cap) != cudaSuccess ||
+        cudaMemsetAsync(P->ws + P->ver_off, 0, P->ver_bytes, cap) != cudaSuccess ||
+        launch_pack_batched<double>(P->d_pack, P->count, cap) != cudaSuccess ||
+        (P->ntasks > 0 && launch_run<double>(P->d_tasks, P->ntasks, P->d_insts, P->ws + P->ctl_off, wait_limit_ns(),
+                                             P->grid, P->smem, cap) != cudaSuccess) ||
+        launch_unpack_batched<double>(P->d_pack, P->count, cap) != cudaSuccess ||
+        cudaMemcpyAsync(P->h_status, P->ws + P->ctl_off, sizeof(int) * 4, cudaMemcpyDeviceToHost, cap) !=
+            cudaSuccess)
+      status = TQR_ERR_CUDA;
+    cudaError_t e = cudaStreamEndCapture(cap, &graph);
+    if (e != cudaSuccess) status = TQR_ERR_CUDA;
+  }
+  if (status == TQR_OK && cudaGraphInstantiate(&P->exec, graph, 0) != cudaSuccess) status = TQR_ERR_CUDA;
+  if (graph) cudaGraphDestroy(graph);
+  cudaStreamDestroy(cap);
+  cudaGetLastError();
+  if (status != TQR_OK) return status;
+  *out = P;
+  return TQR_OK;
+}
+
+}  // namespace tqr
+
+using namespace tqr;
+
+extern "C" {
+
+int tqr_autotune(int64_t m, int64_t n, int* nb, int* ib) {
+  if (m < 1) return -1;
+  if (n < 1) return -2;
+  if (nb == nullptr) return -3;
+  if (ib == nullptr) return -4;
+  autotune(m, n, nb, ib);
+  return TQR_OK;
+}
+
+int tqr_batch_submit(int count, const tqr_desc* d, uint64_t* ticket, void* stream) {
+  if (count < 1) return -1;
+  if (d == nullptr) return -2;
+  if (ticket == nullptr) return -3;
+  std::vector<std::tuple<int64_t, int64_t, int, int>> shape(static_cast<size_t>(count));
+  for (int a = 0; a < count; ++a) {
+    const tqr_desc& x = d[a];
+    int nb = x.nb, ib = x.ib;
+    if (nb == 0 && ib == 0) autotune(x.m, x.n, &nb, &ib);
+    if (x.m < 1 || x.n < 1 || x.m > (1 << 30) || x.n > (1 << 30) || x.A == nullptr || x.T == nullptr ||
+        x.lda < x.m || check_tiles(nb, ib, 1, 2) != 0)
+      return -2;
+    if (ptr_kind(x.A) != PTR_DEVICE || ptr_kind(x.T) != PTR_DEVICE) return -2;
+    shape[a] = std::make_tuple(x.m, x.n, nb, ib);
+  }
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  std::lock_guard<std::mutex> lk(g_bmu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  std::shared_ptr<BatchPlan> P;
+  for (size_t a = 0; a < g_bplans.size(); ++a)
+    if (g_bplans[a]->device == dev && g_bplans[a]->shape == shape) {
+      P = g_bplans[a];
+      g_bplans.erase(g_bplans.begin() + a);
+      g_bplans.insert(g_bplans.begin(), P);
+      break;
+    }
+  if (!P) {
+    const int s = build_batch_plan(shape, &P);
+    if (s != TQR_OK) return s;
+    g_bplans.insert(g_bplans.begin(), P);
+    while (g_bplans.size() > kMaxBatchPlans) g_bplans.pop_back();
+  }
+  if (P->busy) {
+    if (cudaEventQuery(P->done) == cudaErrorNotReady) return TQR_ERR_BUSY;
+    cudaGetLastError();
+    P->busy = false;
+  }
+  for (int a = 0; a < count; ++a) {
+    P->h_insts[a].T = d[a].T;
+    P->h_pack[a].A = d[a].A;
+    P->h_pack[a].lda = d[a].lda;
+  }
+  if (cudaGraphLaunch(P->exec, st) != cudaSuccess || cudaEventRecord(P->done, st) != cudaSuccess) {
+    cudaGetLastError();
+    return TQR_ERR_CUDA;
+  }
+  P->busy = true;
+  const uint64_t t = g_next_ticket++;
+  g_tickets[t] = Ticket{P, count, false, TQR_OK};
+  *ticket = t;
+  return TQR_OK;
+}
+
+static int poll_locked(uint64_t ticket, bool wait, int* done, int* status_per_item) {
+  auto it = g_tickets.find(ticket);
+  if (it == g_tickets.end()) return -1;
+  Ticket& T = it->second;
+  if (!T.finished) {
+    cudaError_t e = wait ? cudaEventSynchronize(T.plan->done) : cudaEventQuery(T.plan->done);
+    if (e == cudaErrorNotReady) {
+      if (done) *done = 0;
+      return TQR_OK;
+    }
+    if (e != cudaSuccess) {
+      cudaGetLastError();
+      T.status = TQR_ERR_CUDA;
+    } else {
+      T.status = T.plan->h_status[1] != 0 ? TQR_ERR_TIMEOUT : TQR_OK;
+    }
+    T.finished = true;
+    T.plan->busy = false;
+  }
+  if (done) *done = 1;
+  if (status_per_item)
+    for (int a = 0; a < T.count; ++a) status_per_item[a] = T.status;
+  const int s = T.status;
+  g_tickets.erase(it);
+  return s;
+}
+
+int tqr_batch_poll(uint64_t ticket, int* done, int* status_per_item) {
+  if (done == nullptr) return -2;
+  std::lock_guard<std::mutex> lk(g_bmu);
+  return poll_locked(ticket, false, done, status_per_item);
+}
+
+int tqr_batch_wait(uint64_t ticket, int* status_per_item) {
+  std::lock_guard<std::mutex> lk(g_bmu);
+  int done = 0;
+  return poll_locked(ticket, true, &done, status_per_item);
+}
+
+}  // extern "C"

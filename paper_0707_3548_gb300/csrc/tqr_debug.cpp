@@ -22,7 +22,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   if (cs < 1 || nb % cs != 0) return -6;
   if (nrhs < 0) return -7;
   if (mode != 0 && nrhs == 0) return -7;
-  if (trsm && (nrhs == 0 || m < n)) return -8;
+  if (trsm && (nrhs == 0 || m < n || (mode != 0 && mode != 1))) return -8;
   if (workers < 1) return -9;
   if (policy < -1 || policy > 1) return -10;
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);
@@ -56,7 +56,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
 
 int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, const int32_t* task,
                     int32_t* waits, int32_t* signals) {
-  Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, 0);
+  Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, 1);
   TaskX t;
   t.kind = task[0]; t.s = task[1]; t.inst = task[2]; t.k = task[3]; t.i = task[4]; t.j = task[5]; t.l = task[6];
   t.pad = 0;

@@ -887,6 +887,45 @@ __global__ void unpack_kernel(const S* __restrict__ Ab, int p, int nb, D* __rest
   }
 }
 
+// Batched pack/unpack: blockIdx.y (strided) picks the matrix, blockIdx.x
+// and the threads stride over its elements.
+template <typename D>
+__global__ void pack_batched_kernel(const PackDesc* __restrict__ descs, int count) {
+  for (int b = blockIdx.y; b < count; b += gridDim.y) {
+    const PackDesc d = descs[b];
+    const long long nb2 = static_cast<long long>(d.nb) * d.nb;
+    const long long total = nb2 * d.p * d.q;
+    D* Ab = static_cast<D*>(d.Ab);
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+      const long long tile = e / nb2;
+      const int rem = static_cast<int>(e - tile * nb2);
+      const int r = rem % d.nb, c = rem / d.nb;
+      const int ti = static_cast<int>(tile % d.p), tj = static_cast<int>(tile / d.p);
+      const long long gi = static_cast<long long>(ti) * d.nb + r, gj = static_cast<long long>(tj) * d.nb + c;
+      Ab[e] = (gi < d.m && gj < d.n) ? static_cast<D>(d.A[gi + gj * d.lda]) : D(0);
+    }
+  }
+}
+
+template <typename S>
+__global__ void unpack_batched_kernel(const PackDesc* __restrict__ descs, int count) {
+  for (int b = blockIdx.y; b < count; b += gridDim.y) {
+    const PackDesc d = descs[b];
+    const long long total = static_cast<long long>(d.m) * d.n;
+    const S* Ab = static_cast<const S*>(d.Ab);
+    for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+         e += static_cast<long long>(gridDim.x) * blockDim.x) {
+      const int gi = static_cast<int>(e % d.m), gj = static_cast<int>(e / d.m);
+      const int ti = gi / d.nb, r = gi - ti * d.nb;
+      const int tj = gj / d.nb, c = gj - tj * d.nb;
+      d.A[gi + static_cast<long long>(gj) * d.lda] = static_cast<double>(
+          Ab[(static_cast<long long>(ti) + static_cast<long long>(tj) * d.p) * d.nb * d.nb +
+             static_cast<long long>(c) * d.nb + r]);
+    }
+  }
+}
+
 __global__ void status_reset_kernel() { g_status = 0; }
 
 // ---------------------------------------------------------------- host launchers
@@ -911,6 +950,22 @@ cudaError_t launch_unpack(const real* Ab, int p, int nb, double* A, long long ld
                           cudaStream_t st) {
   if (static_cast<long long>(m) * n == 0) return cudaSuccess;
   unpack_kernel<real, double><<<grid_for(static_cast<long long>(m) * n, sms), 256, 0, st>>>(Ab, p, nb, A, lda, m, n);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_pack_batched(const PackDesc* d, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  dim3 grid(8, count < 65535 ? count : 65535);
+  pack_batched_kernel<real><<<grid, 256, 0, st>>>(d, count);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_unpack_batched(const PackDesc* d, int count, cudaStream_t st) {
+  if (count <= 0) return cudaSuccess;
+  dim3 grid(8, count < 65535 ? count : 65535);
+  unpack_batched_kernel<real><<<grid, 256, 0, st>>>(d, count);
   return cudaGetLastError();
 }
 
@@ -994,6 +1049,8 @@ template cudaError_t launch_unpack<float>(const float*, int, int, double*, long 
 template cudaError_t launch_run<double>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t);
 template cudaError_t launch_run<float>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t);
 template cudaError_t occupancy<double>(int, int*);
+template cudaError_t launch_pack_batched<double>(const PackDesc*, int, cudaStream_t);
+template cudaError_t launch_unpack_batched<double>(const PackDesc*, int, cudaStream_t);
 template cudaError_t occupancy<float>(int, int*);
 
 }  // namespace tqr

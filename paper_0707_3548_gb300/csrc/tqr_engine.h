@@ -20,6 +20,18 @@ cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* 
 template <typename real>
 cudaError_t occupancy(int smem_bytes, int* blocks_per_sm);
 
+// One matrix of a batch for the batched pack/unpack kernels.
+struct PackDesc {
+  double* A;      // caller's column-major matrix
+  long long lda;
+  void* Ab;       // its tiles in Block Data Layout
+  int m, n, p, q, nb, pad;
+};
+template <typename real>
+cudaError_t launch_pack_batched(const PackDesc* d, int count, cudaStream_t st);
+template <typename real>
+cudaError_t launch_unpack_batched(const PackDesc* d, int count, cudaStream_t st);
+
 // Copies the sticky device status to *status (synchronizing st) and clears it.
 cudaError_t read_status(int* status, cudaStream_t st);
 size_t ctl_bytes();

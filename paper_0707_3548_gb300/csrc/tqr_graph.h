@@ -17,7 +17,8 @@
 //   FACTOR  (Algorithm 1; optional right-hand-side tile columns j >= q are
 //            updated like trailing columns, i.e. Q^T B; optional back
 //            substitution X = R^-1 (Q^T B)[0:n] appended)
-//   APPLY_QT (factors final: LARFB/SSRFB on B only, Algorithm 1's order)
+//   APPLY_QT (factors final: LARFB/SSRFB on B only, Algorithm 1's order;
+//            optional back substitution appended, as in FACTOR)
 //   APPLY_Q  (factors final: the transposed steps in reverse order)
 //   TRSM     (factors final: back substitution on B only)
 //   TRSMT    (factors final: forward substitution R^T X = B)
@@ -135,10 +136,11 @@ TQR_HD int task_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* n
       sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
       break;
     case K_TRSM_UPD: {
-      // C_k -= R_kl X_l, l = kt-1 .. k+1, then SOLVE(k).  In FACTOR mode the
-      // right-hand sides first received p (rows < kt) writes from the
-      // factorization and R's tiles (k, l), k <= l < q, end at version p.
-      int base = a_final ? 0 : p;
+      // C_k -= R_kl X_l, l = kt-1 .. k+1, then SOLVE(k).  In FACTOR and
+      // APPLY_QT modes the right-hand sides first received p writes (rows
+      // < kt) from Algorithm 1's updates, and in FACTOR mode R's tiles (k, l),
+      // k <= l < q, end at version p.
+      const int base = (I.mode == M_FACTOR || I.mode == M_APPLY_QT) ? p : 0;
       if (!a_final) w[nw++] = {ctr_index(I, k, l, 0), NS, p};
       w[nw++] = {ctr_index(I, l, j, s), 1, base + (kt - l)};
       w[nw++] = {ctr_index(I, k, j, s), 1, base + (kt - 1 - l)};
@@ -146,7 +148,7 @@ TQR_HD int task_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* n
       break;
     }
     case K_TRSM_SOLVE: {
-      int base = a_final ? 0 : p;
+      const int base = (I.mode == M_FACTOR || I.mode == M_APPLY_QT) ? p : 0;
       if (!a_final) w[nw++] = {ctr_index(I, k, k, 0), NS, p};
       w[nw++] = {ctr_index(I, k, j, s), 1, base + (kt - 1 - k)};
       sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};

@@ -362,7 +362,10 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
     read_back();
   }
   if (status == TQR_OK) {
-    const double eps = esize == 8 ? 1.1102230246251565e-16 : 5.9604644775390625e-08;
+    // numerical rank test on R with the FP64 unit roundoff in both precisions:
+    // an FP32 factor with a small pivot may still refine to an FP64 answer,
+    // so refinement, not this test, judges the FP32 path
+    const double eps = 1.1102230246251565e-16;
     if (!(hn[3 * nrhs + 2] > n * eps * hn[3 * nrhs + 3])) status = TQR_ERR_RANK;
     berr = berr_host(hn, nrhs, hn[3 * nrhs]);
   }

@@ -53,6 +53,14 @@ void seq_tasks(const Inst& I, int x, std::vector<TaskX>& out) {
           for (int j = q; j < qt; ++j)
             for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_SSRFB, x, k, i, j, s));
       }
+      if (I.trsm) {
+        for (int j = q; j < qt; ++j)
+          for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s)
+            for (int k = kt - 1; k >= 0; --k) {
+              for (int l = kt - 1; l > k; --l) out.push_back(mk(K_TRSM_UPD, x, k, k, j, s, l));
+              out.push_back(mk(K_TRSM_SOLVE, x, k, k, j, s));
+            }
+      }
       break;
     case M_APPLY_Q:
       for (int k = kt - 1; k >= 0; --k) {
@@ -338,6 +346,86 @@ bool order_tasks(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, 
     stats->edges = static_cast<int64_t>(succ.size());
     stats->critical_path_s = cp;
     stats->work_s = work;
+  }
+  return true;
+}
+
+bool order_bottom_level(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, int esize, int ctas_per_sm,
+                        int workers, std::vector<TaskX>& ordered, PlanStats* stats, std::string* err) {
+  const std::vector<int64_t> base = counter_bases(insts);
+  const int64_t nctr = base.back();
+  const int64_t n = static_cast<int64_t>(seq.size());
+  std::vector<int64_t> wptr(nctr + 1, 0);
+  Wait w[4];
+  Signal sg[2];
+  int nsig;
+  for (int64_t t = 0; t < n; ++t) {
+    task_rules(insts[seq[t].inst], seq[t], w, sg, &nsig);
+    for (int a = 0; a < nsig; ++a)
+      for (int c = 0; c < sg[a].cnt; ++c) wptr[base[seq[t].inst] + sg[a].ctr + c + 1]++;
+  }
+  for (int64_t c = 0; c < nctr; ++c) wptr[c + 1] += wptr[c];
+  std::vector<int> writers(static_cast<size_t>(wptr[nctr]));
+  {
+    std::vector<int64_t> fill(wptr.begin(), wptr.end() - 1);
+    for (int64_t t = 0; t < n; ++t) {
+      const int nw = task_rules(insts[seq[t].inst], seq[t], w, sg, &nsig);
+      for (int a = 0; a < nsig; ++a)
+        for (int c = 0; c < sg[a].cnt; ++c) {
+          const int ctr = sg[a].ctr + c;
+          const int64_t g = base[seq[t].inst] + ctr;
+          int need = -1;
+          for (int b = 0; b < nw; ++b)
+            if (ctr >= w[b].ctr && ctr < w[b].ctr + w[b].cnt) need = w[b].ver;
+          if (need != fill[g] - wptr[g]) {
+            if (err) *err = "rule mismatch in task " + std::to_string(t);
+            return false;
+          }
+          writers[fill[g]++] = static_cast<int>(t);
+        }
+    }
+  }
+  std::vector<double> bl(static_cast<size_t>(n)), maxsucc(static_cast<size_t>(n), 0.0);
+  double work = 0, cp = 0;
+  for (int64_t t = n - 1; t >= 0; --t) {
+    const Inst& I = insts[seq[t].inst];
+    const double c = task_cost(I, seq[t], esize, ctas_per_sm);
+    work += c;
+    bl[t] = c + maxsucc[t];
+    cp = std::max(cp, bl[t]);
+    const int nw = task_rules(I, seq[t], w, sg, &nsig);
+    for (int b = 0; b < nw; ++b) {
+      if (w[b].ver <= 0) continue;
+      for (int cc = 0; cc < w[b].cnt; ++cc) {
+        const int64_t g = base[seq[t].inst] + w[b].ctr + cc;
+        if (wptr[g + 1] - wptr[g] < w[b].ver) {
+          if (err) *err = "rule error: missing writer for task " + std::to_string(t);
+          return false;
+        }
+        const int pw = writers[wptr[g] + w[b].ver - 1];
+        if (pw >= t) {
+          if (err) *err = "rule error: task depends on a later task";
+          return false;
+        }
+        if (bl[t] > maxsucc[pw]) maxsucc[pw] = bl[t];
+      }
+    }
+  }
+  std::vector<int> idx(static_cast<size_t>(n));
+  for (int64_t t = 0; t < n; ++t) idx[t] = static_cast<int>(t);
+  std::sort(idx.begin(), idx.end(), [&bl](int x, int y) {
+    if (bl[x] != bl[y]) return bl[x] > bl[y];
+    return x < y;
+  });
+  ordered.resize(static_cast<size_t>(n));
+  for (int64_t a = 0; a < n; ++a) ordered[a] = seq[idx[a]];
+  if (stats) {
+    stats->policy = 2;
+    stats->critical_path_s = cp;
+    stats->work_s = work;
+    stats->makespan_s = std::max(cp, work / std::max(1, workers));
+    stats->makespan_other = 0;
+    stats->edges = 0;
   }
   return true;
 }

@@ -49,4 +49,13 @@ bool order_tasks(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, 
                  int ctas_per_sm, int policy /* -1: best of both */, std::vector<TaskX>& ordered,
                  PlanStats* stats, std::string* err);
 
+// Orders a (possibly multi-instance) task set by decreasing bottom level
+// (longest remaining path, cost model) without simulation and without
+// materialising predecessor lists: one backward sweep over the sequential
+// order propagates each task's bottom level to the writers it waits on.
+// Sorting by strictly decreasing bottom level is a topological order because
+// every task costs more than zero.  Used for large batches.
+bool order_bottom_level(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, int esize, int ctas_per_sm,
+                        int workers, std::vector<TaskX>& ordered, PlanStats* stats, std::string* err);
+
 }  // namespace tqr

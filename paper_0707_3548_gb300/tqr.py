@@ -39,6 +39,12 @@ _ERRNAMES = {1: "TQR_ERR_CUDA", 2: "TQR_ERR_NOMEM", 3: "TQR_ERR_TIMEOUT", 4: "TQ
 
 _lib = None
 
+
+class TqrDesc(ctypes.Structure):
+    """tqr_desc of include/tqr.h."""
+    _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
+                ("T", ctypes.c_void_p), ("nb", ctypes.c_int32), ("ib", ctypes.c_int32)]
+
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
 _vp = ctypes.c_void_p
@@ -56,6 +62,10 @@ SIGNATURES = {
     "tqr_solve_ls": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int,
                             ctypes.POINTER(_int), ctypes.POINTER(_dbl), _int, _int, _vp]),
     "tqr_factor_noalloc": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp]),
+    "tqr_autotune": (_int, [_i64, _i64, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "tqr_batch_submit": (_int, [_int, _vp, ctypes.POINTER(ctypes.c_uint64), _vp]),
+    "tqr_batch_poll": (_int, [ctypes.c_uint64, ctypes.POINTER(_int), _vp]),
+    "tqr_batch_wait": (_int, [ctypes.c_uint64, _vp]),
     "tqr_stream_status": (_int, [_vp]),
     "tqr_set_wait_limit_ms": (_i64, [_i64]),
     "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
@@ -191,6 +201,42 @@ def tqr_factor_noalloc(A, nb, ib, T, stream=None, check=True):
     if check:
         _check("tqr_factor_noalloc", rc)
     return rc
+
+
+def tqr_autotune(m, n):
+    nb = _int(0)
+    ib = _int(0)
+    _check("tqr_autotune", lib().tqr_autotune(m, n, ctypes.byref(nb), ctypes.byref(ib)))
+    return nb.value, ib.value
+
+
+def tqr_batch_submit(mats, Ts, tiles=None, stream=None):
+    """Submit column-major CUDA float64 matrices (factored in place) with T
+    buffers; tiles: list of (nb, ib) or None for the autotuner.  Returns the
+    ticket."""
+    n = len(mats)
+    descs = (TqrDesc * n)()
+    for a, (A, T) in enumerate(zip(mats, Ts)):
+        pa, m, nn, lda, _ = _mat(A, "A")
+        nb, ib = tiles[a] if tiles is not None else (0, 0)
+        descs[a] = TqrDesc(m, nn, pa, lda, _ptr(T), nb, ib)
+    ticket = ctypes.c_uint64(0)
+    _check("tqr_batch_submit", lib().tqr_batch_submit(n, ctypes.cast(descs, _vp), ctypes.byref(ticket),
+                                                       _stream(True, stream)))
+    return ticket.value
+
+
+def tqr_batch_poll(ticket, count):
+    done = _int(0)
+    st = np.zeros(count, dtype=np.int32)
+    rc = lib().tqr_batch_poll(ticket, ctypes.byref(done), st.ctypes.data)
+    return bool(done.value), rc, st
+
+
+def tqr_batch_wait(ticket, count):
+    st = np.zeros(count, dtype=np.int32)
+    rc = lib().tqr_batch_wait(ticket, st.ctypes.data)
+    return rc, st
 
 
 def tqr_factor_ws(A, nb, ib, T, work, stream=None):

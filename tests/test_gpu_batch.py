@@ -1,0 +1,65 @@
+"""Batched factorization: one persistent launch over many independent matrices."""
+import numpy as np
+import pytest
+
+from oracle import tiled as TL
+from paper_0707_3548_gb300 import inputs, tqr
+from tests.gpu_util import to_dev, to_host, torch_cuda
+
+pytestmark = pytest.mark.gpu
+
+
+def _alone(A, nb, ib):
+    dA = to_dev(A)
+    T = tqr.tqr_factor(dA, nb, ib)
+    return to_host(dA), T.cpu().numpy()
+
+
+def _submit(mats, tiles):
+    torch = torch_cuda()
+    dev = [to_dev(A) for A in mats]
+    Ts = []
+    for A, (nb, ib) in zip(mats, tiles):
+        Ts.append(torch.zeros(tqr.tqr_t_size(A.shape[0], A.shape[1], nb, ib) // 8, dtype=torch.float64,
+                              device="cuda"))
+    t = tqr.tqr_batch_submit(dev, Ts, tiles)
+    return t, dev, Ts
+
+
+def test_batch_equals_factoring_each_alone():
+    torch_cuda()
+    shapes = inputs.batch_shapes(40, seed=3, m_lo=16, m_hi=700, n_lo=4)
+    mats = inputs.batch_matrices(shapes, seed=3)
+    tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
+    t, dev, Ts = _submit(mats, tiles)
+    rc, st = tqr.tqr_batch_wait(t, len(mats))
+    assert rc == 0 and not st.any()
+    for A, dA, T, (nb, ib) in zip(mats, dev, Ts, tiles):
+        F, Tr = _alone(A, nb, ib)
+        assert np.array_equal(to_host(dA), F)
+        assert np.array_equal(T.cpu().numpy(), Tr)
+    # a few against the oracle directly
+    for A, dA, (nb, ib) in list(zip(mats, dev, tiles))[:5]:
+        f = TL.tiled_qr(A, nb, ib)
+        assert np.max(np.abs(to_host(dA) - f.F)) <= 1e-11 * max(1.0, np.abs(f.F).max())
+
+
+def test_batch_graph_replay_with_new_data_and_poll():
+    torch = torch_cuda()
+    shapes = [(200, 120), (64, 64), (333, 17), (90, 90)]
+    tiles = [(64, 16), (32, 8), (32, 16), (48, 16)]
+    for seed in (11, 12):      # second submission replays the captured graph
+        mats = [inputs.normal_matrix(m, n, seed * 100 + a) for a, (m, n) in enumerate(shapes)]
+        t, dev, Ts = _submit(mats, tiles)
+        done = False
+        for _ in range(100000):
+            done, rc, st = tqr.tqr_batch_poll(t, len(mats))
+            if done:
+                break
+        if not done:
+            rc, st = tqr.tqr_batch_wait(t, len(mats))
+        assert rc == 0 and not st.any()
+        for A, dA, (nb, ib) in zip(mats, dev, tiles):
+            F, _ = _alone(A, nb, ib)
+            assert np.array_equal(to_host(dA), F)
+    assert tqr.lib().tqr_batch_poll(987654321, tqr.ctypes.byref(tqr.ctypes.c_int(0)), None) == -1

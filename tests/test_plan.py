@@ -108,7 +108,7 @@ def expected_tasks(mode, g, trsm=0):
         if mode == APPLY_Q:
             out += [(LARFB_N, s, k, k, j, 0) for j in cols for s in range(g.slabs(j))]
             out += [(SSRFB_N, s, k, i, j, 0) for i in range(k + 1, g.p) for j in cols for s in range(g.slabs(j))]
-    if mode == TRSM or (mode == FACTOR and trsm):
+    if mode == TRSM or (mode in (FACTOR, APPLY_QT) and trsm):
         for j in range(g.q, g.q + g.qb):
             for s in range(g.slabs(j)):
                 for k in range(g.kt):
@@ -238,6 +238,24 @@ def test_apply_plans(m, n, nb, ib, cs, nrhs):
         for t in random_valid_order(mode, g, plan, 1):
             execute(g, t)
         assert np.allclose(g.B[:m, :nrhs], ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("m,n,nb,ib,cs,nrhs", [(70, 45, 16, 8, 8, 3), (64, 64, 16, 4, 16, 17), (50, 16, 8, 8, 8, 1)])
+def test_resident_factor_solve_plan(m, n, nb, ib, cs, nrhs):
+    """Q^T B followed by back substitution on an existing factorization
+    (the solve of a repeated matrix) as one plan."""
+    A = inputs.normal_matrix(m, n, 15)
+    B = inputs.normal_matrix(m, nrhs, 16)
+    f = TL.tiled_qr(A, nb, ib)
+    g = Grid(m, n, nb, ib, cs, nrhs)
+    g.A[:] = f.Ap
+    g.T = dict(f.T)
+    g.B[:m, :nrhs] = B
+    plan, _ = plan_of(APPLY_QT, g, trsm=1)
+    check_order_satisfies_waits(APPLY_QT, g, plan)
+    for t in random_valid_order(APPLY_QT, g, plan, 2):
+        execute(g, t)
+    assert np.allclose(g.B[:n, :nrhs], LS.lstsq(A, B), atol=1e-11)
 
 
 @pytest.mark.parametrize("n,nb,cs,nrhs", [(45, 16, 8, 3), (64, 16, 16, 2), (20, 8, 8, 9)])
