@@ -201,6 +201,49 @@ int tqr_batch_poll(uint64_t ticket, int* done, int* status_per_item);
 int tqr_batch_wait(uint64_t ticket, int* status_per_item);
 
 /*
+ * Least-squares request server with continuous batching.
+ *
+ * Requests enter a FIFO queue; `slots` worker threads, each with its own
+ * CUDA stream, admit a request as soon as a slot is free and the HBM budget
+ * has room, so requests that arrive while others run start at once and their
+ * task graphs overlap on the device (every persistent launch of a request is
+ * capped at grid_cap CTAs; 0 = 2 * SMs * 2 / slots).  Factorizations stay
+ * resident under the caller's matrix id (least recently used first out when
+ * the budget is needed): a later request with the same id, size and
+ * precision class skips the factorization (Q^T B and the back substitution
+ * only, plus refinement for the FP32 class).
+ *
+ *   tqr_server_create(budget_bytes, slots, grid_cap, &server)
+ *   tqr_server_submit(server, matrix_id, m, n, nrhs, A, lda, B, ldb, X, ldx,
+ *                     prec, tol, &request)
+ *       A (m x n), B (m x nrhs, 1 <= nrhs <= 16) and X (n x nrhs) are device
+ *       pointers owned by the caller; A and B must stay unchanged and X
+ *       untouched until the request completes.  prec: TQR_PREC_FP64 (plain
+ *       FP64) or TQR_PREC_FP32 (FP32 factorization, FP64-residual refinement
+ *       to backward error <= tol).  Returns at once.
+ *   tqr_server_poll(server, request, &done, &status, &iters, &berr,
+ *                   &latency_ms, &reused)   non-blocking; once done the
+ *       request is forgotten.  latency_ms counts from submit to completion.
+ *   tqr_server_wait(...)                     blocking form
+ *   tqr_server_stats(server, out[8])         completed, p50 and p99 latency
+ *       (ms) over completed requests, resident+running bytes, requests that
+ *       reused a resident factorization, failed, queued, resident entries
+ *   tqr_server_destroy(server)               finishes queued requests, frees
+ * Every call returns 0 or -i for invalid argument i.
+ */
+typedef struct tqr_server tqr_server;
+int tqr_server_create(size_t hbm_budget_bytes, int slots, int grid_cap, tqr_server** out);
+int tqr_server_submit(tqr_server* server, uint64_t matrix_id, int64_t m, int64_t n, int64_t nrhs,
+                      const double* A, int64_t lda, const double* B, int64_t ldb, double* X,
+                      int64_t ldx, int prec, double tol, uint64_t* request);
+int tqr_server_poll(tqr_server* server, uint64_t request, int* done, int* status, int* iters,
+                    double* berr, double* latency_ms, int* reused);
+int tqr_server_wait(tqr_server* server, uint64_t request, int* status, int* iters, double* berr,
+                    double* latency_ms, int* reused);
+int tqr_server_stats(tqr_server* server, double* out);
+int tqr_server_destroy(tqr_server* server);
+
+/*
  * tqr_factor without any memory allocation.  (The paper has no counterpart:
  * this is a deployment variant of Algorithm 1.)
  *

@@ -122,7 +122,7 @@ static PlanKey key_of(const Inst& I, int esize, int grid, int dev, int policy) {
   return PlanKey(I.mode, I.m, I.n, I.nb, I.ib, I.cs, I.nrhs, I.trsm, esize, grid, dev, policy);
 }
 
-std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int* status) {
+std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int* status, int grid_cap) {
   int dev = 0;
   cudaGetDevice(&dev);
   const int sms = device_sms();
@@ -136,6 +136,7 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
   // grid: at most ctas_per_sm CTAs per SM (and the debug cap)
   int max_grid = sms * ctas_per_sm;
   if (max_ctas > 0 && max_ctas < max_grid) max_grid = max_ctas;
+  if (grid_cap > 0 && grid_cap < max_grid) max_grid = grid_cap;
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
@@ -256,9 +257,9 @@ WsLayout ws_layout(const Inst& I, int esize, bool with_t) {
 // Clears the counters and control block, uploads the instance and runs the
 // plan.  `I` must already hold the device pointers.
 template <typename real>
-int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st) {
+int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st, int grid_cap) {
   int status = TQR_OK;
-  std::shared_ptr<DevPlan> plan = get_plan(I, sizeof(real), ctas_per_sm, &status);
+  std::shared_ptr<DevPlan> plan = get_plan(I, sizeof(real), ctas_per_sm, &status, grid_cap);
   if (!plan) return status;
   if (plan->ntasks == 0) return TQR_OK;
   if (cudaMemsetAsync(ws + W.oVer, 0, W.oCtl + ctl_bytes() - W.oVer, st) != cudaSuccess) return TQR_ERR_CUDA;
@@ -285,8 +286,8 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
   return TQR_OK;
 }
 
-template int run_plan<double>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t);
-template int run_plan<float>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t);
+template int run_plan<double>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t, int);
+template int run_plan<float>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t, int);
 
 // ---------------------------------------------------------------- pointers
 int ptr_kind(const void* p) {

@@ -24,8 +24,10 @@ long long wait_limit_ns();
 bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem);
 Inst make_inst(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm);
 WsLayout ws_layout(const Inst& I, int esize, bool with_t);
+// grid_cap > 0 limits the persistent grid (concurrent launches share SMs).
 template <typename real>
-int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st);
+int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st,
+             int grid_cap = 0);
 int ptr_kind(const void* p);
 int check_tiles(int nb, int ib, int arg_nb, int arg_ib);
 void clear_plans();

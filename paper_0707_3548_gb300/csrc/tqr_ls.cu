@@ -23,6 +23,7 @@
 #include "tqr.h"
 #include "tqr_api_internal.h"
 #include "tqr_engine.h"
+#include "tqr_ls.h"
 
 namespace tqr {
 
@@ -182,12 +183,6 @@ static int ew_grid(long long total) {
 }
 
 // FP64 helpers on the stream -------------------------------------------------
-struct LsScratch {
-  double* part;    // nsplit * m * nrhs
-  int nsplit;
-  int split_len;
-};
-
 static LsScratch ls_scratch_shape(int m, int n, int nrhs) {
   const int sms = device_sms();
   const int row_blocks = (m + kLsThreads - 1) / kLsThreads;
@@ -220,69 +215,127 @@ static cudaError_t atr(const double* A, long long lda, int m, int n, const doubl
   return cudaGetLastError();
 }
 
-// Backward error of (x, b): needs e = b - A x already in E.  Writes the
-// per-column norms squared of A^T e, x, b and ||A||_F^2 into nrm.
 struct BerrBufs {
   double* G;     // n x nrhs
   double* nrm;   // 3 * nrhs
 };
 
-static cudaError_t berr_terms(const double* A, long long lda, int m, int n, const double* E, const double* Xv,
-                              long long ldx, const double* Bv, long long ldb, int nrhs, const BerrBufs& bb,
-                              cudaStream_t st) {
-  cudaError_t e = atr(A, lda, m, n, E, m, nrhs, 1.0, bb.G, n, st);
-  if (e != cudaSuccess) return e;
-  col_sumsq<<<nrhs, kLsThreads, 0, st>>>(bb.G, n, n, bb.nrm);
-  col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Xv, ldx, n, bb.nrm + nrhs);
-  col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Bv, ldb, m, bb.nrm + 2 * nrhs);
-  return cudaGetLastError();
-}
-
-static double berr_host(const std::vector<double>& h, int nrhs, double nA2) {
-  const double nA = std::sqrt(nA2);
-  double worst = 0.0;
-  for (int c = 0; c < nrhs; ++c) {
-    const double num = std::sqrt(h[c]);
-    const double den = nA * (nA * std::sqrt(h[nrhs + c]) + std::sqrt(h[2 * nrhs + c]));
-    const double eta = den > 0 ? num / den : (num > 0 ? INFINITY : 0.0);
-    if (!(eta <= worst)) worst = eta;  // NaN-propagating max
-  }
-  return worst;
-}
-
 static size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
 // ---------------------------------------------------------------------------
-static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* A, int64_t lda, const double* B,
-                        int64_t ldb, double* X, int64_t ldx, int prec, double tol, int maxit, int* iters_out,
-                        double* berr_out, int nb, int ib, cudaStream_t st) {
-  const int m = static_cast<int>(m64), n = static_cast<int>(n64), nrhs = static_cast<int>(nrhs64);
-  const int esize = prec == TQR_PREC_FP64 ? 8 : 4;
-  int cs, occ, smem;
-  if (!choose_shape(nb, ib, esize, &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
-  Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, nrhs, 1);
-  const WsLayout W = ws_layout(I, esize, true);
-  LsScratch sc = ls_scratch_shape(m, n, nrhs);
-  const size_t mr = static_cast<size_t>(m) * nrhs, nr = static_cast<size_t>(n) * nrhs;
-  // FP64 vectors
+// LsJob: device state of one least-squares problem.  The tiles of A (and T)
+// double as a resident factorization: after factor_solve() a later solve()
+// with new right-hand sides reuses them (Q^T B and back substitution only).
+bool LsJob::init(int m_, int n_, int rhs_cap_, int nb_, int ib_, int prec_, int grid_cap_) {
+  m = m_;
+  n = n_;
+  rhs_cap = rhs_cap_;
+  nb = nb_;
+  ib = ib_;
+  prec = prec_;
+  esize = prec == TQR_PREC_FP64 ? 8 : 4;
+  grid_cap = grid_cap_;
+  if (!choose_shape(nb, ib, esize, &cs, &occ, &smem)) return false;
+  I = make_inst(M_FACTOR, m, n, nb, ib, cs, rhs_cap, 1);
+  W = ws_layout(I, esize, true);
+  sc = ls_scratch_shape(m, n, rhs_cap);
+  const size_t mr = static_cast<size_t>(m) * rhs_cap, nr = static_cast<size_t>(n) * rhs_cap;
   size_t o = al(W.bytes);
-  const size_t o_part = o;  o += al(sizeof(double) * sc.nsplit * mr);
-  const size_t o_e = o;     o += al(sizeof(double) * mr);
-  const size_t o_r = o;     o += al(sizeof(double) * mr);
-  const size_t o_f = o;     o += al(sizeof(double) * mr);
-  const size_t o_d = o;     o += al(sizeof(double) * mr);
-  const size_t o_g = o;     o += al(sizeof(double) * nr);
-  const size_t o_h = o;     o += al(sizeof(double) * nr);
-  const size_t o_x = o;     o += al(sizeof(double) * nr);
-  const size_t o_G = o;     o += al(sizeof(double) * nr);
-  const size_t o_nrm = o;   o += al(sizeof(double) * (4 * nrhs + 4));
-  const size_t total = o;
-  char* ws = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), total, st) != cudaSuccess) {
-    cudaGetLastError();
-    return TQR_ERR_NOMEM;
-  }
+  o_part = o;  o += al(sizeof(double) * sc.nsplit * mr);
+  o_e = o;     o += al(sizeof(double) * mr);
+  o_r = o;     o += al(sizeof(double) * mr);
+  o_f = o;     o += al(sizeof(double) * mr);
+  o_d = o;     o += al(sizeof(double) * mr);
+  o_g = o;     o += al(sizeof(double) * std::max(nr, static_cast<size_t>(n)));
+  o_h = o;     o += al(sizeof(double) * nr);
+  o_x = o;     o += al(sizeof(double) * nr);
+  o_G = o;     o += al(sizeof(double) * nr);
+  o_nrm = o;   o += al(sizeof(double) * (4 * rhs_cap + 4));
+  o_acopy = o;
+  bytes = o;
+  return true;
+}
+
+size_t LsJob::bytes_with_acopy() const { return bytes + al(sizeof(double) * static_cast<size_t>(m) * n); }
+
+void LsJob::bind(char* base, bool with_acopy) {
+  ws = base;
   sc.part = reinterpret_cast<double*>(ws + o_part);
+  I.A = ws + W.oA;
+  I.B = ws + W.oB;
+  I.T = ws + W.oT;
+  I.ver = reinterpret_cast<int*>(ws + W.oVer);
+  Acopy = with_acopy ? reinterpret_cast<double*>(ws + o_acopy) : nullptr;
+}
+
+int LsJob::run_mode(int mode, int trsm, int nrhs_now, cudaStream_t st) {
+  I.mode = mode;
+  I.trsm = trsm;
+  I.nrhs = nrhs_now;
+  I.qb = (nrhs_now + nb - 1) / nb;
+  return esize == 8 ? run_plan<double>(I, ws, W, occ, smem, st, grid_cap)
+                    : run_plan<float>(I, ws, W, occ, smem, st, grid_cap);
+}
+
+int LsJob::pack_rhs(const double* src, long long lds, int rows, int nrhs, cudaStream_t st) {
+  const int sms = device_sms();
+  const int qb = (nrhs + nb - 1) / nb;
+  cudaError_t e = esize == 8
+                      ? launch_pack<double>(src, lds, rows, nrhs, static_cast<double*>(I.B), I.p, qb, nb, sms, st)
+                      : launch_pack<float>(src, lds, rows, nrhs, static_cast<float*>(I.B), I.p, qb, nb, sms, st);
+  return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
+}
+
+int LsJob::unpack_rhs(double* dst, long long ldd, int rows, int nrhs, cudaStream_t st) {
+  const int sms = device_sms();
+  cudaError_t e = esize == 8
+                      ? launch_unpack<double>(static_cast<double*>(I.B), I.p, nb, dst, ldd, rows, nrhs, sms, st)
+                      : launch_unpack<float>(static_cast<float*>(I.B), I.p, nb, dst, ldd, rows, nrhs, sms, st);
+  return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
+}
+
+// factor A (and keep the factors), x0 = the solution through those factors
+int LsJob::factor_solve(const double* A, long long lda, const double* B, long long ldb, int nrhs, cudaStream_t st) {
+  const int sms = device_sms();
+  if (Acopy != nullptr &&
+      cudaMemcpy2DAsync(Acopy, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+    return TQR_ERR_CUDA;
+  cudaError_t e = esize == 8 ? launch_pack<double>(A, lda, m, n, static_cast<double*>(I.A), I.p, I.q, nb, sms, st)
+                             : launch_pack<float>(A, lda, m, n, static_cast<float*>(I.A), I.p, I.q, nb, sms, st);
+  if (e != cudaSuccess) return TQR_ERR_CUDA;
+  int s = pack_rhs(B, ldb, m, nrhs, st);
+  if (s == TQR_OK) s = run_mode(M_FACTOR, 1, nrhs, st);
+  if (s == TQR_OK) s = unpack_rhs(reinterpret_cast<double*>(ws + o_x), n, n, nrhs, st);
+  if (s == TQR_OK) {
+    double* dmm = reinterpret_cast<double*>(ws + o_nrm) + 4 * rhs_cap + 2;
+    if (esize == 8)
+      diag_minmax<double><<<1, kLsThreads, 0, st>>>(static_cast<double*>(I.A), I.p, nb, n, dmm);
+    else
+      diag_minmax<float><<<1, kLsThreads, 0, st>>>(static_cast<float*>(I.A), I.p, nb, n, dmm);
+    double* nA2 = reinterpret_cast<double*>(ws + o_nrm) + 4 * rhs_cap;
+    double* colsq = reinterpret_cast<double*>(ws + o_g);
+    col_sumsq<<<n, kLsThreads, 0, st>>>(A, lda, m, colsq);
+    col_sumsq<<<1, kLsThreads, 0, st>>>(colsq, n, n, nA2);
+    if (cudaGetLastError() != cudaSuccess) s = TQR_ERR_CUDA;
+  }
+  factored = (s == TQR_OK);
+  return s;
+}
+
+// x0 from the resident factors: Q^T B and back substitution, one graph
+int LsJob::solve(const double* B, long long ldb, int nrhs, cudaStream_t st) {
+  int s = pack_rhs(B, ldb, m, nrhs, st);
+  if (s == TQR_OK) s = run_mode(M_APPLY_QT, 1, nrhs, st);
+  if (s == TQR_OK) s = unpack_rhs(reinterpret_cast<double*>(ws + o_x), n, n, nrhs, st);
+  return s;
+}
+
+// Backward error of x, FP32 refinement, copy of x to X.  A is the FP64
+// matrix (caller's or the resident copy).
+int LsJob::finish(const double* A, long long lda, const double* B, long long ldb, int nrhs, double* X, long long ldx,
+                  double tol, int maxit, int* iters_out, double* berr_out, cudaStream_t st) {
+  const size_t mr = static_cast<size_t>(m) * nrhs, nr = static_cast<size_t>(n) * nrhs;
   double* E = reinterpret_cast<double*>(ws + o_e);
   double* Rr = reinterpret_cast<double*>(ws + o_r);
   double* F = reinterpret_cast<double*>(ws + o_f);
@@ -293,89 +346,56 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
   BerrBufs bb;
   bb.G = reinterpret_cast<double*>(ws + o_G);
   bb.nrm = reinterpret_cast<double*>(ws + o_nrm);
-  double* nA2 = bb.nrm + 3 * nrhs;       // ||A||_F^2
-  double* dmm = bb.nrm + 3 * nrhs + 2;   // min, max |r_ii|
-  I.A = ws + W.oA;
-  I.B = ws + W.oB;
-  I.T = ws + W.oT;
-  I.ver = reinterpret_cast<int*>(ws + W.oVer);
-  const int sms = device_sms();
+  const int R = rhs_cap;  // nrm layout: [0,R) |A^T e|^2, [R,2R) |x|^2, [2R,3R) |b|^2, [4R] |A|^2, [4R+2,4R+3] diag
+  double* dx2 = bb.nrm + 3 * R;
+  std::vector<double> hn(4 * R + 4);
   int status = TQR_OK;
   int iters = 0;
   double berr = INFINITY;
-  std::vector<double> hn(4 * nrhs + 4);
-  double* dx2 = bb.nrm + 3 * nrhs + 4;   // ||dx_c||^2 of the last correction
   auto fail = [&](int s) {
-    if (status == TQR_OK) status = s;
-  };
-  auto pack_rhs = [&](const double* src, long long lds, int rows) {
-    cudaError_t e = esize == 8 ? launch_pack<double>(src, lds, rows, nrhs, static_cast<double*>(I.B), I.p, I.qb, nb,
-                                                      sms, st)
-                               : launch_pack<float>(src, lds, rows, nrhs, static_cast<float*>(I.B), I.p, I.qb, nb, sms,
-                                                    st);
-    if (e != cudaSuccess) fail(TQR_ERR_CUDA);
-  };
-  auto unpack_rhs = [&](double* dst, long long ldd, int rows) {
-    cudaError_t e = esize == 8 ? launch_unpack<double>(static_cast<double*>(I.B), I.p, nb, dst, ldd, rows, nrhs, sms, st)
-                               : launch_unpack<float>(static_cast<float*>(I.B), I.p, nb, dst, ldd, rows, nrhs, sms, st);
-    if (e != cudaSuccess) fail(TQR_ERR_CUDA);
-  };
-  auto run = [&](int mode, int trsm) {
-    if (status != TQR_OK) return;
-    I.mode = mode;
-    I.trsm = trsm;
-    const int s = esize == 8 ? run_plan<double>(I, ws, W, occ, smem, st) : run_plan<float>(I, ws, W, occ, smem, st);
-    fail(s);
+    if (status == TQR_OK && s != TQR_OK) status = s;
   };
   auto read_back = [&]() {
     if (cudaMemcpyAsync(hn.data(), bb.nrm, sizeof(double) * hn.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       fail(TQR_ERR_CUDA);
   };
-  // factor + Q^T B + back substitution, one graph
-  {
-    cudaError_t e = esize == 8 ? launch_pack<double>(A, lda, m, n, static_cast<double*>(I.A), I.p, I.q, nb, sms, st)
-                               : launch_pack<float>(A, lda, m, n, static_cast<float*>(I.A), I.p, I.q, nb, sms, st);
-    if (e != cudaSuccess) fail(TQR_ERR_CUDA);
-  }
-  pack_rhs(B, ldb, m);
-  run(M_FACTOR, 1);
-  unpack_rhs(Xw, n, n);
-  if (status == TQR_OK) {
-    if (esize == 8)
-      diag_minmax<double><<<1, kLsThreads, 0, st>>>(static_cast<double*>(I.A), I.p, nb, n, dmm);
-    else
-      diag_minmax<float><<<1, kLsThreads, 0, st>>>(static_cast<float*>(I.A), I.p, nb, n, dmm);
-  }
-  // ||A||_F^2 as the sum of column sums of squares (A may have lda > m)
-  if (status == TQR_OK) {
-    double* colsq = Gv;  // n entries (nrhs >= 1 so Gv holds at least n)
-    col_sumsq<<<n, kLsThreads, 0, st>>>(A, lda, m, colsq);
-    col_sumsq<<<1, kLsThreads, 0, st>>>(colsq, n, n, nA2);
-    if (cudaGetLastError() != cudaSuccess) fail(TQR_ERR_CUDA);
-  }
-  if (status == TQR_OK) {
-    // e = b - A x, backward-error terms
+  auto berr_of = [&]() {
+    double worst = 0.0;
+    const double nA = std::sqrt(hn[4 * R]);
+    for (int c = 0; c < nrhs; ++c) {
+      const double num = std::sqrt(hn[c]);
+      const double den = nA * (nA * std::sqrt(hn[R + c]) + std::sqrt(hn[2 * R + c]));
+      const double eta = den > 0 ? num / den : (num > 0 ? INFINITY : 0.0);
+      if (!(eta <= worst)) worst = eta;
+    }
+    return worst;
+  };
+  auto terms = [&]() {
     if (resid(sc, A, lda, m, n, Xw, n, nrhs, B, ldb, 1.0, nullptr, 0, 0.0, E, m, st) != cudaSuccess ||
-        berr_terms(A, lda, m, n, E, Xw, n, B, ldb, nrhs, bb, st) != cudaSuccess)
+        atr(A, lda, m, n, E, m, nrhs, 1.0, bb.G, n, st) != cudaSuccess)
       fail(TQR_ERR_CUDA);
-    read_back();
-  }
+    col_sumsq<<<nrhs, kLsThreads, 0, st>>>(bb.G, n, n, bb.nrm);
+    col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Xw, n, n, bb.nrm + R);
+    col_sumsq<<<nrhs, kLsThreads, 0, st>>>(B, ldb, m, bb.nrm + 2 * R);
+    if (cudaGetLastError() != cudaSuccess) fail(TQR_ERR_CUDA);
+  };
+  terms();
+  read_back();
   if (status == TQR_OK) {
     // numerical rank test on R with the FP64 unit roundoff in both precisions:
     // an FP32 factor with a small pivot may still refine to an FP64 answer,
     // so refinement, not this test, judges the FP32 path
     const double eps = 1.1102230246251565e-16;
-    if (!(hn[3 * nrhs + 2] > n * eps * hn[3 * nrhs + 3])) status = TQR_ERR_RANK;
-    berr = berr_host(hn, nrhs, hn[3 * nrhs]);
+    if (!(hn[4 * R + 2] > n * eps * hn[4 * R + 3])) status = TQR_ERR_RANK;
+    berr = berr_of();
   }
   if (status == TQR_OK && esize == 4) {
-    // augmented-system refinement; r starts as the residual of x0
-    if (cudaMemcpyAsync(Rr, E, sizeof(double) * mr, cudaMemcpyDeviceToDevice, st) != cudaSuccess) fail(TQR_ERR_CUDA);
     // Refine until the backward error meets tol AND the last correction no
     // longer moves x beyond FP64 rounding (||dx|| <= 2^-50 ||x||), so the
     // answer matches an FP64 solve; stop early on stagnation (neither the
     // backward error nor the correction halves for 3 steps) or at maxit.
+    if (cudaMemcpyAsync(Rr, E, sizeof(double) * mr, cudaMemcpyDeviceToDevice, st) != cudaSuccess) fail(TQR_ERR_CUDA);
     double prev = berr, prev_dx = INFINITY, dxrel = INFINITY;
     int stall = 0;
     while (status == TQR_OK && (berr > tol || dxrel > 0x1p-50) && iters < maxit) {
@@ -383,37 +403,35 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
       axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, E, m, -1.0, Rr, m, F, m);
       if (atr(A, lda, m, n, Rr, m, nrhs, -1.0, Gv, n, st) != cudaSuccess) fail(TQR_ERR_CUDA);
       // h = R^-T g
-      pack_rhs(Gv, n, n);
-      run(M_TRSMT, 0);
-      unpack_rhs(H, n, n);
+      fail(pack_rhs(Gv, n, n, nrhs, st));
+      if (status == TQR_OK) fail(run_mode(M_TRSMT, 0, nrhs, st));
+      fail(unpack_rhs(H, n, n, nrhs, st));
       // d = Q^T f
-      pack_rhs(F, m, m);
-      run(M_APPLY_QT, 0);
-      unpack_rhs(D, m, m);
+      fail(pack_rhs(F, m, m, nrhs, st));
+      if (status == TQR_OK) fail(run_mode(M_APPLY_QT, 0, nrhs, st));
+      fail(unpack_rhs(D, m, m, nrhs, st));
       // dx = R^-1 (d1 - h)
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, D, m, -1.0, H, n, Gv, n);
-      pack_rhs(Gv, n, n);
-      run(M_TRSM, 0);
-      unpack_rhs(Gv, n, n);
+      fail(pack_rhs(Gv, n, n, nrhs, st));
+      if (status == TQR_OK) fail(run_mode(M_TRSM, 0, nrhs, st));
+      fail(unpack_rhs(Gv, n, n, nrhs, st));
       col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0, Gv, n, Xw, n);
       // dr = Q [h; d2]
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, H, n, 0.0, nullptr, 0, D, m);
-      pack_rhs(D, m, m);
-      run(M_APPLY_Q, 0);
-      unpack_rhs(D, m, m);
+      fail(pack_rhs(D, m, m, nrhs, st));
+      if (status == TQR_OK) fail(run_mode(M_APPLY_Q, 0, nrhs, st));
+      fail(unpack_rhs(D, m, m, nrhs, st));
       axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, Rr, m, 1.0, D, m, Rr, m);
       ++iters;
-      if (resid(sc, A, lda, m, n, Xw, n, nrhs, B, ldb, 1.0, nullptr, 0, 0.0, E, m, st) != cudaSuccess ||
-          berr_terms(A, lda, m, n, E, Xw, n, B, ldb, nrhs, bb, st) != cudaSuccess)
-        fail(TQR_ERR_CUDA);
+      terms();
       read_back();
       if (status != TQR_OK) break;
-      berr = berr_host(hn, nrhs, hn[3 * nrhs]);
+      berr = berr_of();
       dxrel = 0.0;
       for (int c = 0; c < nrhs; ++c) {
-        const double xr = std::sqrt(hn[nrhs + c]);
-        const double d = std::sqrt(hn[3 * nrhs + 4 + c]);
+        const double xr = std::sqrt(hn[R + c]);
+        const double d = std::sqrt(hn[3 * R + c]);
         const double rel = xr > 0 ? d / xr : d;
         if (!(rel <= dxrel)) dxrel = rel;
       }
@@ -427,16 +445,34 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
     }
     if (status == TQR_OK && !(berr <= tol)) status = TQR_ERR_NOCONV;
   }
-  // X = x (also on NOCONV / RANK: the best available solution)
-  if (cudaMemcpy2DAsync(X, sizeof(double) * ldx, Xw, sizeof(double) * n, sizeof(double) * n, nrhs,
+  if (X != nullptr &&
+      cudaMemcpy2DAsync(X, sizeof(double) * ldx, Xw, sizeof(double) * n, sizeof(double) * n, nrhs,
                         cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     fail(TQR_ERR_CUDA);
-  cudaFreeAsync(ws, st);
-  int dev_status = TQR_OK;
-  if (read_status(&dev_status, st) != cudaSuccess) fail(TQR_ERR_CUDA);
-  if (dev_status != TQR_OK) status = dev_status;
   if (iters_out) *iters_out = iters;
   if (berr_out) *berr_out = berr;
+  return status;
+}
+
+static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* A, int64_t lda, const double* B,
+                        int64_t ldb, double* X, int64_t ldx, int prec, double tol, int maxit, int* iters_out,
+                        double* berr_out, int nb, int ib, cudaStream_t st) {
+  LsJob job;
+  if (!job.init(static_cast<int>(m64), static_cast<int>(n64), static_cast<int>(nrhs64), nb, ib, prec, 0))
+    return TQR_ERR_UNSUPPORTED;
+  char* ws = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), job.bytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return TQR_ERR_NOMEM;
+  }
+  job.bind(ws, false);
+  int status = job.factor_solve(A, lda, B, ldb, static_cast<int>(nrhs64), st);
+  if (status == TQR_OK)
+    status = job.finish(A, lda, B, ldb, static_cast<int>(nrhs64), X, ldx, tol, maxit, iters_out, berr_out, st);
+  cudaFreeAsync(ws, st);
+  int dev_status = TQR_OK;
+  if (read_status(&dev_status, st) != cudaSuccess && status == TQR_OK) status = TQR_ERR_CUDA;
+  if (dev_status != TQR_OK) status = dev_status;
   return status;
 }
 

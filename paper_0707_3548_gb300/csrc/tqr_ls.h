@@ -1,0 +1,45 @@
+// tqr_ls.h -- one least-squares problem's device state (tqr_ls.cu), shared by
+// tqr_solve_ls and the request server.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "tqr_api_internal.h"
+#include "tqr_graph.h"
+
+namespace tqr {
+
+struct LsScratch {
+  double* part;  // nsplit * m * nrhs partial products
+  int nsplit;
+  int split_len;
+};
+
+struct LsJob {
+  int m = 0, n = 0, rhs_cap = 0, nb = 0, ib = 0, prec = 0, esize = 8;
+  int cs = 0, occ = 0, smem = 0, grid_cap = 0;
+  Inst I = {};
+  WsLayout W = {};
+  LsScratch sc = {};
+  size_t o_part = 0, o_e = 0, o_r = 0, o_f = 0, o_d = 0, o_g = 0, o_h = 0, o_x = 0, o_G = 0, o_nrm = 0, o_acopy = 0;
+  size_t bytes = 0;  // workspace without the FP64 copy of A
+  char* ws = nullptr;
+  double* Acopy = nullptr;
+  bool factored = false;
+
+  // sizes for m x n with up to rhs_cap right-hand sides; false if the tile
+  // shape is unsupported
+  bool init(int m, int n, int rhs_cap, int nb, int ib, int prec, int grid_cap);
+  size_t bytes_with_acopy() const;
+  void bind(char* base, bool with_acopy);
+  int factor_solve(const double* A, long long lda, const double* B, long long ldb, int nrhs, cudaStream_t st);
+  int solve(const double* B, long long ldb, int nrhs, cudaStream_t st);
+  int finish(const double* A, long long lda, const double* B, long long ldb, int nrhs, double* X, long long ldx,
+             double tol, int maxit, int* iters, double* berr, cudaStream_t st);
+  int run_mode(int mode, int trsm, int nrhs, cudaStream_t st);
+  int pack_rhs(const double* src, long long lds, int rows, int nrhs, cudaStream_t st);
+  int unpack_rhs(double* dst, long long ldd, int rows, int nrhs, cudaStream_t st);
+};
+
+}  // namespace tqr

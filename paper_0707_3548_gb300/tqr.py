@@ -63,6 +63,16 @@ SIGNATURES = {
                             ctypes.POINTER(_int), ctypes.POINTER(_dbl), _int, _int, _vp]),
     "tqr_factor_noalloc": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp]),
     "tqr_autotune": (_int, [_i64, _i64, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "tqr_server_create": (_int, [_size, _int, _int, ctypes.POINTER(_vp)]),
+    "tqr_server_submit": (_int, [_vp, ctypes.c_uint64, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int,
+                                 _dbl, ctypes.POINTER(ctypes.c_uint64)]),
+    "tqr_server_poll": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                               ctypes.POINTER(_int), ctypes.POINTER(_dbl), ctypes.POINTER(_dbl),
+                               ctypes.POINTER(_int)]),
+    "tqr_server_wait": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_int), ctypes.POINTER(_int),
+                               ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_int)]),
+    "tqr_server_stats": (_int, [_vp, _vp]),
+    "tqr_server_destroy": (_int, [_vp]),
     "tqr_batch_submit": (_int, [_int, _vp, ctypes.POINTER(ctypes.c_uint64), _vp]),
     "tqr_batch_poll": (_int, [ctypes.c_uint64, ctypes.POINTER(_int), _vp]),
     "tqr_batch_wait": (_int, [ctypes.c_uint64, _vp]),
@@ -333,3 +343,54 @@ def tqr_debug_fp64_peak(stream=None):
     t = _dbl(0)
     _check("tqr_debug_fp64_peak", lib().tqr_debug_fp64_peak(ctypes.byref(t), _stream(True, stream)))
     return t.value
+
+
+class Server:
+    """Thin wrapper of the tqr_server_* calls (device tensors only)."""
+
+    def __init__(self, budget_bytes, slots=4, grid_cap=0):
+        h = _vp()
+        _check("tqr_server_create", lib().tqr_server_create(int(budget_bytes), slots, grid_cap, ctypes.byref(h)))
+        self.h = h
+
+    def submit(self, matrix_id, A, B, X, prec=TQR_PREC_FP64, tol=1e-12):
+        pa, m, n, lda, _ = _mat(A, "A")
+        pb, mb, nrhs, ldb, _ = _mat(B, "B")
+        px, _, _, ldx, _ = _mat(X, "X")
+        r = ctypes.c_uint64(0)
+        _check("tqr_server_submit", lib().tqr_server_submit(self.h, matrix_id, m, n, nrhs, pa, lda, pb, ldb, px, ldx,
+                                                             prec, tol, ctypes.byref(r)))
+        return r.value
+
+    def _out(self):
+        return _int(0), _int(0), _dbl(0), _dbl(0), _int(0)
+
+    def poll(self, request):
+        done = _int(0)
+        st, it, be, lat, ru = self._out()
+        rc = lib().tqr_server_poll(self.h, request, ctypes.byref(done), ctypes.byref(st), ctypes.byref(it),
+                                   ctypes.byref(be), ctypes.byref(lat), ctypes.byref(ru))
+        if rc != 0:
+            raise TqrError("tqr_server_poll", rc)
+        if not done.value:
+            return None
+        return dict(status=st.value, iters=it.value, berr=be.value, latency_ms=lat.value, reused=ru.value)
+
+    def wait(self, request):
+        st, it, be, lat, ru = self._out()
+        rc = lib().tqr_server_wait(self.h, request, ctypes.byref(st), ctypes.byref(it), ctypes.byref(be),
+                                   ctypes.byref(lat), ctypes.byref(ru))
+        if rc != 0:
+            raise TqrError("tqr_server_wait", rc)
+        return dict(status=st.value, iters=it.value, berr=be.value, latency_ms=lat.value, reused=ru.value)
+
+    def stats(self):
+        out = np.zeros(8)
+        _check("tqr_server_stats", lib().tqr_server_stats(self.h, out.ctypes.data))
+        keys = ("completed", "p50_ms", "p99_ms", "bytes_in_use", "reused", "failed", "queued", "resident")
+        return dict(zip(keys, out.tolist()))
+
+    def close(self):
+        if self.h:
+            lib().tqr_server_destroy(self.h)
+            self.h = None
