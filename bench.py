@@ -44,6 +44,11 @@ WORKLOADS = {
     "ls16384x4096k1e5": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e5, ls=True),
     "ls16384x4096k1e8": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e8, ls=True),
     "ls4096x1024k1e2": dict(m=4096, n=1024, nb=128, ib=32, kappa=1e2, ls=True),
+    # served least-squares stream: Poisson arrivals, m log-uniform [128, 8192],
+    # n uniform [64, m/2], 1-16 right-hand sides, 30% repeat-A, FP64 and
+    # refined-FP32 classes, 64 GB HBM budget
+    "serve": dict(rate=2000.0, window=1.0, budget=64 << 30, slots=4, pool_bytes=2 << 30, serve=True),
+    "serve_low": dict(rate=20.0, window=5.0, budget=64 << 30, slots=4, pool_bytes=2 << 30, serve=True),
 }
 METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs FP64 peak"
 
@@ -388,6 +393,88 @@ def run_ls(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_serve(args, w):
+    """Open-loop request stream against the LS server.  The timed region runs
+    from the first submission to the last completion; latency is submit to
+    completion per request (server clock)."""
+    import threading
+
+    import numpy as np
+    import torch
+
+    from paper_0707_3548_gb300 import build as B
+    from paper_0707_3548_gb300 import inputs, tqr
+
+    torch.cuda.set_device(0)
+    B.build()
+    rate = args.rate or w["rate"]
+    window = args.window or w["window"]
+    reqs, mats = inputs.serving_stream(rate, window, seed=0)
+    # distinct matrix data is drawn into a bounded pool; a later matrix id
+    # reuses the leading m x n block of the smallest pool matrix that covers
+    # it (its own identity is kept: a new id is factored again)
+    pool, view_of, used = [], {}, 0
+    for m, n, mid in mats:
+        cover = [k for k, d in enumerate(pool) if d.shape[0] >= m and d.shape[1] >= n]
+        if used + 8 * m * n > w["pool_bytes"] and cover:
+            k = min(cover, key=lambda k: pool[k].numel())
+            view_of[mid] = pool[k][:m, :n]
+            continue
+        A = inputs.normal_matrix(m, n, 10_000 + mid)
+        pool.append(tqr.colmajor(torch.from_numpy(A).cuda()))
+        used += 8 * m * n
+        view_of[mid] = pool[-1]
+    rhs = []
+    for r, q in enumerate(reqs):
+        Bh = inputs.normal_matrix(q["m"], q["nrhs"], 50_000 + r)
+        rhs.append(tqr.colmajor(torch.from_numpy(Bh).cuda()))
+    outs = [tqr.colmajor(torch.zeros((q["n"], q["nrhs"]), dtype=torch.float64, device="cuda")) for q in reqs]
+    torch.cuda.synchronize()
+    srv = tqr.Server(w["budget"], slots=w["slots"])
+    # warm the plan cache and kernels with a few requests outside the window
+    for k, q in enumerate(reqs[:3]):
+        Xw = tqr.colmajor(torch.zeros((q["n"], q["nrhs"]), dtype=torch.float64, device="cuda"))
+        srv.wait(srv.submit(10**9 + q["matrix"], view_of[q["matrix"]], rhs[k], Xw,
+                            prec=tqr.TQR_PREC_FP32 if q["prec"] == "fp32r" else tqr.TQR_PREC_FP64))
+    base = srv.stats()
+    ids = [None] * len(reqs)
+    t0 = time.perf_counter()
+
+    def feeder():
+        for k, q in enumerate(reqs):
+            dt = q["t"] - (time.perf_counter() - t0)
+            if dt > 0:
+                time.sleep(dt)
+            ids[k] = srv.submit(q["matrix"], view_of[q["matrix"]], rhs[k], outs[k],
+                                prec=tqr.TQR_PREC_FP32 if q["prec"] == "fp32r" else tqr.TQR_PREC_FP64)
+
+    th = threading.Thread(target=feeder)
+    th.start()
+    th.join()
+    infos = [srv.wait(r) for r in ids]
+    t1 = time.perf_counter()
+    stats = srv.stats()
+    srv.close()
+    lat = {c: sorted(i["latency_ms"] for i, q in zip(infos, reqs) if q["prec"] == c) for c in ("fp64", "fp32r")}
+    def pct(v, p):
+        return v[min(len(v) - 1, int(p * (len(v) - 1) + 0.5))] if v else None
+    allv = sorted(i["latency_ms"] for i in infos)
+    bad = sum(1 for i in infos if i["status"] != 0)
+    line = {"metric": "LS solves/s + p99 latency (served stream)", "value": len(reqs) / (t1 - t0), "unit": "solves/s",
+            "n_gpus": 1, "steps": 1, "warmup": 3, "ms_per_step": 1e3 * (t1 - t0), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64 / f32+f64 refined",
+            "data": "synthetic: Poisson stream seed 0; matrix data from a %.1f GB pool" % (w["pool_bytes"] / 2**30),
+            "config": {"workload": "served LS stream %.0f req/s for %.1f s, %d requests, %d matrices, budget %d GB, %d slots"
+                       % (rate, window, len(reqs), len(mats), w["budget"] >> 30, w["slots"])},
+            "offered_per_s": len(reqs) / window, "completed": len(reqs) - bad, "failed": bad,
+            "p50_ms": pct(allv, 0.5), "p99_ms": pct(allv, 0.99),
+            "classes": {c: {"count": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)} for c, v in lat.items()},
+            "reused_resident": stats["reused"] - base["reused"],
+            "max_iters_fp32r": max([i["iters"] for i, q in zip(infos, reqs) if q["prec"] == "fp32r"] or [0]),
+            "max_berr": max(i["berr"] for i in infos)}
+    print(json.dumps(line), flush=True)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -399,6 +486,8 @@ def main():
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--nb", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--ib", type=int, default=0, help="override the workload's inner block size")
+    ap.add_argument("--rate", type=float, default=0.0, help="serve: arrival rate (req/s)")
+    ap.add_argument("--window", type=float, default=0.0, help="serve: arrival window (s)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.nb:
@@ -409,6 +498,8 @@ def main():
         run_reference(args, w)
     elif w.get("ls"):
         run_ls(args, w)
+    elif w.get("serve"):
+        run_serve(args, w)
     else:
         run_ours(args, w)
 

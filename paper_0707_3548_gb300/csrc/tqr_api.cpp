@@ -116,7 +116,41 @@ struct DevPlan {
 typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int> PlanKey;
 
 static std::list<std::pair<PlanKey, std::shared_ptr<DevPlan>>> g_plans;
-static const size_t kMaxPlans = 24;
+static const size_t kMaxPlans = 64;
+
+// Launches keep their plan alive until their completion event fires: a plan
+// evicted from the cache while a kernel on some stream still reads its task
+// list is freed only after that kernel is done.
+static std::list<std::pair<cudaEvent_t, std::shared_ptr<DevPlan>>> g_inflight;
+static std::vector<cudaEvent_t> g_event_pool;
+
+static void prune_inflight_locked() {
+  for (auto it = g_inflight.begin(); it != g_inflight.end();) {
+    if (cudaEventQuery(it->first) == cudaSuccess) {
+      g_event_pool.push_back(it->first);
+      it = g_inflight.erase(it);
+    } else {
+      cudaGetLastError();
+      ++it;
+    }
+  }
+}
+
+static void hold_until_done(const std::shared_ptr<DevPlan>& plan, cudaStream_t st) {
+  std::lock_guard<std::mutex> lk(g_mu);
+  prune_inflight_locked();
+  cudaEvent_t ev = nullptr;
+  if (!g_event_pool.empty()) {
+    ev = g_event_pool.back();
+    g_event_pool.pop_back();
+  } else if (cudaEventCreateWithFlags(&ev, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    cudaStreamSynchronize(st);  // no event: keep the plan alive by waiting
+    return;
+  }
+  cudaEventRecord(ev, st);
+  g_inflight.emplace_back(ev, plan);
+}
 
 static PlanKey key_of(const Inst& I, int esize, int grid, int dev, int policy) {
   return PlanKey(I.mode, I.m, I.n, I.nb, I.ib, I.cs, I.nrhs, I.trsm, esize, grid, dev, policy);
@@ -229,6 +263,7 @@ int timing_read(double* ms, int64_t* launches) {
 void clear_plans() {
   std::lock_guard<std::mutex> lk(g_mu);
   g_plans.clear();
+  prune_inflight_locked();
 }
 
 // ---------------------------------------------------------------- workspace
@@ -279,6 +314,7 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
     std::lock_guard<std::mutex> lk(g_mu);
     g_timing.pending.push_back(ev);
   }
+  hold_until_done(plan, st);
   if (e != cudaSuccess) {
     set_last_error(cudaGetErrorString(e));
     return TQR_ERR_CUDA;

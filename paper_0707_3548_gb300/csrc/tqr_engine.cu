@@ -214,35 +214,52 @@ __device__ void apply_block(const real* __restrict__ V, int ldv, int nv, const r
                             int ib, int w, real* W, bool trans) {
   const int tid = threadIdx.x;
   const int nout = ib * w;
-  for (int o = tid; o < nout; o += kThreads) {
-    const int r = o % ib, c = o / ib;
-    const real* vr = V + r * ldv;
-    const real* sc = S + c * lds;
-    real a0 = Top[r + c * ldt], a1 = real(0);
-    if (L != nullptr)
-      for (int t = r + 1; t < ib; ++t) a1 += L[t + r * ldl] * Top[t + c * ldt];
-    int t = 0;
-    for (; t + 3 < nv; t += 4) {
-      a0 += vr[t] * sc[t];
-      a1 += vr[t + 1] * sc[t + 1];
-      a0 += vr[t + 2] * sc[t + 2];
-      a1 += vr[t + 3] * sc[t + 3];
+  // Phase 1: W(r,c) = Top(r,c) + sum_{t>r} L(t,r) Top(t,c) + sum_t V(t,r) S(t,c).
+  // Each output is one FMA chain seeded with Top(r,c); a thread carries two
+  // outputs (o and o + kThreads) for instruction-level parallelism, so no
+  // FP64 instruction is spent beyond the multiply-adds themselves.
+  for (int o = tid; o < nout; o += 2 * kThreads) {
+    const int o2 = o + kThreads;
+    const bool two = o2 < nout;
+    const int r1 = o % ib, c1 = o / ib;
+    const int r2 = two ? o2 % ib : r1, c2 = two ? o2 / ib : c1;
+    const real* v1 = V + r1 * ldv;
+    const real* v2 = V + r2 * ldv;
+    const real* s1 = S + c1 * lds;
+    const real* s2 = S + c2 * lds;
+    real a1 = Top[r1 + c1 * ldt], a2 = Top[r2 + c2 * ldt];
+    if (L != nullptr) {
+      for (int t = r1 + 1; t < ib; ++t) a1 = fma(L[t + r1 * ldl], Top[t + c1 * ldt], a1);
+      for (int t = r2 + 1; t < ib; ++t) a2 = fma(L[t + r2 * ldl], Top[t + c2 * ldt], a2);
     }
-    for (; t < nv; ++t) a0 += vr[t] * sc[t];
-    W[o] = a0 + a1;
+    if (two) {
+#pragma unroll 4
+      for (int t = 0; t < nv; ++t) {
+        a1 = fma(v1[t], s1[t], a1);
+        a2 = fma(v2[t], s2[t], a2);
+      }
+      W[o2] = a2;
+    } else {
+#pragma unroll 4
+      for (int t = 0; t < nv; ++t) a1 = fma(v1[t], s1[t], a1);
+    }
+    W[o] = a1;
   }
   __syncthreads();
+  // Phase 2: W = T^T W (trans) or T W, T upper triangular.
   real tmp[kMaxOutPerThread];
   {
     int cnt = 0;
     for (int o = tid; o < nout; o += kThreads, ++cnt) {
       const int r = o % ib, c = o / ib;
       const real* wc = W + c * ib;
-      real a = real(0);
+      real a;
       if (trans) {
-        for (int s = 0; s <= r; ++s) a += Tm[s + r * ldT] * wc[s];
+        a = Tm[r * ldT] * wc[0];
+        for (int s = 1; s <= r; ++s) a = fma(Tm[s + r * ldT], wc[s], a);
       } else {
-        for (int s = r; s < ib; ++s) a += Tm[r + s * ldT] * wc[s];
+        a = Tm[r + r * ldT] * wc[r];
+        for (int s = r + 1; s < ib; ++s) a = fma(Tm[r + s * ldT], wc[s], a);
       }
       tmp[cnt] = a;
     }
@@ -253,26 +270,37 @@ __device__ void apply_block(const real* __restrict__ V, int ldv, int nv, const r
     for (int o = tid; o < nout; o += kThreads, ++cnt) W[o] = tmp[cnt];
   }
   __syncthreads();
+  // Phase 3: Top -= L W (unit lower), S -= V W; single FMA chains seeded with
+  // the old value, two outputs per thread.
   for (int o = tid; o < nout; o += kThreads) {
     const int r = o % ib, c = o / ib;
     const real* wc = W + c * ib;
-    real a = wc[r];
+    real a = Top[r + c * ldt] - wc[r];
     if (L != nullptr)
-      for (int t = 0; t < r; ++t) a += L[r + t * ldl] * wc[t];
-    Top[r + c * ldt] -= a;
+      for (int t = 0; t < r; ++t) a = fma(-L[r + t * ldl], wc[t], a);
+    Top[r + c * ldt] = a;
   }
   const int nS = nv * w;
-  for (int o = tid; o < nS; o += kThreads) {
-    const int t = o % nv, c = o / nv;
-    const real* wc = W + c * ib;
-    real a0 = real(0), a1 = real(0);
-    int r = 0;
-    for (; r + 1 < ib; r += 2) {
-      a0 += V[t + r * ldv] * wc[r];
-      a1 += V[t + (r + 1) * ldv] * wc[r + 1];
+  for (int o = tid; o < nS; o += 2 * kThreads) {
+    const int o2 = o + kThreads;
+    const bool two = o2 < nS;
+    const int t1 = o % nv, c1 = o / nv;
+    const int t2 = two ? o2 % nv : t1, c2 = two ? o2 / nv : c1;
+    const real* w1 = W + c1 * ib;
+    const real* w2 = W + c2 * ib;
+    real a1 = S[t1 + c1 * lds], a2 = S[t2 + c2 * lds];
+    if (two) {
+#pragma unroll 4
+      for (int r = 0; r < ib; ++r) {
+        a1 = fma(-V[t1 + r * ldv], w1[r], a1);
+        a2 = fma(-V[t2 + r * ldv], w2[r], a2);
+      }
+      S[t2 + c2 * lds] = a2;
+    } else {
+#pragma unroll 4
+      for (int r = 0; r < ib; ++r) a1 = fma(-V[t1 + r * ldv], w1[r], a1);
     }
-    if (r < ib) a0 += V[t + r * ldv] * wc[r];
-    S[t + c * lds] -= a0 + a1;
+    S[t1 + c1 * lds] = a1;
   }
   __syncthreads();
 }
@@ -969,11 +997,18 @@ cudaError_t launch_unpack_batched(const PackDesc* d, int count, cudaStream_t st)
   return cudaGetLastError();
 }
 
+// The kernel's dynamic shared-memory limit is set to the per-block maximum
+// (the same value every time): launches from several host threads with
+// different tile shapes must not lower it under one another.  Occupancy is
+// set by each launch's own size, not by this limit.
+constexpr int kMaxDynSmem = 232448;
+
 template <typename real>
 cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
                        int smem_bytes, cudaStream_t st) {
+  if (smem_bytes > kMaxDynSmem) return cudaErrorInvalidValue;
   cudaError_t e = cudaFuncSetAttribute(run_tasks_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_bytes);
+                                       kMaxDynSmem);
   if (e != cudaSuccess) return e;
   run_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl), limit_ns);
   return cudaGetLastError();
@@ -982,7 +1017,7 @@ cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* 
 template <typename real>
 cudaError_t occupancy(int smem_bytes, int* blocks_per_sm) {
   cudaError_t e = cudaFuncSetAttribute(run_tasks_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       smem_bytes);
+                                       kMaxDynSmem);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, run_tasks_kernel<real>, kThreads, smem_bytes);
 }

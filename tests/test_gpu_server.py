@@ -61,7 +61,8 @@ def test_server_results_same_alone_and_in_the_mix():
         X_alone, info_alone = _run(alone_server, dmats, reqs, one_at_a_time=True)
     finally:
         alone_server.close()
-    assert stats["completed"] == len(reqs) and stats["failed"] == 0
+    bad = [(k, i["status"], i["iters"], i["berr"]) for k, i in enumerate(info_mix + info_alone) if i["status"] != 0]
+    assert stats["completed"] == len(reqs) and stats["failed"] == 0, bad
     assert stats["reused"] == sum(i["reused"] for i in info_mix) > 0
     for (mid, B, prec), xm, xa, im, ia in zip(reqs, X_mix, X_alone, info_mix, info_alone):
         assert im["status"] == 0 and ia["status"] == 0
