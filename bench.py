@@ -1,12 +1,13 @@
 #!/usr/bin/env python
 """Benchmark of the GB300 tiled Householder QR (libtqr).
 
-Default workload: one 8192 x 8192 FP64 factorization, entries N(0,1) from
-NumPy PCG64 seed 0, tile nb = 128, inner block ib = 16 -- one point of the
-square-size sweep of the plain-FP64 tiled QR (the fastest (nb, ib) of the
-nb in {128, 192, 256} x ib in {16, 32, 64} sweep at this size).  A step restores the matrix
-from a pristine device copy and calls tqr_factor (pack to Block Data Layout,
-the persistent task kernel, unpack).  The 512 MiB input is larger than L2.
+Default workload: one 16384 x 16384 FP64 factorization, entries N(0,1) from
+NumPy PCG64 seed 0, tile nb = 128, inner block ib = 16 -- the largest square
+of the plain-FP64 tiled QR sweep (nb = 128, ib = 16 was the fastest of the
+nb in {128, 192, 256} x ib in {16, 32, 64} grid measured at n = 8192).  A step
+restores the matrix from a pristine device copy and calls tqr_factor (pack to
+Block Data Layout, the persistent task kernel, unpack).  The 2 GiB input is
+larger than L2.
 
 Metric: TFLOP/s counting 2 m n^2 - 2 n^3 / 3 per factorization, and its
 fraction of this GPU's FP64 FMA peak (measured in the run by a DFMA probe).
@@ -481,7 +482,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qr8192", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="qr16384", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--nb", type=int, default=0, help="override the workload's tile size")

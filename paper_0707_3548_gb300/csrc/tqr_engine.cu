@@ -124,7 +124,7 @@ __device__ int g_status;  // sticky device status of asynchronous launches
 
 template <typename real>
 struct Ctx {
-  real *P, *T, *S, *Top, *W, *Rb;
+  real *P, *T, *S, *Top, *W, *Rb, *Part;
   double* red;       // reduction scratch (>= 2*kThreads + 160 doubles)
   uint32_t bar;
   uint32_t phase;
@@ -305,102 +305,258 @@ __device__ void apply_block(const real* __restrict__ V, int ldv, int nv, const r
   __syncthreads();
 }
 
-// Householder reflector for column c of a panel (LAPACK convention; FP64):
-// warp 0 computes ||x2|| over x2[0..len) (stride 1), then lane 0 derives
-// beta = -sign(alpha) ||[alpha; x2]||, tau = (beta - alpha)/beta and the scale
-// 1/(alpha - beta) of v, and stores them in red[0..2] (tau also in taus[c]).
-// The sum of squares is taken directly when max|x| lies in [2^-500, 2^500]
-// (no intermediate can overflow or lose the result to underflow there);
-// otherwise it is recomputed on x scaled by an exact power of two.
+// FP32 form of apply_block with 4 x 4 register micro-tiles (the FP32 pipe is
+// ~58x the FP64 one, so here shared-memory traffic, not arithmetic, is the
+// limit).  Requires ib, w, nv multiples of 4, leading dimensions multiples of
+// 4 and 16-byte aligned V, S (checked by the caller).
+//   Phase 1: W = Top + L^T Top + V^T S.  The (ib/4) x (w/4) micro-tiles are
+//            split over the rows of V and S (split-K); each thread writes its
+//            16 partial sums to Part, then every output sums its partials in
+//            a fixed order (deterministic).
+//   Phase 3: S -= V W with one 4 x 4 micro-tile per thread per pass.
+__device__ void apply_block_f32(const float* __restrict__ V, int ldv, int nv, const float* __restrict__ L, int ldl,
+                                float* Top, int ldt, float* S, int lds, const float* __restrict__ Tm, int ldT,
+                                int ib, int w, float* W, float* Part, bool trans) {
+  const int tid = threadIdx.x;
+  const int nout = ib * w;
+  const int rt = ib / 4, MT = rt * (w / 4);
+  const int KS = kThreads / MT;
+  const int chunk = ((nv + 4 * KS - 1) / (4 * KS)) * 4;
+  {
+    const int tile = tid % MT, ks = tid / MT;
+    if (ks < KS) {
+      const int r0 = 4 * (tile % rt), c0 = 4 * (tile / rt);
+      float acc[4][4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) acc[i][j] = 0.f;
+      const int t1 = min(nv, (ks + 1) * chunk);
+      for (int t = ks * chunk; t < t1; t += 4) {
+        float4 vq[4], sq[4];
+#pragma unroll
+        for (int i = 0; i < 4; ++i) vq[i] = *reinterpret_cast<const float4*>(V + t + (r0 + i) * ldv);
+#pragma unroll
+        for (int j = 0; j < 4; ++j) sq[j] = *reinterpret_cast<const float4*>(S + t + (c0 + j) * lds);
+#pragma unroll
+        for (int i = 0; i < 4; ++i)
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            acc[i][j] = fmaf(vq[i].x, sq[j].x, acc[i][j]);
+            acc[i][j] = fmaf(vq[i].y, sq[j].y, acc[i][j]);
+            acc[i][j] = fmaf(vq[i].z, sq[j].z, acc[i][j]);
+            acc[i][j] = fmaf(vq[i].w, sq[j].w, acc[i][j]);
+          }
+      }
+      float* pp = Part + (ks * MT + tile) * 16;
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) pp[i * 4 + j] = acc[i][j];
+    }
+  }
+  __syncthreads();
+  for (int o = tid; o < nout; o += kThreads) {
+    const int r = o % ib, c = o / ib;
+    const int tile = (r / 4) + (c / 4) * rt;
+    float a = Top[r + c * ldt];
+    if (L != nullptr)
+      for (int t = r + 1; t < ib; ++t) a = fmaf(L[t + r * ldl], Top[t + c * ldt], a);
+    for (int ks = 0; ks < KS; ++ks) a += Part[(ks * MT + tile) * 16 + (r % 4) * 4 + (c % 4)];
+    W[o] = a;
+  }
+  __syncthreads();
+  float tmp[kMaxOutPerThread];
+  {
+    int cnt = 0;
+    for (int o = tid; o < nout; o += kThreads, ++cnt) {
+      const int r = o % ib, c = o / ib;
+      const float* wc = W + c * ib;
+      float a;
+      if (trans) {
+        a = Tm[r * ldT] * wc[0];
+        for (int q = 1; q <= r; ++q) a = fmaf(Tm[q + r * ldT], wc[q], a);
+      } else {
+        a = Tm[r + r * ldT] * wc[r];
+        for (int q = r + 1; q < ib; ++q) a = fmaf(Tm[r + q * ldT], wc[q], a);
+      }
+      tmp[cnt] = a;
+    }
+  }
+  __syncthreads();
+  {
+    int cnt = 0;
+    for (int o = tid; o < nout; o += kThreads, ++cnt) W[o] = tmp[cnt];
+  }
+  __syncthreads();
+  for (int o = tid; o < nout; o += kThreads) {
+    const int r = o % ib, c = o / ib;
+    const float* wc = W + c * ib;
+    float a = Top[r + c * ldt] - wc[r];
+    if (L != nullptr)
+      for (int t = 0; t < r; ++t) a = fmaf(-L[r + t * ldl], wc[t], a);
+    Top[r + c * ldt] = a;
+  }
+  const int ntile = (nv / 4) * (w / 4);
+  for (int tile = tid; tile < ntile; tile += kThreads) {
+    const int t0 = 4 * (tile % (nv / 4)), c0 = 4 * (tile / (nv / 4));
+    float4 acc[4];
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[j] = *reinterpret_cast<const float4*>(S + t0 + (c0 + j) * lds);
+    for (int r = 0; r < ib; ++r) {
+      const float4 vq = *reinterpret_cast<const float4*>(V + t0 + r * ldv);
+#pragma unroll
+      for (int j = 0; j < 4; ++j) {
+        const float wv = W[r + (c0 + j) * ib];
+        acc[j].x = fmaf(-vq.x, wv, acc[j].x);
+        acc[j].y = fmaf(-vq.y, wv, acc[j].y);
+        acc[j].z = fmaf(-vq.z, wv, acc[j].z);
+        acc[j].w = fmaf(-vq.w, wv, acc[j].w);
+      }
+    }
+#pragma unroll
+    for (int j = 0; j < 4; ++j) *reinterpret_cast<float4*>(S + t0 + (c0 + j) * lds) = acc[j];
+  }
+  __syncthreads();
+}
+
+// Dispatch: the register-blocked FP32 form when the shapes allow it.
 template <typename real>
-__device__ void reflector(const real* x2, int len, real alpha_r, double* red, double* taus, int c) {
-  if (threadIdx.x >= 32) return;
-  const int lane = threadIdx.x;
+__device__ __forceinline__ void apply_any(const real* V, int ldv, int nv, const real* L, int ldl, real* Top, int ldt,
+                                          real* S, int lds, const real* Tm, int ldT, int ib, int w, real* W,
+                                          real* Part, bool trans) {
+  if constexpr (sizeof(real) == 4) {
+    const bool ok = (ib % 4 == 0) && (w % 4 == 0) && (nv % 4 == 0) && (ldv % 4 == 0) && (lds % 4 == 0) &&
+                    ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(S)) & 15) == 0 &&
+                    (ib / 4) * (w / 4) <= kThreads;
+    if (ok) {
+      apply_block_f32(V, ldv, nv, L, ldl, Top, ldt, S, lds, Tm, ldT, ib, w, W, Part, trans);
+      return;
+    }
+  }
+  apply_block<real>(V, ldv, nv, L, ldl, Top, ldt, S, lds, Tm, ldT, ib, w, W, trans);
+}
+
+// ||x|| over x[0..len) (stride 1) by one warp, in FP64; every lane returns
+// the same bits (xor-butterfly reductions).  The sum of squares is taken
+// directly when max|x| lies in [2^-500, 2^500] (no intermediate can overflow
+// or lose the result to underflow there); otherwise it is recomputed on x
+// scaled by an exact power of two.
+template <typename real>
+__device__ double warp_norm(const real* x, int len) {
+  const int lane = threadIdx.x & 31;
   double ssq = 0.0;
   unsigned long long mx = 0;
   for (int r = lane; r < len; r += 32) {
-    const double x = static_cast<double>(x2[r]);
-    ssq = fma(x, x, ssq);
-    const unsigned long long b = abs_bits(x2[r]);
+    const double v = static_cast<double>(x[r]);
+    ssq = fma(v, v, ssq);
+    const unsigned long long b = abs_bits(x[r]);
     mx = b > mx ? b : mx;
   }
   ssq = warp_sum(ssq);
   mx = warp_max_u64(mx);
   const double amax = __longlong_as_double(static_cast<long long>(mx));
-  double xnorm;
   if (amax != 0.0 && isfinite(amax) && (amax < 0x1p-500 || amax > 0x1p500)) {
     const int e = ilogb(amax);
     const double sc = scalbn(1.0, -e);
     double s2 = 0.0;
     for (int r = lane; r < len; r += 32) {
-      const double x = static_cast<double>(x2[r]) * sc;
-      s2 = fma(x, x, s2);
+      const double v = static_cast<double>(x[r]) * sc;
+      s2 = fma(v, v, s2);
     }
     s2 = warp_sum(s2);
-    xnorm = scalbn(sqrt(s2), e);
+    return scalbn(sqrt(s2), e);
+  }
+  return sqrt(ssq);
+}
+
+// Householder reflector (LAPACK convention, FP64) from alpha and ||x2||:
+//   beta = -sign(alpha) ||[alpha; x2]||, tau = (beta - alpha)/beta and the
+//   scale 1/(alpha - beta) of v.  Pure function of its inputs, so threads
+//   that call it on the same values agree bit for bit.
+struct Refl {
+  double tau, beta, scal;
+};
+
+__device__ __forceinline__ Refl make_refl(double alpha, double xnorm) {
+  Refl f;
+  if (xnorm == 0.0) {
+    f.tau = 0.0;
+    f.beta = alpha;
+    f.scal = 0.0;
   } else {
-    xnorm = sqrt(ssq);
+    const double h = hypot(alpha, xnorm);
+    f.beta = (alpha >= 0.0) ? -h : h;  // sign(0) = +1, also for -0.0
+    f.tau = (f.beta - alpha) / f.beta;
+    f.scal = 1.0 / (alpha - f.beta);
   }
-  if (lane == 0) {
-    const double alpha = static_cast<double>(alpha_r);
-    double tau, beta, scal;
-    if (xnorm == 0.0) {
-      tau = 0.0;
-      beta = alpha;
-      scal = 0.0;
-    } else {
-      const double h = hypot(alpha, xnorm);
-      beta = (alpha >= 0.0) ? -h : h;  // sign(0) = +1, also for -0.0
-      tau = (beta - alpha) / beta;
-      scal = 1.0 / (alpha - beta);
-    }
-    red[0] = tau;
-    red[1] = beta;
-    red[2] = scal;
-    taus[c] = tau;
-  }
+  return f;
 }
 
 // Unblocked QR of an ib-wide panel (DGEQR2 on the panel, Section 2).
-//   TS == false (GEQRT): P is nr x ib; reflector c has v = [1; P(c+1:nr, c)].
+//   TS == false (GEQRT): P is nr x ib; reflector c has v = [1; s x], x =
+//                        P(c+1:nr, c), s = 1/(alpha - beta).
 //   TS == true  (TSQRT): the top is the ib x ib triangle R (ld ldr) and P is
-//                        nr x ib below it; reflector c has v = [e_c; P(:, c)].
+//                        nr x ib below it; reflector c has v = [e_c; s x],
+//                        x = P(:, c).
+// One barrier per column.  The norm of column c's x2 was computed during
+// step c-1 by the warp that updated column c (warp 0), in the same pass, and
+// left in red[c & 1]; every thread derives the reflector from it.  The warps
+// owning columns d > c apply it with v formed on the fly from the unscaled x:
+// w = top + s (x^T p_d), p_d -= (tau w s) x, top -= tau w.  Column c itself
+// (v = s x, beta, tau) is written by warp 0 during the next step, when no
+// warp reads it.
 template <typename real, bool TS>
 __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, double* red, double* taus) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int nwarps = kThreads / 32;
-  for (int c = 0; c < ib; ++c) {
-    real* pc = P + c * ldP;
-    if constexpr (TS)
-      reflector<real>(pc, nr, R[c + c * ldr], red, taus, c);
-    else
-      reflector<real>(pc + c + 1, nr - c - 1, pc[c], red, taus, c);
-    __syncthreads();
-    const real tau = static_cast<real>(red[0]);
-    const real beta = static_cast<real>(red[1]);
-    const real scal = static_cast<real>(red[2]);
-    const int r0 = TS ? 0 : c + 1;
-    for (int r = r0 + tid; r < nr; r += kThreads) pc[r] *= scal;
-    __syncthreads();
-    if (tid == 0) {
-      if constexpr (TS)
-        R[c + c * ldr] = beta;
-      else
-        pc[c] = beta;
+  // norm of column 0's x2
+  if (wid == 0) {
+    const double xn = TS ? warp_norm<real>(P, nr) : warp_norm<real>(P + 1, nr - 1);
+    if (lane == 0) red[0] = xn;
+  }
+  __syncthreads();
+  Refl prev = {0.0, 0.0, 0.0};
+  for (int c = 0; c <= ib; ++c) {
+    // deferred writes of column c-1
+    if (wid == 0 && c > 0) {
+      real* pp = P + (c - 1) * ldP;
+      const int r0p = TS ? 0 : c;
+      const real sp = static_cast<real>(prev.scal);
+      for (int r = r0p + lane; r < nr; r += 32) pp[r] *= sp;
+      if (lane == 0) {
+        if constexpr (TS)
+          R[(c - 1) + (c - 1) * ldr] = static_cast<real>(prev.beta);
+        else
+          pp[c - 1] = static_cast<real>(prev.beta);
+        taus[c - 1] = prev.tau;
+      }
     }
-    if (tau != real(0)) {
-      for (int d = c + 1 + wid; d < ib; d += nwarps) {
-        real* pd = P + d * ldP;
+    if (c == ib) break;
+    real* pc = P + c * ldP;
+    const int r0 = TS ? 0 : c + 1;
+    real alpha_r;
+    if constexpr (TS)
+      alpha_r = R[c + c * ldr];
+    else
+      alpha_r = pc[c];
+    const Refl f = make_refl(static_cast<double>(alpha_r), red[c & 1]);
+    const real tau = static_cast<real>(f.tau);
+    const real scal = static_cast<real>(f.scal);
+    for (int d = c + 1 + wid; d < ib; d += nwarps) {
+      real* pd = P + d * ldP;
+      if (tau != real(0)) {
         real acc = real(0);
-        for (int r = r0 + lane; r < nr; r += 32) acc += pc[r] * pd[r];
+        for (int r = r0 + lane; r < nr; r += 32) acc = fma(pc[r], pd[r], acc);
         acc = warp_sum(acc);
         real top;
         if constexpr (TS)
           top = R[c + d * ldr];
         else
           top = pd[c];
-        const real wv = tau * (top + acc);
-        for (int r = r0 + lane; r < nr; r += 32) pd[r] -= wv * pc[r];
+        const real wv = tau * fma(scal, acc, top);
+        const real coef = -(wv * scal);
+        for (int r = r0 + lane; r < nr; r += 32) pd[r] = fma(coef, pc[r], pd[r]);
         if (lane == 0) {
           if constexpr (TS)
             R[c + d * ldr] = top - wv;
@@ -408,9 +564,17 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
             pd[c] = top - wv;
         }
       }
+      if (d == c + 1) {
+        // this warp owns the next column: its norm, for step c + 1
+        __syncwarp();
+        const double xn = TS ? warp_norm<real>(pd, nr) : warp_norm<real>(pd + c + 2, nr - c - 2);
+        if (lane == 0) red[(c + 1) & 1] = xn;
+      }
     }
+    prev = f;
     __syncthreads();
   }
+  __syncthreads();
 }
 
 // Compact-WY T of the panel's reflectors (DLARFT, forward, columnwise):
@@ -501,8 +665,8 @@ __device__ void exec_geqrt(Ctx<real>& cx, const Inst& I, int k) {
       const int w = nb - c0 < cs ? nb - c0 : cs;
       load_block(cx.S, cx.ldS, A + l0 + static_cast<long long>(c0) * nb, nb, nr, w);
       __syncthreads();
-      apply_block<real>(cx.P + ib, cx.ldP, nr - ib, cx.P, cx.ldP, cx.S, cx.ldS, cx.S + ib, cx.ldS, cx.T, cx.ldT,
-                        ib, w, cx.W, true);
+      apply_any<real>(cx.P + ib, cx.ldP, nr - ib, cx.P, cx.ldP, cx.S, cx.ldS, cx.S + ib, cx.ldS, cx.T, cx.ldT,
+                        ib, w, cx.W, cx.Part, true);
       store_block(A + l0 + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nr, w);
       __syncthreads();
     }
@@ -541,7 +705,7 @@ __device__ void exec_tsqrt(Ctx<real>& cx, const Inst& I, int k, int i) {
       load_block(cx.Top, ib, Rt + l0 + static_cast<long long>(c0) * nb, nb, ib, w);
       bulk_cols(cx, cx.S, cx.ldS, Ai + static_cast<long long>(c0) * nb, nb, nb, w);
       __syncthreads();
-      apply_block<real>(cx.P, cx.ldP, nb, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, true);
+      apply_any<real>(cx.P, cx.ldP, nb, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, true);
       store_block(Rt + l0 + static_cast<long long>(c0) * nb, nb, cx.Top, ib, ib, w);
       store_block(Ai + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nb, w);
       __syncthreads();
@@ -571,8 +735,8 @@ __device__ void exec_larfb(Ctx<real>& cx, const Inst& I, int k, int j, int s, bo
     }
     load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
     __syncthreads();
-    apply_block<real>(cx.P + ib, cx.ldP, nr - ib, cx.P, cx.ldP, cx.S + l0, cx.ldS, cx.S + l0 + ib, cx.ldS, cx.T,
-                      cx.ldT, ib, w, cx.W, trans);
+    apply_any<real>(cx.P + ib, cx.ldP, nr - ib, cx.P, cx.ldP, cx.S + l0, cx.ldS, cx.S + l0 + ib, cx.ldS, cx.T,
+                      cx.ldT, ib, w, cx.W, cx.Part, trans);
   }
   store_block(C, nb, cx.S, cx.ldS, nb, w);
   __syncthreads();
@@ -597,7 +761,7 @@ __device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int i, int j, in
     load_block(cx.Top, ib, Ct + l0, nb, ib, w);
     bulk_cols(cx, cx.P, cx.ldP, Vt + static_cast<long long>(l0) * nb, nb, nb, ib);
     __syncthreads();
-    apply_block<real>(cx.P, cx.ldP, nb, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, trans);
+    apply_any<real>(cx.P, cx.ldP, nb, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, trans);
     store_block(Ct + l0, nb, cx.Top, ib, ib, w);
     __syncthreads();
   }
@@ -849,6 +1013,7 @@ __global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __rest
       cx.Top = reinterpret_cast<real*>(smem + L.oTop);
       cx.W = reinterpret_cast<real*>(smem + L.oW);
       cx.red = reinterpret_cast<double*>(smem + L.oRed);
+      cx.Part = reinterpret_cast<real*>(smem + L.oPart);
       cx.Rb = L.r_in_s ? cx.S : cx.Top;
       cx.nb = I.nb;
       cx.ib = I.ib;
@@ -997,18 +1162,38 @@ cudaError_t launch_unpack_batched(const PackDesc* d, int count, cudaStream_t st)
   return cudaGetLastError();
 }
 
-// The kernel's dynamic shared-memory limit is set to the per-block maximum
-// (the same value every time): launches from several host threads with
-// different tile shapes must not lower it under one another.  Occupancy is
-// set by each launch's own size, not by this limit.
-constexpr int kMaxDynSmem = 232448;
+// The kernel's dynamic shared-memory limit is set to the largest value the
+// device allows (its opt-in per-block maximum minus the kernel's static
+// shared memory), the same value on every call: launches from several host
+// threads with different tile shapes must not lower it under one another.
+// Occupancy follows each launch's own size, not this limit.
+template <typename real>
+cudaError_t max_dyn_smem(int* out) {
+  int dev = 0, optin = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, run_tasks_kernel<real>);
+  if (e != cudaSuccess) return e;
+  *out = optin - static_cast<int>(fa.sharedSizeBytes);
+  return cudaSuccess;
+}
+
+template <typename real>
+cudaError_t set_max_dyn_smem(int smem_bytes) {
+  int mx = 0;
+  cudaError_t e = max_dyn_smem<real>(&mx);
+  if (e != cudaSuccess) return e;
+  if (smem_bytes > mx) return cudaErrorInvalidValue;
+  return cudaFuncSetAttribute(run_tasks_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+}
 
 template <typename real>
 cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
                        int smem_bytes, cudaStream_t st) {
-  if (smem_bytes > kMaxDynSmem) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(run_tasks_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kMaxDynSmem);
+  cudaError_t e = set_max_dyn_smem<real>(smem_bytes);
   if (e != cudaSuccess) return e;
   run_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl), limit_ns);
   return cudaGetLastError();
@@ -1016,8 +1201,7 @@ cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* 
 
 template <typename real>
 cudaError_t occupancy(int smem_bytes, int* blocks_per_sm) {
-  cudaError_t e = cudaFuncSetAttribute(run_tasks_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       kMaxDynSmem);
+  cudaError_t e = set_max_dyn_smem<real>(smem_bytes);
   if (e != cudaSuccess) return e;
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, run_tasks_kernel<real>, kThreads, smem_bytes);
 }

@@ -199,9 +199,10 @@ constexpr int kMaxOutPerThread = 8;
 //                  TSQRT's triangle)
 //   W   ib x cs    W = V^T S products
 //   Red doubles    reduction scratch and per-column scalars
+//   Part           FP32 only: split-K partials of the blocked W = V^T S
 //   Bar 8 bytes    mbarrier for the bulk (TMA) copies
 struct SmemLayout {
-  int oP, oT, oS, oTop, oW, oRed, oBar, bytes;
+  int oP, oT, oS, oTop, oW, oRed, oPart, oBar, bytes;
   bool r_in_s;
 };
 
@@ -225,6 +226,8 @@ TQR_HD SmemLayout smem_layout(int nb, int ib, int cs, int esize) {
   L.oTop = o; o += align16(top_elems * esize);
   L.oW = o;   o += align16(ib * cs * esize);
   L.oRed = o; o += align16((2 * kThreads + 2 * 64 + 32) * 8);
+  // FP32 only: split-K partial sums of the register-blocked update (16 per thread)
+  L.oPart = o; if (esize == 4) o += align16(kThreads * 16 * esize);
   L.oBar = o; o += 16;
   L.bytes = o;
   return L;
