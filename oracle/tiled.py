@@ -24,6 +24,9 @@ Readings of the paper used here (each listed with the design notes):
 * Edge tiles: A is zero-padded to p*b x q*b.  Zero rows stay zero under the
   reflectors and zero columns get tau = 0, so R[:m, :n] is unchanged.
 * The second loop of Algorithm 1 prints "i = k+1, k+1, ..."; read k+1, k+2, ...
+
+The end of the file adds the reduction-tree variant (tree_qr), an extension
+beyond the paper's flat panel.
 """
 
 import math
@@ -244,3 +247,140 @@ def form_q(f, ncols=None):
     if ncols is None:
         ncols = f.m
     return apply_q(f, np.eye(f.m, ncols))
+
+
+# ---------------------------------------------------------------------------
+# Reduction-tree variant (an extension: the paper's panel is the flat chain of
+# Algorithm 1).  For step k the rows k..p-1 are cut into domains of D tile
+# rows.  Each domain is factored as in Algorithm 1 with its first row as the
+# head (GEQRT on the head tile, TSQRT of the head's triangle with each later
+# row of the domain); then the heads' triangles are merged by a binary tree of
+# TTQRT (QR of two stacked upper triangles).  D >= p - k gives one domain:
+# exactly Algorithm 1.  TTQRT's reflectors are upper triangular and are
+# stored in the upper triangle of the eliminated head's tile (whose strictly
+# lower part keeps its GEQRT reflectors); their T factors are kept apart.
+
+def ttqrt(R1, R2, ib):
+    """TTQRT: QR of the upper triangle R1 stacked on the upper triangle R2.
+    This is TSQRT applied to [R1; triu(R2)]: the zeros below R2's diagonal
+    stay exactly zero, so V comes out upper triangular.  Returns (R, V, T)."""
+    return tsqrt(R1, np.triu(R2), ib)
+
+
+def tree_heads(k, p, D):
+    """Domain heads of step k: rows k, k+D, k+2D, ... below p."""
+    return list(range(k, p, D))
+
+
+def tree_merges(heads):
+    """Binary-tree merges of the heads, level by level: at level l the head
+    with index d (a multiple of 2^(l+1)) absorbs the head with index
+    d + 2^l.  Returns [(level, a_row, b_row)] in execution order."""
+    out = []
+    H = len(heads)
+    lvl = 0
+    while (1 << lvl) < H:
+        step = 1 << (lvl + 1)
+        for d in range(0, H, step):
+            if d + (1 << lvl) < H:
+                out.append((lvl, heads[d], heads[d + (1 << lvl)]))
+        lvl += 1
+    return out
+
+
+class TreeFactors(TiledFactors):
+    """Tiled factors of the tree variant: T for GEQRT/TSQRT keyed (i, k), T2
+    for TTQRT keyed (b, k) (b = the eliminated head)."""
+
+    def __init__(self, m, n, nb, ib, D, Ap, T, T2):
+        super().__init__(m, n, nb, ib, Ap, T)
+        self.D = D
+        self.T2 = T2
+
+
+def _tt_v(tile):
+    """The TTQRT reflectors stored in the upper triangle of a head tile."""
+    return np.triu(tile)
+
+
+def tree_qr(A, nb, ib, D):
+    """Tiled QR with a per-panel reduction tree (domains of D tile rows)."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    p, q = grid(m, n, nb)
+    Ap = np.zeros((p * nb, q * nb))
+    Ap[:m, :n] = A
+    f = TreeFactors(m, n, nb, ib, D, Ap, {}, {})
+    tile = f.tile
+    for k in range(min(p, q)):
+        heads = tree_heads(k, p, D)
+        for h in heads:
+            F, T = geqrt(tile(h, k), ib)
+            tile(h, k)[:] = F
+            f.T[(h, k)] = T
+            for j in range(k + 1, q):
+                tile(h, j)[:] = larfb(tile(h, j), tile(h, k), T, ib, trans=True)
+            for i in range(h + 1, min(h + D, p)):
+                R, V, T = tsqrt(tile(h, k), tile(i, k), ib)
+                tile(h, k)[:] = R
+                tile(i, k)[:] = V
+                f.T[(i, k)] = T
+                for j in range(k + 1, q):
+                    top, bot = ssrfb(tile(h, j), tile(i, j), V, T, ib, trans=True)
+                    tile(h, j)[:] = top
+                    tile(i, j)[:] = bot
+        for _, a, b in tree_merges(heads):
+            R, V, T = ttqrt(tile(a, k), tile(b, k), ib)
+            tile(a, k)[:] = R                                   # upper: merged R
+            tile(b, k)[:] = np.tril(tile(b, k), -1) + np.triu(V)  # upper: V_tt
+            f.T2[(b, k)] = T
+            for j in range(k + 1, q):
+                top, bot = ssrfb(tile(a, j), tile(b, j), _tt_v(tile(b, k)), T, ib, trans=True)
+                tile(a, j)[:] = top
+                tile(b, j)[:] = bot
+    return f
+
+
+def _tree_steps(f, B_rows_tile, trans):
+    """Q^T (trans) or Q applied to the row tiles of a right-hand side."""
+    nb, ib, D = f.nb, f.ib, f.D
+    kt = min(f.p, f.q)
+
+    def ops(k):
+        out = []
+        heads = tree_heads(k, f.p, D)
+        for h in heads:
+            out.append(("G", h, None))
+            for i in range(h + 1, min(h + D, f.p)):
+                out.append(("S", h, i))
+        for _, a, b in tree_merges(heads):
+            out.append(("T", a, b))
+        return out
+
+    steps = [(k, o) for k in range(kt) for o in ops(k)]
+    if not trans:
+        steps.reverse()
+    Bt = B_rows_tile
+    for k, (kind, a, b) in steps:
+        if kind == "G":
+            Bt(a)[:] = larfb(Bt(a), f.tile(a, k), f.T[(a, k)], ib, trans=trans)
+        elif kind == "S":
+            top, bot = ssrfb(Bt(a), Bt(b), f.tile(b, k), f.T[(b, k)], ib, trans=trans)
+            Bt(a)[:], Bt(b)[:] = top, bot
+        else:
+            top, bot = ssrfb(Bt(a), Bt(b), _tt_v(f.tile(b, k)), f.T2[(b, k)], ib, trans=trans)
+            Bt(a)[:], Bt(b)[:] = top, bot
+
+
+def tree_apply_qt(f, B):
+    Bp = _padded_rows(f, B)
+    nb = f.nb
+    _tree_steps(f, lambda i: Bp[i * nb:(i + 1) * nb], trans=True)
+    return Bp[:f.m]
+
+
+def tree_apply_q(f, B):
+    Bp = _padded_rows(f, B)
+    nb = f.nb
+    _tree_steps(f, lambda i: Bp[i * nb:(i + 1) * nb], trans=False)
+    return Bp[:f.m]
