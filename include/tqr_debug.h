@@ -23,30 +23,32 @@ extern "C" {
  *   cs       (arg 6)  slab width (columns) of the column-slab tasks; must
  *                     divide nb
  *   nrhs     (arg 7)  right-hand-side columns (0: none)
- *   trsm     (arg 8)  factor mode: append the back substitution (1) or not
- *   workers  (arg 9)  CTAs assumed by the list-scheduling simulation
- *   policy   (arg 10) -1 best of both, 0 paper priorities, 1 bottom level
- *   out      (arg 11) int32[8 * cap]: per task kind, s, inst, k, i, j, l, 0
+ *   trsm     (arg 8)  factor / apply-Q^T mode: append the back substitution
+ *   D        (arg 9)  0: Algorithm 1's flat panel; > 0: reduction-tree
+ *                     variant with domains of D tile rows
+ *   workers  (arg 10) CTAs assumed by the list-scheduling simulation
+ *   policy   (arg 11) -1 best of both, 0 paper priorities, 1 bottom level
+ *   out      (arg 12) int32[8 * cap]: per task kind, s, inst, k, i, j, l, 0
  *                     (may be NULL to query the count)
- *   cap      (arg 12) capacity of `out` in tasks
- *   stats    (arg 13) double[6] or NULL: chosen makespan, other makespan,
+ *   cap      (arg 13) capacity of `out` in tasks
+ *   stats    (arg 14) double[6] or NULL: chosen makespan, other makespan,
  *                     policy, edges, critical path, total work (seconds of
  *                     the cost model)
  * Returns the number of tasks (>= 0), or -i for invalid argument i, or
  * -100 if the rules contradict the sequential order (message via
  * tqr_debug_last_error).
  */
-int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int workers,
-                       int policy, int32_t* out, int64_t cap, double* stats);
+int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int D,
+                       int workers, int policy, int32_t* out, int64_t cap, double* stats);
 
 /*
  * The version waits and signals the device scheduler derives for one task
  * (kind, k, i, j, s, l as in tqr_debug_plan) of a launch described by
- * (mode, m, n, nb, ib, cs, nrhs).  waits: int32[4*3] (counter, count,
+ * (mode, m, n, nb, ib, cs, nrhs, D).  waits: int32[4*3] (counter, count,
  * version), signals: int32[2*2] (counter, count).  Returns
  * nwaits + 16 * nsignals.
  */
-int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, const int32_t* task,
+int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int D, const int32_t* task,
                     int32_t* waits, int32_t* signals);
 
 /*

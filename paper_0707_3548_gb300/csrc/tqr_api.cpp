@@ -77,6 +77,17 @@ bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* sme
   return true;
 }
 
+// Prefix tables of the tree variant for host-side planning, one per
+// (p, kt, D); kept for the life of the process (a few KB each).
+const int32_t* host_vtab(const Inst& I) {
+  static std::mutex mu;
+  static std::map<std::tuple<int, int, int>, std::vector<int32_t>> tabs;
+  std::lock_guard<std::mutex> lk(mu);
+  std::vector<int32_t>& v = tabs[std::make_tuple(I.p, I.kt, I.D)];
+  if (v.empty()) tree_table(I, v);
+  return v.data();
+}
+
 Inst make_inst(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm) {
   Inst I = {};
   I.m = static_cast<int>(m);

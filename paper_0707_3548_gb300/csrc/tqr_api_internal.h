@@ -32,6 +32,8 @@ int ptr_kind(const void* p);
 int check_tiles(int nb, int ib, int arg_nb, int arg_ib);
 void clear_plans();
 void autotune(int64_t m, int64_t n, int* nb, int* ib);
+// Host copy of the tree variant's prefix table for planning (Inst.D > 0).
+const int32_t* host_vtab(const Inst& I);
 void set_schedule(int policy, int max_ctas);
 int timing_enable(int on);
 int timing_read(double* ms, int64_t* launches);

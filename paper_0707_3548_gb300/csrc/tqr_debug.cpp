@@ -13,8 +13,8 @@ using namespace tqr;
 
 extern "C" {
 
-int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int workers,
-                       int policy, int32_t* out, int64_t cap, double* stats) {
+int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int D,
+                       int workers, int policy, int32_t* out, int64_t cap, double* stats) {
   if (mode < 0 || mode > 4) return -1;
   if (m < 1) return -2;
   if (n < 1) return -3;
@@ -23,9 +23,12 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   if (nrhs < 0) return -7;
   if (mode != 0 && nrhs == 0) return -7;
   if (trsm && (nrhs == 0 || m < n || (mode != 0 && mode != 1))) return -8;
-  if (workers < 1) return -9;
-  if (policy < -1 || policy > 1) return -10;
+  if (D < 0) return -9;
+  if (workers < 1) return -10;
+  if (policy < -1 || policy > 1) return -11;
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);
+  I.D = D;
+  if (D > 0) I.vtab = host_vtab(I);
   std::vector<TaskX> seq, ordered;
   seq_tasks(I, 0, seq);
   PlanStats st;
@@ -54,9 +57,11 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   return static_cast<int64_t>(seq.size());
 }
 
-int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, const int32_t* task,
+int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int D, const int32_t* task,
                     int32_t* waits, int32_t* signals) {
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, 1);
+  I.D = D;
+  if (D > 0) I.vtab = host_vtab(I);
   TaskX t;
   t.kind = task[0]; t.s = task[1]; t.inst = task[2]; t.k = task[3]; t.i = task[4]; t.j = task[5]; t.l = task[6];
   t.pad = 0;

@@ -45,7 +45,14 @@ enum Kind : int {
   K_TRSM_SOLVE = 7,  // X_k <- R_kk^-1 C_k
   K_TRSMT_UPD = 8,   // C_k <- C_k - R_lk^T X_l (l < k)
   K_TRSMT_SOLVE = 9, // X_k <- R_kk^-T C_k
-  K_NKINDS = 10
+  // reduction-tree variant (Inst.D > 0): TSQRT/SSRFB carry the domain head
+  // in l; GEQRT/LARFB act on head row i; TT kernels merge head l (kept) and
+  // head i (eliminated), whose tile keeps the TT reflectors in its upper
+  // triangle
+  K_TTQRT = 10,      // QR of the triangles of (l,k) and (i,k)
+  K_TTMQR = 11,      // slab s of [(l,j); (i,j)] <- Q_tt^T [.]
+  K_TTMQR_N = 12,    // slab s of [(l,j); (i,j)] <- Q_tt [.]
+  K_NKINDS = 13
 };
 
 enum Mode : int { M_FACTOR = 0, M_APPLY_QT = 1, M_APPLY_Q = 2, M_TRSM = 3, M_TRSMT = 4 };
@@ -68,7 +75,10 @@ struct Inst {
   int32_t nb, ib, cs, NS;   // NS = nb/cs slabs per full tile column
   int32_t mode;
   int32_t trsm;             // FACTOR mode: back substitution appended (1) or not (0)
-  int32_t pad0, pad1;
+  int32_t D;                // 0: Algorithm 1's flat panel; >0: domains of D tile rows + binary tree
+  int32_t pad0;
+  const int32_t* vtab;      // tree variant: writes per trailing tile of row r before step k,
+                            // vtab[k * p + r] for k = 0..kt (see tree_writes)
 };
 
 // Number of slabs of tile column j (A columns: NS; right-hand-side columns:
@@ -89,10 +99,145 @@ struct Wait { int ctr, cnt, ver; };
 // A signal: counters ctr .. ctr+cnt-1 are incremented.
 struct Signal { int ctr, cnt; };
 
+// ---- reduction-tree variant --------------------------------------------
+// Step k cuts rows k..p-1 into domains of D rows; domain d has head row
+// k + d*D.  Within a domain the head is GEQRT'ed and TSQRT'ed with each later
+// row (positions 1, 2, ... of the head's writers in the step); then the
+// heads merge in a binary tree: at level L head index d (multiple of 2^(L+1))
+// absorbs head d + 2^L, if present.
+struct TreePos {
+  int d, mi, h, dsz, H;  // domain, index in the domain (0 = head), head row, domain size, #domains
+};
+
+TQR_HD TreePos tree_pos(const Inst& I, int k, int r) {
+  TreePos t;
+  const int o = r - k;
+  t.d = o / I.D;
+  t.mi = o - t.d * I.D;
+  t.h = k + t.d * I.D;
+  t.dsz = (I.p - t.h) < I.D ? (I.p - t.h) : I.D;
+  t.H = (I.p - k + I.D - 1) / I.D;
+  return t;
+}
+
+// Merges head d takes part in as the surviving head at levels below lvl.
+TQR_HD int tree_cnt_a(int d, int lvl, int H) {
+  int c = 0;
+  for (int L = 0; L < lvl && (1 << L) < H; ++L)
+    if (d % (2 << L) == 0 && d + (1 << L) < H) ++c;
+  return c;
+}
+
+// Level at which head d (> 0) is eliminated: its lowest set bit.
+TQR_HD int tree_level(int d) {
+  int L = 0;
+  while (!(d & (1 << L))) ++L;
+  return L;
+}
+
+// Writes a trailing tile (or the panel tile) of row r >= k receives in step k.
+TQR_HD int tree_writes(const Inst& I, int k, int r) {
+  const TreePos t = tree_pos(I, k, r);
+  if (t.mi > 0) return 1;
+  return t.dsz + tree_cnt_a(t.d, 31, t.H) + (t.d > 0 ? 1 : 0);
+}
+
+TQR_HD int tree_base(const Inst& I, int k, int r) { return I.vtab[k * I.p + r]; }
+TQR_HD int tree_fin(const Inst& I, int r) { return I.vtab[I.kt * I.p + r]; }
+
+// Rules of the tree variant (all modes).  Forward modes (FACTOR, APPLY_QT)
+// need version base + pos for the writer at position pos of step k; APPLY_Q
+// replays the same writers in reverse, so it needs fin - 1 - (base + pos).
+TQR_HD int tree_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* nsig) {
+  const int kt = I.kt, NS = I.NS;
+  const int k = t.k, i = t.i, j = t.j, s = t.s, l = t.l;
+  const bool a_final = I.mode != M_FACTOR;
+  const bool rev = I.mode == M_APPLY_Q;
+  int nw = 0;
+  *nsig = 0;
+  auto ver = [&](int r, int pos) {
+    const int f = tree_base(I, k, r) + pos;
+    return rev ? tree_fin(I, r) - 1 - f : f;
+  };
+  switch (t.kind) {
+    case K_GEQRT:
+      w[nw++] = {ctr_index(I, i, k, 0), NS, tree_base(I, k, i)};
+      sg[(*nsig)++] = {ctr_index(I, i, k, 0), NS};
+      break;
+    case K_LARFB:
+    case K_LARFB_N:
+      if (!a_final) w[nw++] = {ctr_index(I, i, k, 0), NS, tree_base(I, k, i) + 1};
+      w[nw++] = {ctr_index(I, i, j, s), 1, ver(i, 0)};
+      sg[(*nsig)++] = {ctr_index(I, i, j, s), 1};
+      break;
+    case K_TSQRT: {
+      const TreePos ti = tree_pos(I, k, i);
+      w[nw++] = {ctr_index(I, l, k, 0), NS, tree_base(I, k, l) + ti.mi};
+      w[nw++] = {ctr_index(I, i, k, 0), NS, tree_base(I, k, i)};
+      sg[(*nsig)++] = {ctr_index(I, l, k, 0), NS};
+      sg[(*nsig)++] = {ctr_index(I, i, k, 0), NS};
+      break;
+    }
+    case K_SSRFB:
+    case K_SSRFB_N: {
+      const TreePos ti = tree_pos(I, k, i);
+      if (!a_final) w[nw++] = {ctr_index(I, i, k, 0), NS, tree_base(I, k, i) + 1};
+      w[nw++] = {ctr_index(I, l, j, s), 1, ver(l, ti.mi)};
+      w[nw++] = {ctr_index(I, i, j, s), 1, ver(i, 0)};
+      sg[(*nsig)++] = {ctr_index(I, l, j, s), 1};
+      sg[(*nsig)++] = {ctr_index(I, i, j, s), 1};
+      break;
+    }
+    case K_TTQRT:
+    case K_TTMQR:
+    case K_TTMQR_N: {
+      const TreePos ta = tree_pos(I, k, l), tb = tree_pos(I, k, i);
+      const int L = tree_level(tb.d);
+      const int pa = ta.dsz + tree_cnt_a(ta.d, L, ta.H);
+      const int pb = tb.dsz + tree_cnt_a(tb.d, L, tb.H);
+      if (t.kind == K_TTQRT) {
+        w[nw++] = {ctr_index(I, l, k, 0), NS, tree_base(I, k, l) + pa};
+        w[nw++] = {ctr_index(I, i, k, 0), NS, tree_base(I, k, i) + pb};
+        sg[(*nsig)++] = {ctr_index(I, l, k, 0), NS};
+        sg[(*nsig)++] = {ctr_index(I, i, k, 0), NS};
+      } else {
+        if (!a_final) w[nw++] = {ctr_index(I, i, k, 0), NS, tree_base(I, k, i) + pb + 1};
+        w[nw++] = {ctr_index(I, l, j, s), 1, ver(l, pa)};
+        w[nw++] = {ctr_index(I, i, j, s), 1, ver(i, pb)};
+        sg[(*nsig)++] = {ctr_index(I, l, j, s), 1};
+        sg[(*nsig)++] = {ctr_index(I, i, j, s), 1};
+      }
+      break;
+    }
+    case K_TRSM_UPD: {
+      // after the factorization (or Q^T B) every tile of row r has fin(r) writes
+      const bool fw = (I.mode == M_FACTOR || I.mode == M_APPLY_QT);
+      if (!a_final) w[nw++] = {ctr_index(I, k, l, 0), NS, tree_fin(I, k)};
+      w[nw++] = {ctr_index(I, l, j, s), 1, (fw ? tree_fin(I, l) : 0) + (kt - l)};
+      w[nw++] = {ctr_index(I, k, j, s), 1, (fw ? tree_fin(I, k) : 0) + (kt - 1 - l)};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    }
+    case K_TRSM_SOLVE: {
+      const bool fw = (I.mode == M_FACTOR || I.mode == M_APPLY_QT);
+      if (!a_final) w[nw++] = {ctr_index(I, k, k, 0), NS, tree_fin(I, k)};
+      w[nw++] = {ctr_index(I, k, j, s), 1, (fw ? tree_fin(I, k) : 0) + (kt - 1 - k)};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    }
+    default:
+      break;
+  }
+  return nw;
+}
+
 // Fills up to 4 waits and 2 signals; returns the number of waits, writes the
 // number of signals to *nsig.  `a_final` (APPLY/TRSM modes): A's tiles were
 // factored by an earlier launch, so waits on them are dropped.
 TQR_HD int task_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* nsig) {
+  if (I.D > 0 && t.kind != K_TRSMT_UPD && t.kind != K_TRSMT_SOLVE &&
+      !((t.kind == K_TRSM_UPD || t.kind == K_TRSM_SOLVE) && I.mode == M_TRSM))
+    return tree_rules(I, t, w, sg, nsig);
   const int p = I.p, kt = I.kt, NS = I.NS;
   const int k = t.k, i = t.i, j = t.j, s = t.s, l = t.l;
   const bool a_final = I.mode != M_FACTOR;
@@ -179,6 +324,12 @@ TQR_HD int64_t t_offset(int p, int nb, int ib, int i, int k) {
 TQR_HD int64_t t_elems(int p, int q, int nb, int ib) {
   int kt = p < q ? p : q;
   return t_offset(p, nb, ib, kt, kt);  // first index past the last block
+}
+
+// Tree variant: the TTQRT factors of eliminated head (b, k) follow the
+// GEQRT/TSQRT ones with the same indexing.
+TQR_HD int64_t t2_offset(int p, int q, int nb, int ib, int b, int k) {
+  return t_elems(p, q, nb, ib) + t_offset(p, nb, ib, b, k);
 }
 
 }  // namespace tqr

@@ -21,7 +21,83 @@ static TaskX mk(int kind, int inst, int k, int i, int j, int s, int l = 0) {
   return t;
 }
 
+// Reduction-tree variant: Algorithm 1's step k with the rows cut into
+// domains (GEQRT on each head, TSQRT/SSRFB of the head with each later row of
+// its domain) followed by the binary tree of TT merges of the heads.  `cols`
+// selects the updated tile columns: all j > k (factor) or only the
+// right-hand-side columns (apply).
+static void tree_step(const Inst& I, int x, int k, bool factor, std::vector<TaskX>& out) {
+  const int p = I.p, D = I.D, qt = I.q + I.qb;
+  const int j0 = factor ? k + 1 : I.q;
+  std::vector<int> heads;
+  for (int h = k; h < p; h += D) heads.push_back(h);
+  for (int h : heads) {
+    if (factor) out.push_back(mk(K_GEQRT, x, k, h, k, 0));
+    for (int j = j0; j < qt; ++j)
+      for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_LARFB, x, k, h, j, s));
+    for (int i = h + 1; i < h + D && i < p; ++i) {
+      if (factor) out.push_back(mk(K_TSQRT, x, k, i, k, 0, h));
+      for (int j = j0; j < qt; ++j)
+        for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_SSRFB, x, k, i, j, s, h));
+    }
+  }
+  const int H = static_cast<int>(heads.size());
+  for (int L = 0; (1 << L) < H; ++L)
+    for (int d = 0; d + (1 << L) < H; d += (2 << L)) {
+      const int a = heads[d], b = heads[d + (1 << L)];
+      if (factor) out.push_back(mk(K_TTQRT, x, k, b, k, 0, a));
+      for (int j = j0; j < qt; ++j)
+        for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_TTMQR, x, k, b, j, s, a));
+    }
+}
+
+static void trsm_tasks(const Inst& I, int x, std::vector<TaskX>& out) {
+  const int q = I.q, kt = I.kt, qt = I.q + I.qb;
+  for (int j = q; j < qt; ++j)
+    for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s)
+      for (int k = kt - 1; k >= 0; --k) {
+        for (int l = kt - 1; l > k; --l) out.push_back(mk(K_TRSM_UPD, x, k, k, j, s, l));
+        out.push_back(mk(K_TRSM_SOLVE, x, k, k, j, s));
+      }
+}
+
+static bool tree_seq(const Inst& I, int x, std::vector<TaskX>& out) {
+  if (I.D <= 0) return false;
+  switch (I.mode) {
+    case M_FACTOR:
+      for (int k = 0; k < I.kt; ++k) tree_step(I, x, k, true, out);
+      if (I.trsm) trsm_tasks(I, x, out);
+      return true;
+    case M_APPLY_QT:
+      for (int k = 0; k < I.kt; ++k) tree_step(I, x, k, false, out);
+      if (I.trsm) trsm_tasks(I, x, out);
+      return true;
+    case M_APPLY_Q: {
+      // the transposed updates in exactly the reverse order
+      std::vector<TaskX> fw;
+      for (int k = 0; k < I.kt; ++k) tree_step(I, x, k, false, fw);
+      for (size_t a = fw.size(); a-- > 0;) {
+        TaskX t = fw[a];
+        t.kind = t.kind == K_LARFB ? K_LARFB_N : t.kind == K_SSRFB ? K_SSRFB_N : K_TTMQR_N;
+        out.push_back(t);
+      }
+      return true;
+    }
+    default:
+      return false;  // triangular solves do not depend on the tree
+  }
+}
+
+void tree_table(const Inst& I, std::vector<int32_t>& vt) {
+  vt.assign(static_cast<size_t>(I.kt + 1) * I.p, 0);
+  for (int k = 0; k < I.kt; ++k)
+    for (int r = 0; r < I.p; ++r)
+      vt[static_cast<size_t>(k + 1) * I.p + r] =
+          vt[static_cast<size_t>(k) * I.p + r] + (r >= k ? tree_writes(I, k, r) : 0);
+}
+
 void seq_tasks(const Inst& I, int x, std::vector<TaskX>& out) {
+  if (tree_seq(I, x, out)) return;
   const int p = I.p, q = I.q, kt = I.kt, qt = I.q + I.qb;
   switch (I.mode) {
     case M_FACTOR:
@@ -220,6 +296,16 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
       f = (nb / ib) * (4.0 * nb * ib * w + ib * ib * w);
       lat = (nb / ib) * blk_lat;
       break;
+    case K_TTQRT:
+      for (double l0 = 0; l0 < nb; l0 += ib)
+        f += 1.5 * (l0 + ib) * ib * ib + 2.0 * (l0 + ib) * ib * (nb - l0 - ib);
+      lat = nb * col_lat;
+      break;
+    case K_TTMQR:
+    case K_TTMQR_N:
+      for (double l0 = 0; l0 < nb; l0 += ib) f += 4.0 * (l0 + ib) * ib * w + ib * ib * w;
+      lat = (nb / ib) * blk_lat;
+      break;
     case K_TRSM_UPD:
     case K_TRSMT_UPD:
       f = 2.0 * nb * nb * w;
@@ -239,11 +325,14 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
 static int kind_rank(int kind) {
   switch (kind) {
     case K_GEQRT: return 0;
-    case K_TSQRT: return 1;
+    case K_TSQRT:
+    case K_TTQRT: return 1;
     case K_LARFB:
     case K_LARFB_N: return 2;
     case K_SSRFB:
-    case K_SSRFB_N: return 3;
+    case K_SSRFB_N:
+    case K_TTMQR:
+    case K_TTMQR_N: return 3;
     case K_TRSM_SOLVE:
     case K_TRSMT_SOLVE: return 4;
     default: return 5;

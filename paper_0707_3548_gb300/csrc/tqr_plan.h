@@ -33,6 +33,9 @@ struct PlanStats {
   double work_s = 0;         // sum of task costs
 };
 
+// Tree variant: the prefix table of writes per row (Inst.vtab), (kt+1) x p.
+void tree_table(const Inst& I, std::vector<int32_t>& vt);
+
 // Tasks of one instance in the sequential order of its mode.
 void seq_tasks(const Inst& I, int inst_index, std::vector<TaskX>& out);
 

@@ -78,8 +78,8 @@ SIGNATURES = {
     "tqr_batch_wait": (_int, [ctypes.c_uint64, _vp]),
     "tqr_stream_status": (_int, [_vp]),
     "tqr_set_wait_limit_ms": (_i64, [_i64]),
-    "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
-    "tqr_debug_rules": (_int, [_int, _i64, _i64, _int, _int, _int, _int, _vp, _vp, _vp]),
+    "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
+    "tqr_debug_rules": (_int, [_int, _i64, _i64, _int, _int, _int, _int, _int, _vp, _vp, _vp]),
     "tqr_debug_set_schedule": (_int, [_int, _int]),
     "tqr_debug_stalled_launch": (_int, [_i64, _vp]),
     "tqr_debug_timing": (_int, [_int]),
@@ -296,25 +296,25 @@ def tqr_set_wait_limit_ms(ms):
 
 
 # ------------------------------------------------------------------ host-only introspection
-def tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs=0, trsm=0, workers=8, policy=-1):
+def tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs=0, trsm=0, workers=8, policy=-1, D=0):
     """(tasks int32[N, 8], stats float64[6]) of the ordered plan of one launch."""
     L = lib()
-    cnt = L.tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs, trsm, workers, policy, None, 0, None)
+    cnt = L.tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs, trsm, D, workers, policy, None, 0, None)
     if cnt < 0:
         raise RuntimeError("tqr_debug_plan: %d %s" % (cnt, L.tqr_debug_last_error().decode()))
     out = np.zeros((cnt, 8), dtype=np.int32)
     stats = np.zeros(6)
-    L.tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs, trsm, workers, policy, out.ctypes.data, cnt,
+    L.tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs, trsm, D, workers, policy, out.ctypes.data, cnt,
                      stats.ctypes.data)
     return out, stats
 
 
-def tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, task):
+def tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, task, D=0):
     """(waits [(ctr, cnt, ver)], signals [(ctr, cnt)]) of one task."""
     t = np.asarray(list(task) + [0] * (8 - len(task)), dtype=np.int32)
     w = np.zeros(12, dtype=np.int32)
     s = np.zeros(4, dtype=np.int32)
-    r = lib().tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, t.ctypes.data, w.ctypes.data, s.ctypes.data)
+    r = lib().tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, D, t.ctypes.data, w.ctypes.data, s.ctypes.data)
     nw, ns = r % 16, r // 16
     return [tuple(w[3 * a:3 * a + 3]) for a in range(nw)], [tuple(s[2 * a:2 * a + 2]) for a in range(ns)]
 
