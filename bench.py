@@ -39,6 +39,8 @@ WORKLOADS = {
     "qr4096": dict(m=4096, n=4096, nb=128, ib=16),
     "qr2048": dict(m=2048, n=2048, nb=128, ib=16),
     "ts65536x2048": dict(m=65536, n=2048, nb=128, ib=16),
+    # the same with the reduction-tree panel (domain size chosen by the library)
+    "ts65536x2048_tree": dict(m=65536, n=2048, nb=128, ib=16, tree=True),
     # least squares A = U diag(sigma) V^T, kappa 1e2 / 1e5 / 1e8: plain FP64
     # against FP32 factorization + FP64-residual refinement
     "ls16384x4096k1e2": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e2, ls=True),
@@ -62,7 +64,8 @@ def qr_flops(m, n):
 
 
 def workload_name(w):
-    return "tiled QR %dx%d FP64, N(0,1) seed 0, nb=%d ib=%d" % (w["m"], w["n"], w["nb"], w["ib"])
+    return "tiled QR %dx%d FP64, N(0,1) seed 0, nb=%d ib=%d%s" % (w["m"], w["n"], w["nb"], w["ib"],
+                                                               ", reduction-tree panel" if w.get("tree") else "")
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -242,12 +245,22 @@ def run_ours(args, w):
     dev = torch.device("cuda", local)
     dA0 = tqr.colmajor(torch.from_numpy(A).to(dev))
     dA = tqr.colmajor(torch.empty((m, n), dtype=torch.float64, device=dev))
-    T = tqr.new_t(m, n, nb, ib, dA)
+    tree = bool(w.get("tree"))
+    if tree:
+        T = torch.zeros(tqr.tqr_t_size_tree(m, n, nb, ib) // 8, dtype=torch.float64, device=dev)
+        dA.copy_(dA0)
+        _, D = tqr.tqr_factor_tree(dA, nb, ib, 0, T)   # the library's domain choice, reused below
+    else:
+        T = tqr.new_t(m, n, nb, ib, dA)
+        D = 0
     stream = torch.cuda.current_stream()
 
     def step():
         dA.copy_(dA0)
-        tqr.tqr_factor(dA, nb, ib, T)
+        if tree:
+            tqr.tqr_factor_tree(dA, nb, ib, D, T)
+        else:
+            tqr.tqr_factor(dA, nb, ib, T)
 
     for _ in range(args.warmup):
         step()
@@ -292,7 +305,10 @@ def run_ours(args, w):
     for it in range(0 if args.no_e2e else args.warmup + args.steps):
         np.copyto(hA, A)
         t0 = time.perf_counter()
-        tqr.tqr_factor(hA, nb, ib, hT)
+        if tree:
+            tqr.tqr_factor_tree(hA, nb, ib, D, hT)
+        else:
+            tqr.tqr_factor(hA, nb, ib, hT)
         t1 = time.perf_counter()
         if it >= args.warmup:
             e2e_times.append(t1 - t0)
@@ -333,7 +349,8 @@ def run_ours(args, w):
         "data": "synthetic: N(0,1) entries, NumPy PCG64 seed 0",
         "config": {"workload": workload_name(w), "m": m, "n": n, "nb": nb, "ib": ib,
                    "l2": "input 8*m*n bytes > 129 MB L2, restored from a device copy each step",
-                   "parallelism": "replicas" if world > 1 else "single GPU"},
+                   "parallelism": "replicas" if world > 1 else "single GPU",
+                   "panel": ("reduction tree, domains of %d tile rows" % D) if tree else "flat (Algorithm 1)"},
         "fp64_peak_fraction": value / world / peak,
         "roofline": roofline,
         "cpu_baseline": cpu,

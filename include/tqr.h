@@ -119,6 +119,35 @@ int tqr_apply_qt(char trans, int64_t m, int64_t n, int64_t nrhs,
                  double* B, int64_t ldb, void* stream);
 
 /*
+ * Reduction-tree variant of the factorization (an extension; the paper's
+ * panel is Algorithm 1's flat chain TSQRT(k, k+1), TSQRT(k, k+2), ...).  In
+ * step k the rows k..p-1 are cut into domains of D tile rows; each domain is
+ * factored flat with its first row as head (GEQRT of the head tile, TSQRT of
+ * the head's triangle with every later row of the domain), then the heads'
+ * triangles merge by a binary tree of TTQRT kernels (QR of two stacked upper
+ * triangles; their reflectors are upper triangular and overwrite the
+ * eliminated head's triangle, its lower part keeping that head's GEQRT
+ * reflectors).  The panel's critical path drops from p - k tasks to about
+ * D + log2((p - k) / D), which is what tall-skinny matrices need.
+ *   tqr_t_size_tree: bytes of T for this variant (twice tqr_t_size: the
+ *     GEQRT/TSQRT factors in tqr_t_size's layout, then the TTQRT factors of
+ *     the eliminated heads in the same layout).
+ *   tqr_factor_tree(m, n, A, lda, nb, ib, D, T, stream): as tqr_factor; *D
+ *     (arg 7) is the domain size in tile rows, or 0 to let the library choose
+ *     it (from a model of the task graph's critical path and work; the flat
+ *     panel when no tree is clearly better) -- the chosen value is written
+ *     back.  T (arg 8) has tqr_t_size_tree bytes.
+ *   tqr_apply_qt_tree(trans, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb,
+ *     stream): tqr_apply_qt for factors of tqr_factor_tree with domain size D
+ *     (arg 9).
+ */
+size_t tqr_t_size_tree(int64_t m, int64_t n, int nb, int ib);
+int tqr_factor_tree(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, int* D,
+                    double* T, void* stream);
+int tqr_apply_qt_tree(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                      int nb, int ib, int D, const double* T, double* B, int64_t ldb, void* stream);
+
+/*
  * Least squares  min ||A x - b||_2  for full-rank A, m >= n, through the
  * tiled QR: x = R[0:n,0:n]^{-1} (Q^T b)[0:n].  The factorization, Q^T B and
  * the back substitution run as one task graph on the device.
@@ -139,6 +168,8 @@ int tqr_apply_qt(char trans, int64_t m, int64_t n, int64_t nrhs,
  *                           max_c ||A^T r_c|| / (||A||_F (||A||_F ||x_c|| + ||b_c||))
  *   nb, ib     (args 15-16) tile and inner block size (0, 0 = library choice)
  *   stream     (arg 17)
+ * Tall problems use the reduction-tree variant when the library's model of
+ * the task graph predicts a shorter run (see tqr_factor_tree).
  * Synchronizes the stream (the refinement loop needs the backward error on
  * the host).  Returns TQR_ERR_RANK for a numerically rank-deficient R and
  * TQR_ERR_NOCONV when refinement stalls (neither the backward error nor the

@@ -124,7 +124,7 @@ struct DevPlan {
   }
 };
 
-typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int> PlanKey;
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int, int> PlanKey;
 
 static std::list<std::pair<PlanKey, std::shared_ptr<DevPlan>>> g_plans;
 static const size_t kMaxPlans = 64;
@@ -164,7 +164,7 @@ static void hold_until_done(const std::shared_ptr<DevPlan>& plan, cudaStream_t s
 }
 
 static PlanKey key_of(const Inst& I, int esize, int grid, int dev, int policy) {
-  return PlanKey(I.mode, I.m, I.n, I.nb, I.ib, I.cs, I.nrhs, I.trsm, esize, grid, dev, policy);
+  return PlanKey(I.mode, I.m, I.n, I.nb, I.ib, I.cs, I.nrhs, I.trsm, esize, grid, dev, policy, I.D);
 }
 
 std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int* status, int grid_cap) {
@@ -189,14 +189,17 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
       if (std::get<0>(k) == I.mode && std::get<1>(k) == I.m && std::get<2>(k) == I.n && std::get<3>(k) == I.nb &&
           std::get<4>(k) == I.ib && std::get<5>(k) == I.cs && std::get<6>(k) == I.nrhs && std::get<7>(k) == I.trsm &&
           std::get<8>(k) == esize && std::get<10>(k) == dev && std::get<11>(k) == policy &&
-          std::get<9>(k) == max_grid) {
+          std::get<9>(k) == max_grid && std::get<12>(k) == I.D) {
         auto p = it->second;
         g_plans.splice(g_plans.begin(), g_plans, it);
         return p;
       }
     }
   }
-  seq_tasks(I, 0, seq);
+  // planning runs on the host: the tree variant's table must be host memory
+  Inst Ih = I;
+  if (Ih.D > 0) Ih.vtab = host_vtab(Ih);
+  seq_tasks(Ih, 0, seq);
   auto plan = std::make_shared<DevPlan>();
   plan->device = dev;
   plan->ntasks = static_cast<int>(seq.size());
@@ -204,7 +207,7 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
   if (!seq.empty()) {
     std::vector<TaskX> ordered;
     std::string err;
-    std::vector<Inst> insts(1, I);
+    std::vector<Inst> insts(1, Ih);
     if (!order_tasks(insts, seq, plan->grid, esize, ctas_per_sm, policy, ordered, &plan->stats, &err)) {
       set_last_error(err);
       *status = TQR_ERR_UNSUPPORTED;
@@ -277,6 +280,63 @@ void clear_plans() {
   prune_inflight_locked();
 }
 
+// ---------------------------------------------------------------- tree
+// Domain size of the reduction-tree variant for an m x n factorization: the
+// candidate (flat Algorithm 1 or D in {64, ..., 1} tile rows) with the
+// smallest max(critical path, work / CTAs) under the scheduler's cost model;
+// the flat panel is kept unless a tree is at least 5% better.  Cached.
+int choose_domain(int64_t m, int64_t n, int nb, int ib, int esize) {
+  static std::mutex mu;
+  static std::map<std::tuple<int64_t, int64_t, int, int, int>, int> cache;
+  const auto key = std::make_tuple(m, n, nb, ib, esize);
+  {
+    std::lock_guard<std::mutex> lk(mu);
+    auto it = cache.find(key);
+    if (it != cache.end()) return it->second;
+  }
+  int cs, occ, smem;
+  if (!choose_shape(nb, ib, esize, &cs, &occ, &smem)) return 0;
+  const int workers = std::max(1, device_sms()) * occ;
+  int best_d = 0;
+  double best = INFINITY, flat = INFINITY;
+  for (int D : {0, 64, 32, 16, 8, 4, 2, 1}) {
+    Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
+    if (D >= I.p) continue;
+    I.D = D;
+    if (D > 0) I.vtab = host_vtab(I);
+    std::vector<TaskX> seq, ordered;
+    seq_tasks(I, 0, seq);
+    PlanStats st;
+    std::string err;
+    std::vector<Inst> insts(1, I);
+    if (seq.empty() || !order_bottom_level(insts, seq, esize, occ, workers, ordered, &st, &err)) continue;
+    const double est = std::max(st.critical_path_s, st.work_s / workers);
+    if (D == 0) flat = est;
+    if (est < best) {
+      best = est;
+      best_d = D;
+    }
+  }
+  if (best_d != 0 && !(best < 0.95 * flat)) best_d = 0;
+  std::lock_guard<std::mutex> lk(mu);
+  cache[key] = best_d;
+  return best_d;
+}
+
+// Points I.vtab at the workspace copy of the tree table and uploads it.
+int upload_vtab(Inst& I, char* ws, const WsLayout& W, cudaStream_t st) {
+  if (I.D <= 0) {
+    I.vtab = nullptr;
+    return TQR_OK;
+  }
+  I.vtab = reinterpret_cast<const int32_t*>(ws + W.oVtab);
+  const int32_t* h = host_vtab(I);
+  return cudaMemcpyAsync(ws + W.oVtab, h, sizeof(int32_t) * static_cast<size_t>(I.kt + 1) * I.p,
+                         cudaMemcpyHostToDevice, st) == cudaSuccess
+             ? TQR_OK
+             : TQR_ERR_CUDA;
+}
+
 // ---------------------------------------------------------------- workspace
 static size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
@@ -289,7 +349,9 @@ WsLayout ws_layout(const Inst& I, int esize, bool with_t) {
   W.oB = o;
   o += al256(nb2 * I.p * I.qb * esize);
   W.oT = o;
-  if (with_t) o += al256(static_cast<size_t>(t_elems(I.p, I.q, I.nb, I.ib)) * esize);
+  if (with_t) o += al256(static_cast<size_t>(t_elems(I.p, I.q, I.nb, I.ib)) * esize * (I.D > 0 ? 2 : 1));
+  W.oVtab = o;
+  if (I.D > 0) o += al256(sizeof(int32_t) * static_cast<size_t>(I.kt + 1) * I.p);
   W.oVer = o;
   o += al256(sizeof(int) * static_cast<size_t>(I.p) * (I.q + I.qb) * I.NS);
   W.oInst = o;
@@ -361,11 +423,12 @@ using namespace tqr;
 
 // ---------------------------------------------------------------- factor
 template <typename real>
-static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, real* T, void* work,
+static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, int D, real* T, void* work,
                          size_t work_bytes, cudaStream_t st) {
   int cs, occ, smem;
   if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
   Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
+  I.D = D;
   const WsLayout W = ws_layout(I, sizeof(real), false);
   char* ws = static_cast<char*>(work);
   bool own = false;
@@ -383,8 +446,9 @@ static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   I.T = T;
   I.ver = reinterpret_cast<int*>(ws + W.oVer);
   const int sms = device_sms();
-  int status = TQR_OK;
-  if (launch_pack<real>(A, lda, static_cast<int>(m), static_cast<int>(n), static_cast<real*>(I.A), I.p, I.q, nb, sms,
+  int status = upload_vtab(I, ws, W, st);
+  if (status == TQR_OK &&
+      launch_pack<real>(A, lda, static_cast<int>(m), static_cast<int>(n), static_cast<real*>(I.A), I.p, I.q, nb, sms,
                         st) != cudaSuccess)
     status = TQR_ERR_CUDA;
   if (status == TQR_OK) status = run_plan<real>(I, ws, W, occ, smem, st);
@@ -396,7 +460,7 @@ static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   return status;
 }
 
-static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* work,
+static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, int D, double* T, void* work,
                          size_t work_bytes, void* stream) {
   if (m < 0) return -1;
   if (n < 0) return -2;
@@ -410,9 +474,9 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ka = ptr_kind(A), kt = ptr_kind(T);
   if (ka != kt) return -7;
-  if (ka == PTR_DEVICE) return factor_device<double>(m, n, A, lda, nb, ib, T, work, work_bytes, st);
+  if (ka == PTR_DEVICE) return factor_device<double>(m, n, A, lda, nb, ib, D, T, work, work_bytes, st);
   // host buffers: stage through the device, synchronously
-  const size_t tbytes = tqr_t_size(m, n, nb, ib);
+  const size_t tbytes = tqr_t_size(m, n, nb, ib) * (D > 0 ? 2 : 1);
   double *dA = nullptr, *dT = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
       cudaMallocAsync(reinterpret_cast<void**>(&dT), tbytes, st) != cudaSuccess) {
@@ -424,7 +488,7 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
     status = TQR_ERR_CUDA;
-  if (status == TQR_OK) status = factor_device<double>(m, n, dA, m, nb, ib, dT, work, work_bytes, st);
+  if (status == TQR_OK) status = factor_device<double>(m, n, dA, m, nb, ib, D, dT, work, work_bytes, st);
   if (status == TQR_OK &&
       (cudaMemcpy2DAsync(A, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
                          cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -441,10 +505,11 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
 // ---------------------------------------------------------------- apply
 template <typename real>
 static int apply_device(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb,
-                        int ib, const real* T, double* B, int64_t ldb, cudaStream_t st) {
+                        int ib, int D, const real* T, double* B, int64_t ldb, cudaStream_t st) {
   int cs, occ, smem;
   if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
   Inst I = make_inst(trans == 'T' ? M_APPLY_QT : M_APPLY_Q, m, n, nb, ib, cs, static_cast<int>(nrhs), 0);
+  I.D = D;
   const WsLayout W = ws_layout(I, sizeof(real), false);
   char* ws = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
@@ -456,8 +521,9 @@ static int apply_device(char trans, int64_t m, int64_t n, int64_t nrhs, const do
   I.T = const_cast<real*>(T);
   I.ver = reinterpret_cast<int*>(ws + W.oVer);
   const int sms = device_sms();
-  int status = TQR_OK;
-  if (launch_pack<real>(A, lda, static_cast<int>(m), static_cast<int>(n), static_cast<real*>(I.A), I.p, I.q, nb, sms,
+  int status = upload_vtab(I, ws, W, st);
+  if (status != TQR_OK ||
+      launch_pack<real>(A, lda, static_cast<int>(m), static_cast<int>(n), static_cast<real*>(I.A), I.p, I.q, nb, sms,
                         st) != cudaSuccess ||
       launch_pack<real>(B, ldb, static_cast<int>(m), static_cast<int>(nrhs), static_cast<real*>(I.B), I.p, I.qb, nb,
                         sms, st) != cudaSuccess)
@@ -467,6 +533,57 @@ static int apply_device(char trans, int64_t m, int64_t n, int64_t nrhs, const do
                                               static_cast<int>(nrhs), sms, st) != cudaSuccess)
     status = TQR_ERR_CUDA;
   cudaFreeAsync(ws, st);
+  return status;
+}
+
+static int apply_common(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
+                        int D, const double* T, double* B, int64_t ldb, void* stream) {
+  if (trans != 'T' && trans != 'N' && trans != 't' && trans != 'n') return -1;
+  trans = (trans == 't' || trans == 'T') ? 'T' : 'N';
+  if (m < 0) return -2;
+  if (n < 0) return -3;
+  if (nrhs < 0) return -4;
+  if (m > (1LL << 30) || n > (1LL << 30) || nrhs > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
+  if (lda < std::max<int64_t>(1, m)) return -6;
+  int c = check_tiles(nb, ib, 7, 8);
+  if (c) return c;
+  if (ldb < std::max<int64_t>(1, m)) return -11;
+  if (m == 0 || n == 0 || nrhs == 0) return TQR_OK;
+  if (A == nullptr) return -5;
+  if (T == nullptr) return -9;
+  if (B == nullptr) return -10;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int ka = ptr_kind(A);
+  if (ptr_kind(T) != ka) return -9;
+  if (ptr_kind(B) != ka) return -10;
+  if (ka == PTR_DEVICE) return apply_device<double>(trans, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, st);
+  const size_t tbytes = tqr_t_size(m, n, nb, ib) * (D > 0 ? 2 : 1);
+  double *dA = nullptr, *dT = nullptr, *dB = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dT), tbytes, st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (dA) cudaFreeAsync(dA, st);
+    if (dT) cudaFreeAsync(dT, st);
+    return TQR_ERR_NOMEM;
+  }
+  int status = TQR_OK;
+  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpyAsync(dT, T, tbytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemcpy2DAsync(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
+                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  if (status == TQR_OK) status = apply_device<double>(trans, m, n, nrhs, dA, m, nb, ib, D, dT, dB, m, st);
+  if (status == TQR_OK && cudaMemcpy2DAsync(B, sizeof(double) * ldb, dB, sizeof(double) * m, sizeof(double) * m,
+                                            nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  cudaFreeAsync(dA, st);
+  cudaFreeAsync(dT, st);
+  cudaFreeAsync(dB, st);
+  int dev_status = TQR_OK;
+  if (read_status(&dev_status, st) != cudaSuccess) return TQR_ERR_CUDA;
+  if (status == TQR_OK) status = dev_status;
   return status;
 }
 
@@ -490,7 +607,7 @@ size_t tqr_work_size(int64_t m, int64_t n, int nb, int ib) {
 }
 
 int tqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* stream) {
-  return factor_common(m, n, A, lda, nb, ib, T, nullptr, 0, stream);
+  return factor_common(m, n, A, lda, nb, ib, 0, T, nullptr, 0, stream);
 }
 
 int tqr_factor_ws(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* work,
@@ -498,58 +615,35 @@ int tqr_factor_ws(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, 
   if (work == nullptr) return -8;
   if (ptr_kind(work) != PTR_DEVICE) return -8;
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -8;
-  return factor_common(m, n, A, lda, nb, ib, T, work, work_bytes, stream);
+  return factor_common(m, n, A, lda, nb, ib, 0, T, work, work_bytes, stream);
 }
 
 int tqr_apply_qt(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
                  const double* T, double* B, int64_t ldb, void* stream) {
-  if (trans != 'T' && trans != 'N' && trans != 't' && trans != 'n') return -1;
-  trans = (trans == 't' || trans == 'T') ? 'T' : 'N';
-  if (m < 0) return -2;
-  if (n < 0) return -3;
-  if (nrhs < 0) return -4;
-  if (m > (1LL << 30) || n > (1LL << 30) || nrhs > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
-  if (lda < std::max<int64_t>(1, m)) return -6;
-  int c = check_tiles(nb, ib, 7, 8);
+  return apply_common(trans, m, n, nrhs, A, lda, nb, ib, 0, T, B, ldb, stream);
+}
+
+size_t tqr_t_size_tree(int64_t m, int64_t n, int nb, int ib) { return 2 * tqr_t_size(m, n, nb, ib); }
+
+int tqr_factor_tree(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, int* D, double* T, void* stream) {
+  if (D == nullptr || *D < 0) return -7;
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  const int c = check_tiles(nb, ib, 5, 6);
   if (c) return c;
-  if (ldb < std::max<int64_t>(1, m)) return -11;
-  if (m == 0 || n == 0 || nrhs == 0) return TQR_OK;
-  if (A == nullptr) return -5;
-  if (T == nullptr) return -9;
-  if (B == nullptr) return -10;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int ka = ptr_kind(A);
-  if (ptr_kind(T) != ka) return -9;
-  if (ptr_kind(B) != ka) return -10;
-  if (ka == PTR_DEVICE) return apply_device<double>(trans, m, n, nrhs, A, lda, nb, ib, T, B, ldb, st);
-  const size_t tbytes = tqr_t_size(m, n, nb, ib);
-  double *dA = nullptr, *dT = nullptr, *dB = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dT), tbytes, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess) {
-    cudaGetLastError();
-    if (dA) cudaFreeAsync(dA, st);
-    if (dT) cudaFreeAsync(dT, st);
-    return TQR_ERR_NOMEM;
+  if (*D == 0 && m > 0 && n > 0) {
+    *D = choose_domain(m, n, nb, ib, sizeof(double));
+    if (*D == 0) *D = static_cast<int>((m + nb - 1) / nb);  // one domain: Algorithm 1's flat panel
   }
-  int status = TQR_OK;
-  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(dT, T, tbytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpy2DAsync(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess)
-    status = TQR_ERR_CUDA;
-  if (status == TQR_OK) status = apply_device<double>(trans, m, n, nrhs, dA, m, nb, ib, dT, dB, m, st);
-  if (status == TQR_OK && cudaMemcpy2DAsync(B, sizeof(double) * ldb, dB, sizeof(double) * m, sizeof(double) * m,
-                                            nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    status = TQR_ERR_CUDA;
-  cudaFreeAsync(dA, st);
-  cudaFreeAsync(dT, st);
-  cudaFreeAsync(dB, st);
-  int dev_status = TQR_OK;
-  if (read_status(&dev_status, st) != cudaSuccess) return TQR_ERR_CUDA;
-  if (status == TQR_OK) status = dev_status;
-  return status;
+  const int r = factor_common(m, n, A, lda, nb, ib, *D, T, nullptr, 0, stream);
+  return r == -7 ? -8 : r;  // T is argument 8 here
+}
+
+int tqr_apply_qt_tree(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
+                      int D, const double* T, double* B, int64_t ldb, void* stream) {
+  if (D < 1) return -9;
+  const int r = apply_common(trans, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, stream);
+  return (r <= -9) ? r - 1 : r;  // arguments after ib shift by one
 }
 
 int tqr_stream_status(void* stream) {

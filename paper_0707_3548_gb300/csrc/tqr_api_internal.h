@@ -14,7 +14,7 @@ namespace tqr {
 enum { PTR_NULL = 0, PTR_HOST = 1, PTR_DEVICE = 2 };
 
 struct WsLayout {
-  size_t oA, oB, oT, oVer, oInst, oCtl, bytes;
+  size_t oA, oB, oT, oVtab, oVer, oInst, oCtl, bytes;
 };
 
 void set_last_error(const std::string& s);
@@ -34,6 +34,9 @@ void clear_plans();
 void autotune(int64_t m, int64_t n, int* nb, int* ib);
 // Host copy of the tree variant's prefix table for planning (Inst.D > 0).
 const int32_t* host_vtab(const Inst& I);
+// Tree variant: chosen domain size (0 = flat) and the device table upload.
+int choose_domain(int64_t m, int64_t n, int nb, int ib, int esize);
+int upload_vtab(Inst& I, char* ws, const WsLayout& W, cudaStream_t st);
 void set_schedule(int policy, int max_ctas);
 int timing_enable(int on);
 int timing_read(double* ms, int64_t* launches);

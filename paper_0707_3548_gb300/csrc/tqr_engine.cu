@@ -635,6 +635,12 @@ __device__ __forceinline__ real* t_ptr(const Inst& I, int i, int k) {
   return static_cast<real*>(I.T) + t_offset(I.p, I.nb, I.ib, i, k);
 }
 
+// T factors of the tree variant's TTQRT of eliminated head (i, k).
+template <typename real>
+__device__ __forceinline__ real* t2_ptr(const Inst& I, int i, int k) {
+  return static_cast<real*>(I.T) + t2_offset(I.p, I.q, I.nb, I.ib, i, k);
+}
+
 // Width of slab s of tile column j.
 __device__ __forceinline__ int slab_width(const Inst& I, int j, int s) {
   int w = I.cs;
@@ -646,12 +652,13 @@ __device__ __forceinline__ int slab_width(const Inst& I, int j, int s) {
   return w;
 }
 
-// GEQRT(k): Section 3.1 DGEQT2 with inner blocking.
+// GEQRT(k) on tile (row, k): Section 3.1 DGEQT2 with inner blocking (row = k
+// in Algorithm 1; a domain head in the tree variant).
 template <typename real>
-__device__ void exec_geqrt(Ctx<real>& cx, const Inst& I, int k) {
+__device__ void exec_geqrt(Ctx<real>& cx, const Inst& I, int k, int row) {
   const int nb = I.nb, ib = I.ib, cs = I.cs;
-  real* A = tile_ptr<real>(I, k, k);
-  real* Tg = t_ptr<real>(I, k, k);
+  real* A = tile_ptr<real>(I, row, k);
+  real* Tg = t_ptr<real>(I, row, k);
   double* taus = cx.red + 2 * kThreads;
   for (int l0 = 0; l0 < nb; l0 += ib) {
     const int nr = nb - l0;
@@ -674,13 +681,17 @@ __device__ void exec_geqrt(Ctx<real>& cx, const Inst& I, int k) {
   }
 }
 
-// TSQRT(k, i): Section 3.1 DTSQT2 with inner blocking.
+// TSQRT(k, i) with top tile (head, k): Section 3.1 DTSQT2 with inner
+// blocking (head = k in Algorithm 1).  tt: the tree variant's TTQRT -- the
+// bottom is the upper triangle of (i, k) (its strictly lower part holds that
+// head's GEQRT reflectors and is neither read nor written); block l's
+// reflectors then live in its first l0 + ib rows only.
 template <typename real>
-__device__ void exec_tsqrt(Ctx<real>& cx, const Inst& I, int k, int i) {
+__device__ void exec_tsqrt(Ctx<real>& cx, const Inst& I, int k, int head, int i, bool tt) {
   const int nb = I.nb, ib = I.ib, cs = I.cs;
-  real* Rt = tile_ptr<real>(I, k, k);
+  real* Rt = tile_ptr<real>(I, head, k);
   real* Ai = tile_ptr<real>(I, i, k);
-  real* Tg = t_ptr<real>(I, i, k);
+  real* Tg = tt ? t2_ptr<real>(I, i, k) : t_ptr<real>(I, i, k);
   double* taus = cx.red + 2 * kThreads;
   real* Rb = cx.Rb;  // ib x ib triangle, ld ib
   for (int l0 = 0; l0 < nb; l0 += ib) {
@@ -690,37 +701,51 @@ __device__ void exec_tsqrt(Ctx<real>& cx, const Inst& I, int k, int i) {
       Rb[r + c * ib] = (r <= c) ? ldg_cg(Rt + (l0 + r) + static_cast<long long>(l0 + c) * nb) : real(0);
     }
     bulk_cols(cx, cx.P, cx.ldP, Ai + static_cast<long long>(l0) * nb, nb, nb, ib);
+    const int nv = tt ? l0 + ib : nb;  // rows that can hold reflector entries
+    if (tt)
+      for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
+        const int r = e % nv, c = e / nv;
+        if (r > l0 + c) cx.P[r + c * cx.ldP] = real(0);
+      }
     __syncthreads();
-    panel_qr<real, true>(cx.P, cx.ldP, nb, ib, Rb, ib, cx.red, taus);
+    panel_qr<real, true>(cx.P, cx.ldP, nv, ib, Rb, ib, cx.red, taus);
     for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
       const int r = e % ib, c = e / ib;
       if (r <= c) Rt[(l0 + r) + static_cast<long long>(l0 + c) * nb] = Rb[r + c * ib];
     }
-    store_block(Ai + static_cast<long long>(l0) * nb, nb, cx.P, cx.ldP, nb, ib);
+    if (tt) {
+      for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
+        const int r = e % nv, c = e / nv;
+        if (r <= l0 + c) Ai[r + static_cast<long long>(l0 + c) * nb] = cx.P[r + c * cx.ldP];
+      }
+    } else {
+      store_block(Ai + static_cast<long long>(l0) * nb, nb, cx.P, cx.ldP, nb, ib);
+    }
     __syncthreads();
-    form_t<real, true>(cx.P, cx.ldP, nb, ib, taus, cx.Rb, cx.T, cx.ldT);
+    form_t<real, true>(cx.P, cx.ldP, nv, ib, taus, cx.Rb, cx.T, cx.ldT);
     store_block(Tg + static_cast<long long>(l0) * ib, ib, cx.T, cx.ldT, ib, ib);
     for (int c0 = l0 + ib; c0 < nb; c0 += cs) {
       const int w = nb - c0 < cs ? nb - c0 : cs;
       load_block(cx.Top, ib, Rt + l0 + static_cast<long long>(c0) * nb, nb, ib, w);
       bulk_cols(cx, cx.S, cx.ldS, Ai + static_cast<long long>(c0) * nb, nb, nb, w);
       __syncthreads();
-      apply_any<real>(cx.P, cx.ldP, nb, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, true);
+      apply_any<real>(cx.P, cx.ldP, nv, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, true);
       store_block(Rt + l0 + static_cast<long long>(c0) * nb, nb, cx.Top, ib, ib, w);
-      store_block(Ai + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nb, w);
+      store_block(Ai + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nv, w);
       __syncthreads();
     }
     __syncthreads();
   }
 }
 
-// LARFB(k, j, s): slab s of tile (k, j) <- Q_kk^T (or Q_kk) times it.
+// LARFB(k, j, s) on row `row`: slab s of tile (row, j) <- Q^T (or Q) of the
+// GEQRT'ed tile (row, k) times it (row = k in Algorithm 1).
 template <typename real>
-__device__ void exec_larfb(Ctx<real>& cx, const Inst& I, int k, int j, int s, bool trans) {
+__device__ void exec_larfb(Ctx<real>& cx, const Inst& I, int k, int row, int j, int s, bool trans) {
   const int nb = I.nb, ib = I.ib;
-  const real* Vt = tile_ptr<real>(I, k, k);
-  const real* Tg = t_ptr<real>(I, k, k);
-  real* C = tile_ptr<real>(I, k, j) + static_cast<long long>(s) * I.cs * nb;
+  const real* Vt = tile_ptr<real>(I, row, k);
+  const real* Tg = t_ptr<real>(I, row, k);
+  real* C = tile_ptr<real>(I, row, j) + static_cast<long long>(s) * I.cs * nb;
   const int w = slab_width(I, j, s);
   bulk_cols(cx, cx.S, cx.ldS, C, nb, nb, w);
   const int nblk = nb / ib;
@@ -742,14 +767,16 @@ __device__ void exec_larfb(Ctx<real>& cx, const Inst& I, int k, int j, int s, bo
   __syncthreads();
 }
 
-// SSRFB(k, i, j, s): slab s of [(k, j); (i, j)] <- Q_ik^T (or Q_ik) times it.
+// SSRFB(k, i, j, s): slab s of [(head, j); (i, j)] <- Q_ik^T (or Q_ik) times
+// it (head = k in Algorithm 1).  tt: the tree variant's TTMQR, whose
+// reflectors are the upper triangle of (i, k) (block l: first l0 + ib rows).
 template <typename real>
-__device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int i, int j, int s, bool trans) {
+__device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int head, int i, int j, int s, bool trans, bool tt) {
   const int nb = I.nb, ib = I.ib;
   const real* Vt = tile_ptr<real>(I, i, k);
-  const real* Tg = t_ptr<real>(I, i, k);
+  const real* Tg = tt ? t2_ptr<real>(I, i, k) : t_ptr<real>(I, i, k);
   const long long soff = static_cast<long long>(s) * I.cs * nb;
-  real* Ct = tile_ptr<real>(I, k, j) + soff;
+  real* Ct = tile_ptr<real>(I, head, j) + soff;
   real* Cb = tile_ptr<real>(I, i, j) + soff;
   const int w = slab_width(I, j, s);
   const int nblk = nb / ib;
@@ -760,8 +787,14 @@ __device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int i, int j, in
     load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
     load_block(cx.Top, ib, Ct + l0, nb, ib, w);
     bulk_cols(cx, cx.P, cx.ldP, Vt + static_cast<long long>(l0) * nb, nb, nb, ib);
+    const int nv = tt ? l0 + ib : nb;
+    if (tt)
+      for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
+        const int r = e % nv, c = e / nv;
+        if (r > l0 + c) cx.P[r + c * cx.ldP] = real(0);
+      }
     __syncthreads();
-    apply_any<real>(cx.P, cx.ldP, nb, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, trans);
+    apply_any<real>(cx.P, cx.ldP, nv, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, trans);
     store_block(Ct + l0, nb, cx.Top, ib, ib, w);
     __syncthreads();
   }
@@ -1026,12 +1059,15 @@ __global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __rest
       cur_cs = I.cs;
     }
     switch (t.kind) {
-      case K_GEQRT: exec_geqrt(cx, I, t.k); break;
-      case K_TSQRT: exec_tsqrt(cx, I, t.k, t.i); break;
-      case K_LARFB: exec_larfb(cx, I, t.k, t.j, t.s, true); break;
-      case K_LARFB_N: exec_larfb(cx, I, t.k, t.j, t.s, false); break;
-      case K_SSRFB: exec_ssrfb(cx, I, t.k, t.i, t.j, t.s, true); break;
-      case K_SSRFB_N: exec_ssrfb(cx, I, t.k, t.i, t.j, t.s, false); break;
+      case K_GEQRT: exec_geqrt(cx, I, t.k, t.i); break;
+      case K_TSQRT: exec_tsqrt(cx, I, t.k, I.D > 0 ? t.l : t.k, t.i, false); break;
+      case K_LARFB: exec_larfb(cx, I, t.k, t.i, t.j, t.s, true); break;
+      case K_LARFB_N: exec_larfb(cx, I, t.k, t.i, t.j, t.s, false); break;
+      case K_SSRFB: exec_ssrfb(cx, I, t.k, I.D > 0 ? t.l : t.k, t.i, t.j, t.s, true, false); break;
+      case K_SSRFB_N: exec_ssrfb(cx, I, t.k, I.D > 0 ? t.l : t.k, t.i, t.j, t.s, false, false); break;
+      case K_TTQRT: exec_tsqrt(cx, I, t.k, t.l, t.i, true); break;
+      case K_TTMQR: exec_ssrfb(cx, I, t.k, t.l, t.i, t.j, t.s, true, true); break;
+      case K_TTMQR_N: exec_ssrfb(cx, I, t.k, t.l, t.i, t.j, t.s, false, true); break;
       case K_TRSM_UPD: exec_trsm_upd(cx, I, t.k, t.l, t.j, t.s); break;
       case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
       case K_TRSMT_UPD: exec_trsmt_upd(cx, I, t.k, t.l, t.j, t.s); break;

@@ -237,6 +237,7 @@ bool LsJob::init(int m_, int n_, int rhs_cap_, int nb_, int ib_, int prec_, int 
   grid_cap = grid_cap_;
   if (!choose_shape(nb, ib, esize, &cs, &occ, &smem)) return false;
   I = make_inst(M_FACTOR, m, n, nb, ib, cs, rhs_cap, 1);
+  I.D = choose_domain(m, n, nb, ib, esize);  // reduction tree when it shortens the run
   W = ws_layout(I, esize, true);
   sc = ls_scratch_shape(m, n, rhs_cap);
   const size_t mr = static_cast<size_t>(m) * rhs_cap, nr = static_cast<size_t>(n) * rhs_cap;
@@ -297,6 +298,7 @@ int LsJob::unpack_rhs(double* dst, long long ldd, int rows, int nrhs, cudaStream
 // factor A (and keep the factors), x0 = the solution through those factors
 int LsJob::factor_solve(const double* A, long long lda, const double* B, long long ldb, int nrhs, cudaStream_t st) {
   const int sms = device_sms();
+  if (upload_vtab(I, ws, W, st) != TQR_OK) return TQR_ERR_CUDA;
   if (Acopy != nullptr &&
       cudaMemcpy2DAsync(Acopy, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
                         cudaMemcpyDeviceToDevice, st) != cudaSuccess)

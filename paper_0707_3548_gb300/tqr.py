@@ -76,6 +76,9 @@ SIGNATURES = {
     "tqr_batch_submit": (_int, [_int, _vp, ctypes.POINTER(ctypes.c_uint64), _vp]),
     "tqr_batch_poll": (_int, [ctypes.c_uint64, ctypes.POINTER(_int), _vp]),
     "tqr_batch_wait": (_int, [ctypes.c_uint64, _vp]),
+    "tqr_t_size_tree": (_size, [_i64, _i64, _int, _int]),
+    "tqr_factor_tree": (_int, [_i64, _i64, _vp, _i64, _int, _int, ctypes.POINTER(_int), _vp, _vp]),
+    "tqr_apply_qt_tree": (_int, [ctypes.c_char, _i64, _i64, _i64, _vp, _i64, _int, _int, _int, _vp, _vp, _i64, _vp]),
     "tqr_stream_status": (_int, [_vp]),
     "tqr_set_wait_limit_ms": (_i64, [_i64]),
     "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
@@ -201,6 +204,33 @@ def tqr_factor(A, nb, ib, T=None, stream=None, check=True):
     if check:
         _check("tqr_factor", rc)
     return T if check else (T, rc)
+
+
+def tqr_t_size_tree(m, n, nb, ib):
+    return lib().tqr_t_size_tree(m, n, nb, ib)
+
+
+def tqr_factor_tree(A, nb, ib, D=0, T=None, stream=None):
+    """Reduction-tree factorization in place; returns (T, D) with the domain
+    size used (D = 0 lets the library choose)."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    if T is None:
+        cnt = tqr_t_size_tree(m, n, nb, ib) // 8
+        T = np.zeros(cnt) if isinstance(A, np.ndarray) else _torch().zeros(cnt, dtype=_torch().float64,
+                                                                             device=A.device)
+    d = _int(D)
+    _check("tqr_factor_tree", lib().tqr_factor_tree(m, n, pa, lda, nb, ib, ctypes.byref(d), _ptr(T),
+                                                     _stream(cuda, stream)))
+    return T, d.value
+
+
+def tqr_apply_qt_tree(trans, A, nb, ib, D, T, B, stream=None):
+    pa, m, n, lda, cuda = _mat(A, "A")
+    pb, mb, nrhs, ldb, _ = _mat(B, "B")
+    _check("tqr_apply_qt_tree", lib().tqr_apply_qt_tree(trans.encode() if isinstance(trans, str) else trans, m, n,
+                                                         nrhs, pa, lda, nb, ib, D, _ptr(T), pb, ldb,
+                                                         _stream(cuda, stream)))
+    return B
 
 
 def tqr_factor_noalloc(A, nb, ib, T, stream=None, check=True):
