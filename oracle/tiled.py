@@ -384,3 +384,35 @@ def tree_apply_q(f, B):
     nb = f.nb
     _tree_steps(f, lambda i: Bp[i * nb:(i + 1) * nb], trans=False)
     return Bp[:f.m]
+
+
+# ---------------------------------------------------------------------------
+# Applying and forming Q (the LAPACK DORMQR / DORGQR pair that the paper's
+# conclusion names as direct derivations of the tiled factorization).  These
+# are the plain definitions on top of apply_q / apply_qt: the right-hand side
+# forms follow from (C Q)^T = Q^T C^T and (C Q^T)^T = Q C^T, and the explicit
+# Q columns are Q applied to the leading columns of the identity.
+
+def _left(f, trans, C):
+    tree = isinstance(f, TreeFactors)
+    if trans:
+        return tree_apply_qt(f, C) if tree else apply_qt(f, C)
+    return tree_apply_q(f, C) if tree else apply_q(f, C)
+
+
+def ormqr(f, side, trans, C):
+    """op(Q) C (side 'L') or C op(Q) (side 'R'), op(Q) = Q^T when trans is
+    'T' and Q when 'N'.  Q is m x m (m = f.m); C is m x c ('L') or c x m ('R')."""
+    C = np.asarray(C, dtype=np.float64)
+    t = trans in ("T", "t")
+    if side in ("L", "l"):
+        assert C.shape[0] == f.m
+        return _left(f, t, C)
+    assert C.shape[1] == f.m
+    return _left(f, not t, C.T).T
+
+
+def orgqr(f, ncols):
+    """The first ncols columns of Q (m x ncols, 0 <= ncols <= m)."""
+    assert 0 <= ncols <= f.m
+    return _left(f, False, np.eye(f.m, ncols))
