@@ -53,6 +53,11 @@ WORKLOADS = {
     # batched QR: 4096 independent matrices, m log-uniform [64, 2048], n uniform
     # [32, m], N(0,1), tile sizes from the autotuner, one persistent launch
     "batch4096": dict(count=4096, batch=True),
+    # Q suite on the 16384 x 16384 factorization: the explicit thin Q
+    # (DORGQR analogue) and C Q for a 4096 x 16384 block C (DORMQR analogue,
+    # right side)
+    "orgqr16384": dict(m=16384, n=16384, nb=128, ib=16, qsuite="orgqr"),
+    "ormqr16384r4096": dict(m=16384, n=16384, nb=128, ib=16, qsuite="ormqr", mc=4096),
     "serve": dict(rate=2000.0, window=1.0, budget=64 << 30, slots=4, pool_bytes=2 << 30, serve=True),
     "serve_low": dict(rate=20.0, window=5.0, budget=64 << 30, slots=4, pool_bytes=2 << 30, serve=True),
 }
@@ -416,6 +421,112 @@ def run_ls(args, w):
     print(json.dumps(line), flush=True)
 
 
+def run_qsuite(args, w):
+    """tqr_orgqr (explicit thin Q) or tqr_ormqr (C Q, right side) on a
+    factorization made once before the timed region.  LAPACK's operation
+    counts: DORGQR 4 m c k - 2 (m + c) k^2 + 4 k^3 / 3 (c columns, k
+    reflector columns), DORMQR right side 4 mc m k - 2 mc k^2."""
+    import numpy as np
+    import torch
+
+    from paper_0707_3548_gb300 import build as B
+    from paper_0707_3548_gb300 import inputs, tqr
+
+    torch.cuda.set_device(0)
+    B.build()
+    m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
+    k = min(m, n)
+    A = inputs.normal_matrix(m, n, 0)
+    dA = tqr.colmajor(torch.from_numpy(A).cuda())
+    T = tqr.tqr_factor(dA, nb, ib)
+    org = w["qsuite"] == "orgqr"
+    if org:
+        c = n
+        out = tqr.colmajor(torch.empty((m, c), dtype=torch.float64, device="cuda"))
+        flops = 4.0 * m * c * k - 2.0 * (m + c) * k * k + 4.0 * k ** 3 / 3.0
+        name = "explicit thin Q (%dx%d) of the tiled QR of a %dx%d N(0,1) matrix, nb=%d ib=%d" % (m, c, m, n, nb, ib)
+        metric = "DORGQR-analogue TFLOP/s (4mck-2(m+c)k^2+4k^3/3) vs FP64 peak"
+
+        def step():
+            tqr.tqr_orgqr(dA, nb, ib, T, c, Q=out)
+    else:
+        mc = w["mc"]
+        C0 = tqr.colmajor(torch.from_numpy(inputs.normal_matrix(mc, m, 1)).cuda())
+        out = torch.empty_like(C0)
+        out = tqr.colmajor(out)
+        flops = 4.0 * mc * m * k - 2.0 * mc * k * k
+        name = "C Q, C %dx%d N(0,1), Q of the tiled QR of a %dx%d N(0,1) matrix, nb=%d ib=%d" % (mc, m, m, n, nb, ib)
+        metric = "DORMQR-analogue TFLOP/s (right side, 4 mc m k - 2 mc k^2) vs FP64 peak"
+
+        def step():
+            out.copy_(C0)
+            tqr.tqr_ormqr("R", "N", dA, nb, ib, T, out)
+    stream = torch.cuda.current_stream()
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    assert tqr.tqr_stream_status() == tqr.TQR_OK
+    props = torch.cuda.get_device_properties(0)
+    try:
+        bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except AttributeError:
+        bus = None
+    tqr.tqr_debug_timing(1)
+    tqr.tqr_debug_timing_read()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    with ClockSampler(bus) as clk:
+        torch.cuda.synchronize()
+        e0.record(stream)
+        for _ in range(args.steps):
+            step()
+        e1.record(stream)
+        torch.cuda.synchronize()
+    kern_ms, launches = tqr.tqr_debug_timing_read()
+    tqr.tqr_debug_timing(0)
+    status = tqr.tqr_stream_status()
+    elapsed_ms = e0.elapsed_time(e1)
+    value = flops * args.steps / (elapsed_ms * 1e-3) / 1e12
+    # end to end with host buffers (A, T and the operand copied in, the result out)
+    e2e = None
+    if not args.no_e2e:
+        hA, hT = dA.cpu().numpy(), T.cpu().numpy()
+        hA = np.asfortranarray(hA)
+        hO = np.asfortranarray(out.cpu().numpy())
+        hC0 = None if org else np.asfortranarray(C0.cpu().numpy())
+        ts = []
+        for it in range(args.warmup + args.steps):
+            if not org:
+                np.copyto(hO, hC0)
+            t0 = time.perf_counter()
+            if org:
+                tqr.tqr_orgqr(hA, nb, ib, hT, n, Q=hO)
+            else:
+                tqr.tqr_ormqr("R", "N", hA, nb, ib, hT, hO)
+            if it >= args.warmup:
+                ts.append(time.perf_counter() - t0)
+        sec = statistics.mean(ts)
+        h2d = 8 * (m * n + hT.size) + (0 if org else 8 * hO.size)
+        e2e = {"value": flops / sec / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
+               "d2h_bytes_per_step": 8 * hO.size, "ms_per_step": 1e3 * sec}
+    peak = tqr.tqr_debug_fp64_peak()
+    kern_avg_ms = kern_ms / max(1, launches)
+    achieved = flops / (kern_avg_ms * 1e-3) / 1e12
+    line = {"metric": metric, "value": value, "unit": "TFLOP/s", "n_gpus": 1, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: N(0,1), NumPy PCG64",
+            "config": {"workload": name, "m": m, "n": n, "nb": nb, "ib": ib, "flops_per_step": flops,
+                       "l2": "operands (2 GiB A, %d MiB result) > 129 MB L2" % (8 * out.numel() >> 20)},
+            "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                         "frac": achieved / peak, "traffic": None,
+                         "kernel": "tqr::run_tasks_kernel<double> (persistent task scheduler)",
+                         "peak_source": "FP64 DFMA probe measured in this run (tqr_debug_fp64_peak)",
+                         "kernel_ms_per_launch": kern_avg_ms},
+            "cpu_baseline": None, "e2e": e2e, "gpu_launches": 4 * args.steps,
+            "clocks": clk.summary(), "status": status}
+    print(json.dumps(line), flush=True)
+
+
 def run_batch(args, w):
     """Batched factorization: all matrices in one persistent launch (CUDA
     graph), value = total 2mn^2 - 2n^3/3 over the batch / device time."""
@@ -475,6 +586,7 @@ def run_batch(args, w):
             "config": {"workload": "batched QR of %d matrices, m log-uniform [64, 2048], n uniform [32, m], one "
                                    "persistent launch, autotuned nb/ib" % len(shapes),
                        "total_flops": flops, "total_bytes": 8 * sum(m * n for m, n in shapes),
+                       "l2": "inputs > 129 MB L2, restored from device copies before each step",
                        "tile_classes": classes},
             "first_submit_s_incl_plan": t_plan, "gpu_launches": 3 * args.steps}
     print(json.dumps(line), flush=True)
@@ -589,6 +701,8 @@ def main():
         run_serve(args, w)
     elif w.get("batch"):
         run_batch(args, w)
+    elif w.get("qsuite"):
+        run_qsuite(args, w)
     else:
         run_ours(args, w)
 

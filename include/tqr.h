@@ -148,6 +148,47 @@ int tqr_apply_qt_tree(char trans, int64_t m, int64_t n, int64_t nrhs, const doub
                       int nb, int ib, int D, const double* T, double* B, int64_t ldb, void* stream);
 
 /*
+ * Applying and forming Q -- the DORMQR / DORGQR pair that the paper's
+ * conclusion (Section 5) names as direct derivations of the tiled
+ * factorization.  Q is the m x m orthogonal factor of a factorization made by
+ * tqr_factor (D = 0) or tqr_factor_tree (D = its domain size), given by the
+ * factored A (m x n, lda), nb, ib and T exactly as that call left them.
+ *
+ * tqr_ormqr(side, trans, m, n, A, lda, nb, ib, D, T, mc, nc, C, ldc, stream)
+ *   side   (arg 1)   'L': C <- op(Q) C, C is m x nc (mc must equal m)
+ *                    'R': C <- C op(Q), C is mc x m (nc must equal m)
+ *   trans  (arg 2)   'N': op(Q) = Q, 'T': op(Q) = Q^T
+ *   m, n   (args 3, 4), A, lda (5, 6), nb, ib (7, 8): the factorization
+ *   D      (arg 9)   0 for tqr_factor, the domain size for tqr_factor_tree
+ *   T      (arg 10)  tqr_t_size (D = 0) or tqr_t_size_tree bytes
+ *   mc, nc (args 11, 12), C, ldc (13, 14): column-major, ldc >= max(1, mc),
+ *                    overwritten with the product
+ *   The right side runs as the left-side task graph on C^T: the library packs
+ *   C transposed into its tiles and unpacks it back, since
+ *   C Q = (Q^T C^T)^T and C Q^T = (Q C^T)^T.
+ *
+ * tqr_orgqr(m, n, A, lda, nb, ib, D, T, ncols, Q, ldq, stream)
+ *   Writes the first ncols (0 <= ncols <= m, arg 9) columns of Q to Q (arg 10,
+ *   m x ncols, ldq >= max(1, m), arg 11); ncols = n gives the thin Q of
+ *   A = Q R.  Other arguments as for tqr_ormqr (A is arg 3, T arg 8).  With
+ *   the flat panel (D = 0) step k of the reverse accumulation skips the
+ *   identity's tile columns < k, which its reflectors cannot reach (they
+ *   touch rows >= k*nb only), so the work is that of the factorization's
+ *   updates, not of a full m x ncols product.
+ *
+ * Both calls: A, T, C / Q all on the device (asynchronous on stream) or all
+ * on the host (staged through device copies; the call synchronizes).  They
+ * return 0, -i for an invalid argument i, TQR_ERR_NOMEM, TQR_ERR_CUDA or a
+ * device status (TQR_ERR_TIMEOUT).  m, n, mc, nc above 2^30 give
+ * TQR_ERR_UNSUPPORTED; empty operands return 0 at once (n = 0 means Q = I).
+ */
+int tqr_ormqr(char side, char trans, int64_t m, int64_t n, const double* A, int64_t lda, int nb,
+              int ib, int D, const double* T, int64_t mc, int64_t nc, double* C, int64_t ldc,
+              void* stream);
+int tqr_orgqr(int64_t m, int64_t n, const double* A, int64_t lda, int nb, int ib, int D,
+              const double* T, int64_t ncols, double* Q, int64_t ldq, void* stream);
+
+/*
  * Least squares  min ||A x - b||_2  for full-rank A, m >= n, through the
  * tiled QR: x = R[0:n,0:n]^{-1} (Q^T b)[0:n].  The factorization, Q^T B and
  * the back substitution run as one task graph on the device.

@@ -18,7 +18,10 @@ extern "C" {
 /*
  * Builds the ordered task list of one launch.
  *   mode     (arg 1)  0 factor, 1 apply Q^T, 2 apply Q, 3 back substitution,
- *                     4 forward substitution with R^T
+ *                     4 forward substitution with R^T, 5 apply Q to the
+ *                     leading columns of the identity (explicit Q; step k
+ *                     skips right-hand-side tile columns < k; flat panel
+ *                     only, D must be 0)
  *   m, n     (args 2, 3), nb, ib (args 4, 5) as for tqr_factor
  *   cs       (arg 6)  slab width (columns) of the column-slab tasks; must
  *                     divide nb

@@ -503,12 +503,19 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
 }
 
 // ---------------------------------------------------------------- apply
+// How the right-hand-side tiles are filled and returned.
+//   RHS_PLAIN       B is m x nrhs (ldb), packed and unpacked as is
+//   RHS_TRANSPOSED  B holds C = X^T, nrhs x m (ldb >= nrhs); the tiles hold X
+//   RHS_IDENTITY    the tiles start as the leading nrhs columns of I_m; B
+//                   (m x nrhs) receives the result
+enum RhsForm { RHS_PLAIN = 0, RHS_TRANSPOSED = 1, RHS_IDENTITY = 2 };
+
 template <typename real>
-static int apply_device(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb,
+static int apply_device(int mode, int form, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb,
                         int ib, int D, const real* T, double* B, int64_t ldb, cudaStream_t st) {
   int cs, occ, smem;
   if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
-  Inst I = make_inst(trans == 'T' ? M_APPLY_QT : M_APPLY_Q, m, n, nb, ib, cs, static_cast<int>(nrhs), 0);
+  Inst I = make_inst(mode, m, n, nb, ib, cs, static_cast<int>(nrhs), 0);
   I.D = D;
   const WsLayout W = ws_layout(I, sizeof(real), false);
   char* ws = nullptr;
@@ -521,18 +528,69 @@ static int apply_device(char trans, int64_t m, int64_t n, int64_t nrhs, const do
   I.T = const_cast<real*>(T);
   I.ver = reinterpret_cast<int*>(ws + W.oVer);
   const int sms = device_sms();
-  int status = upload_vtab(I, ws, W, st);
-  if (status != TQR_OK ||
-      launch_pack<real>(A, lda, static_cast<int>(m), static_cast<int>(n), static_cast<real*>(I.A), I.p, I.q, nb, sms,
-                        st) != cudaSuccess ||
-      launch_pack<real>(B, ldb, static_cast<int>(m), static_cast<int>(nrhs), static_cast<real*>(I.B), I.p, I.qb, nb,
-                        sms, st) != cudaSuccess)
-    status = TQR_ERR_CUDA;
-  if (status == TQR_OK) status = run_plan<real>(I, ws, W, occ, smem, st);
-  if (status == TQR_OK && launch_unpack<real>(static_cast<real*>(I.B), I.p, nb, B, ldb, static_cast<int>(m),
-                                              static_cast<int>(nrhs), sms, st) != cudaSuccess)
-    status = TQR_ERR_CUDA;
+  const int mi = static_cast<int>(m), ni = static_cast<int>(n), ri = static_cast<int>(nrhs);
+  real* Bt = static_cast<real*>(I.B);
+  int status = n > 0 ? upload_vtab(I, ws, W, st) : TQR_OK;
+  cudaError_t e = cudaSuccess;
+  if (status == TQR_OK && n > 0) e = launch_pack<real>(A, lda, mi, ni, static_cast<real*>(I.A), I.p, I.q, nb, sms, st);
+  if (status == TQR_OK && e == cudaSuccess) {
+    if (form == RHS_PLAIN) e = launch_pack<real>(B, ldb, mi, ri, Bt, I.p, I.qb, nb, sms, st);
+    else if (form == RHS_TRANSPOSED) e = launch_pack_t<real>(B, ldb, mi, ri, Bt, I.p, I.qb, nb, sms, st);
+    else e = launch_identity<real>(mi, ri, Bt, I.p, I.qb, nb, sms, st);
+  }
+  if (e != cudaSuccess) status = TQR_ERR_CUDA;
+  if (status == TQR_OK && n > 0) status = run_plan<real>(I, ws, W, occ, smem, st);
+  if (status == TQR_OK) {
+    e = form == RHS_TRANSPOSED ? launch_unpack_t<real>(Bt, I.p, nb, B, ldb, mi, ri, sms, st)
+                               : launch_unpack<real>(Bt, I.p, nb, B, ldb, mi, ri, sms, st);
+    if (e != cudaSuccess) status = TQR_ERR_CUDA;
+  }
   cudaFreeAsync(ws, st);
+  return status;
+}
+
+// Device or host operands.  B is brows x bcols with leading dimension ldb
+// (m x nrhs, or nrhs x m for RHS_TRANSPOSED).  Host operands are staged
+// through device copies on the stream; the call then synchronizes.
+static int apply_staged(int mode, int form, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb,
+                        int ib, int D, const double* T, double* B, int64_t ldb, int argA, int argT, int argB,
+                        void* stream) {
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int64_t brows = form == RHS_TRANSPOSED ? nrhs : m, bcols = form == RHS_TRANSPOSED ? m : nrhs;
+  const int ka = n > 0 ? ptr_kind(A) : ptr_kind(B);
+  if (n > 0 && ptr_kind(T) != ka) return -argT;
+  if (ptr_kind(B) != ka) return -argB;
+  if (ka == PTR_DEVICE) return apply_device<double>(mode, form, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, st);
+  const size_t tbytes = tqr_t_size(m, n, nb, ib) * (D > 0 ? 2 : 1);
+  double *dA = nullptr, *dT = nullptr, *dB = nullptr;
+  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * std::max<int64_t>(1, m * n), st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dT), std::max<size_t>(8, tbytes), st) != cudaSuccess ||
+      cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * brows * bcols, st) != cudaSuccess) {
+    cudaGetLastError();
+    if (dA) cudaFreeAsync(dA, st);
+    if (dT) cudaFreeAsync(dT, st);
+    return TQR_ERR_NOMEM;
+  }
+  int status = TQR_OK;
+  if ((n > 0 && (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                                   cudaMemcpyHostToDevice, st) != cudaSuccess ||
+                 cudaMemcpyAsync(dT, T, tbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)) ||
+      (form != RHS_IDENTITY && cudaMemcpy2DAsync(dB, sizeof(double) * brows, B, sizeof(double) * ldb,
+                                                 sizeof(double) * brows, bcols, cudaMemcpyHostToDevice,
+                                                 st) != cudaSuccess))
+    status = TQR_ERR_CUDA;
+  if (status == TQR_OK)
+    status = apply_device<double>(mode, form, m, n, nrhs, dA, std::max<int64_t>(1, m), nb, ib, D, dT, dB, brows, st);
+  if (status == TQR_OK && cudaMemcpy2DAsync(B, sizeof(double) * ldb, dB, sizeof(double) * brows,
+                                            sizeof(double) * brows, bcols, cudaMemcpyDeviceToHost,
+                                            st) != cudaSuccess)
+    status = TQR_ERR_CUDA;
+  cudaFreeAsync(dA, st);
+  cudaFreeAsync(dT, st);
+  cudaFreeAsync(dB, st);
+  int dev_status = TQR_OK;
+  if (read_status(&dev_status, st) != cudaSuccess) return TQR_ERR_CUDA;
+  if (status == TQR_OK) status = dev_status;
   return status;
 }
 
@@ -552,39 +610,8 @@ static int apply_common(char trans, int64_t m, int64_t n, int64_t nrhs, const do
   if (A == nullptr) return -5;
   if (T == nullptr) return -9;
   if (B == nullptr) return -10;
-  cudaStream_t st = static_cast<cudaStream_t>(stream);
-  const int ka = ptr_kind(A);
-  if (ptr_kind(T) != ka) return -9;
-  if (ptr_kind(B) != ka) return -10;
-  if (ka == PTR_DEVICE) return apply_device<double>(trans, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, st);
-  const size_t tbytes = tqr_t_size(m, n, nb, ib) * (D > 0 ? 2 : 1);
-  double *dA = nullptr, *dT = nullptr, *dB = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dT), tbytes, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess) {
-    cudaGetLastError();
-    if (dA) cudaFreeAsync(dA, st);
-    if (dT) cudaFreeAsync(dT, st);
-    return TQR_ERR_NOMEM;
-  }
-  int status = TQR_OK;
-  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpyAsync(dT, T, tbytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpy2DAsync(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess)
-    status = TQR_ERR_CUDA;
-  if (status == TQR_OK) status = apply_device<double>(trans, m, n, nrhs, dA, m, nb, ib, D, dT, dB, m, st);
-  if (status == TQR_OK && cudaMemcpy2DAsync(B, sizeof(double) * ldb, dB, sizeof(double) * m, sizeof(double) * m,
-                                            nrhs, cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    status = TQR_ERR_CUDA;
-  cudaFreeAsync(dA, st);
-  cudaFreeAsync(dT, st);
-  cudaFreeAsync(dB, st);
-  int dev_status = TQR_OK;
-  if (read_status(&dev_status, st) != cudaSuccess) return TQR_ERR_CUDA;
-  if (status == TQR_OK) status = dev_status;
-  return status;
+  return apply_staged(trans == 'T' ? M_APPLY_QT : M_APPLY_Q, RHS_PLAIN, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, 5,
+                      9, 10, stream);
 }
 
 extern "C" {
@@ -644,6 +671,52 @@ int tqr_apply_qt_tree(char trans, int64_t m, int64_t n, int64_t nrhs, const doub
   if (D < 1) return -9;
   const int r = apply_common(trans, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, stream);
   return (r <= -9) ? r - 1 : r;  // arguments after ib shift by one
+}
+
+int tqr_ormqr(char side, char trans, int64_t m, int64_t n, const double* A, int64_t lda, int nb, int ib, int D,
+              const double* T, int64_t mc, int64_t nc, double* C, int64_t ldc, void* stream) {
+  const bool left = side == 'L' || side == 'l';
+  if (!left && side != 'R' && side != 'r') return -1;
+  if (trans != 'T' && trans != 'N' && trans != 't' && trans != 'n') return -2;
+  const bool tr = trans == 'T' || trans == 't';
+  if (m < 0) return -3;
+  if (n < 0) return -4;
+  if (lda < std::max<int64_t>(1, m)) return -6;
+  const int c = check_tiles(nb, ib, 7, 8);
+  if (c) return c;
+  if (D < 0) return -9;
+  if (mc < 0 || (left && mc != m)) return -11;
+  if (nc < 0 || (!left && nc != m)) return -12;
+  if (ldc < std::max<int64_t>(1, mc)) return -14;
+  if (m > (1LL << 30) || n > (1LL << 30) || mc > (1LL << 30) || nc > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
+  if (m == 0 || n == 0 || mc == 0 || nc == 0) return TQR_OK;
+  if (A == nullptr) return -5;
+  if (T == nullptr) return -10;
+  if (C == nullptr) return -13;
+  // left: op(Q) C directly; right: C op(Q) = (op(Q)^T C^T)^T on the transposed tiles
+  const bool qt = left ? tr : !tr;
+  return apply_staged(qt ? M_APPLY_QT : M_APPLY_Q, left ? RHS_PLAIN : RHS_TRANSPOSED, m, n, left ? nc : mc, A, lda,
+                      nb, ib, D, T, C, ldc, 5, 10, 13, stream);
+}
+
+int tqr_orgqr(int64_t m, int64_t n, const double* A, int64_t lda, int nb, int ib, int D, const double* T,
+              int64_t ncols, double* Q, int64_t ldq, void* stream) {
+  if (m < 0) return -1;
+  if (n < 0) return -2;
+  if (lda < std::max<int64_t>(1, m)) return -4;
+  const int c = check_tiles(nb, ib, 5, 6);
+  if (c) return c;
+  if (D < 0) return -7;
+  if (ncols < 0 || ncols > m) return -9;
+  if (ldq < std::max<int64_t>(1, m)) return -11;
+  if (m > (1LL << 30) || n > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
+  if (m == 0 || ncols == 0) return TQR_OK;
+  if (n > 0 && A == nullptr) return -3;
+  if (n > 0 && T == nullptr) return -8;
+  if (Q == nullptr) return -10;
+  // flat panel: identity columns skip the steps that cannot touch them
+  return apply_staged(D == 0 ? M_FORM_Q : M_APPLY_Q, RHS_IDENTITY, m, n, ncols, A, lda, nb, ib, D, T, Q, ldq, 3, 8,
+                      10, stream);
 }
 
 int tqr_stream_status(void* stream) {

@@ -15,7 +15,7 @@ extern "C" {
 
 int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int D,
                        int workers, int policy, int32_t* out, int64_t cap, double* stats) {
-  if (mode < 0 || mode > 4) return -1;
+  if (mode < 0 || mode > M_FORM_Q) return -1;
   if (m < 1) return -2;
   if (n < 1) return -3;
   if (check_tiles(nb, ib, 4, 5) != 0) return check_tiles(nb, ib, 4, 5);
@@ -23,7 +23,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   if (nrhs < 0) return -7;
   if (mode != 0 && nrhs == 0) return -7;
   if (trsm && (nrhs == 0 || m < n || (mode != 0 && mode != 1))) return -8;
-  if (D < 0) return -9;
+  if (D < 0 || (D > 0 && mode == M_FORM_Q)) return -9;
   if (workers < 1) return -10;
   if (policy < -1 || policy > 1) return -11;
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);

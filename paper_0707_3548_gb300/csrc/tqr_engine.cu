@@ -1155,6 +1155,80 @@ __global__ void unpack_batched_kernel(const PackDesc* __restrict__ descs, int co
   }
 }
 
+// Transposed operands (right-hand application C op(Q) = (op(Q)^T C^T)^T):
+// X = C^T, mt x nt with X(a, b) = C[b + a*ldc], goes into BDL tiles (p x q,
+// zero padded) and comes back the same way.  32 x 32 blocks pass through
+// shared memory so that both C (along b) and the tiles (along a) are
+// accessed with consecutive lanes on consecutive addresses.  256 threads:
+// lane tx = threadIdx.x % 32, row group ty = threadIdx.x / 32 (8 groups).
+template <typename D>
+__global__ void pack_t_kernel(const double* __restrict__ C, long long ldc, int mt, int nt, D* __restrict__ Ab,
+                              int p, int q, int nb) {
+  __shared__ double tile[32][33];
+  const long long rows = static_cast<long long>(p) * nb, cols = static_cast<long long>(q) * nb;
+  const long long ba = (rows + 31) / 32, bb = (cols + 31) / 32;
+  const long long nb2 = static_cast<long long>(nb) * nb;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (long long blk = blockIdx.x; blk < ba * bb; blk += gridDim.x) {
+    const long long a0 = (blk % ba) * 32, b0 = (blk / ba) * 32;
+    for (int r = ty; r < 32; r += 8) {
+      const long long a = a0 + r, b = b0 + tx;
+      tile[r][tx] = (a < mt && b < nt) ? C[b + a * ldc] : 0.0;   // X(a0 + r, b0 + tx)
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const long long a = a0 + tx, b = b0 + r;
+      if (a < rows && b < cols) {
+        const long long ti = a / nb, tj = b / nb;
+        Ab[(ti + tj * p) * nb2 + (b - tj * nb) * nb + (a - ti * nb)] = static_cast<D>(tile[tx][r]);
+      }
+    }
+    __syncthreads();
+  }
+}
+
+template <typename S>
+__global__ void unpack_t_kernel(const S* __restrict__ Ab, int p, int nb, double* __restrict__ C, long long ldc,
+                                int mt, int nt) {
+  __shared__ double tile[32][33];
+  const long long ba = (static_cast<long long>(mt) + 31) / 32, bb = (static_cast<long long>(nt) + 31) / 32;
+  const long long nb2 = static_cast<long long>(nb) * nb;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;
+  for (long long blk = blockIdx.x; blk < ba * bb; blk += gridDim.x) {
+    const long long a0 = (blk % ba) * 32, b0 = (blk / ba) * 32;
+    for (int r = ty; r < 32; r += 8) {
+      const long long a = a0 + tx, b = b0 + r;
+      double v = 0.0;
+      if (a < mt && b < nt) {
+        const long long ti = a / nb, tj = b / nb;
+        v = static_cast<double>(Ab[(ti + tj * p) * nb2 + (b - tj * nb) * nb + (a - ti * nb)]);
+      }
+      tile[r][tx] = v;                                            // X(a0 + tx, b0 + r)
+    }
+    __syncthreads();
+    for (int r = ty; r < 32; r += 8) {
+      const long long a = a0 + r, b = b0 + tx;
+      if (a < mt && b < nt) C[b + a * ldc] = tile[tx][r];
+    }
+    __syncthreads();
+  }
+}
+
+// The leading ncols columns of the m x m identity in BDL (p x q tiles).
+template <typename D>
+__global__ void identity_kernel(int m, int ncols, D* __restrict__ Ab, int p, int q, int nb) {
+  const long long nb2 = static_cast<long long>(nb) * nb;
+  const long long total = nb2 * p * q;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const long long tile = e / nb2;
+    const int rem = static_cast<int>(e - tile * nb2);
+    const int r = rem % nb, c = rem / nb;
+    const long long gi = (tile % p) * nb + r, gj = (tile / p) * nb + c;
+    Ab[e] = (gi == gj && gi < m && gj < ncols) ? D(1) : D(0);
+  }
+}
+
 __global__ void status_reset_kernel() { g_status = 0; }
 
 // ---------------------------------------------------------------- host launchers
@@ -1179,6 +1253,32 @@ cudaError_t launch_unpack(const real* Ab, int p, int nb, double* A, long long ld
                           cudaStream_t st) {
   if (static_cast<long long>(m) * n == 0) return cudaSuccess;
   unpack_kernel<real, double><<<grid_for(static_cast<long long>(m) * n, sms), 256, 0, st>>>(Ab, p, nb, A, lda, m, n);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_pack_t(const double* C, long long ldc, int mt, int nt, real* Ab, int p, int q, int nb, int sms,
+                          cudaStream_t st) {
+  const long long blocks = ((static_cast<long long>(p) * nb + 31) / 32) * ((static_cast<long long>(q) * nb + 31) / 32);
+  const long long cap = static_cast<long long>(sms) * 8;
+  pack_t_kernel<real><<<static_cast<int>(blocks < cap ? blocks : cap), 256, 0, st>>>(C, ldc, mt, nt, Ab, p, q, nb);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_unpack_t(const real* Ab, int p, int nb, double* C, long long ldc, int mt, int nt, int sms,
+                            cudaStream_t st) {
+  if (static_cast<long long>(mt) * nt == 0) return cudaSuccess;
+  const long long blocks = ((static_cast<long long>(mt) + 31) / 32) * ((static_cast<long long>(nt) + 31) / 32);
+  const long long cap = static_cast<long long>(sms) * 8;
+  unpack_t_kernel<real><<<static_cast<int>(blocks < cap ? blocks : cap), 256, 0, st>>>(Ab, p, nb, C, ldc, mt, nt);
+  return cudaGetLastError();
+}
+
+template <typename real>
+cudaError_t launch_identity(int m, int ncols, real* Ab, int p, int q, int nb, int sms, cudaStream_t st) {
+  const long long total = static_cast<long long>(nb) * nb * p * q;
+  identity_kernel<real><<<grid_for(total, sms), 256, 0, st>>>(m, ncols, Ab, p, q, nb);
   return cudaGetLastError();
 }
 
@@ -1304,6 +1404,11 @@ template cudaError_t launch_unpack<float>(const float*, int, int, double*, long 
 template cudaError_t launch_run<double>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t);
 template cudaError_t launch_run<float>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t);
 template cudaError_t occupancy<double>(int, int*);
+template cudaError_t launch_pack_t<double>(const double*, long long, int, int, double*, int, int, int, int,
+                                           cudaStream_t);
+template cudaError_t launch_unpack_t<double>(const double*, int, int, double*, long long, int, int, int,
+                                             cudaStream_t);
+template cudaError_t launch_identity<double>(int, int, double*, int, int, int, int, cudaStream_t);
 template cudaError_t launch_pack_batched<double>(const PackDesc*, int, cudaStream_t);
 template cudaError_t launch_unpack_batched<double>(const PackDesc*, int, cudaStream_t);
 template cudaError_t occupancy<float>(int, int*);

@@ -14,6 +14,16 @@ cudaError_t launch_pack(const double* A, long long lda, int m, int n, real* Ab, 
 template <typename real>
 cudaError_t launch_unpack(const real* Ab, int p, int nb, double* A, long long lda, int m, int n, int sms,
                           cudaStream_t st);
+// Transposed pack/unpack: X = C^T (mt x nt, X(a, b) = C[b + a*ldc]) to and
+// from BDL tiles; identity: the leading ncols columns of I_m in BDL.
+template <typename real>
+cudaError_t launch_pack_t(const double* C, long long ldc, int mt, int nt, real* Ab, int p, int q, int nb, int sms,
+                          cudaStream_t st);
+template <typename real>
+cudaError_t launch_unpack_t(const real* Ab, int p, int nb, double* C, long long ldc, int mt, int nt, int sms,
+                            cudaStream_t st);
+template <typename real>
+cudaError_t launch_identity(int m, int ncols, real* Ab, int p, int q, int nb, int sms, cudaStream_t st);
 template <typename real>
 cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
                        int smem_bytes, cudaStream_t st);

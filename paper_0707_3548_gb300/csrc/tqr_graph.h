@@ -55,7 +55,11 @@ enum Kind : int {
   K_NKINDS = 13
 };
 
-enum Mode : int { M_FACTOR = 0, M_APPLY_QT = 1, M_APPLY_Q = 2, M_TRSM = 3, M_TRSMT = 4 };
+// M_FORM_Q: M_APPLY_Q on right-hand sides that start as the leading columns
+// of the identity (flat panel only).  Column c of the identity has no entry in
+// the rows that step k's reflectors touch (rows >= k*nb) when c < k*nb, so
+// step k skips right-hand-side tile columns jb < k: those stay exact.
+enum Mode : int { M_FACTOR = 0, M_APPLY_QT = 1, M_APPLY_Q = 2, M_TRSM = 3, M_TRSMT = 4, M_FORM_Q = 5 };
 
 // One task (32 bytes, two vector loads on the device).  k: elimination step;
 // i: row tile; j: column tile (A columns < q, right-hand-side columns >= q);
@@ -267,9 +271,18 @@ TQR_HD int task_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* n
       sg[(*nsig)++] = {ctr_index(I, i, j, s), 1};
       break;
     case K_SSRFB_N: {
-      // sequential order: for k = kt-1..0 { for i = p-1..k+1 SSRFB_N(k,i); LARFB_N(k) }
+      // sequential order: for k = kt-1..0 { for i = p-1..k+1 SSRFB_N(k,i); LARFB_N(k) }.
+      // Tile (i,j) receives one write from each step k' in (k, min(i,kt)) and
+      // p - i writes from step i (if i < kt); M_FORM_Q keeps only steps
+      // k' <= jb = j - q.
       int mi = i < kt ? i : kt;
-      int bot = (i < kt ? (p - i) : 0) + (mi - 1 - k);
+      bool own = i < kt;
+      if (I.mode == M_FORM_Q) {
+        const int jb1 = j - I.q + 1;
+        if (jb1 < mi) mi = jb1;
+        own = own && i < jb1;
+      }
+      int bot = (own ? (p - i) : 0) + (mi - 1 - k);
       w[nw++] = {ctr_index(I, k, j, s), 1, p - 1 - i};
       w[nw++] = {ctr_index(I, i, j, s), 1, bot};
       sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};

@@ -147,6 +147,16 @@ void seq_tasks(const Inst& I, int x, std::vector<TaskX>& out) {
           for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_LARFB_N, x, k, k, j, s));
       }
       break;
+    case M_FORM_Q:
+      for (int k = kt - 1; k >= 0; --k) {
+        const int j0 = q + k < qt ? q + k : qt;
+        for (int i = p - 1; i > k; --i)
+          for (int j = j0; j < qt; ++j)
+            for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_SSRFB_N, x, k, i, j, s));
+        for (int j = j0; j < qt; ++j)
+          for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_LARFB_N, x, k, k, j, s));
+      }
+      break;
     case M_TRSM:
       for (int j = q; j < qt; ++j)
         for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s)

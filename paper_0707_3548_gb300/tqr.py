@@ -79,6 +79,9 @@ SIGNATURES = {
     "tqr_t_size_tree": (_size, [_i64, _i64, _int, _int]),
     "tqr_factor_tree": (_int, [_i64, _i64, _vp, _i64, _int, _int, ctypes.POINTER(_int), _vp, _vp]),
     "tqr_apply_qt_tree": (_int, [ctypes.c_char, _i64, _i64, _i64, _vp, _i64, _int, _int, _int, _vp, _vp, _i64, _vp]),
+    "tqr_ormqr": (_int, [ctypes.c_char, ctypes.c_char, _i64, _i64, _vp, _i64, _int, _int, _int, _vp, _i64, _i64, _vp,
+                         _i64, _vp]),
+    "tqr_orgqr": (_int, [_i64, _i64, _vp, _i64, _int, _int, _int, _vp, _i64, _vp, _i64, _vp]),
     "tqr_stream_status": (_int, [_vp]),
     "tqr_set_wait_limit_ms": (_i64, [_i64]),
     "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
@@ -231,6 +234,36 @@ def tqr_apply_qt_tree(trans, A, nb, ib, D, T, B, stream=None):
                                                          nrhs, pa, lda, nb, ib, D, _ptr(T), pb, ldb,
                                                          _stream(cuda, stream)))
     return B
+
+
+def _ch(c):
+    return c.encode() if isinstance(c, str) else c
+
+
+def tqr_ormqr(side, trans, A, nb, ib, T, C, D=0, stream=None):
+    """C <- op(Q) C (side 'L') or C op(Q) (side 'R') in place, for the
+    factorization held in (A, nb, ib, T, D); returns C."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    pc, mc, nc, ldc, _ = _mat(C, "C")
+    _check("tqr_ormqr", lib().tqr_ormqr(_ch(side), _ch(trans), m, n, pa, lda, nb, ib, D, _ptr(T), mc, nc, pc, ldc,
+                                        _stream(cuda, stream)))
+    return C
+
+
+def tqr_orgqr(A, nb, ib, T, ncols=None, D=0, Q=None, stream=None):
+    """The first ncols columns of Q (default n: the thin Q), written to Q
+    (allocated column-major on A's device if not given); returns Q."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    if ncols is None:
+        ncols = n
+    if Q is None:
+        if isinstance(A, np.ndarray):
+            Q = np.zeros((m, ncols), order="F")
+        else:
+            Q = colmajor(_torch().zeros((m, ncols), dtype=_torch().float64, device=A.device))
+    pq, mq, nq, ldq, _ = _mat(Q, "Q")
+    _check("tqr_orgqr", lib().tqr_orgqr(m, n, pa, lda, nb, ib, D, _ptr(T), nq, pq, ldq, _stream(cuda, stream)))
+    return Q
 
 
 def tqr_factor_noalloc(A, nb, ib, T, stream=None, check=True):

@@ -17,7 +17,7 @@ from oracle import tiled as TL
 from paper_0707_3548_gb300 import inputs, tqr
 
 GEQRT, TSQRT, LARFB, SSRFB, LARFB_N, SSRFB_N, TRSM_UPD, TRSM_SOLVE, TRSMT_UPD, TRSMT_SOLVE = range(10)
-FACTOR, APPLY_QT, APPLY_Q, TRSM, TRSMT = range(5)
+FACTOR, APPLY_QT, APPLY_Q, TRSM, TRSMT, FORM_Q = range(6)
 
 
 class Grid:
@@ -105,7 +105,9 @@ def expected_tasks(mode, g, trsm=0):
         if mode in (FACTOR, APPLY_QT):
             out += [(LARFB, s, k, k, j, 0) for j in cols for s in range(g.slabs(j))]
             out += [(SSRFB, s, k, i, j, 0) for i in range(k + 1, g.p) for j in cols for s in range(g.slabs(j))]
-        if mode == APPLY_Q:
+        if mode == FORM_Q:
+            cols = [j for j in cols if j - g.q >= k]
+        if mode in (APPLY_Q, FORM_Q):
             out += [(LARFB_N, s, k, k, j, 0) for j in cols for s in range(g.slabs(j))]
             out += [(SSRFB_N, s, k, i, j, 0) for i in range(k + 1, g.p) for j in cols for s in range(g.slabs(j))]
     if mode == TRSM or (mode in (FACTOR, APPLY_QT) and trsm):
@@ -238,6 +240,35 @@ def test_apply_plans(m, n, nb, ib, cs, nrhs):
         for t in random_valid_order(mode, g, plan, 1):
             execute(g, t)
         assert np.allclose(g.B[:m, :nrhs], ref, atol=1e-12)
+
+
+@pytest.mark.parametrize("m,n,nb,ib,cs,ncols", [(70, 45, 16, 8, 8, 45), (64, 64, 16, 4, 16, 64), (50, 16, 8, 8, 8, 50),
+                                                 (45, 70, 16, 4, 8, 45), (80, 33, 16, 16, 16, 20), (40, 24, 8, 4, 4, 1)])
+def test_form_q_plan_skips_identity_columns(m, n, nb, ib, cs, ncols):
+    """Explicit Q: apply Q to [I; 0] while step k skips right-hand-side tile
+    columns < k.  The skipped tiles are exact zeros under those reflectors,
+    so the result must equal the oracle's Q columns."""
+    A = inputs.normal_matrix(m, n, 17)
+    f = TL.tiled_qr(A, nb, ib)
+    ref = TL.orgqr(f, ncols)
+    for order_seed in (None, 3):
+        g = Grid(m, n, nb, ib, cs, ncols)
+        g.A[:] = f.Ap
+        g.T = dict(f.T)
+        g.B[:m, :ncols] = np.eye(m, ncols)
+        plan, _ = plan_of(FORM_Q, g)
+        check_order_satisfies_waits(FORM_Q, g, plan)
+        order = plan if order_seed is None else random_valid_order(FORM_Q, g, plan, order_seed)
+        for t in order:
+            execute(g, t)
+        assert np.allclose(g.B[:m, :ncols], ref, rtol=0, atol=1e-13)
+    full, _ = plan_of(APPLY_Q, Grid(m, n, nb, ib, cs, ncols))
+    assert len(plan) < len(full) or g.kt == 1
+
+
+def test_form_q_plan_rejects_tree_panel():
+    with pytest.raises(Exception):
+        tqr.tqr_debug_plan(FORM_Q, 64, 64, 16, 4, 8, 16, 0, 7, -1, D=2)
 
 
 @pytest.mark.parametrize("m,n,nb,ib,cs,nrhs", [(70, 45, 16, 8, 8, 3), (64, 64, 16, 4, 16, 17), (50, 16, 8, 8, 8, 1)])
