@@ -119,6 +119,89 @@ def oracle_sample(m, n, target_s, steps):
     return rates, r["c"], r["times"]
 
 
+_ORACLE_KIND_SNIPPET = r"""
+import json, sys, time
+sys.path.insert(0, %(root)r)
+import numpy as np
+from oracle import householder as H
+from oracle import lstsq as LS
+from paper_0707_3548_gb300 import inputs
+kind, p, target = %(kind)r, json.loads(%(params)r), %(target)f
+
+def fit_cols(make, m, cmax):
+    # t(c) = a c + b c^2 from two widths, then c for `target` seconds
+    ts = []
+    for c in (32, 64):
+        X = make(c); t0 = time.perf_counter(); H.geqr2(X); ts.append(time.perf_counter() - t0)
+    b = max((ts[1] / 64 - ts[0] / 32) / 32, 1e-12)
+    a = max(ts[0] / 32 - b * 32, 0.0)
+    return int(max(16, min(cmax, (-a + (a * a + 4 * b * target) ** 0.5) / (2 * b))))
+
+out = {}
+if kind == "batch":
+    shapes = inputs.batch_shapes(p["count"], seed=0)
+    fl, tt, cnt = 0.0, 0.0, 0
+    for t, (m, n) in enumerate(shapes):
+        A = inputs.normal_matrix(m, n, t)
+        t0 = time.perf_counter(); H.geqr2(A); tt += time.perf_counter() - t0
+        fl += 2.0 * m * n * n - 2.0 * n ** 3 / 3.0 if m >= n else 2.0 * n * m * m - 2.0 * m ** 3 / 3.0
+        cnt += 1
+        if tt >= target:
+            break
+    out = {"flops": fl, "time": tt, "sample": "unblocked Householder QR (oracle) of the first %%d matrices of the batch" %% cnt}
+elif kind == "ls":
+    m, n, kappa = p["m"], p["n"], p["kappa"]
+    c = fit_cols(lambda c: inputs.conditioned_ls_problem(m, c, kappa, seed=0)[0], m, n)
+    A, b, _ = inputs.conditioned_ls_problem(m, c, kappa, seed=0)
+    t0 = time.perf_counter(); LS.lstsq(A, b[:, None]); tt = time.perf_counter() - t0
+    out = {"flops": 2.0 * m * c * c - 2.0 * c ** 3 / 3.0 + 4.0 * m * c, "time": tt,
+           "sample": "oracle least squares (unblocked QR, Q^T b, back substitution) of a %%dx%%d problem of the same "
+                     "construction (kappa=%%g)" %% (m, c, kappa)}
+elif kind == "serve":
+    # the stream's requests in arrival order, each solved by the oracle from
+    # scratch (no resident factorizations), until the time budget is spent
+    reqs, _ = inputs.serving_stream(p["rate"], p["window"], seed=0)
+    tt, cnt = 0.0, 0
+    for q in reqs:
+        A = inputs.normal_matrix(q["m"], q["n"], q["matrix"])
+        B = inputs.normal_matrix(q["m"], q["nrhs"], 7 + cnt)
+        t0 = time.perf_counter(); LS.lstsq(A, B); tt += time.perf_counter() - t0
+        cnt += 1
+        if tt >= target:
+            break
+    out = {"flops": float(cnt), "time": tt,
+           "sample": "oracle least squares (unblocked QR) of the stream's first %%d requests in order" %% cnt}
+elif kind in ("orgqr", "ormqr"):
+    m = p["m"]
+    c = fit_cols(lambda c: inputs.normal_matrix(m, c, 0), m, p["n"])
+    F, tau = H.geqr2(inputs.normal_matrix(m, c, 0))
+    if kind == "orgqr":
+        t0 = time.perf_counter(); H.apply_q(F, tau, np.eye(m, c)); tt = time.perf_counter() - t0
+        out = {"flops": 4.0 * m * c * c - 2.0 * (m + c) * c * c + 4.0 * c ** 3 / 3.0, "time": tt,
+               "sample": "oracle unblocked Q accumulation of %%d columns from %%d reflectors of length %%d" %% (c, c, m)}
+    else:
+        r = 64
+        C = inputs.normal_matrix(r, m, 1)
+        t0 = time.perf_counter(); H.apply_qt(F, tau, C.T); tt = time.perf_counter() - t0
+        out = {"flops": 4.0 * r * m * c - 2.0 * r * c * c, "time": tt,
+               "sample": "oracle unblocked C Q = (Q^T C^T)^T for %%d rows of C and %%d reflectors of length %%d" %% (r, c, m)}
+print(json.dumps(out))
+"""
+
+
+def oracle_kind_sample(kind, params, target_s):
+    """Times the oracle on a bounded sample of a non-default workload in a
+    single-threaded subprocess; returns (flops, seconds, description)."""
+    code = _ORACLE_KIND_SNIPPET % dict(root=ROOT, kind=kind, params=json.dumps(params), target=target_s)
+    env = dict(os.environ)
+    for k in ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS", "BLIS_NUM_THREADS"):
+        env[k] = "1"
+    env["CUDA_VISIBLE_DEVICES"] = ""
+    out = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, check=True)
+    r = json.loads(out.stdout.strip().splitlines()[-1])
+    return r["flops"], r["time"], r["sample"]
+
+
 def run_reference(args, w):
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
@@ -412,12 +495,19 @@ def run_ls(args, w):
                      "berr": max(berrs), "status": rcs[-1]}
     ref = xs["fp64"]
     out["fp32_refined"]["rel_diff_vs_fp64"] = float(np.linalg.norm(xs["fp32_refined"] - ref) / np.linalg.norm(ref))
+    cpu = None
+    if not args.no_cpu_baseline:
+        fl, tt, smp = oracle_kind_sample("ls", {"m": m, "n": n, "kappa": w["kappa"]}, 8.0)
+        full = 2.0 * m * n * n - 2.0 * n ** 3 / 3.0 + 4.0 * m * n
+        cpu = {"value": fl / tt / full, "unit": "solves/s", "cores": 1, "kind": "oracle",
+               "sample": smp + ", %.1f s; scaled to this workload by its flop count" % tt}
     line = {"metric": "LS solves/s, plain FP64 vs FP32+refinement at backward error <= 1e-12",
             "value": out["fp32_refined"]["solves_per_s"], "unit": "solves/s", "n_gpus": 1,
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic: A = U diag(sigma) V^T, seed 0",
             "config": {"workload": "least squares %dx%d kappa=%g, nrhs=1, nb=%d ib=%d" % (m, n, w["kappa"], nb, ib)},
-            "ls": out, "speedup_vs_fp64": out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"]}
+            "ls": out, "speedup_vs_fp64": out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"],
+            "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -509,6 +599,11 @@ def run_qsuite(args, w):
         h2d = 8 * (m * n + hT.size) + (0 if org else 8 * hO.size)
         e2e = {"value": flops / sec / 1e12, "unit": "TFLOP/s", "h2d_bytes_per_step": h2d,
                "d2h_bytes_per_step": 8 * hO.size, "ms_per_step": 1e3 * sec}
+    cpu = None
+    if not args.no_cpu_baseline:
+        fl, tt, smp = oracle_kind_sample(w["qsuite"], {"m": m, "n": n}, 8.0)
+        cpu = {"value": fl / tt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": smp + ", %.1f s" % tt}
     peak = tqr.tqr_debug_fp64_peak()
     kern_avg_ms = kern_ms / max(1, launches)
     achieved = flops / (kern_avg_ms * 1e-3) / 1e12
@@ -522,7 +617,7 @@ def run_qsuite(args, w):
                          "kernel": "tqr::run_tasks_kernel<double> (persistent task scheduler)",
                          "peak_source": "FP64 DFMA probe measured in this run (tqr_debug_fp64_peak)",
                          "kernel_ms_per_launch": kern_avg_ms},
-            "cpu_baseline": None, "e2e": e2e, "gpu_launches": 4 * args.steps,
+            "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": 4 * args.steps,
             "clocks": clk.summary(), "status": status}
     print(json.dumps(line), flush=True)
 
@@ -577,6 +672,11 @@ def run_batch(args, w):
         assert rc == 0 and not st.any()
         times.append(e0.elapsed_time(e1) * 1e-3)
     sec = statistics.mean(times)
+    cpu = None
+    if not args.no_cpu_baseline:
+        fl, tt, smp = oracle_kind_sample("batch", {"count": w["count"]}, 8.0)
+        cpu = {"value": fl / tt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": smp + ", %.1f s" % tt}
     classes = {}
     for nb, ib in tiles:
         classes["%d/%d" % (nb, ib)] = classes.get("%d/%d" % (nb, ib), 0) + 1
@@ -588,7 +688,7 @@ def run_batch(args, w):
                        "total_flops": flops, "total_bytes": 8 * sum(m * n for m, n in shapes),
                        "l2": "inputs > 129 MB L2, restored from device copies before each step",
                        "tile_classes": classes},
-            "first_submit_s_incl_plan": t_plan, "gpu_launches": 3 * args.steps}
+            "first_submit_s_incl_plan": t_plan, "gpu_launches": 3 * args.steps, "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
 
@@ -671,6 +771,10 @@ def run_serve(args, w):
             "reused_resident": stats["reused"] - base["reused"],
             "max_iters_fp32r": max([i["iters"] for i, q in zip(infos, reqs) if q["prec"] == "fp32r"] or [0]),
             "max_berr": max(i["berr"] for i in infos)}
+    if not args.no_cpu_baseline:
+        cnt, tt, smp = oracle_kind_sample("serve", {"rate": rate, "window": window}, 8.0)
+        line["cpu_baseline"] = {"value": cnt / tt, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                                "sample": smp + ", %.1f s" % tt}
     print(json.dumps(line), flush=True)
 
 
