@@ -189,6 +189,46 @@ int tqr_orgqr(int64_t m, int64_t n, const double* A, int64_t lda, int nb, int ib
               const double* T, int64_t ncols, double* Q, int64_t ldq, void* stream);
 
 /*
+ * Tiled LU with pairwise pivoting -- the LU analogue of Algorithm 1 that the
+ * paper's conclusion (Section 5) names.  Algorithm 1's loop nest with
+ *   GETRF(k)       partially pivoted LU of tile (k,k)
+ *   GESSM(k,j)     tile (k,j) <- L_kk^-1 P_kk tile (k,j)
+ *   TSTRF(k,i)     LU of [U_kk; tile (i,k)], pivoting row c of U_kk against
+ *                  the rows of tile (i,k) for each column c (pairwise)
+ *   SSSSM(k,i,j)   [tile (k,j); tile (i,j)] <- TSTRF(k,i)'s transformations
+ * in ib-column blocks (within a block interchanges move whole block rows;
+ * blocks apply in sequence).  The result is not P A = L U with one
+ * permutation: it is U (upper triangle of A) plus the sequence of
+ * transformations, which tqr_lu_solve replays.
+ *
+ * tqr_lu_piv_size(m, n, nb): bytes of the pivot array (int32, nb per tile
+ *   pair (i, k), i >= k).  The L array has tqr_t_size(m, n, nb, ib) bytes.
+ * tqr_lu_factor(m, n, A, lda, nb, ib, L, piv, stream)
+ *   A (arg 3, m x n, lda >= max(1, m)) is overwritten with U on and above its
+ *   diagonal and the multipliers below; L (arg 7) receives, per tile pair and
+ *   ib block, the inverse of the block's unit lower triangle (ib x ib,
+ *   stored transposed); piv (arg 8) the interchanges: for GETRF tiles the
+ *   tile row exchanged with row c, for TSTRF pairs -1 (no exchange) or the
+ *   bottom tile's row exchanged with row c of U_kk.  nb, ib (args 5, 6) as
+ *   for tqr_factor.  An exact zero pivot leaves its column unscaled; a zero
+ *   then remains on U's diagonal (tqr_lu_solve divides by it).
+ * tqr_lu_solve(n, nrhs, A, lda, nb, ib, L, piv, B, ldb, stream)
+ *   A, L, piv (args 3, 7, 8): the factors of a square n x n matrix from
+ *   tqr_lu_factor with the same nb, ib; B (arg 9, n x nrhs, ldb >= max(1, n),
+ *   arg 10) is overwritten with A^-1 B: the transformations and the back
+ *   substitution with U run as one task graph.
+ * All device pointers (asynchronous on stream) or all host pointers (staged,
+ * the call synchronizes).  Returns 0, -i for an invalid argument i,
+ * TQR_ERR_NOMEM, TQR_ERR_CUDA, TQR_ERR_UNSUPPORTED (sizes above 2^30) or a
+ * device status (TQR_ERR_TIMEOUT).
+ */
+size_t tqr_lu_piv_size(int64_t m, int64_t n, int nb);
+int tqr_lu_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* L,
+                  int32_t* piv, void* stream);
+int tqr_lu_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
+                 const double* L, const int32_t* piv, double* B, int64_t ldb, void* stream);
+
+/*
  * Least squares  min ||A x - b||_2  for full-rank A, m >= n, through the
  * tiled QR: x = R[0:n,0:n]^{-1} (Q^T b)[0:n].  The factorization, Q^T B and
  * the back substitution run as one task graph on the device.

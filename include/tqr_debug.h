@@ -21,7 +21,9 @@ extern "C" {
  *                     4 forward substitution with R^T, 5 apply Q to the
  *                     leading columns of the identity (explicit Q; step k
  *                     skips right-hand-side tile columns < k; flat panel
- *                     only, D must be 0)
+ *                     only, D must be 0); add 16 to modes 0, 1 and 3 for
+ *                     the tiled LU's task lists (GETRF / GESSM / TSTRF /
+ *                     SSSSM kinds 13-16, D must be 0)
  *   m, n     (args 2, 3), nb, ib (args 4, 5) as for tqr_factor
  *   cs       (arg 6)  slab width (columns) of the column-slab tasks; must
  *                     divide nb

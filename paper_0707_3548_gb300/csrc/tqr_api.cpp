@@ -164,7 +164,7 @@ static void hold_until_done(const std::shared_ptr<DevPlan>& plan, cudaStream_t s
 }
 
 static PlanKey key_of(const Inst& I, int esize, int grid, int dev, int policy) {
-  return PlanKey(I.mode, I.m, I.n, I.nb, I.ib, I.cs, I.nrhs, I.trsm, esize, grid, dev, policy, I.D);
+  return PlanKey(I.mode + 16 * I.lu, I.m, I.n, I.nb, I.ib, I.cs, I.nrhs, I.trsm, esize, grid, dev, policy, I.D);
 }
 
 std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int* status, int grid_cap) {
@@ -186,7 +186,7 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
       const PlanKey& k = it->first;
-      if (std::get<0>(k) == I.mode && std::get<1>(k) == I.m && std::get<2>(k) == I.n && std::get<3>(k) == I.nb &&
+      if (std::get<0>(k) == I.mode + 16 * I.lu && std::get<1>(k) == I.m && std::get<2>(k) == I.n && std::get<3>(k) == I.nb &&
           std::get<4>(k) == I.ib && std::get<5>(k) == I.cs && std::get<6>(k) == I.nrhs && std::get<7>(k) == I.trsm &&
           std::get<8>(k) == esize && std::get<10>(k) == dev && std::get<11>(k) == policy &&
           std::get<9>(k) == max_grid && std::get<12>(k) == I.D) {
@@ -381,7 +381,7 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
     }
   }
   cudaError_t e = launch_run<real>(plan->d_tasks, plan->ntasks, reinterpret_cast<const Inst*>(ws + W.oInst),
-                                   ws + W.oCtl, wait_limit_ns(), plan->grid, smem, st);
+                                   ws + W.oCtl, wait_limit_ns(), plan->grid, smem, st, I.lu != 0);
   if (ev.first) {
     cudaEventRecord(ev.second, st);
     std::lock_guard<std::mutex> lk(g_mu);

@@ -15,7 +15,11 @@ extern "C" {
 
 int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int D,
                        int workers, int policy, int32_t* out, int64_t cap, double* stats) {
+  const int lu = (mode & 16) ? 1 : 0;
+  mode &= ~16;
   if (mode < 0 || mode > M_FORM_Q) return -1;
+  if (lu && mode != M_FACTOR && mode != M_APPLY_QT && mode != M_TRSM) return -1;
+  if (lu && D > 0) return -9;
   if (m < 1) return -2;
   if (n < 1) return -3;
   if (check_tiles(nb, ib, 4, 5) != 0) return check_tiles(nb, ib, 4, 5);
@@ -28,6 +32,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   if (policy < -1 || policy > 1) return -11;
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);
   I.D = D;
+  I.lu = lu;
   if (D > 0) I.vtab = host_vtab(I);
   std::vector<TaskX> seq, ordered;
   seq_tasks(I, 0, seq);
@@ -59,8 +64,10 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
 
 int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int D, const int32_t* task,
                     int32_t* waits, int32_t* signals) {
-  Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, 1);
+  const int lu = (mode & 16) ? 1 : 0;
+  Inst I = make_inst(mode & ~16, m, n, nb, ib, cs, nrhs, 1);
   I.D = D;
+  I.lu = lu;
   if (D > 0) I.vtab = host_vtab(I);
   TaskX t;
   t.kind = task[0]; t.s = task[1]; t.inst = task[2]; t.k = task[3]; t.i = task[4]; t.j = task[5]; t.l = task[6];

@@ -951,6 +951,345 @@ __device__ void exec_trsmt_solve(Ctx<real>& cx, const Inst& I, int k, int j, int
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- tiled LU
+// Pairwise-pivoting LU kernels (the LU analogue of Algorithm 1, Section 5).
+// Each works in blocks of ib columns: within a block the interchanges act on
+// whole block rows; applying a block to other columns is its interchanges in
+// order, then W = L11^-1 Top, Top = W, S -= L21 W.  L11^-1 (unit lower) is
+// formed once by the factoring kernel and stored transposed in the ib x ib
+// slot that QR uses for T_l, so that X(r, s) = Tm[s + r * ldT] (s <= r).
+
+// Row of largest magnitude in x[r0..n), ties to the smallest index; one warp,
+// every lane returns the same index (n if the range is empty).
+template <typename real>
+__device__ int warp_iamax(const real* x, int r0, int n, unsigned long long* best_out) {
+  const int lane = threadIdx.x & 31;
+  unsigned long long best = 0;
+  int bi = n;
+  for (int r = r0 + lane; r < n; r += 32) {
+    const unsigned long long b = abs_bits(x[r]);
+    if (bi == n || b > best) {
+      best = b;
+      bi = r;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const unsigned long long ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (oi != n && (bi == n || ob > best || (ob == best && oi < bi))) {
+      best = ob;
+      bi = oi;
+    }
+  }
+  if (best_out) *best_out = best;
+  return bi;
+}
+
+// X = L^-1 for the unit lower ib x ib triangle below the diagonal of L (ld
+// ldl), written as Tm[s + r * ldT] = X(r, s) (zeros for s > r).  One thread
+// per column s of X (forward substitution down the column).
+template <typename real>
+__device__ void unit_lower_inverse_t(const real* L, int ldl, int ib, real* Tm, int ldT) {
+  for (int s = threadIdx.x; s < ib; s += kThreads) {
+    for (int r = 0; r < s; ++r) Tm[s + r * ldT] = real(0);
+    Tm[s + s * ldT] = real(1);
+    for (int r = s + 1; r < ib; ++r) {
+      real a = -L[r + s * ldl];
+      for (int t = s + 1; t < r; ++t) a = fma(-L[r + t * ldl], Tm[s + t * ldT], a);
+      Tm[s + r * ldT] = a;
+    }
+  }
+}
+
+// One LU block applied to a column slab after its interchanges:
+//   W = X Top (X = L11^-1 from Tm), Top = W, S -= V W.
+// V is nv x ib (ldv), Top ib x w (ldt), S nv x w (lds).
+template <typename real>
+__device__ void apply_block_lu(const real* __restrict__ V, int ldv, int nv, real* Top, int ldt, real* S, int lds,
+                               const real* __restrict__ Tm, int ldT, int ib, int w, real* W) {
+  const int tid = threadIdx.x;
+  const int nout = ib * w;
+  for (int o = tid; o < nout; o += kThreads) {
+    const int r = o % ib, c = o / ib;
+    const real* tc = Top + c * ldt;
+    real a = tc[r];
+    for (int s = 0; s < r; ++s) a = fma(Tm[s + r * ldT], tc[s], a);
+    W[o] = a;
+  }
+  __syncthreads();
+  for (int o = tid; o < nout; o += kThreads) Top[(o % ib) + (o / ib) * ldt] = W[o];
+  const int nS = nv * w;
+  for (int o = tid; o < nS; o += 2 * kThreads) {
+    const int o2 = o + kThreads;
+    const bool two = o2 < nS;
+    const int t1 = o % nv, c1 = o / nv;
+    const int t2 = two ? o2 % nv : t1, c2 = two ? o2 / nv : c1;
+    const real* w1 = W + c1 * ib;
+    const real* w2 = W + c2 * ib;
+    real a1 = S[t1 + c1 * lds], a2 = S[t2 + c2 * lds];
+    if (two) {
+#pragma unroll 4
+      for (int r = 0; r < ib; ++r) {
+        a1 = fma(-V[t1 + r * ldv], w1[r], a1);
+        a2 = fma(-V[t2 + r * ldv], w2[r], a2);
+      }
+      S[t2 + c2 * lds] = a2;
+    } else {
+#pragma unroll 4
+      for (int r = 0; r < ib; ++r) a1 = fma(-V[t1 + r * ldv], w1[r], a1);
+    }
+    S[t1 + c1 * lds] = a1;
+  }
+  __syncthreads();
+}
+
+// Interchanges of one GETRF block on a slab whose row 0 is the block's first
+// row: rows q <-> pv[q] (pv[q] >= q, < rows), in order; one thread per column.
+template <typename real>
+__device__ void swap_rows_local(real* S, int lds, int rows, int w, const int* pv, int ib) {
+  for (int c = threadIdx.x; c < w; c += kThreads) {
+    real* col = S + c * lds;
+    for (int q = 0; q < ib; ++q) {
+      const int r = pv[q];
+      if (r > q && r < rows) {
+        const real t = col[q];
+        col[q] = col[r];
+        col[r] = t;
+      }
+    }
+  }
+}
+
+// Interchanges of one TSTRF block: top row q <-> bottom row pv[q] (>= 0).
+template <typename real>
+__device__ void swap_rows_pair(real* Top, int ldt, real* S, int lds, int rows, int w, const int* pv, int ib) {
+  for (int c = threadIdx.x; c < w; c += kThreads) {
+    real* tc = Top + c * ldt;
+    real* sc = S + c * lds;
+    for (int q = 0; q < ib; ++q) {
+      const int r = pv[q];
+      if (r >= 0 && r < rows) {
+        const real t = tc[q];
+        tc[q] = sc[r];
+        sc[r] = t;
+      }
+    }
+  }
+}
+
+// Partially pivoted LU of the nr x ib panel P (GETRF's block): pivot rows
+// from c .. nr-1 for column c; pv[c] receives the chosen row.
+template <typename real>
+__device__ void panel_lu(real* P, int ldP, int nr, int ib, int* pv) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c = 0; c < ib; ++c) {
+    real* pc = P + c * ldP;
+    if (wid == 0) {
+      int r = warp_iamax<real>(pc, c, nr, nullptr);
+      if (r >= nr) r = c;
+      if (lane == 0) pv[c] = r;
+    }
+    __syncthreads();
+    const int r = pv[c];
+    if (r != c)
+      for (int d = tid; d < ib; d += kThreads) {
+        const real t = P[c + d * ldP];
+        P[c + d * ldP] = P[r + d * ldP];
+        P[r + d * ldP] = t;
+      }
+    __syncthreads();
+    const real piv = pc[c];
+    if (piv != real(0))
+      for (int rr = c + 1 + tid; rr < nr; rr += kThreads) pc[rr] = pc[rr] / piv;
+    __syncthreads();
+    const int ncol = ib - c - 1, nrow = nr - c - 1;
+    for (int e = tid; e < ncol * nrow; e += kThreads) {
+      const int rr = c + 1 + e % nrow, d = c + 1 + e / nrow;
+      P[rr + d * ldP] = fma(-pc[rr], P[c + d * ldP], P[rr + d * ldP]);
+    }
+    __syncthreads();
+  }
+}
+
+// Pairwise-pivoted LU of [Rb; P] (Rb: the ib x ib top block, ld ib, upper
+// triangular on entry; P: nv x ib bottom rows): for column c the pivot is row
+// c of Rb (ties) or the largest bottom row; pv[c] = -1 or that row.  Block
+// rows are exchanged whole; only bottom rows are eliminated.
+template <typename real>
+__device__ void panel_tslu(real* Rb, real* P, int ldP, int nv, int ib, int* pv) {
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  for (int c = 0; c < ib; ++c) {
+    real* pc = P + c * ldP;
+    if (wid == 0) {
+      unsigned long long best = 0;
+      const int r = warp_iamax<real>(pc, 0, nv, &best);
+      const bool top = r >= nv || abs_bits(Rb[c + c * ib]) >= best;
+      if (lane == 0) pv[c] = top ? -1 : r;
+    }
+    __syncthreads();
+    const int r = pv[c];
+    if (r >= 0)
+      for (int d = tid; d < ib; d += kThreads) {
+        const real t = Rb[c + d * ib];
+        Rb[c + d * ib] = P[r + d * ldP];
+        P[r + d * ldP] = t;
+      }
+    __syncthreads();
+    const real piv = Rb[c + c * ib];
+    if (piv != real(0))
+      for (int rr = tid; rr < nv; rr += kThreads) pc[rr] = pc[rr] / piv;
+    __syncthreads();
+    const int ncol = ib - c - 1;
+    for (int e = tid; e < ncol * nv; e += kThreads) {
+      const int rr = e % nv, d = c + 1 + e / nv;
+      P[rr + d * ldP] = fma(-pc[rr], Rb[c + d * ib], P[rr + d * ldP]);
+    }
+    __syncthreads();
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ int32_t* piv_ptr(const Inst& I, int i, int k) {
+  return I.piv + piv_offset(I.p, I.nb, i, k);
+}
+
+// GETRF(k): partially pivoted LU of tile (k, k) in ib blocks.
+template <typename real>
+__device__ void exec_getrf(Ctx<real>& cx, const Inst& I, int k) {
+  const int nb = I.nb, ib = I.ib, cs = I.cs;
+  real* A = tile_ptr<real>(I, k, k);
+  real* Lg = t_ptr<real>(I, k, k);
+  int32_t* pg = piv_ptr<real>(I, k, k);
+  int* pv = reinterpret_cast<int*>(cx.red + 2 * kThreads);
+  for (int l0 = 0; l0 < nb; l0 += ib) {
+    const int nr = nb - l0;
+    load_block(cx.P, cx.ldP, A + l0 + static_cast<long long>(l0) * nb, nb, nr, ib);
+    __syncthreads();
+    panel_lu<real>(cx.P, cx.ldP, nr, ib, pv);
+    store_block(A + l0 + static_cast<long long>(l0) * nb, nb, cx.P, cx.ldP, nr, ib);
+    if (threadIdx.x < ib) pg[l0 + threadIdx.x] = l0 + pv[threadIdx.x];
+    unit_lower_inverse_t<real>(cx.P, cx.ldP, ib, cx.T, cx.ldT);
+    __syncthreads();
+    store_block(Lg + static_cast<long long>(l0) * ib, ib, cx.T, cx.ldT, ib, ib);
+    for (int c0 = l0 + ib; c0 < nb; c0 += cs) {
+      const int w = nb - c0 < cs ? nb - c0 : cs;
+      load_block(cx.S, cx.ldS, A + l0 + static_cast<long long>(c0) * nb, nb, nr, w);
+      __syncthreads();
+      swap_rows_local<real>(cx.S, cx.ldS, nr, w, pv, ib);
+      __syncthreads();
+      apply_block_lu<real>(cx.P + ib, cx.ldP, nr - ib, cx.S, cx.ldS, cx.S + ib, cx.ldS, cx.T, cx.ldT, ib, w, cx.W);
+      store_block(A + l0 + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nr, w);
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// GESSM(k, j, s): slab s of tile (k, j) <- L_kk^-1 P_kk times it.
+template <typename real>
+__device__ void exec_gessm(Ctx<real>& cx, const Inst& I, int k, int j, int s) {
+  const int nb = I.nb, ib = I.ib;
+  const real* Lt = tile_ptr<real>(I, k, k);
+  const real* Lg = t_ptr<real>(I, k, k);
+  const int32_t* pg = piv_ptr<real>(I, k, k);
+  int* pv = reinterpret_cast<int*>(cx.red + 2 * kThreads);
+  real* C = tile_ptr<real>(I, k, j) + static_cast<long long>(s) * I.cs * nb;
+  const int w = slab_width(I, j, s);
+  bulk_cols(cx, cx.S, cx.ldS, C, nb, nb, w);
+  for (int l0 = 0; l0 < nb; l0 += ib) {
+    const int nr = nb - l0, nv = nr - ib;
+    // L21 of block l: strictly below the diagonal (TSQRT-like kernels of the
+    // same step may rewrite the tile's upper triangle meanwhile)
+    for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
+      const int r = e % nv, c = e / nv;
+      cx.P[r + c * cx.ldP] = ldg_cg(Lt + (l0 + ib + r) + static_cast<long long>(l0 + c) * nb);
+    }
+    load_block(cx.T, cx.ldT, Lg + static_cast<long long>(l0) * ib, ib, ib, ib);
+    if (threadIdx.x < ib) pv[threadIdx.x] = ldg_cg(pg + l0 + threadIdx.x) - l0;
+    __syncthreads();
+    swap_rows_local<real>(cx.S + l0, cx.ldS, nr, w, pv, ib);
+    __syncthreads();
+    apply_block_lu<real>(cx.P, cx.ldP, nv, cx.S + l0, cx.ldS, cx.S + l0 + ib, cx.ldS, cx.T, cx.ldT, ib, w, cx.W);
+  }
+  store_block(C, nb, cx.S, cx.ldS, nb, w);
+  __syncthreads();
+}
+
+// TSTRF(k, i): pairwise-pivoted LU of [U_kk; A_ik] in ib blocks.  Writes
+// U_kk's upper triangle, the multipliers in (i, k), the pivots and L11^-1.
+template <typename real>
+__device__ void exec_tstrf(Ctx<real>& cx, const Inst& I, int k, int i) {
+  const int nb = I.nb, ib = I.ib, cs = I.cs;
+  real* Ut = tile_ptr<real>(I, k, k);
+  real* Ai = tile_ptr<real>(I, i, k);
+  real* Lg = t_ptr<real>(I, i, k);
+  int32_t* pg = piv_ptr<real>(I, i, k);
+  int* pv = reinterpret_cast<int*>(cx.red + 2 * kThreads);
+  real* Rb = cx.Rb;  // ib x ib, ld ib
+  for (int l0 = 0; l0 < nb; l0 += ib) {
+    for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+      const int r = e % ib, c = e / ib;
+      Rb[r + c * ib] = (r <= c) ? ldg_cg(Ut + (l0 + r) + static_cast<long long>(l0 + c) * nb) : real(0);
+    }
+    bulk_cols(cx, cx.P, cx.ldP, Ai + static_cast<long long>(l0) * nb, nb, nb, ib);
+    __syncthreads();
+    panel_tslu<real>(Rb, cx.P, cx.ldP, nb, ib, pv);
+    for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+      const int r = e % ib, c = e / ib;
+      if (r <= c) Ut[(l0 + r) + static_cast<long long>(l0 + c) * nb] = Rb[r + c * ib];
+    }
+    store_block(Ai + static_cast<long long>(l0) * nb, nb, cx.P, cx.ldP, nb, ib);
+    if (threadIdx.x < ib) pg[l0 + threadIdx.x] = pv[threadIdx.x];
+    unit_lower_inverse_t<real>(Rb, ib, ib, cx.T, cx.ldT);
+    __syncthreads();
+    store_block(Lg + static_cast<long long>(l0) * ib, ib, cx.T, cx.ldT, ib, ib);
+    for (int c0 = l0 + ib; c0 < nb; c0 += cs) {
+      const int w = nb - c0 < cs ? nb - c0 : cs;
+      load_block(cx.Top, ib, Ut + l0 + static_cast<long long>(c0) * nb, nb, ib, w);
+      bulk_cols(cx, cx.S, cx.ldS, Ai + static_cast<long long>(c0) * nb, nb, nb, w);
+      __syncthreads();
+      swap_rows_pair<real>(cx.Top, ib, cx.S, cx.ldS, nb, w, pv, ib);
+      __syncthreads();
+      apply_block_lu<real>(cx.P, cx.ldP, nb, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W);
+      store_block(Ut + l0 + static_cast<long long>(c0) * nb, nb, cx.Top, ib, ib, w);
+      store_block(Ai + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nb, w);
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// SSSSM(k, i, j, s): slab s of [(k, j); (i, j)] <- TSTRF(k, i)'s
+// transformations applied to it.
+template <typename real>
+__device__ void exec_ssssm(Ctx<real>& cx, const Inst& I, int k, int i, int j, int s) {
+  const int nb = I.nb, ib = I.ib;
+  const real* Lb = tile_ptr<real>(I, i, k);
+  const real* Lg = t_ptr<real>(I, i, k);
+  const int32_t* pg = piv_ptr<real>(I, i, k);
+  int* pv = reinterpret_cast<int*>(cx.red + 2 * kThreads);
+  const long long soff = static_cast<long long>(s) * I.cs * nb;
+  real* Ct = tile_ptr<real>(I, k, j) + soff;
+  real* Cb = tile_ptr<real>(I, i, j) + soff;
+  const int w = slab_width(I, j, s);
+  bulk_cols(cx, cx.S, cx.ldS, Cb, nb, nb, w);
+  for (int l0 = 0; l0 < nb; l0 += ib) {
+    load_block(cx.T, cx.ldT, Lg + static_cast<long long>(l0) * ib, ib, ib, ib);
+    load_block(cx.Top, ib, Ct + l0, nb, ib, w);
+    if (threadIdx.x < ib) pv[threadIdx.x] = ldg_cg(pg + l0 + threadIdx.x);
+    bulk_cols(cx, cx.P, cx.ldP, Lb + static_cast<long long>(l0) * nb, nb, nb, ib);
+    __syncthreads();
+    swap_rows_pair<real>(cx.Top, ib, cx.S, cx.ldS, nb, w, pv, ib);
+    __syncthreads();
+    apply_block_lu<real>(cx.P, cx.ldP, nb, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W);
+    store_block(Ct + l0, nb, cx.Top, ib, ib, w);
+    __syncthreads();
+  }
+  store_block(Cb, nb, cx.S, cx.ldS, nb, w);
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- scheduler
 // Thread 0 waits until every counter of every wait has reached its version.
 template <typename real>
@@ -990,10 +1329,11 @@ __device__ void signal_done(const Inst& I, const TaskX& t) {
     for (int c = 0; c < sg[a].cnt; ++c) atomicAdd(I.ver + sg[a].ctr + c, 1);
 }
 
-template <typename real>
-__global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
-                                                             const Inst* __restrict__ insts, Ctl* ctl,
-                                                             long long limit_ns) {
+// The persistent task loop.  LU: the tiled LU's kernel (its own kernel, so
+// the LU tile kernels do not enter the QR kernel's register allocation).
+template <typename real, bool LU>
+__device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int ntasks, const Inst* __restrict__ insts,
+                                          Ctl* ctl, long long limit_ns) {
   extern __shared__ __align__(128) unsigned char smem[];
   __shared__ TaskX s_task;
   __shared__ Inst s_inst;
@@ -1058,7 +1398,17 @@ __global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __rest
       cur_ib = I.ib;
       cur_cs = I.cs;
     }
-    switch (t.kind) {
+    if constexpr (LU) {
+      switch (t.kind) {
+        case K_GETRF: exec_getrf(cx, I, t.k); break;
+        case K_GESSM: exec_gessm(cx, I, t.k, t.j, t.s); break;
+        case K_TSTRF: exec_tstrf(cx, I, t.k, t.i); break;
+        case K_SSSSM: exec_ssssm(cx, I, t.k, t.i, t.j, t.s); break;
+        case K_TRSM_UPD: exec_trsm_upd(cx, I, t.k, t.l, t.j, t.s); break;
+        case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
+        default: break;
+      }
+    } else switch (t.kind) {
       case K_GEQRT: exec_geqrt(cx, I, t.k, t.i); break;
       case K_TSQRT: exec_tsqrt(cx, I, t.k, I.D > 0 ? t.l : t.k, t.i, false); break;
       case K_LARFB: exec_larfb(cx, I, t.k, t.i, t.j, t.s, true); break;
@@ -1077,6 +1427,20 @@ __global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __rest
     __syncthreads();
     if (threadIdx.x == 0) signal_done(I, t);
   }
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
+                                                             const Inst* __restrict__ insts, Ctl* ctl,
+                                                             long long limit_ns) {
+  task_loop<real, false>(tasks, ntasks, insts, ctl, limit_ns);
+}
+
+template <typename real>
+__global__ void __launch_bounds__(kThreads, 2) run_lu_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
+                                                                   const Inst* __restrict__ insts, Ctl* ctl,
+                                                                   long long limit_ns) {
+  task_loop<real, true>(tasks, ntasks, insts, ctl, limit_ns);
 }
 
 // ---------------------------------------------------------------- BDL
@@ -1304,42 +1668,60 @@ cudaError_t launch_unpack_batched(const PackDesc* d, int count, cudaStream_t st)
 // threads with different tile shapes must not lower it under one another.
 // Occupancy follows each launch's own size, not this limit.
 template <typename real>
-cudaError_t max_dyn_smem(int* out) {
+static const void* task_kernel(bool lu) {
+  return lu ? reinterpret_cast<const void*>(run_lu_tasks_kernel<real>)
+            : reinterpret_cast<const void*>(run_tasks_kernel<real>);
+}
+
+template <typename real>
+cudaError_t max_dyn_smem(int* out, bool lu) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
   e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
   if (e != cudaSuccess) return e;
   cudaFuncAttributes fa;
-  e = cudaFuncGetAttributes(&fa, run_tasks_kernel<real>);
+  e = cudaFuncGetAttributes(&fa, task_kernel<real>(lu));
   if (e != cudaSuccess) return e;
   *out = optin - static_cast<int>(fa.sharedSizeBytes);
   return cudaSuccess;
 }
 
 template <typename real>
-cudaError_t set_max_dyn_smem(int smem_bytes) {
+cudaError_t set_max_dyn_smem(int smem_bytes, bool lu) {
   int mx = 0;
-  cudaError_t e = max_dyn_smem<real>(&mx);
+  cudaError_t e = max_dyn_smem<real>(&mx, lu);
   if (e != cudaSuccess) return e;
   if (smem_bytes > mx) return cudaErrorInvalidValue;
-  return cudaFuncSetAttribute(run_tasks_kernel<real>, cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
+  return cudaFuncSetAttribute(task_kernel<real>(lu), cudaFuncAttributeMaxDynamicSharedMemorySize, mx);
 }
 
 template <typename real>
 cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
-                       int smem_bytes, cudaStream_t st) {
-  cudaError_t e = set_max_dyn_smem<real>(smem_bytes);
+                       int smem_bytes, cudaStream_t st, bool lu) {
+  cudaError_t e = set_max_dyn_smem<real>(smem_bytes, lu);
   if (e != cudaSuccess) return e;
-  run_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl), limit_ns);
+  if (lu)
+    run_lu_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl),
+                                                                  limit_ns);
+  else
+    run_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl), limit_ns);
   return cudaGetLastError();
 }
 
 template <typename real>
 cudaError_t occupancy(int smem_bytes, int* blocks_per_sm) {
-  cudaError_t e = set_max_dyn_smem<real>(smem_bytes);
+  cudaError_t e = set_max_dyn_smem<real>(smem_bytes, false);
   if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, run_tasks_kernel<real>, kThreads, smem_bytes);
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, run_tasks_kernel<real>, kThreads, smem_bytes);
+  if (e != cudaSuccess || sizeof(real) != 8) return e;
+  // the LU instantiation (FP64 only) must fit the same number of CTAs
+  int lu_blocks = 0;
+  e = set_max_dyn_smem<real>(smem_bytes, true);
+  if (e != cudaSuccess) return e;
+  e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lu_blocks, run_lu_tasks_kernel<real>, kThreads, smem_bytes);
+  if (e == cudaSuccess && lu_blocks < *blocks_per_sm) *blocks_per_sm = lu_blocks;
+  return e;
 }
 
 cudaError_t read_status(int* status, cudaStream_t st) {
@@ -1401,8 +1783,10 @@ template cudaError_t launch_pack<float>(const double*, long long, int, int, floa
 template cudaError_t launch_unpack<double>(const double*, int, int, double*, long long, int, int, int,
                                            cudaStream_t);
 template cudaError_t launch_unpack<float>(const float*, int, int, double*, long long, int, int, int, cudaStream_t);
-template cudaError_t launch_run<double>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t);
-template cudaError_t launch_run<float>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t);
+template cudaError_t launch_run<double>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t,
+                                        bool);
+template cudaError_t launch_run<float>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t,
+                                       bool);
 template cudaError_t occupancy<double>(int, int*);
 template cudaError_t launch_pack_t<double>(const double*, long long, int, int, double*, int, int, int, int,
                                            cudaStream_t);

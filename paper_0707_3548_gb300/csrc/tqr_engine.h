@@ -24,9 +24,10 @@ cudaError_t launch_unpack_t(const real* Ab, int p, int nb, double* C, long long 
                             cudaStream_t st);
 template <typename real>
 cudaError_t launch_identity(int m, int ncols, real* Ab, int p, int q, int nb, int sms, cudaStream_t st);
+// lu: the tiled LU's instantiation of the task kernel (FP64 only).
 template <typename real>
 cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
-                       int smem_bytes, cudaStream_t st);
+                       int smem_bytes, cudaStream_t st, bool lu = false);
 template <typename real>
 cudaError_t occupancy(int smem_bytes, int* blocks_per_sm);
 

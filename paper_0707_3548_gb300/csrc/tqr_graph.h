@@ -52,8 +52,37 @@ enum Kind : int {
   K_TTQRT = 10,      // QR of the triangles of (l,k) and (i,k)
   K_TTMQR = 11,      // slab s of [(l,j); (i,j)] <- Q_tt^T [.]
   K_TTMQR_N = 12,    // slab s of [(l,j); (i,j)] <- Q_tt [.]
-  K_NKINDS = 13
+  // tiled LU with pairwise pivoting (Inst.lu = 1, flat panel only): the same
+  // loop nest and data flow as GEQRT / LARFB / TSQRT / SSRFB, so the same
+  // dependency rules (qr_kind maps them)
+  K_GETRF = 13,      // (k,k) -> L_kk, U_kk, row interchanges within the tile
+  K_GESSM = 14,      // slab s of (k,j) <- L_kk^-1 P_kk (k,j)
+  K_TSTRF = 15,      // [U_kk; (i,k)] -> U_kk, L_ik, pairwise interchanges
+  K_SSSSM = 16,      // slab s of [(k,j); (i,j)] <- TSTRF(k,i)'s transformations [.]
+  K_NKINDS = 17
 };
+
+// The QR kind whose data flow an LU kind shares.
+TQR_HD int qr_kind(int kind) {
+  switch (kind) {
+    case K_GETRF: return K_GEQRT;
+    case K_GESSM: return K_LARFB;
+    case K_TSTRF: return K_TSQRT;
+    case K_SSSSM: return K_SSRFB;
+    default: return kind;
+  }
+}
+
+// The LU kind replacing a QR kind in an LU task list.
+TQR_HD int lu_kind(int kind) {
+  switch (kind) {
+    case K_GEQRT: return K_GETRF;
+    case K_LARFB: return K_GESSM;
+    case K_TSQRT: return K_TSTRF;
+    case K_SSRFB: return K_SSSSM;
+    default: return kind;
+  }
+}
 
 // M_FORM_Q: M_APPLY_Q on right-hand sides that start as the leading columns
 // of the identity (flat panel only).  Column c of the identity has no entry in
@@ -80,9 +109,10 @@ struct Inst {
   int32_t mode;
   int32_t trsm;             // FACTOR mode: back substitution appended (1) or not (0)
   int32_t D;                // 0: Algorithm 1's flat panel; >0: domains of D tile rows + binary tree
-  int32_t pad0;
+  int32_t lu;               // 1: LU kernels (GETRF/GESSM/TSTRF/SSSSM) in place of the QR ones
   const int32_t* vtab;      // tree variant: writes per trailing tile of row r before step k,
                             // vtab[k * p + r] for k = 0..kt (see tree_writes)
+  int32_t* piv;             // LU: row interchanges, nb per (i,k) slot at piv_offset
 };
 
 // Number of slabs of tile column j (A columns: NS; right-hand-side columns:
@@ -238,7 +268,9 @@ TQR_HD int tree_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* n
 // Fills up to 4 waits and 2 signals; returns the number of waits, writes the
 // number of signals to *nsig.  `a_final` (APPLY/TRSM modes): A's tiles were
 // factored by an earlier launch, so waits on them are dropped.
-TQR_HD int task_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* nsig) {
+TQR_HD int task_rules(const Inst& I, const TaskX& t0, Wait* w, Signal* sg, int* nsig) {
+  TaskX t = t0;
+  t.kind = qr_kind(t0.kind);
   if (I.D > 0 && t.kind != K_TRSMT_UPD && t.kind != K_TRSMT_SOLVE &&
       !((t.kind == K_TRSM_UPD || t.kind == K_TRSM_SOLVE) && I.mode == M_TRSM))
     return tree_rules(I, t, w, sg, nsig);
@@ -332,6 +364,12 @@ TQR_HD int task_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* n
 TQR_HD int64_t t_offset(int p, int nb, int ib, int i, int k) {
   int64_t idx = (int64_t)k * p - (int64_t)k * (k - 1) / 2 + (i - k);
   return idx * (int64_t)ib * nb;
+}
+
+// LU pivots of slot (i, k): nb int32 at this offset (the slots of t_offset).
+TQR_HD int64_t piv_offset(int p, int nb, int i, int k) {
+  int64_t idx = (int64_t)k * p - (int64_t)k * (k - 1) / 2 + (i - k);
+  return idx * (int64_t)nb;
 }
 
 TQR_HD int64_t t_elems(int p, int q, int nb, int ib) {

@@ -96,7 +96,17 @@ void tree_table(const Inst& I, std::vector<int32_t>& vt) {
           vt[static_cast<size_t>(k) * I.p + r] + (r >= k ? tree_writes(I, k, r) : 0);
 }
 
+static void seq_tasks_qr(const Inst& I, int x, std::vector<TaskX>& out);
+
+// LU task lists are the QR ones (flat panel) with the LU kinds substituted.
 void seq_tasks(const Inst& I, int x, std::vector<TaskX>& out) {
+  const size_t first = out.size();
+  seq_tasks_qr(I, x, out);
+  if (I.lu)
+    for (size_t a = first; a < out.size(); ++a) out[a].kind = lu_kind(out[a].kind);
+}
+
+static void seq_tasks_qr(const Inst& I, int x, std::vector<TaskX>& out) {
   if (tree_seq(I, x, out)) return;
   const int p = I.p, q = I.q, kt = I.kt, qt = I.q + I.qb;
   switch (I.mode) {
@@ -285,6 +295,22 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
   }
   double f = 0, lat = 0;
   switch (t.kind) {
+    case K_GETRF:
+      f = 2.0 * nb * nb * nb / 3.0;
+      lat = 2.0 * nb * col_lat;
+      break;
+    case K_TSTRF:
+      f = nb * nb * nb;
+      lat = 2.0 * nb * col_lat;
+      break;
+    case K_GESSM:
+      f = nb * nb * w;
+      lat = (nb / ib) * blk_lat;
+      break;
+    case K_SSSSM:
+      f = (nb / ib) * (2.0 * nb * ib * w + ib * ib * w);
+      lat = (nb / ib) * blk_lat;
+      break;
     case K_GEQRT:
       for (double l0 = 0; l0 < nb; l0 += ib) {
         const double nr = nb - l0;
@@ -333,7 +359,7 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
 }
 
 static int kind_rank(int kind) {
-  switch (kind) {
+  switch (qr_kind(kind)) {
     case K_GEQRT: return 0;
     case K_TSQRT:
     case K_TTQRT: return 1;

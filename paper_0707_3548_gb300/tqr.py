@@ -82,6 +82,9 @@ SIGNATURES = {
     "tqr_ormqr": (_int, [ctypes.c_char, ctypes.c_char, _i64, _i64, _vp, _i64, _int, _int, _int, _vp, _i64, _i64, _vp,
                          _i64, _vp]),
     "tqr_orgqr": (_int, [_i64, _i64, _vp, _i64, _int, _int, _int, _vp, _i64, _vp, _i64, _vp]),
+    "tqr_lu_piv_size": (ctypes.c_size_t, [_i64, _i64, _int]),
+    "tqr_lu_factor": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp]),
+    "tqr_lu_solve": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp, _i64, _vp]),
     "tqr_stream_status": (_int, [_vp]),
     "tqr_set_wait_limit_ms": (_i64, [_i64]),
     "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
@@ -264,6 +267,33 @@ def tqr_orgqr(A, nb, ib, T, ncols=None, D=0, Q=None, stream=None):
     pq, mq, nq, ldq, _ = _mat(Q, "Q")
     _check("tqr_orgqr", lib().tqr_orgqr(m, n, pa, lda, nb, ib, D, _ptr(T), nq, pq, ldq, _stream(cuda, stream)))
     return Q
+
+
+def tqr_lu_piv_size(m, n, nb):
+    return lib().tqr_lu_piv_size(m, n, nb)
+
+
+def tqr_lu_factor(A, nb, ib, L=None, piv=None, stream=None):
+    """Tiled LU (pairwise pivoting) of column-major A in place; returns
+    (L, piv), allocated on A's device (or host) if not given."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    if L is None:
+        L = new_t(m, n, nb, ib, A)
+    if piv is None:
+        cnt = tqr_lu_piv_size(m, n, nb) // 4
+        piv = np.zeros(cnt, dtype=np.int32) if isinstance(A, np.ndarray) else \
+            _torch().zeros(cnt, dtype=_torch().int32, device=A.device)
+    _check("tqr_lu_factor", lib().tqr_lu_factor(m, n, pa, lda, nb, ib, _ptr(L), _ptr(piv), _stream(cuda, stream)))
+    return L, piv
+
+
+def tqr_lu_solve(A, nb, ib, L, piv, B, stream=None):
+    """B <- A^-1 B in place from tqr_lu_factor's (A, L, piv); returns B."""
+    pa, n, n2, lda, cuda = _mat(A, "A")
+    pb, nb_rows, nrhs, ldb, _ = _mat(B, "B")
+    _check("tqr_lu_solve", lib().tqr_lu_solve(n, nrhs, pa, lda, nb, ib, _ptr(L), _ptr(piv), pb, ldb,
+                                              _stream(cuda, stream)))
+    return B
 
 
 def tqr_factor_noalloc(A, nb, ib, T, stream=None, check=True):

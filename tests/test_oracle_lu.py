@@ -152,3 +152,14 @@ def test_planted_mistakes_fail_the_pins(monkeypatch):
     monkeypatch.setattr(LU, "_block_solve", transposed_l11)
     bad = LU.lu_solve(LU.tiled_lu(A, nb, ib), B)
     assert np.linalg.norm(A @ bad - B) > 1e-3 * np.linalg.norm(B)
+
+
+def test_zero_diagonal_tile_takes_pivots_from_below():
+    nb = 8
+    Q = inputs.normal_matrix(nb, nb, 16) + 4 * np.eye(nb)
+    A = np.block([[np.zeros((nb, nb)), np.eye(nb)], [Q, inputs.normal_matrix(nb, nb, 17)]])
+    f = LU.tiled_lu(A, nb, 4)
+    assert (f.piv[(1, 0)] >= 0).all()
+    B = inputs.normal_matrix(2 * nb, 2, 18)
+    X = LU.lu_solve(f, B)
+    assert np.linalg.norm(A @ X - B) <= 1e-12 * np.linalg.norm(B) * np.linalg.cond(A)
