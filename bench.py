@@ -629,7 +629,7 @@ def run_qsuite(args, w):
             "config": {"workload": name, "m": m, "n": n, "nb": nb, "ib": ib, "flops_per_step": flops,
                        "l2": "operands (2 GiB A, %d MiB result) > 129 MB L2" % (8 * out.numel() >> 20)},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(args.workload),
                          "kernel": "tqr::run_tasks_kernel<double> (persistent task scheduler)",
                          "peak_source": "FP64 DFMA probe measured in this run (tqr_debug_fp64_peak)",
                          "kernel_ms_per_launch": kern_avg_ms},
@@ -719,7 +719,7 @@ def run_lu(args, w):
                                    % (m, n, nb, ib), "m": m, "n": n, "nb": nb, "ib": ib,
                        "l2": "input 8*m*n bytes > 129 MB L2, restored from a device copy each step"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                         "frac": achieved / peak, "traffic": None,
+                         "frac": achieved / peak, "traffic": measured_traffic(args.workload),
                          "kernel": "tqr::run_lu_tasks_kernel<double> (persistent task scheduler)",
                          "peak_source": "FP64 DFMA probe measured in this run (tqr_debug_fp64_peak)",
                          "kernel_ms_per_launch": kern_avg_ms},

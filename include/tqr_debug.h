@@ -32,7 +32,8 @@ extern "C" {
  *   D        (arg 9)  0: Algorithm 1's flat panel; > 0: reduction-tree
  *                     variant with domains of D tile rows
  *   workers  (arg 10) CTAs assumed by the list-scheduling simulation
- *   policy   (arg 11) -1 best of both, 0 paper priorities, 1 bottom level
+ *   policy   (arg 11) -1 best of both, 0 paper priorities, 1 bottom level,
+ *                     2 bottom-level sort without simulation
  *   out      (arg 12) int32[8 * cap]: per task kind, s, inst, k, i, j, l, 0
  *                     (may be NULL to query the count)
  *   cap      (arg 13) capacity of `out` in tasks

@@ -124,10 +124,17 @@ struct DevPlan {
   }
 };
 
-typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int, int> PlanKey;
+// A plan depends on the instance only through its task-list structure: the
+// tile grid (p, q), the right-hand-side tile columns and the slab count of
+// the last one, nb, ib, cs, the mode and its flags -- not on m, n or nrhs
+// themselves (edge tiles and slab widths are read from the instance on the
+// device).  Keying on the structure lets differently sized problems on the
+// same grid share one plan.
+typedef std::tuple<int, int, int, int, int, int, int, int, int, int, int, int, int, int> PlanKey;
 
 static std::list<std::pair<PlanKey, std::shared_ptr<DevPlan>>> g_plans;
-static const size_t kMaxPlans = 64;
+static const size_t kMaxPlans = 512;
+static const size_t kMaxPlanBytes = size_t(256) << 20;  // device task lists held by the cache
 
 // Launches keep their plan alive until their completion event fires: a plan
 // evicted from the cache while a kernel on some stream still reads its task
@@ -164,7 +171,9 @@ static void hold_until_done(const std::shared_ptr<DevPlan>& plan, cudaStream_t s
 }
 
 static PlanKey key_of(const Inst& I, int esize, int grid, int dev, int policy) {
-  return PlanKey(I.mode + 16 * I.lu, I.m, I.n, I.nb, I.ib, I.cs, I.nrhs, I.trsm, esize, grid, dev, policy, I.D);
+  const int last = I.qb > 0 ? slabs_of_col(I, I.q + I.qb - 1) : 0;
+  return PlanKey(I.mode + 16 * I.lu, I.p, I.q, I.nb, I.ib, I.cs, I.qb * 256 + last, I.trsm, esize, grid, dev, policy,
+                 I.D, 0);
 }
 
 std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int* status, int grid_cap) {
@@ -182,14 +191,12 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
   int max_grid = sms * ctas_per_sm;
   if (max_ctas > 0 && max_ctas < max_grid) max_grid = max_ctas;
   if (grid_cap > 0 && grid_cap < max_grid) max_grid = grid_cap;
+  // the grid of a cached plan is min(max_grid, ntasks); look up by max_grid
+  const PlanKey want = key_of(I, esize, max_grid, dev, policy);
   {
     std::lock_guard<std::mutex> lk(g_mu);
     for (auto it = g_plans.begin(); it != g_plans.end(); ++it) {
-      const PlanKey& k = it->first;
-      if (std::get<0>(k) == I.mode + 16 * I.lu && std::get<1>(k) == I.m && std::get<2>(k) == I.n && std::get<3>(k) == I.nb &&
-          std::get<4>(k) == I.ib && std::get<5>(k) == I.cs && std::get<6>(k) == I.nrhs && std::get<7>(k) == I.trsm &&
-          std::get<8>(k) == esize && std::get<10>(k) == dev && std::get<11>(k) == policy &&
-          std::get<9>(k) == max_grid && std::get<12>(k) == I.D) {
+      if (it->first == want) {
         auto p = it->second;
         g_plans.splice(g_plans.begin(), g_plans, it);
         return p;
@@ -208,7 +215,13 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
     std::vector<TaskX> ordered;
     std::string err;
     std::vector<Inst> insts(1, Ih);
-    if (!order_tasks(insts, seq, plan->grid, esize, ctas_per_sm, policy, ordered, &plan->stats, &err)) {
+    // capped launches (concurrent server requests, many distinct shapes) take
+    // the bottom-level order without the list-scheduling simulation: about a
+    // third of the planning time, and a shared device is not the simulated one
+    const bool ok = (grid_cap > 0 && policy < 0)
+                        ? order_bottom_level(insts, seq, esize, ctas_per_sm, plan->grid, ordered, &plan->stats, &err)
+                        : order_tasks(insts, seq, plan->grid, esize, ctas_per_sm, policy, ordered, &plan->stats, &err);
+    if (!ok) {
       set_last_error(err);
       *status = TQR_ERR_UNSUPPORTED;
       return nullptr;
@@ -224,8 +237,13 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
     }
   }
   std::lock_guard<std::mutex> lk(g_mu);
-  g_plans.emplace_front(key_of(I, esize, max_grid, dev, policy), plan);
-  while (g_plans.size() > kMaxPlans) g_plans.pop_back();
+  g_plans.emplace_front(want, plan);
+  size_t bytes = 0;
+  for (const auto& e : g_plans) bytes += sizeof(TaskX) * static_cast<size_t>(e.second->ntasks);
+  while (g_plans.size() > 1 && (g_plans.size() > kMaxPlans || bytes > kMaxPlanBytes)) {
+    bytes -= sizeof(TaskX) * static_cast<size_t>(g_plans.back().second->ntasks);
+    g_plans.pop_back();
+  }
   return plan;
 }
 

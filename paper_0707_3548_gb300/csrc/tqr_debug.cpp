@@ -29,7 +29,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   if (trsm && (nrhs == 0 || m < n || (mode != 0 && mode != 1))) return -8;
   if (D < 0 || (D > 0 && mode == M_FORM_Q)) return -9;
   if (workers < 1) return -10;
-  if (policy < -1 || policy > 1) return -11;
+  if (policy < -1 || policy > 2) return -11;
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);
   I.D = D;
   I.lu = lu;
@@ -39,7 +39,9 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   PlanStats st;
   std::string err;
   std::vector<Inst> insts(1, I);
-  if (!seq.empty() && !order_tasks(insts, seq, workers, 8, 2, policy, ordered, &st, &err)) {
+  const bool ok = seq.empty() || (policy == 2 ? order_bottom_level(insts, seq, 8, 2, workers, ordered, &st, &err)
+                                               : order_tasks(insts, seq, workers, 8, 2, policy, ordered, &st, &err));
+  if (!ok) {
     set_last_error(err);
     return -100;
   }

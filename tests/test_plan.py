@@ -176,7 +176,7 @@ FACTOR_SHAPES = [
 
 
 @pytest.mark.parametrize("m,n,nb,ib,cs", FACTOR_SHAPES)
-@pytest.mark.parametrize("policy", [0, 1])
+@pytest.mark.parametrize("policy", [0, 1, 2])
 def test_factor_plan_replays_algorithm1(m, n, nb, ib, cs, policy):
     A = inputs.uniform_matrix(m, n, m + n)
     g = Grid(m, n, nb, ib, cs)
