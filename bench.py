@@ -897,12 +897,15 @@ def main():
     ap.add_argument("--ib", type=int, default=0, help="override the workload's inner block size")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: arrival rate (req/s)")
     ap.add_argument("--window", type=float, default=0.0, help="serve: arrival window (s)")
+    ap.add_argument("--slots", type=int, default=0, help="serve: concurrent request slots")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.nb:
         w["nb"] = args.nb
     if args.ib:
         w["ib"] = args.ib
+    if args.slots:
+        w["slots"] = args.slots
     if args.impl == "reference":
         run_reference(args, w)
     elif w.get("ls"):

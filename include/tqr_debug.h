@@ -54,6 +54,16 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
  * version), signals: int32[2*2] (counter, count).  Returns
  * nwaits + 16 * nsignals.
  */
+/*
+ * Critical path and total work (seconds of the scheduler's cost model, FP64,
+ * 2 CTAs per SM) of the launch described as for tqr_debug_plan, computed in
+ * one pass over the sequential task order (the estimate the library uses to
+ * choose the tree variant's domain size).  out: double[2].  Returns 0, or -1
+ * / -2 for invalid arguments.
+ */
+int tqr_debug_critical_path(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int D,
+                            double* out);
+
 int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int D, const int32_t* task,
                     int32_t* waits, int32_t* signals);
 

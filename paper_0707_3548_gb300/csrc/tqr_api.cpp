@@ -304,9 +304,11 @@ void clear_plans() {
 // smallest max(critical path, work / CTAs) under the scheduler's cost model;
 // the flat panel is kept unless a tree is at least 5% better.  Cached.
 int choose_domain(int64_t m, int64_t n, int nb, int ib, int esize) {
+  // the choice depends on the tile grid only
   static std::mutex mu;
   static std::map<std::tuple<int64_t, int64_t, int, int, int>, int> cache;
-  const auto key = std::make_tuple(m, n, nb, ib, esize);
+  const int64_t p = std::max<int64_t>(1, (m + nb - 1) / nb), q = std::max<int64_t>(1, (n + nb - 1) / nb);
+  const auto key = std::make_tuple(p, q, nb, ib, esize);
   {
     std::lock_guard<std::mutex> lk(mu);
     auto it = cache.find(key);
@@ -322,13 +324,9 @@ int choose_domain(int64_t m, int64_t n, int nb, int ib, int esize) {
     if (D >= I.p) continue;
     I.D = D;
     if (D > 0) I.vtab = host_vtab(I);
-    std::vector<TaskX> seq, ordered;
-    seq_tasks(I, 0, seq);
-    PlanStats st;
-    std::string err;
-    std::vector<Inst> insts(1, I);
-    if (seq.empty() || !order_bottom_level(insts, seq, esize, occ, workers, ordered, &st, &err)) continue;
-    const double est = std::max(st.critical_path_s, st.work_s / workers);
+    double cp = 0, work = 0;
+    critical_path_estimate(I, esize, occ, &cp, &work);
+    const double est = std::max(cp, work / workers);
     if (D == 0) flat = est;
     if (est < best) {
       best = est;

@@ -64,6 +64,20 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   return static_cast<int64_t>(seq.size());
 }
 
+int tqr_debug_critical_path(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int D,
+                            double* out) {
+  const int lu = (mode & 16) ? 1 : 0;
+  mode &= ~16;
+  if (mode < 0 || mode > M_FORM_Q || out == nullptr) return -1;
+  if (m < 1 || n < 1 || check_tiles(nb, ib, 4, 5) != 0 || cs < 1 || nb % cs != 0) return -2;
+  Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);
+  I.D = D;
+  I.lu = lu;
+  if (D > 0) I.vtab = host_vtab(I);
+  critical_path_estimate(I, 8, 2, &out[0], &out[1]);
+  return 0;
+}
+
 int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int D, const int32_t* task,
                     int32_t* waits, int32_t* signals) {
   const int lu = (mode & 16) ? 1 : 0;

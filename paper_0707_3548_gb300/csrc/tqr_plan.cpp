@@ -475,6 +475,31 @@ bool order_tasks(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, 
   return true;
 }
 
+void critical_path_estimate(const Inst& I, int esize, int ctas_per_sm, double* critical_path_s, double* work_s) {
+  std::vector<TaskX> seq;
+  seq_tasks(I, 0, seq);
+  const int64_t nctr = static_cast<int64_t>(I.p) * (I.q + I.qb) * I.NS;
+  std::vector<double> ready(static_cast<size_t>(nctr), 0.0);
+  Wait w[4];
+  Signal sg[2];
+  int nsig;
+  double cp = 0, work = 0;
+  for (const TaskX& t : seq) {
+    const int nw = task_rules(I, t, w, sg, &nsig);
+    double start = 0;
+    for (int a = 0; a < nw; ++a)
+      for (int c = 0; c < w[a].cnt; ++c) start = std::max(start, ready[w[a].ctr + c]);
+    const double cost = task_cost(I, t, esize, ctas_per_sm);
+    const double fin = start + cost;
+    work += cost;
+    for (int a = 0; a < nsig; ++a)
+      for (int c = 0; c < sg[a].cnt; ++c) ready[sg[a].ctr + c] = fin;
+    cp = std::max(cp, fin);
+  }
+  *critical_path_s = cp;
+  *work_s = work;
+}
+
 bool order_bottom_level(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, int esize, int ctas_per_sm,
                         int workers, std::vector<TaskX>& ordered, PlanStats* stats, std::string* err) {
   const std::vector<int64_t> base = counter_bases(insts);

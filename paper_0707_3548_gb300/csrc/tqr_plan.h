@@ -61,4 +61,10 @@ bool order_tasks(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, 
 bool order_bottom_level(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, int esize, int ctas_per_sm,
                         int workers, std::vector<TaskX>& ordered, PlanStats* stats, std::string* err);
 
+// Critical path and total work (seconds of the cost model) of one
+// instance's task graph, without building it: one pass over the sequential
+// order, where every wait is on the preceding writer of its counter, so a
+// task starts when the last writers of its counters finish.
+void critical_path_estimate(const Inst& I, int esize, int ctas_per_sm, double* critical_path_s, double* work_s);
+
 }  // namespace tqr

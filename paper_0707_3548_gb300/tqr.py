@@ -83,6 +83,7 @@ SIGNATURES = {
                          _i64, _vp]),
     "tqr_orgqr": (_int, [_i64, _i64, _vp, _i64, _int, _int, _int, _vp, _i64, _vp, _i64, _vp]),
     "tqr_lu_piv_size": (ctypes.c_size_t, [_i64, _i64, _int]),
+    "tqr_debug_critical_path": (_int, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _vp]),
     "tqr_lu_factor": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp]),
     "tqr_lu_solve": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp, _i64, _vp]),
     "tqr_stream_status": (_int, [_vp]),
@@ -400,6 +401,15 @@ def tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs=0, trsm=0, workers=8, policy=-1,
     L.tqr_debug_plan(mode, m, n, nb, ib, cs, nrhs, trsm, D, workers, policy, out.ctypes.data, cnt,
                      stats.ctypes.data)
     return out, stats
+
+
+def tqr_debug_critical_path(mode, m, n, nb, ib, cs, nrhs=0, trsm=0, D=0):
+    """(critical path, work) in seconds of the cost model, one-pass estimate."""
+    out = np.zeros(2)
+    rc = lib().tqr_debug_critical_path(mode, m, n, nb, ib, cs, nrhs, trsm, D, out.ctypes.data)
+    if rc != 0:
+        raise RuntimeError("tqr_debug_critical_path: %d" % rc)
+    return float(out[0]), float(out[1])
 
 
 def tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, task, D=0):

@@ -312,3 +312,16 @@ def test_bottom_level_policy_no_worse_in_simulation_for_wide_dag():
     _, s1 = plan_of(FACTOR, g, workers=304, policy=1)
     _, sb = plan_of(FACTOR, g, workers=304, policy=-1)
     assert sb[0] == min(s0[0], s1[0])
+
+
+@pytest.mark.parametrize("m,n,nb,ib,cs,D", [(2048, 2048, 128, 32, 32, 0), (4096, 512, 64, 16, 16, 0),
+                                            (4096, 512, 64, 16, 16, 4), (8192, 1024, 128, 16, 32, 2),
+                                            (700, 500, 64, 16, 16, 0)])
+def test_one_pass_critical_path_equals_bottom_level(m, n, nb, ib, cs, D):
+    """The estimate used to choose the tree's domain size (one forward pass,
+    every wait on the preceding writer) equals the longest path of the DAG
+    built from the same rules; the work is the sum of the task costs."""
+    cp, work = tqr.tqr_debug_critical_path(FACTOR, m, n, nb, ib, cs, D=D)
+    _, st = tqr.tqr_debug_plan(FACTOR, m, n, nb, ib, cs, 0, 0, 304, 2, D=D)
+    assert abs(cp - st[4]) <= 1e-9 * st[4]
+    assert abs(work - st[5]) <= 1e-9 * st[5]
