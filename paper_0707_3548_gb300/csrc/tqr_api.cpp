@@ -327,7 +327,11 @@ int choose_domain(int64_t m, int64_t n, int nb, int ib, int esize) {
     double cp = 0, work = 0;
     critical_path_estimate(I, esize, occ, &cp, &work);
     const double est = std::max(cp, work / workers);
-    if (D == 0) flat = est;
+    if (D == 0) {
+      flat = est;
+      // work-bound: a tree only adds work
+      if (cp <= work / workers) break;
+    }
     if (est < best) {
       best = est;
       best_d = D;
