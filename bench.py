@@ -61,8 +61,8 @@ WORKLOADS = {
     "lu8192": dict(m=8192, n=8192, nb=128, ib=16, lu=True),
     "orgqr16384": dict(m=16384, n=16384, nb=128, ib=16, qsuite="orgqr"),
     "ormqr16384r4096": dict(m=16384, n=16384, nb=128, ib=16, qsuite="ormqr", mc=4096),
-    "serve": dict(rate=2000.0, window=1.0, budget=64 << 30, slots=4, pool_bytes=2 << 30, serve=True),
-    "serve_low": dict(rate=20.0, window=5.0, budget=64 << 30, slots=4, pool_bytes=2 << 30, serve=True),
+    "serve": dict(rate=2000.0, window=1.0, budget=64 << 30, slots=8, pool_bytes=2 << 30, serve=True),
+    "serve_low": dict(rate=20.0, window=5.0, budget=64 << 30, slots=8, pool_bytes=2 << 30, serve=True),
 }
 METRIC = "QR TFLOP/s (2mn^2-2n^3/3) vs FP64 peak"
 
@@ -835,7 +835,7 @@ def run_serve(args, w):
         rhs.append(tqr.colmajor(torch.from_numpy(Bh).cuda()))
     outs = [tqr.colmajor(torch.zeros((q["n"], q["nrhs"]), dtype=torch.float64, device="cuda")) for q in reqs]
     torch.cuda.synchronize()
-    srv = tqr.Server(w["budget"], slots=w["slots"])
+    srv = tqr.Server(w["budget"], slots=w["slots"], grid_cap=args.grid_cap)
     # warm the plan cache and kernels with a few requests outside the window
     for k, q in enumerate(reqs[:3]):
         Xw = tqr.colmajor(torch.zeros((q["n"], q["nrhs"]), dtype=torch.float64, device="cuda"))
@@ -858,6 +858,11 @@ def run_serve(args, w):
     th.join()
     infos = [srv.wait(r) for r in ids]
     t1 = time.perf_counter()
+    failures = {}
+    for i, q in zip(infos, reqs):
+        if i["status"] != 0:
+            key = "%s status %d" % (q["prec"], i["status"])
+            failures[key] = failures.get(key, 0) + 1
     stats = srv.stats()
     srv.close()
     lat = {c: sorted(i["latency_ms"] for i, q in zip(infos, reqs) if q["prec"] == c) for c in ("fp64", "fp32r")}
@@ -872,6 +877,7 @@ def run_serve(args, w):
             "config": {"workload": "served LS stream %.0f req/s for %.1f s, %d requests, %d matrices, budget %d GB, %d slots"
                        % (rate, window, len(reqs), len(mats), w["budget"] >> 30, w["slots"])},
             "offered_per_s": len(reqs) / window, "completed": len(reqs) - bad, "failed": bad,
+            "failures": failures, "slots": w["slots"], "grid_cap": args.grid_cap,
             "p50_ms": pct(allv, 0.5), "p99_ms": pct(allv, 0.99),
             "classes": {c: {"count": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)} for c, v in lat.items()},
             "reused_resident": stats["reused"] - base["reused"],
@@ -898,6 +904,7 @@ def main():
     ap.add_argument("--rate", type=float, default=0.0, help="serve: arrival rate (req/s)")
     ap.add_argument("--window", type=float, default=0.0, help="serve: arrival window (s)")
     ap.add_argument("--slots", type=int, default=0, help="serve: concurrent request slots")
+    ap.add_argument("--grid-cap", type=int, default=0, help="serve: CTAs per request launch (0: library default)")
     args = ap.parse_args()
     w = dict(WORKLOADS[args.workload])
     if args.nb:

@@ -107,6 +107,24 @@ Inst make_inst(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs,
 }
 
 // ---------------------------------------------------------------- plan cache
+// Task lists live in stream-ordered allocations made, uploaded and freed on a
+// private stream per device: no cudaMalloc / cudaFree (the latter waits for
+// the whole device) runs while launches on other streams are in flight.
+static cudaStream_t plan_stream(int dev) {
+  static std::mutex mu;
+  static std::map<int, cudaStream_t> streams;
+  std::lock_guard<std::mutex> lk(mu);
+  auto it = streams.find(dev);
+  if (it != streams.end()) return it->second;
+  cudaStream_t s = nullptr;
+  if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    s = nullptr;
+  }
+  streams[dev] = s;
+  return s;
+}
+
 struct DevPlan {
   TaskX* d_tasks = nullptr;
   int ntasks = 0;
@@ -118,7 +136,8 @@ struct DevPlan {
       int cur = -1;
       cudaGetDevice(&cur);
       if (device >= 0 && device != cur) cudaSetDevice(device);
-      cudaFree(d_tasks);
+      // no launch still reads the list (in-flight holders keep it alive)
+      if (cudaFreeAsync(d_tasks, plan_stream(device)) != cudaSuccess) cudaGetLastError();
       if (device >= 0 && device != cur) cudaSetDevice(cur);
     }
   }
@@ -226,12 +245,25 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
       *status = TQR_ERR_UNSUPPORTED;
       return nullptr;
     }
-    if (cudaMalloc(&plan->d_tasks, sizeof(TaskX) * ordered.size()) != cudaSuccess) {
+    // a capped launch shares the device: take about twice the graph's average
+    // parallelism (work / critical path), not CTAs that would mostly wait
+    if (grid_cap > 0 && plan->stats.critical_path_s > 0) {
+      const double par = plan->stats.work_s / plan->stats.critical_path_s;
+      const int want = static_cast<int>(std::min<double>(plan->grid, std::max(8.0, std::ceil(2.0 * par))));
+      plan->grid = std::max(1, std::min(plan->grid, want));
+    }
+    cudaStream_t ps = plan_stream(dev);
+    if (cudaMallocAsync(reinterpret_cast<void**>(&plan->d_tasks), sizeof(TaskX) * ordered.size(), ps) !=
+        cudaSuccess) {
+      cudaGetLastError();
+      plan->d_tasks = nullptr;
       *status = TQR_ERR_NOMEM;
       return nullptr;
     }
-    if (cudaMemcpy(plan->d_tasks, ordered.data(), sizeof(TaskX) * ordered.size(), cudaMemcpyHostToDevice) !=
-        cudaSuccess) {
+    // published only once uploaded: other threads may launch it on any stream
+    if (cudaMemcpyAsync(plan->d_tasks, ordered.data(), sizeof(TaskX) * ordered.size(), cudaMemcpyHostToDevice,
+                        ps) != cudaSuccess ||
+        cudaStreamSynchronize(ps) != cudaSuccess) {
       *status = TQR_ERR_CUDA;
       return nullptr;
     }

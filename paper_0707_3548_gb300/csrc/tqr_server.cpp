@@ -72,6 +72,11 @@ struct tqr_server {
   size_t in_use = 0;                              // resident + running bytes
   uint64_t next_rid = 1;
   bool stop = false;
+  // request workspaces come from the server's own stream-ordered pool, which
+  // keeps freed memory (up to the budget) instead of returning it to the
+  // driver at every synchronization, so admitting a request does not map
+  // fresh physical memory
+  cudaMemPool_t pool = nullptr;
   std::vector<std::thread> workers;
   std::vector<double> lat_ms;  // completed requests
   int64_t completed = 0, reused = 0, failed = 0;
@@ -181,7 +186,8 @@ static void worker(tqr_server* S) {
         continue;
       }
       char* ws = nullptr;
-      if (cudaMallocAsync(reinterpret_cast<void**>(&ws), job->bytes, st) != cudaSuccess) {
+      if ((S->pool ? cudaMallocFromPoolAsync(reinterpret_cast<void**>(&ws), job->bytes, S->pool, st)
+                   : cudaMallocAsync(reinterpret_cast<void**>(&ws), job->bytes, st)) != cudaSuccess) {
         cudaGetLastError();
         break;  // device memory is short of the budget: retry after a completion
       }
@@ -236,6 +242,20 @@ int tqr_server_create(size_t hbm_budget_bytes, int slots, int grid_cap, tqr_serv
   cudaGetDevice(&S->device);
   const int sms = device_sms();
   S->grid_cap = grid_cap > 0 ? grid_cap : std::max(8, (2 * sms * 2) / slots);
+  {
+    cudaMemPoolProps props;
+    std::memset(&props, 0, sizeof(props));
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = S->device;
+    if (cudaMemPoolCreate(&S->pool, &props) == cudaSuccess) {
+      uint64_t keep = hbm_budget_bytes;
+      cudaMemPoolSetAttribute(S->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    } else {
+      cudaGetLastError();
+      S->pool = nullptr;  // fall back to the device's default pool
+    }
+  }
   for (int a = 0; a < slots; ++a) S->workers.emplace_back(worker, S);
   *out = S;
   return TQR_OK;
@@ -249,8 +269,9 @@ int tqr_server_destroy(tqr_server* S) {
   }
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
+  for (auto& e : S->cache) cudaFreeAsync(e->ws, nullptr);
   cudaDeviceSynchronize();
-  for (auto& e : S->cache) cudaFree(e->ws);
+  if (S->pool) cudaMemPoolDestroy(S->pool);
   delete S;
   return TQR_OK;
 }
