@@ -162,3 +162,34 @@ def critical_path(p, q, weights=None):
     for t in tasks(p, q):
         best[t] = w[t[0]] + max((best[a] for a in preds.get(t, ())), default=0.0)
     return max(best.values())
+
+
+# ---------------------------------------------------------------------------
+# 2b x b bottoms (Section 3.2's remark: 2b x b blocks cut the extra work from
+# 25 % to 12.5 %).  The per-task counts follow the same accounting as the
+# b x b ones: a TSQRT whose bottom has h*b rows does the Householder updates
+# (2 h b^3) and the T formation (h b^3 + b^3/3); an SSRFB forms W = top +
+# V^T bottom (2 h b^3), T^T W (b^3) and bottom -= V W (2 h b^3).  h = 1 gives
+# Section 3.2's 10/3 and 5.
+
+def tall_kernel_flops_b3(kind, h):
+    """Per-task count in b^3 of a TS kernel with an h*b-row bottom."""
+    if kind == TSQRT:
+        return 3.0 * h + 1.0 / 3.0
+    if kind == SSRFB:
+        return 4.0 * h + 1.0
+    return KERNEL_FLOPS_B3[kind]
+
+
+def opcount_pairs(p, q):
+    """Operation count in b^3 of Algorithm 1 with the rows below each
+    diagonal tile taken in pairs (2b x b bottoms; an odd last row alone)."""
+    total = 0.0
+    for k in range(min(p, q)):
+        total += KERNEL_FLOPS_B3[GEQRT] + (q - k - 1) * KERNEL_FLOPS_B3[LARFB]
+        i = k + 1
+        while i < p:
+            h = 2 if i + 1 < p else 1
+            total += tall_kernel_flops_b3(TSQRT, h) + (q - k - 1) * tall_kernel_flops_b3(SSRFB, h)
+            i += h
+    return total

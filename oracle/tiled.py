@@ -37,9 +37,10 @@ from .householder import householder, geqr2, unit_lower, larft
 
 
 def _stacked_v(V2, l0, ib, nb):
-    """Explicit [I; V2] for block l of a TSQRT: 2b x ib, with the identity's
-    ones in rows l0 .. l0+ib-1 of the top tile (Section 3.1, DTSQT2)."""
-    Vfull = np.zeros((2 * nb, ib))
+    """Explicit [I; V2] for block l of a TSQRT: (b + rows of V2) x ib, with
+    the identity's ones in rows l0 .. l0+ib-1 of the top tile (Section 3.1,
+    DTSQT2)."""
+    Vfull = np.zeros((nb + V2.shape[0], ib))
     for c in range(ib):
         Vfull[l0 + c, c] = 1.0
     Vfull[nb:, :] = V2
@@ -98,7 +99,8 @@ def tsqrt(Rkk, Aik, ib):
     R = np.array(Rkk, dtype=np.float64, copy=True)
     A = np.array(Aik, dtype=np.float64, copy=True)
     nb = R.shape[0]
-    assert R.shape == (nb, nb) and A.shape == (nb, nb) and nb % ib == 0
+    # the bottom may be taller than b (the 2b x b tiles of Section 3.2's remark)
+    assert R.shape == (nb, nb) and A.shape[1] == nb and nb % ib == 0
     T = np.zeros((ib, nb))
     for l0 in range(0, nb, ib):
         l1 = l0 + ib
@@ -131,7 +133,7 @@ def ssrfb(Akj, Aij, Vik, Tik, ib, trans=True):
 
     trans=True applies Q^T (blocks l = 0, 1, ..., T_l^T); trans=False Q.
     """
-    nb = Vik.shape[0]
+    nb = Vik.shape[1]                       # the top is b rows; the bottom may be taller
     C = np.vstack([np.asarray(Akj, dtype=np.float64),
                    np.asarray(Aij, dtype=np.float64)])
     blocks = list(range(0, nb, ib))
@@ -416,3 +418,101 @@ def orgqr(f, ncols):
     """The first ncols columns of Q (m x ncols, 0 <= ncols <= m)."""
     assert 0 <= ncols <= f.m
     return _left(f, False, np.eye(f.m, ncols))
+
+
+
+# ---------------------------------------------------------------------------
+# 2b x b tiles below the diagonal (Section 3.2 remarks that 2b x b blocks cut
+# the tiled algorithm's extra work from 25 % to 12.5 %; Section 5 repeats it).
+# Reading: the diagonal tile stays b x b (GEQRT, LARFB); below it, step k
+# takes the rows k+1, k+2, ... in pairs, so each TSQRT factors R_kk stacked
+# on a 2b x b block (two b x b storage tiles) and each SSRFB updates the top
+# tile with a 2b-row bottom.  An odd last row is a single b x b bottom.  The
+# reflectors of a pair are stored in its two tiles and its T under the pair's
+# first row.
+
+def pair_groups(k, p):
+    """Bottom groups of step k: [(h, rows)], rows = (h,) or (h, h + 1)."""
+    out = []
+    h = k + 1
+    while h < p:
+        rows = (h, h + 1) if h + 1 < p else (h,)
+        out.append((h, rows))
+        h += len(rows)
+    return out
+
+
+class PairFactors(TiledFactors):
+    pass
+
+
+def _stack(f, rows, j):
+    return np.vstack([f.tile(r, j) for r in rows])
+
+
+def _unstack(f, rows, j, X):
+    nb = f.nb
+    for a, r in enumerate(rows):
+        f.tile(r, j)[:] = X[a * nb:(a + 1) * nb]
+
+
+def tiled_qr_pairs(A, nb, ib):
+    """Algorithm 1 with 2b x b bottoms (pair_groups) on the zero-padded grid."""
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    p, q = grid(m, n, nb)
+    Ap = np.zeros((p * nb, q * nb))
+    Ap[:m, :n] = A
+    f = PairFactors(m, n, nb, ib, Ap, {})
+    tile = f.tile
+    for k in range(min(p, q)):
+        Fkk, Tkk = geqrt(tile(k, k), ib)
+        tile(k, k)[:] = Fkk
+        f.T[(k, k)] = Tkk
+        for j in range(k + 1, q):
+            tile(k, j)[:] = larfb(tile(k, j), tile(k, k), Tkk, ib, trans=True)
+        for h, rows in pair_groups(k, p):
+            R, V, Th = tsqrt(tile(k, k), _stack(f, rows, k), ib)
+            tile(k, k)[:] = R
+            _unstack(f, rows, k, V)
+            f.T[(h, k)] = Th
+            for j in range(k + 1, q):
+                top, bot = ssrfb(tile(k, j), _stack(f, rows, j), V, Th, ib, trans=True)
+                tile(k, j)[:] = top
+                _unstack(f, rows, j, bot)
+    return f
+
+
+def _pair_steps(f, Bp, trans):
+    nb = f.nb
+    rows_of = lambda i: Bp[i * nb:(i + 1) * nb]
+    steps = list(range(min(f.p, f.q)))
+    if not trans:
+        steps.reverse()
+    for k in steps:
+        groups = pair_groups(k, f.p)
+        if trans:
+            rows_of(k)[:] = larfb(rows_of(k), f.tile(k, k), f.T[(k, k)], f.ib, trans=True)
+        else:
+            groups.reverse()
+        for h, rows in groups:
+            V = _stack(f, rows, k)
+            bot = np.vstack([rows_of(r) for r in rows])
+            top, bot = ssrfb(rows_of(k), bot, V, f.T[(h, k)], f.ib, trans=trans)
+            rows_of(k)[:] = top
+            for a, r in enumerate(rows):
+                rows_of(r)[:] = bot[a * nb:(a + 1) * nb]
+        if not trans:
+            rows_of(k)[:] = larfb(rows_of(k), f.tile(k, k), f.T[(k, k)], f.ib, trans=False)
+
+
+def pairs_apply_qt(f, B):
+    Bp = _padded_rows(f, B)
+    _pair_steps(f, Bp, trans=True)
+    return Bp[:f.m]
+
+
+def pairs_apply_q(f, B):
+    Bp = _padded_rows(f, B)
+    _pair_steps(f, Bp, trans=False)
+    return Bp[:f.m]
