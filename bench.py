@@ -39,6 +39,9 @@ WORKLOADS = {
     "qr4096": dict(m=4096, n=4096, nb=128, ib=16),
     "qr2048": dict(m=2048, n=2048, nb=128, ib=16),
     "ts65536x2048": dict(m=65536, n=2048, nb=128, ib=16),
+    # 2b x b bottoms (pairs of tile rows below the diagonal)
+    "qr16384_pairs": dict(m=16384, n=16384, nb=128, ib=16, pairs=True),
+    "qr8192_pairs": dict(m=8192, n=8192, nb=128, ib=16, pairs=True),
     # the same with the reduction-tree panel (domain size chosen by the library)
     "ts65536x2048_tree": dict(m=65536, n=2048, nb=128, ib=16, tree=True),
     # least squares A = U diag(sigma) V^T, kappa 1e2 / 1e5 / 1e8: plain FP64
@@ -75,8 +78,8 @@ def qr_flops(m, n):
 
 
 def workload_name(w):
-    return "tiled QR %dx%d FP64, N(0,1) seed 0, nb=%d ib=%d%s" % (w["m"], w["n"], w["nb"], w["ib"],
-                                                               ", reduction-tree panel" if w.get("tree") else "")
+    extra = ", reduction-tree panel" if w.get("tree") else (", 2b x b bottoms" if w.get("pairs") else "")
+    return "tiled QR %dx%d FP64, N(0,1) seed 0, nb=%d ib=%d%s" % (w["m"], w["n"], w["nb"], w["ib"], extra)
 
 
 # ---------------------------------------------------------------- CPU oracle sample
@@ -353,6 +356,7 @@ def run_ours(args, w):
     dA0 = tqr.colmajor(torch.from_numpy(A).to(dev))
     dA = tqr.colmajor(torch.empty((m, n), dtype=torch.float64, device=dev))
     tree = bool(w.get("tree"))
+    pairs = bool(w.get("pairs"))
     if tree:
         T = torch.zeros(tqr.tqr_t_size_tree(m, n, nb, ib) // 8, dtype=torch.float64, device=dev)
         dA.copy_(dA0)
@@ -366,6 +370,8 @@ def run_ours(args, w):
         dA.copy_(dA0)
         if tree:
             tqr.tqr_factor_tree(dA, nb, ib, D, T)
+        elif pairs:
+            tqr.tqr_factor_pairs(dA, nb, ib, T)
         else:
             tqr.tqr_factor(dA, nb, ib, T)
 
@@ -414,6 +420,8 @@ def run_ours(args, w):
         t0 = time.perf_counter()
         if tree:
             tqr.tqr_factor_tree(hA, nb, ib, D, hT)
+        elif pairs:
+            tqr.tqr_factor_pairs(hA, nb, ib, hT)
         else:
             tqr.tqr_factor(hA, nb, ib, hT)
         t1 = time.perf_counter()
@@ -459,7 +467,8 @@ def run_ours(args, w):
         "config": {"workload": workload_name(w), "m": m, "n": n, "nb": nb, "ib": ib,
                    "l2": "input 8*m*n bytes > 129 MB L2, restored from a device copy each step",
                    "parallelism": "replicas" if world > 1 else "single GPU",
-                   "panel": ("reduction tree, domains of %d tile rows" % D) if tree else "flat (Algorithm 1)"},
+                   "panel": ("reduction tree, domains of %d tile rows" % D) if tree else
+                            ("flat, 2b x b bottoms (pairs of tile rows)" if pairs else "flat (Algorithm 1)")},
         "fp64_peak_fraction": value / world / peak,
         "roofline": roofline,
         "cpu_baseline": cpu,

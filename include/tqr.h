@@ -148,6 +148,26 @@ int tqr_apply_qt_tree(char trans, int64_t m, int64_t n, int64_t nrhs, const doub
                       int nb, int ib, int D, const double* T, double* B, int64_t ldb, void* stream);
 
 /*
+ * 2b x b bottoms -- Section 3.2 remarks that non-square 2b x b blocks cut the
+ * tiled algorithm's extra work from 25 % to 12.5 % (Section 5 repeats it).
+ * Algorithm 1 with the tile rows below each diagonal tile taken in pairs
+ * (k+1, k+2), (k+3, k+4), ... (the last alone if their count is odd): every
+ * TSQRT factors R_kk stacked on a 2b x b block and every SSRFB updates the
+ * top tile with a 2b-row bottom, so the T factors' extra work is spread over
+ * twice the rows.  Tiles stay b x b in memory (a pair is two storage tiles).
+ *   tqr_factor_pairs(m, n, A, lda, nb, ib, T, stream): arguments and errors
+ *     as tqr_factor; T has tqr_t_size bytes (the slot of each pair's second
+ *     row is unused).  R is that of tqr_factor up to rounding; the
+ *     reflectors differ and belong to this variant only.
+ *   tqr_apply_qt_pairs(trans, m, n, nrhs, A, lda, nb, ib, T, B, ldb, stream):
+ *     tqr_apply_qt for factors of tqr_factor_pairs.
+ */
+int tqr_factor_pairs(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T,
+                     void* stream);
+int tqr_apply_qt_pairs(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda,
+                       int nb, int ib, const double* T, double* B, int64_t ldb, void* stream);
+
+/*
  * Applying and forming Q -- the DORMQR / DORGQR pair that the paper's
  * conclusion (Section 5) names as direct derivations of the tiled
  * factorization.  Q is the m x m orthogonal factor of a factorization made by

@@ -23,7 +23,10 @@ extern "C" {
  *                     skips right-hand-side tile columns < k; flat panel
  *                     only, D must be 0); add 16 to modes 0, 1 and 3 for
  *                     the tiled LU's task lists (GETRF / GESSM / TSTRF /
- *                     SSSSM kinds 13-16, D must be 0)
+ *                     SSSSM kinds 13-16, D must be 0); add 32 to modes 0-4
+ *                     for 2b x b bottoms (pairs of tile rows below the
+ *                     diagonal: TSQRT2 / SSRFB2 / SSRFB2_N kinds 17-19 with
+ *                     l = the group's row count, D must be 0)
  *   m, n     (args 2, 3), nb, ib (args 4, 5) as for tqr_factor
  *   cs       (arg 6)  slab width (columns) of the column-slab tasks; must
  *                     divide nb
@@ -51,7 +54,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
  * The version waits and signals the device scheduler derives for one task
  * (kind, k, i, j, s, l as in tqr_debug_plan) of a launch described by
  * (mode, m, n, nb, ib, cs, nrhs, D).  waits: int32[4*3] (counter, count,
- * version), signals: int32[2*2] (counter, count).  Returns
+ * version), signals: int32[3*2] (counter, count).  Returns
  * nwaits + 16 * nsignals.
  */
 /*

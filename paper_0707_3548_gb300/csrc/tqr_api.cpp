@@ -54,13 +54,13 @@ long long wait_limit_ns() { return g_wait_limit_ms * 1000000LL; }
 
 // Tile shape choice: the widest slab (32, 16 or 8 columns dividing nb) that
 // keeps the most CTAs per SM (up to 2: 128 registers x 256 threads).
-bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem) {
+bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem, int rows) {
   const int kSmemPerSM = 233472, kSmemPerBlock = 232448, kReserved = 1024;
   int best_cs = 0, best_occ = 0, best_smem = 0;
   for (int c : {32, 16, 8}) {
     if (c > nb || nb % c != 0) continue;
     if (ib * c > kThreads * kMaxOutPerThread) continue;
-    const SmemLayout L = smem_layout(nb, ib, c, esize);
+    const SmemLayout L = smem_layout(nb, ib, c, esize, rows);
     if (L.bytes > kSmemPerBlock) continue;
     int occ = kSmemPerSM / (L.bytes + kReserved);
     if (occ > 2) occ = 2;
@@ -433,7 +433,7 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
     }
   }
   cudaError_t e = launch_run<real>(plan->d_tasks, plan->ntasks, reinterpret_cast<const Inst*>(ws + W.oInst),
-                                   ws + W.oCtl, wait_limit_ns(), plan->grid, smem, st, I.lu != 0);
+                                   ws + W.oCtl, wait_limit_ns(), plan->grid, smem, st, I.lu ? 1 : (I.pair ? 2 : 0));
   if (ev.first) {
     cudaEventRecord(ev.second, st);
     std::lock_guard<std::mutex> lk(g_mu);
@@ -475,12 +475,13 @@ using namespace tqr;
 
 // ---------------------------------------------------------------- factor
 template <typename real>
-static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, int D, real* T, void* work,
-                         size_t work_bytes, cudaStream_t st) {
+static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, int D, int pair, real* T,
+                         void* work, size_t work_bytes, cudaStream_t st) {
   int cs, occ, smem;
-  if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
+  if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem, pair ? 2 * nb : 0)) return TQR_ERR_UNSUPPORTED;
   Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
   I.D = D;
+  I.pair = pair;
   const WsLayout W = ws_layout(I, sizeof(real), false);
   char* ws = static_cast<char*>(work);
   bool own = false;
@@ -512,8 +513,8 @@ static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   return status;
 }
 
-static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, int D, double* T, void* work,
-                         size_t work_bytes, void* stream) {
+static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, int D, int pair, double* T,
+                         void* work, size_t work_bytes, void* stream) {
   if (m < 0) return -1;
   if (n < 0) return -2;
   if (m > (1LL << 30) || n > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
@@ -526,7 +527,7 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int ka = ptr_kind(A), kt = ptr_kind(T);
   if (ka != kt) return -7;
-  if (ka == PTR_DEVICE) return factor_device<double>(m, n, A, lda, nb, ib, D, T, work, work_bytes, st);
+  if (ka == PTR_DEVICE) return factor_device<double>(m, n, A, lda, nb, ib, D, pair, T, work, work_bytes, st);
   // host buffers: stage through the device, synchronously
   const size_t tbytes = tqr_t_size(m, n, nb, ib) * (D > 0 ? 2 : 1);
   double *dA = nullptr, *dT = nullptr;
@@ -540,7 +541,7 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
     status = TQR_ERR_CUDA;
-  if (status == TQR_OK) status = factor_device<double>(m, n, dA, m, nb, ib, D, dT, work, work_bytes, st);
+  if (status == TQR_OK) status = factor_device<double>(m, n, dA, m, nb, ib, D, pair, dT, work, work_bytes, st);
   if (status == TQR_OK &&
       (cudaMemcpy2DAsync(A, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
                          cudaMemcpyDeviceToHost, st) != cudaSuccess ||
@@ -564,11 +565,12 @@ enum RhsForm { RHS_PLAIN = 0, RHS_TRANSPOSED = 1, RHS_IDENTITY = 2 };
 
 template <typename real>
 static int apply_device(int mode, int form, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb,
-                        int ib, int D, const real* T, double* B, int64_t ldb, cudaStream_t st) {
+                        int ib, int D, int pair, const real* T, double* B, int64_t ldb, cudaStream_t st) {
   int cs, occ, smem;
-  if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
+  if (!choose_shape(nb, ib, sizeof(real), &cs, &occ, &smem, pair ? 2 * nb : 0)) return TQR_ERR_UNSUPPORTED;
   Inst I = make_inst(mode, m, n, nb, ib, cs, static_cast<int>(nrhs), 0);
   I.D = D;
+  I.pair = pair;
   const WsLayout W = ws_layout(I, sizeof(real), false);
   char* ws = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
@@ -605,14 +607,14 @@ static int apply_device(int mode, int form, int64_t m, int64_t n, int64_t nrhs, 
 // (m x nrhs, or nrhs x m for RHS_TRANSPOSED).  Host operands are staged
 // through device copies on the stream; the call then synchronizes.
 static int apply_staged(int mode, int form, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb,
-                        int ib, int D, const double* T, double* B, int64_t ldb, int argA, int argT, int argB,
+                        int ib, int D, int pair, const double* T, double* B, int64_t ldb, int argA, int argT, int argB,
                         void* stream) {
   cudaStream_t st = static_cast<cudaStream_t>(stream);
   const int64_t brows = form == RHS_TRANSPOSED ? nrhs : m, bcols = form == RHS_TRANSPOSED ? m : nrhs;
   const int ka = n > 0 ? ptr_kind(A) : ptr_kind(B);
   if (n > 0 && ptr_kind(T) != ka) return -argT;
   if (ptr_kind(B) != ka) return -argB;
-  if (ka == PTR_DEVICE) return apply_device<double>(mode, form, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, st);
+  if (ka == PTR_DEVICE) return apply_device<double>(mode, form, m, n, nrhs, A, lda, nb, ib, D, pair, T, B, ldb, st);
   const size_t tbytes = tqr_t_size(m, n, nb, ib) * (D > 0 ? 2 : 1);
   double *dA = nullptr, *dT = nullptr, *dB = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * std::max<int64_t>(1, m * n), st) != cudaSuccess ||
@@ -632,7 +634,8 @@ static int apply_staged(int mode, int form, int64_t m, int64_t n, int64_t nrhs, 
                                                  st) != cudaSuccess))
     status = TQR_ERR_CUDA;
   if (status == TQR_OK)
-    status = apply_device<double>(mode, form, m, n, nrhs, dA, std::max<int64_t>(1, m), nb, ib, D, dT, dB, brows, st);
+    status = apply_device<double>(mode, form, m, n, nrhs, dA, std::max<int64_t>(1, m), nb, ib, D, pair, dT, dB,
+                                  brows, st);
   if (status == TQR_OK && cudaMemcpy2DAsync(B, sizeof(double) * ldb, dB, sizeof(double) * brows,
                                             sizeof(double) * brows, bcols, cudaMemcpyDeviceToHost,
                                             st) != cudaSuccess)
@@ -647,7 +650,7 @@ static int apply_staged(int mode, int form, int64_t m, int64_t n, int64_t nrhs, 
 }
 
 static int apply_common(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
-                        int D, const double* T, double* B, int64_t ldb, void* stream) {
+                        int D, int pair, const double* T, double* B, int64_t ldb, void* stream) {
   if (trans != 'T' && trans != 'N' && trans != 't' && trans != 'n') return -1;
   trans = (trans == 't' || trans == 'T') ? 'T' : 'N';
   if (m < 0) return -2;
@@ -662,8 +665,8 @@ static int apply_common(char trans, int64_t m, int64_t n, int64_t nrhs, const do
   if (A == nullptr) return -5;
   if (T == nullptr) return -9;
   if (B == nullptr) return -10;
-  return apply_staged(trans == 'T' ? M_APPLY_QT : M_APPLY_Q, RHS_PLAIN, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, 5,
-                      9, 10, stream);
+  return apply_staged(trans == 'T' ? M_APPLY_QT : M_APPLY_Q, RHS_PLAIN, m, n, nrhs, A, lda, nb, ib, D, pair, T, B,
+                      ldb, 5, 9, 10, stream);
 }
 
 extern "C" {
@@ -686,7 +689,7 @@ size_t tqr_work_size(int64_t m, int64_t n, int nb, int ib) {
 }
 
 int tqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* stream) {
-  return factor_common(m, n, A, lda, nb, ib, 0, T, nullptr, 0, stream);
+  return factor_common(m, n, A, lda, nb, ib, 0, 0, T, nullptr, 0, stream);
 }
 
 int tqr_factor_ws(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* work,
@@ -694,12 +697,12 @@ int tqr_factor_ws(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, 
   if (work == nullptr) return -8;
   if (ptr_kind(work) != PTR_DEVICE) return -8;
   if (reinterpret_cast<uintptr_t>(work) % 256 != 0) return -8;
-  return factor_common(m, n, A, lda, nb, ib, 0, T, work, work_bytes, stream);
+  return factor_common(m, n, A, lda, nb, ib, 0, 0, T, work, work_bytes, stream);
 }
 
 int tqr_apply_qt(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
                  const double* T, double* B, int64_t ldb, void* stream) {
-  return apply_common(trans, m, n, nrhs, A, lda, nb, ib, 0, T, B, ldb, stream);
+  return apply_common(trans, m, n, nrhs, A, lda, nb, ib, 0, 0, T, B, ldb, stream);
 }
 
 size_t tqr_t_size_tree(int64_t m, int64_t n, int nb, int ib) { return 2 * tqr_t_size(m, n, nb, ib); }
@@ -714,14 +717,14 @@ int tqr_factor_tree(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib
     *D = choose_domain(m, n, nb, ib, sizeof(double));
     if (*D == 0) *D = static_cast<int>((m + nb - 1) / nb);  // one domain: Algorithm 1's flat panel
   }
-  const int r = factor_common(m, n, A, lda, nb, ib, *D, T, nullptr, 0, stream);
+  const int r = factor_common(m, n, A, lda, nb, ib, *D, 0, T, nullptr, 0, stream);
   return r == -7 ? -8 : r;  // T is argument 8 here
 }
 
 int tqr_apply_qt_tree(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
                       int D, const double* T, double* B, int64_t ldb, void* stream) {
   if (D < 1) return -9;
-  const int r = apply_common(trans, m, n, nrhs, A, lda, nb, ib, D, T, B, ldb, stream);
+  const int r = apply_common(trans, m, n, nrhs, A, lda, nb, ib, D, 0, T, B, ldb, stream);
   return (r <= -9) ? r - 1 : r;  // arguments after ib shift by one
 }
 
@@ -748,7 +751,7 @@ int tqr_ormqr(char side, char trans, int64_t m, int64_t n, const double* A, int6
   // left: op(Q) C directly; right: C op(Q) = (op(Q)^T C^T)^T on the transposed tiles
   const bool qt = left ? tr : !tr;
   return apply_staged(qt ? M_APPLY_QT : M_APPLY_Q, left ? RHS_PLAIN : RHS_TRANSPOSED, m, n, left ? nc : mc, A, lda,
-                      nb, ib, D, T, C, ldc, 5, 10, 13, stream);
+                      nb, ib, D, 0, T, C, ldc, 5, 10, 13, stream);
 }
 
 int tqr_orgqr(int64_t m, int64_t n, const double* A, int64_t lda, int nb, int ib, int D, const double* T,
@@ -767,8 +770,17 @@ int tqr_orgqr(int64_t m, int64_t n, const double* A, int64_t lda, int nb, int ib
   if (n > 0 && T == nullptr) return -8;
   if (Q == nullptr) return -10;
   // flat panel: identity columns skip the steps that cannot touch them
-  return apply_staged(D == 0 ? M_FORM_Q : M_APPLY_Q, RHS_IDENTITY, m, n, ncols, A, lda, nb, ib, D, T, Q, ldq, 3, 8,
+  return apply_staged(D == 0 ? M_FORM_Q : M_APPLY_Q, RHS_IDENTITY, m, n, ncols, A, lda, nb, ib, D, 0, T, Q, ldq, 3, 8,
                       10, stream);
+}
+
+int tqr_factor_pairs(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* stream) {
+  return factor_common(m, n, A, lda, nb, ib, 0, 1, T, nullptr, 0, stream);
+}
+
+int tqr_apply_qt_pairs(char trans, int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
+                       const double* T, double* B, int64_t ldb, void* stream) {
+  return apply_common(trans, m, n, nrhs, A, lda, nb, ib, 0, 1, T, B, ldb, stream);
 }
 
 int tqr_stream_status(void* stream) {

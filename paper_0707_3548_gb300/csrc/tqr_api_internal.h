@@ -21,7 +21,8 @@ void set_last_error(const std::string& s);
 const char* last_error();
 int device_sms();
 long long wait_limit_ns();
-bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem);
+// rows: the tallest operand of the launch (0: nb; 2 nb for 2b x b bottoms).
+bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem, int rows = 0);
 Inst make_inst(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm);
 WsLayout ws_layout(const Inst& I, int esize, bool with_t);
 // grid_cap > 0 limits the persistent grid (concurrent launches share SMs).

@@ -16,10 +16,12 @@ extern "C" {
 int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int D,
                        int workers, int policy, int32_t* out, int64_t cap, double* stats) {
   const int lu = (mode & 16) ? 1 : 0;
-  mode &= ~16;
+  const int pair = (mode & 32) ? 1 : 0;
+  mode &= ~48;
   if (mode < 0 || mode > M_FORM_Q) return -1;
   if (lu && mode != M_FACTOR && mode != M_APPLY_QT && mode != M_TRSM) return -1;
-  if (lu && D > 0) return -9;
+  if (pair && (lu || mode == M_FORM_Q)) return -1;
+  if ((lu || pair) && D > 0) return -9;
   if (m < 1) return -2;
   if (n < 1) return -3;
   if (check_tiles(nb, ib, 4, 5) != 0) return check_tiles(nb, ib, 4, 5);
@@ -33,6 +35,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);
   I.D = D;
   I.lu = lu;
+  I.pair = pair;
   if (D > 0) I.vtab = host_vtab(I);
   std::vector<TaskX> seq, ordered;
   seq_tasks(I, 0, seq);
@@ -67,12 +70,14 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
 int tqr_debug_critical_path(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm, int D,
                             double* out) {
   const int lu = (mode & 16) ? 1 : 0;
-  mode &= ~16;
+  const int pair = (mode & 32) ? 1 : 0;
+  mode &= ~48;
   if (mode < 0 || mode > M_FORM_Q || out == nullptr) return -1;
   if (m < 1 || n < 1 || check_tiles(nb, ib, 4, 5) != 0 || cs < 1 || nb % cs != 0) return -2;
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);
   I.D = D;
   I.lu = lu;
+  I.pair = pair;
   if (D > 0) I.vtab = host_vtab(I);
   critical_path_estimate(I, 8, 2, &out[0], &out[1]);
   return 0;
@@ -81,15 +86,17 @@ int tqr_debug_critical_path(int mode, int64_t m, int64_t n, int nb, int ib, int 
 int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int D, const int32_t* task,
                     int32_t* waits, int32_t* signals) {
   const int lu = (mode & 16) ? 1 : 0;
-  Inst I = make_inst(mode & ~16, m, n, nb, ib, cs, nrhs, 1);
+  const int pair = (mode & 32) ? 1 : 0;
+  Inst I = make_inst(mode & ~48, m, n, nb, ib, cs, nrhs, 1);
   I.D = D;
   I.lu = lu;
+  I.pair = pair;
   if (D > 0) I.vtab = host_vtab(I);
   TaskX t;
   t.kind = task[0]; t.s = task[1]; t.inst = task[2]; t.k = task[3]; t.i = task[4]; t.j = task[5]; t.l = task[6];
   t.pad = 0;
-  Wait w[4];
-  Signal sg[2];
+  Wait w[kMaxWaits];
+  Signal sg[kMaxSignals];
   int nsig = 0;
   const int nw = task_rules(I, t, w, sg, &nsig);
   for (int a = 0; a < nw; ++a) {

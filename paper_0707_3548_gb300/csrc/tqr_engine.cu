@@ -951,6 +951,78 @@ __device__ void exec_trsmt_solve(Ctx<real>& cx, const Inst& I, int k, int j, int
   __syncthreads();
 }
 
+// ---------------------------------------------------------------- 2b x b bottoms
+// TSQRT2(k, h, rows): TSQRT with the bottom made of `rows` stacked tiles
+// (h .. h+rows-1, k): the 2b x b blocks of Section 3.2's remark, held as b x b
+// storage tiles.  The panel and slabs are staged with rows*nb rows.
+template <typename real>
+__device__ void exec_tsqrt2(Ctx<real>& cx, const Inst& I, int k, int h, int rows) {
+  const int nb = I.nb, ib = I.ib, cs = I.cs, nv = rows * nb;
+  real* Rt = tile_ptr<real>(I, k, k);
+  real* Tg = t_ptr<real>(I, h, k);
+  double* taus = cx.red + 2 * kThreads;
+  real* Rb = cx.Rb;  // ib x ib triangle, ld ib
+  for (int l0 = 0; l0 < nb; l0 += ib) {
+    for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+      const int r = e % ib, c = e / ib;
+      Rb[r + c * ib] = (r <= c) ? ldg_cg(Rt + (l0 + r) + static_cast<long long>(l0 + c) * nb) : real(0);
+    }
+    for (int a = 0; a < rows; ++a)
+      bulk_cols(cx, cx.P + a * nb, cx.ldP, tile_ptr<real>(I, h + a, k) + static_cast<long long>(l0) * nb, nb, nb, ib);
+    __syncthreads();
+    panel_qr<real, true>(cx.P, cx.ldP, nv, ib, Rb, ib, cx.red, taus);
+    for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+      const int r = e % ib, c = e / ib;
+      if (r <= c) Rt[(l0 + r) + static_cast<long long>(l0 + c) * nb] = Rb[r + c * ib];
+    }
+    for (int a = 0; a < rows; ++a)
+      store_block(tile_ptr<real>(I, h + a, k) + static_cast<long long>(l0) * nb, nb, cx.P + a * nb, cx.ldP, nb, ib);
+    __syncthreads();
+    form_t<real, true>(cx.P, cx.ldP, nv, ib, taus, cx.Rb, cx.T, cx.ldT);
+    store_block(Tg + static_cast<long long>(l0) * ib, ib, cx.T, cx.ldT, ib, ib);
+    for (int c0 = l0 + ib; c0 < nb; c0 += cs) {
+      const int w = nb - c0 < cs ? nb - c0 : cs;
+      load_block(cx.Top, ib, Rt + l0 + static_cast<long long>(c0) * nb, nb, ib, w);
+      for (int a = 0; a < rows; ++a)
+        bulk_cols(cx, cx.S + a * nb, cx.ldS, tile_ptr<real>(I, h + a, k) + static_cast<long long>(c0) * nb, nb, nb, w);
+      __syncthreads();
+      apply_any<real>(cx.P, cx.ldP, nv, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, true);
+      store_block(Rt + l0 + static_cast<long long>(c0) * nb, nb, cx.Top, ib, ib, w);
+      for (int a = 0; a < rows; ++a)
+        store_block(tile_ptr<real>(I, h + a, k) + static_cast<long long>(c0) * nb, nb, cx.S + a * nb, cx.ldS, nb, w);
+      __syncthreads();
+    }
+    __syncthreads();
+  }
+}
+
+// SSRFB2(k, h, rows, j, s): slab s of [(k, j); (h .. h+rows-1, j)] <- the
+// transformations of TSQRT2(k, h, rows) (Q^T if trans, else Q).
+template <typename real>
+__device__ void exec_ssrfb2(Ctx<real>& cx, const Inst& I, int k, int h, int rows, int j, int s, bool trans) {
+  const int nb = I.nb, ib = I.ib, nv = rows * nb;
+  const real* Tg = t_ptr<real>(I, h, k);
+  const long long soff = static_cast<long long>(s) * I.cs * nb;
+  real* Ct = tile_ptr<real>(I, k, j) + soff;
+  const int w = slab_width(I, j, s);
+  const int nblk = nb / ib;
+  for (int a = 0; a < rows; ++a) bulk_cols(cx, cx.S + a * nb, cx.ldS, tile_ptr<real>(I, h + a, j) + soff, nb, nb, w);
+  for (int bb = 0; bb < nblk; ++bb) {
+    const int blk = trans ? bb : nblk - 1 - bb;
+    const int l0 = blk * ib;
+    load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
+    load_block(cx.Top, ib, Ct + l0, nb, ib, w);
+    for (int a = 0; a < rows; ++a)
+      bulk_cols(cx, cx.P + a * nb, cx.ldP, tile_ptr<real>(I, h + a, k) + static_cast<long long>(l0) * nb, nb, nb, ib);
+    __syncthreads();
+    apply_any<real>(cx.P, cx.ldP, nv, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, trans);
+    store_block(Ct + l0, nb, cx.Top, ib, ib, w);
+    __syncthreads();
+  }
+  for (int a = 0; a < rows; ++a) store_block(tile_ptr<real>(I, h + a, j) + soff, nb, cx.S + a * nb, cx.ldS, nb, w);
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------- tiled LU
 // Pairwise-pivoting LU kernels (the LU analogue of Algorithm 1, Section 5).
 // Each works in blocks of ib columns: within a block the interchanges act on
@@ -1292,12 +1364,20 @@ __device__ void exec_ssssm(Ctx<real>& cx, const Inst& I, int k, int i, int j, in
 
 // ---------------------------------------------------------------- scheduler
 // Thread 0 waits until every counter of every wait has reached its version.
-template <typename real>
+template <bool PAIR>
+__device__ __forceinline__ int device_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* nsig) {
+  if constexpr (PAIR)
+    return task_rules(I, t, w, sg, nsig);
+  else
+    return task_rules_base(I, t, w, sg, nsig);
+}
+
+template <typename real, bool PAIR>
 __device__ bool wait_deps(Ctx<real>& cx, const Inst& I, const TaskX& t) {
-  Wait w[4];
-  Signal sg[2];
+  Wait w[kMaxWaits];
+  Signal sg[kMaxSignals];
   int nsig;
-  const int nw = task_rules(I, t, w, sg, &nsig);
+  const int nw = device_rules<PAIR>(I, t, w, sg, &nsig);
   unsigned long long t0 = 0;
   for (int a = 0; a < nw; ++a) {
     for (int c = 0; c < w[a].cnt; ++c) {
@@ -1319,11 +1399,12 @@ __device__ bool wait_deps(Ctx<real>& cx, const Inst& I, const TaskX& t) {
   return true;
 }
 
+template <bool PAIR>
 __device__ void signal_done(const Inst& I, const TaskX& t) {
-  Wait w[4];
-  Signal sg[2];
+  Wait w[kMaxWaits];
+  Signal sg[kMaxSignals];
   int nsig;
-  task_rules(I, t, w, sg, &nsig);
+  device_rules<PAIR>(I, t, w, sg, &nsig);
   __threadfence();
   for (int a = 0; a < nsig; ++a)
     for (int c = 0; c < sg[a].cnt; ++c) atomicAdd(I.ver + sg[a].ctr + c, 1);
@@ -1331,7 +1412,9 @@ __device__ void signal_done(const Inst& I, const TaskX& t) {
 
 // The persistent task loop.  LU: the tiled LU's kernel (its own kernel, so
 // the LU tile kernels do not enter the QR kernel's register allocation).
-template <typename real, bool LU>
+enum KernelVariant { KV_QR = 0, KV_LU = 1, KV_PAIR = 2 };
+
+template <typename real, int V>
 __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int ntasks, const Inst* __restrict__ insts,
                                           Ctl* ctl, long long limit_ns) {
   extern __shared__ __align__(128) unsigned char smem[];
@@ -1344,7 +1427,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
   cx.ctl = ctl;
   cx.limit_ns = limit_ns;
   cx.phase = 0;
-  int cur_nb = -1, cur_ib = -1, cur_cs = -1;
+  int cur_nb = -1, cur_ib = -1, cur_cs = -1, cur_pair = -1;
   if (threadIdx.x == 0) {
     // the barrier sits at the end of the largest layout; its offset is passed
     // through the kernel's dynamic size
@@ -1369,7 +1452,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
           s_task = tasks[t];
           s_inst = insts[s_task.inst];
           cx.task = t;
-          go = wait_deps(cx, s_inst, s_task) ? 1 : 0;
+          go = wait_deps<real, V == KV_PAIR>(cx, s_inst, s_task) ? 1 : 0;
         }
       }
       s_go = go;
@@ -1378,8 +1461,8 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
     if (!s_go) break;
     const TaskX t = s_task;
     const Inst& I = s_inst;
-    if (I.nb != cur_nb || I.ib != cur_ib || I.cs != cur_cs) {
-      const SmemLayout L = smem_layout(I.nb, I.ib, I.cs, sizeof(real));
+    if (I.nb != cur_nb || I.ib != cur_ib || I.cs != cur_cs || I.pair != cur_pair) {
+      const SmemLayout L = smem_layout(I.nb, I.ib, I.cs, sizeof(real), I.pair ? 2 * I.nb : 0);
       cx.P = reinterpret_cast<real*>(smem + L.oP);
       cx.T = reinterpret_cast<real*>(smem + L.oT);
       cx.S = reinterpret_cast<real*>(smem + L.oS);
@@ -1391,14 +1474,27 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
       cx.nb = I.nb;
       cx.ib = I.ib;
       cx.cs = I.cs;
-      cx.ldP = ld_pad(I.nb, sizeof(real));
-      cx.ldS = ld_pad(I.nb, sizeof(real));
+      cx.ldP = ld_pad(I.pair ? 2 * I.nb : I.nb, sizeof(real));
+      cx.ldS = cx.ldP;
       cx.ldT = I.ib + 1;
       cur_nb = I.nb;
       cur_ib = I.ib;
       cur_cs = I.cs;
+      cur_pair = I.pair;
     }
-    if constexpr (LU) {
+    if constexpr (V == KV_PAIR) {
+      switch (t.kind) {
+        case K_GEQRT: exec_geqrt(cx, I, t.k, t.i); break;
+        case K_LARFB: exec_larfb(cx, I, t.k, t.i, t.j, t.s, true); break;
+        case K_LARFB_N: exec_larfb(cx, I, t.k, t.i, t.j, t.s, false); break;
+        case K_TSQRT2: exec_tsqrt2(cx, I, t.k, t.i, t.l); break;
+        case K_SSRFB2: exec_ssrfb2(cx, I, t.k, t.i, t.l, t.j, t.s, true); break;
+        case K_SSRFB2_N: exec_ssrfb2(cx, I, t.k, t.i, t.l, t.j, t.s, false); break;
+        case K_TRSM_UPD: exec_trsm_upd(cx, I, t.k, t.l, t.j, t.s); break;
+        case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
+        default: break;
+      }
+    } else if constexpr (V == KV_LU) {
       switch (t.kind) {
         case K_GETRF: exec_getrf(cx, I, t.k); break;
         case K_GESSM: exec_gessm(cx, I, t.k, t.j, t.s); break;
@@ -1425,7 +1521,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
       default: break;
     }
     __syncthreads();
-    if (threadIdx.x == 0) signal_done(I, t);
+    if (threadIdx.x == 0) signal_done<V == KV_PAIR>(I, t);
   }
 }
 
@@ -1433,14 +1529,22 @@ template <typename real>
 __global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
                                                              const Inst* __restrict__ insts, Ctl* ctl,
                                                              long long limit_ns) {
-  task_loop<real, false>(tasks, ntasks, insts, ctl, limit_ns);
+  task_loop<real, KV_QR>(tasks, ntasks, insts, ctl, limit_ns);
 }
 
 template <typename real>
 __global__ void __launch_bounds__(kThreads, 2) run_lu_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
                                                                    const Inst* __restrict__ insts, Ctl* ctl,
                                                                    long long limit_ns) {
-  task_loop<real, true>(tasks, ntasks, insts, ctl, limit_ns);
+  task_loop<real, KV_LU>(tasks, ntasks, insts, ctl, limit_ns);
+}
+
+// 2b x b bottoms: GEQRT / LARFB with the paired TS kernels.
+template <typename real>
+__global__ void __launch_bounds__(kThreads) run_pair_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
+                                                                  const Inst* __restrict__ insts, Ctl* ctl,
+                                                                  long long limit_ns) {
+  task_loop<real, KV_PAIR>(tasks, ntasks, insts, ctl, limit_ns);
 }
 
 // ---------------------------------------------------------------- BDL
@@ -1668,13 +1772,14 @@ cudaError_t launch_unpack_batched(const PackDesc* d, int count, cudaStream_t st)
 // threads with different tile shapes must not lower it under one another.
 // Occupancy follows each launch's own size, not this limit.
 template <typename real>
-static const void* task_kernel(bool lu) {
-  return lu ? reinterpret_cast<const void*>(run_lu_tasks_kernel<real>)
-            : reinterpret_cast<const void*>(run_tasks_kernel<real>);
+static const void* task_kernel(int variant) {
+  if (variant == KV_LU) return reinterpret_cast<const void*>(run_lu_tasks_kernel<real>);
+  if (variant == KV_PAIR) return reinterpret_cast<const void*>(run_pair_tasks_kernel<real>);
+  return reinterpret_cast<const void*>(run_tasks_kernel<real>);
 }
 
 template <typename real>
-cudaError_t max_dyn_smem(int* out, bool lu) {
+cudaError_t max_dyn_smem(int* out, int lu) {
   int dev = 0, optin = 0;
   cudaError_t e = cudaGetDevice(&dev);
   if (e != cudaSuccess) return e;
@@ -1688,7 +1793,7 @@ cudaError_t max_dyn_smem(int* out, bool lu) {
 }
 
 template <typename real>
-cudaError_t set_max_dyn_smem(int smem_bytes, bool lu) {
+cudaError_t set_max_dyn_smem(int smem_bytes, int lu) {
   int mx = 0;
   cudaError_t e = max_dyn_smem<real>(&mx, lu);
   if (e != cudaSuccess) return e;
@@ -1698,12 +1803,15 @@ cudaError_t set_max_dyn_smem(int smem_bytes, bool lu) {
 
 template <typename real>
 cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
-                       int smem_bytes, cudaStream_t st, bool lu) {
-  cudaError_t e = set_max_dyn_smem<real>(smem_bytes, lu);
+                       int smem_bytes, cudaStream_t st, int variant) {
+  cudaError_t e = set_max_dyn_smem<real>(smem_bytes, variant);
   if (e != cudaSuccess) return e;
-  if (lu)
+  if (variant == KV_LU)
     run_lu_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl),
                                                                   limit_ns);
+  else if (variant == KV_PAIR)
+    run_pair_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl),
+                                                                    limit_ns);
   else
     run_tasks_kernel<real><<<grid, kThreads, smem_bytes, st>>>(tasks, ntasks, insts, static_cast<Ctl*>(ctl), limit_ns);
   return cudaGetLastError();
@@ -1711,13 +1819,13 @@ cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* 
 
 template <typename real>
 cudaError_t occupancy(int smem_bytes, int* blocks_per_sm) {
-  cudaError_t e = set_max_dyn_smem<real>(smem_bytes, false);
+  cudaError_t e = set_max_dyn_smem<real>(smem_bytes, KV_QR);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, run_tasks_kernel<real>, kThreads, smem_bytes);
   if (e != cudaSuccess || sizeof(real) != 8) return e;
   // the LU instantiation (FP64 only) must fit the same number of CTAs
   int lu_blocks = 0;
-  e = set_max_dyn_smem<real>(smem_bytes, true);
+  e = set_max_dyn_smem<real>(smem_bytes, KV_LU);
   if (e != cudaSuccess) return e;
   e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&lu_blocks, run_lu_tasks_kernel<real>, kThreads, smem_bytes);
   if (e == cudaSuccess && lu_blocks < *blocks_per_sm) *blocks_per_sm = lu_blocks;
@@ -1784,9 +1892,9 @@ template cudaError_t launch_unpack<double>(const double*, int, int, double*, lon
                                            cudaStream_t);
 template cudaError_t launch_unpack<float>(const float*, int, int, double*, long long, int, int, int, cudaStream_t);
 template cudaError_t launch_run<double>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t,
-                                        bool);
+                                        int);
 template cudaError_t launch_run<float>(const TaskX*, int, const Inst*, void*, long long, int, int, cudaStream_t,
-                                       bool);
+                                       int);
 template cudaError_t occupancy<double>(int, int*);
 template cudaError_t launch_pack_t<double>(const double*, long long, int, int, double*, int, int, int, int,
                                            cudaStream_t);

@@ -24,10 +24,11 @@ cudaError_t launch_unpack_t(const real* Ab, int p, int nb, double* C, long long 
                             cudaStream_t st);
 template <typename real>
 cudaError_t launch_identity(int m, int ncols, real* Ab, int p, int q, int nb, int sms, cudaStream_t st);
-// lu: the tiled LU's instantiation of the task kernel (FP64 only).
+// variant: 0 the QR task kernel, 1 the tiled LU's (FP64 only), 2 the one
+// with the 2b x b bottom kernels (Inst.pair).
 template <typename real>
 cudaError_t launch_run(const TaskX* tasks, int ntasks, const Inst* insts, void* ctl, long long limit_ns, int grid,
-                       int smem_bytes, cudaStream_t st, bool lu = false);
+                       int smem_bytes, cudaStream_t st, int variant = 0);
 template <typename real>
 cudaError_t occupancy(int smem_bytes, int* blocks_per_sm);
 

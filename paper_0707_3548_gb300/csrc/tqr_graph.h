@@ -59,12 +59,26 @@ enum Kind : int {
   K_GESSM = 14,      // slab s of (k,j) <- L_kk^-1 P_kk (k,j)
   K_TSTRF = 15,      // [U_kk; (i,k)] -> U_kk, L_ik, pairwise interchanges
   K_SSSSM = 16,      // slab s of [(k,j); (i,j)] <- TSTRF(k,i)'s transformations [.]
-  K_NKINDS = 17
+  // 2b x b bottoms (Inst.pair = 1, flat panel only): the rows below the
+  // diagonal tile are taken in groups of l = 2 tile rows (the last may be 1)
+  // starting at row i; TSQRT2 factors [R_kk; (i..i+l-1, k)], SSRFB2 updates
+  // slab s of [(k,j); (i..i+l-1, j)]
+  K_TSQRT2 = 17,
+  K_SSRFB2 = 18,
+  K_SSRFB2_N = 19,   // (apply Q)
+  K_NKINDS = 20
 };
+
+// Most waits / signals a task has (SSRFB2: 4 waits, 3 signals).
+constexpr int kMaxWaits = 4;
+constexpr int kMaxSignals = 3;
 
 // The QR kind whose data flow an LU kind shares.
 TQR_HD int qr_kind(int kind) {
   switch (kind) {
+    case K_TSQRT2: return K_TSQRT;
+    case K_SSRFB2: return K_SSRFB;
+    case K_SSRFB2_N: return K_SSRFB_N;
     case K_GETRF: return K_GEQRT;
     case K_GESSM: return K_LARFB;
     case K_TSTRF: return K_TSQRT;
@@ -113,6 +127,8 @@ struct Inst {
   const int32_t* vtab;      // tree variant: writes per trailing tile of row r before step k,
                             // vtab[k * p + r] for k = 0..kt (see tree_writes)
   int32_t* piv;             // LU: row interchanges, nb per (i,k) slot at piv_offset
+  int32_t pair;             // 1: 2b x b bottoms (K_TSQRT2 / K_SSRFB2 kinds)
+  int32_t pad1;
 };
 
 // Number of slabs of tile column j (A columns: NS; right-hand-side columns:
@@ -265,10 +281,70 @@ TQR_HD int tree_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* n
   return nw;
 }
 
-// Fills up to 4 waits and 2 signals; returns the number of waits, writes the
+// ---- 2b x b bottoms ----------------------------------------------------
+// Groups of step k: rows k+1, k+2 | k+3, k+4 | ...; the last may hold one row.
+TQR_HD int pair_groups(const Inst& I, int k) { return (I.p - k - 1 + 1) / 2; }
+TQR_HD int pair_index(int k, int h) { return (h - k - 1) / 2; }
+
+// Writes every tile of row r < kt has received at the end of the
+// factorization (or of Q^T B on a right-hand side): one per earlier step,
+// plus GEQRT/LARFB and one per bottom group (or bottom row) of its own step.
+TQR_HD int fin_row(const Inst& I, int r) {
+  if (!I.pair) return I.p;
+  return r + 1 + pair_groups(I, r);
+}
+
+// Rules of the pair kinds (and LARFB_N, whose count depends on the groups).
+TQR_HD int pair_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* nsig) {
+  const int kt = I.kt, NS = I.NS;
+  const int k = t.k, h = t.i, j = t.j, s = t.s, l = t.l;
+  const bool a_final = I.mode != M_FACTOR;
+  const int g = pair_index(k, h);
+  int nw = 0;
+  *nsig = 0;
+  // reverse-order writes a right-hand-side tile of row r got before step k
+  auto bot = [&](int r) {
+    const int mr = r < kt ? r : kt;
+    return (r < kt ? pair_groups(I, r) + 1 : 0) + (mr - 1 - k);
+  };
+  switch (t.kind) {
+    case K_TSQRT2:
+      w[nw++] = {ctr_index(I, k, k, 0), NS, k + 1 + g};
+      for (int a = 0; a < l; ++a) w[nw++] = {ctr_index(I, h + a, k, 0), NS, k};
+      sg[(*nsig)++] = {ctr_index(I, k, k, 0), NS};
+      for (int a = 0; a < l; ++a) sg[(*nsig)++] = {ctr_index(I, h + a, k, 0), NS};
+      break;
+    case K_SSRFB2:
+      if (!a_final) w[nw++] = {ctr_index(I, h, k, 0), NS, k + 1};
+      w[nw++] = {ctr_index(I, k, j, s), 1, k + 1 + g};
+      for (int a = 0; a < l; ++a) w[nw++] = {ctr_index(I, h + a, j, s), 1, k};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      for (int a = 0; a < l; ++a) sg[(*nsig)++] = {ctr_index(I, h + a, j, s), 1};
+      break;
+    case K_SSRFB2_N:
+      // sequential order: for k = kt-1..0 { groups in reverse: SSRFB2_N; LARFB_N(k) }
+      w[nw++] = {ctr_index(I, k, j, s), 1, pair_groups(I, k) - 1 - g};
+      for (int a = 0; a < l; ++a) w[nw++] = {ctr_index(I, h + a, j, s), 1, bot(h + a)};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      for (int a = 0; a < l; ++a) sg[(*nsig)++] = {ctr_index(I, h + a, j, s), 1};
+      break;
+    case K_LARFB_N:
+      w[nw++] = {ctr_index(I, k, j, s), 1, pair_groups(I, k)};
+      sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
+      break;
+    default:
+      break;
+  }
+  return nw;
+}
+
+// Fills up to kMaxWaits waits and kMaxSignals signals; returns the number of waits, writes the
 // number of signals to *nsig.  `a_final` (APPLY/TRSM modes): A's tiles were
 // factored by an earlier launch, so waits on them are dropped.
-TQR_HD int task_rules(const Inst& I, const TaskX& t0, Wait* w, Signal* sg, int* nsig) {
+// task_rules_base: every rule but the 2b x b bottoms' (the QR and LU task
+// kernels evaluate only this one: the pair branch would weigh on their
+// register allocation, and they never run pair tasks).
+TQR_HD int task_rules_base(const Inst& I, const TaskX& t0, Wait* w, Signal* sg, int* nsig) {
   TaskX t = t0;
   t.kind = qr_kind(t0.kind);
   if (I.D > 0 && t.kind != K_TRSMT_UPD && t.kind != K_TRSMT_SOLVE &&
@@ -330,16 +406,16 @@ TQR_HD int task_rules(const Inst& I, const TaskX& t0, Wait* w, Signal* sg, int* 
       // APPLY_QT modes the right-hand sides first received p writes (rows
       // < kt) from Algorithm 1's updates, and in FACTOR mode R's tiles (k, l),
       // k <= l < q, end at version p.
-      const int base = (I.mode == M_FACTOR || I.mode == M_APPLY_QT) ? p : 0;
-      if (!a_final) w[nw++] = {ctr_index(I, k, l, 0), NS, p};
-      w[nw++] = {ctr_index(I, l, j, s), 1, base + (kt - l)};
-      w[nw++] = {ctr_index(I, k, j, s), 1, base + (kt - 1 - l)};
+      const bool fw = (I.mode == M_FACTOR || I.mode == M_APPLY_QT);
+      if (!a_final) w[nw++] = {ctr_index(I, k, l, 0), NS, fin_row(I, k)};
+      w[nw++] = {ctr_index(I, l, j, s), 1, (fw ? fin_row(I, l) : 0) + (kt - l)};
+      w[nw++] = {ctr_index(I, k, j, s), 1, (fw ? fin_row(I, k) : 0) + (kt - 1 - l)};
       sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
       break;
     }
     case K_TRSM_SOLVE: {
-      const int base = (I.mode == M_FACTOR || I.mode == M_APPLY_QT) ? p : 0;
-      if (!a_final) w[nw++] = {ctr_index(I, k, k, 0), NS, p};
+      const int base = (I.mode == M_FACTOR || I.mode == M_APPLY_QT) ? fin_row(I, k) : 0;
+      if (!a_final) w[nw++] = {ctr_index(I, k, k, 0), NS, fin_row(I, k)};
       w[nw++] = {ctr_index(I, k, j, s), 1, base + (kt - 1 - k)};
       sg[(*nsig)++] = {ctr_index(I, k, j, s), 1};
       break;
@@ -358,6 +434,12 @@ TQR_HD int task_rules(const Inst& I, const TaskX& t0, Wait* w, Signal* sg, int* 
       break;
   }
   return nw;
+}
+
+TQR_HD int task_rules(const Inst& I, const TaskX& t0, Wait* w, Signal* sg, int* nsig) {
+  if (I.pair && (t0.kind == K_TSQRT2 || t0.kind == K_SSRFB2 || t0.kind == K_SSRFB2_N || t0.kind == K_LARFB_N))
+    return pair_rules(I, t0, w, sg, nsig);
+  return task_rules_base(I, t0, w, sg, nsig);
 }
 
 // Offset (in elements) of T block (i, k), i >= k, each ib x nb.
@@ -415,9 +497,10 @@ TQR_HD int align16(int x) { return (x + 15) & ~15; }
 // lanes that walk along a row do not all hit one bank.
 TQR_HD int ld_pad(int nb, int esize) { return nb + 16 / esize; }
 
-TQR_HD SmemLayout smem_layout(int nb, int ib, int cs, int esize) {
+// rows: the tallest operand (nb, or 2 nb for 2b x b bottoms).
+TQR_HD SmemLayout smem_layout(int nb, int ib, int cs, int esize, int rows = 0) {
   SmemLayout L;
-  const int ld = ld_pad(nb, esize);
+  const int ld = ld_pad(rows > nb ? rows : nb, esize);
   L.r_in_s = (ld * cs >= ib * ib);
   int top_elems = ib * cs;
   if (!L.r_in_s && ib * ib > top_elems) top_elems = ib * ib;

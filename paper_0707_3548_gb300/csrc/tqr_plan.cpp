@@ -106,8 +106,48 @@ void seq_tasks(const Inst& I, int x, std::vector<TaskX>& out) {
     for (size_t a = first; a < out.size(); ++a) out[a].kind = lu_kind(out[a].kind);
 }
 
+// 2b x b bottoms: Algorithm 1 with the rows below the diagonal tile taken in
+// groups of two (the last may be one).  Task field l holds the group size.
+static void pair_step(const Inst& I, int x, int k, bool factor, std::vector<TaskX>& out) {
+  const int p = I.p, qt = I.q + I.qb;
+  const int j0 = factor ? k + 1 : I.q;
+  if (factor) out.push_back(mk(K_GEQRT, x, k, k, k, 0));
+  for (int j = j0; j < qt; ++j)
+    for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_LARFB, x, k, k, j, s));
+  for (int h = k + 1; h < p; h += 2) {
+    const int l = h + 1 < p ? 2 : 1;
+    if (factor) out.push_back(mk(K_TSQRT2, x, k, h, k, 0, l));
+    for (int j = j0; j < qt; ++j)
+      for (int s = 0, ns = slabs_of_col(I, j); s < ns; ++s) out.push_back(mk(K_SSRFB2, x, k, h, j, s, l));
+  }
+}
+
+static bool pair_seq(const Inst& I, int x, std::vector<TaskX>& out) {
+  if (!I.pair) return false;
+  switch (I.mode) {
+    case M_FACTOR:
+    case M_APPLY_QT:
+      for (int k = 0; k < I.kt; ++k) pair_step(I, x, k, I.mode == M_FACTOR, out);
+      if (I.trsm) trsm_tasks(I, x, out);
+      return true;
+    case M_APPLY_Q: {
+      std::vector<TaskX> fw;
+      for (int k = 0; k < I.kt; ++k) pair_step(I, x, k, false, fw);
+      for (size_t a = fw.size(); a-- > 0;) {
+        TaskX t = fw[a];
+        t.kind = t.kind == K_LARFB ? K_LARFB_N : K_SSRFB2_N;
+        out.push_back(t);
+      }
+      return true;
+    }
+    default:
+      return false;  // triangular solves do not depend on the pairing
+  }
+}
+
 static void seq_tasks_qr(const Inst& I, int x, std::vector<TaskX>& out) {
   if (tree_seq(I, x, out)) return;
+  if (pair_seq(I, x, out)) return;
   const int p = I.p, q = I.q, kt = I.kt, qt = I.q + I.qb;
   switch (I.mode) {
     case M_FACTOR:
@@ -205,8 +245,8 @@ bool build_dag(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, st
   const int64_t n = static_cast<int64_t>(seq.size());
   // writers of every counter, in sequential order (CSR, two passes)
   std::vector<int64_t> wptr(nctr + 1, 0);
-  Wait w[4];
-  Signal sg[2];
+  Wait w[kMaxWaits];
+  Signal sg[kMaxSignals];
   int nsig;
   for (int64_t t = 0; t < n; ++t) {
     const Inst& I = insts[seq[t].inst];
@@ -295,6 +335,15 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
   }
   double f = 0, lat = 0;
   switch (t.kind) {
+    case K_TSQRT2:
+      for (double l0 = 0; l0 < nb; l0 += ib) f += 3.0 * t.l * nb * ib * ib + 4.0 * t.l * nb * ib * (nb - l0 - ib);
+      lat = nb * col_lat;
+      break;
+    case K_SSRFB2:
+    case K_SSRFB2_N:
+      f = (nb / ib) * (4.0 * t.l * nb * ib * w + ib * ib * w);
+      lat = (nb / ib) * blk_lat;
+      break;
     case K_GETRF:
       f = 2.0 * nb * nb * nb / 3.0;
       lat = 2.0 * nb * col_lat;
@@ -480,8 +529,8 @@ void critical_path_estimate(const Inst& I, int esize, int ctas_per_sm, double* c
   seq_tasks(I, 0, seq);
   const int64_t nctr = static_cast<int64_t>(I.p) * (I.q + I.qb) * I.NS;
   std::vector<double> ready(static_cast<size_t>(nctr), 0.0);
-  Wait w[4];
-  Signal sg[2];
+  Wait w[kMaxWaits];
+  Signal sg[kMaxSignals];
   int nsig;
   double cp = 0, work = 0;
   for (const TaskX& t : seq) {
@@ -506,8 +555,8 @@ bool order_bottom_level(const std::vector<Inst>& insts, const std::vector<TaskX>
   const int64_t nctr = base.back();
   const int64_t n = static_cast<int64_t>(seq.size());
   std::vector<int64_t> wptr(nctr + 1, 0);
-  Wait w[4];
-  Signal sg[2];
+  Wait w[kMaxWaits];
+  Signal sg[kMaxSignals];
   int nsig;
   for (int64_t t = 0; t < n; ++t) {
     task_rules(insts[seq[t].inst], seq[t], w, sg, &nsig);

@@ -83,6 +83,8 @@ SIGNATURES = {
                          _i64, _vp]),
     "tqr_orgqr": (_int, [_i64, _i64, _vp, _i64, _int, _int, _int, _vp, _i64, _vp, _i64, _vp]),
     "tqr_lu_piv_size": (ctypes.c_size_t, [_i64, _i64, _int]),
+    "tqr_factor_pairs": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp]),
+    "tqr_apply_qt_pairs": (_int, [ctypes.c_char, _i64, _i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _i64, _vp]),
     "tqr_debug_critical_path": (_int, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _vp]),
     "tqr_lu_factor": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp]),
     "tqr_lu_solve": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp, _i64, _vp]),
@@ -270,6 +272,23 @@ def tqr_orgqr(A, nb, ib, T, ncols=None, D=0, Q=None, stream=None):
     return Q
 
 
+def tqr_factor_pairs(A, nb, ib, T=None, stream=None):
+    """Tiled QR with 2b x b bottoms (pairs of tile rows), A in place; returns T."""
+    pa, m, n, lda, cuda = _mat(A, "A")
+    if T is None:
+        T = new_t(m, n, nb, ib, A)
+    _check("tqr_factor_pairs", lib().tqr_factor_pairs(m, n, pa, lda, nb, ib, _ptr(T), _stream(cuda, stream)))
+    return T
+
+
+def tqr_apply_qt_pairs(trans, A, nb, ib, T, B, stream=None):
+    pa, m, n, lda, cuda = _mat(A, "A")
+    pb, mb, nrhs, ldb, _ = _mat(B, "B")
+    _check("tqr_apply_qt_pairs", lib().tqr_apply_qt_pairs(_ch(trans), m, n, nrhs, pa, lda, nb, ib, _ptr(T), pb, ldb,
+                                                           _stream(cuda, stream)))
+    return B
+
+
 def tqr_lu_piv_size(m, n, nb):
     return lib().tqr_lu_piv_size(m, n, nb)
 
@@ -416,7 +435,7 @@ def tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, task, D=0):
     """(waits [(ctr, cnt, ver)], signals [(ctr, cnt)]) of one task."""
     t = np.asarray(list(task) + [0] * (8 - len(task)), dtype=np.int32)
     w = np.zeros(12, dtype=np.int32)
-    s = np.zeros(4, dtype=np.int32)
+    s = np.zeros(6, dtype=np.int32)
     r = lib().tqr_debug_rules(mode, m, n, nb, ib, cs, nrhs, D, t.ctypes.data, w.ctypes.data, s.ctypes.data)
     nw, ns = r % 16, r // 16
     return [tuple(w[3 * a:3 * a + 3]) for a in range(nw)], [tuple(s[2 * a:2 * a + 2]) for a in range(ns)]

@@ -1,0 +1,97 @@
+"""GPU parity of the 2b x b bottom variant (tqr_factor_pairs /
+tqr_apply_qt_pairs through the C ABI) against the oracle."""
+import numpy as np
+import pytest
+
+from oracle import householder as H
+from oracle import tiled as TL
+from paper_0707_3548_gb300 import inputs, tqr
+from tests.gpu_util import t_blocks, to_dev, to_host, torch_cuda
+
+pytestmark = pytest.mark.gpu
+U53 = 2.0 ** -53
+
+SHAPES = [
+    # m, n, nb, ib -- odd and even tile-row counts, ragged tails, ib = nb
+    (512, 512, 128, 32),
+    (700, 500, 128, 32),
+    (1000, 300, 64, 16),
+    (320, 256, 64, 64),
+    (300, 600, 64, 16),
+    (33, 17, 8, 4),
+]
+
+
+@pytest.mark.parametrize("m,n,nb,ib", SHAPES)
+def test_pair_factor_matches_oracle(m, n, nb, ib):
+    torch_cuda()
+    A = inputs.normal_matrix(m, n, 201 + m + n)
+    dA = to_dev(A)
+    T = tqr.tqr_factor_pairs(dA, nb, ib)
+    f = TL.tiled_qr_pairs(A, nb, ib)
+    F = to_host(dA)
+    assert np.max(np.abs(F - f.F)) <= 1e-11 * max(1.0, np.abs(f.F).max())
+    Tg = t_blocks(T.cpu().numpy(), m, n, nb, ib)
+    for key, Tk in f.T.items():
+        assert np.max(np.abs(Tg[key] - Tk)) <= 1e-11 * max(1.0, np.abs(Tk).max()), key
+    k = min(m, n)
+    Ru = H.sign_normalize(H.r_factor(H.geqr2(A)[0]))[:k]
+    assert np.linalg.norm(H.sign_normalize(np.triu(F))[:k] - Ru) / np.linalg.norm(Ru) <= 1e-11
+
+
+@pytest.mark.parametrize("m,n,nb,ib,nrhs", [(700, 500, 128, 32, 3), (1000, 300, 64, 16, 40), (320, 256, 64, 64, 1)])
+def test_pair_apply_matches_oracle(m, n, nb, ib, nrhs):
+    A = inputs.normal_matrix(m, n, 211)
+    B = inputs.normal_matrix(m, nrhs, 212)
+    dA = to_dev(A)
+    T = tqr.tqr_factor_pairs(dA, nb, ib)
+    f = TL.tiled_qr_pairs(A, nb, ib)
+    for trans, ref in (("T", TL.pairs_apply_qt(f, B)), ("N", TL.pairs_apply_q(f, B))):
+        dB = to_dev(B)
+        tqr.tqr_apply_qt_pairs(trans, dA, nb, ib, T, dB)
+        assert np.max(np.abs(to_host(dB) - ref)) <= 1e-11 * max(1.0, np.abs(ref).max())
+
+
+def test_pair_deterministic_across_schedules():
+    A = inputs.normal_matrix(900, 700, 213)
+    outs = []
+    try:
+        for policy, cap in ((-1, 0), (0, 0), (1, 0), (1, 3)):
+            tqr.tqr_debug_set_schedule(policy, cap)
+            dA = to_dev(A)
+            T = tqr.tqr_factor_pairs(dA, 128, 32)
+            outs.append((to_host(dA), T.cpu().numpy()))
+    finally:
+        tqr.tqr_debug_set_schedule(-1, 0)
+    for F, T in outs[1:]:
+        assert np.array_equal(F, outs[0][0]) and np.array_equal(T, outs[0][1])
+
+
+def test_pair_host_path_equals_device_path():
+    A = inputs.normal_matrix(400, 300, 214)
+    dA = to_dev(A)
+    T = tqr.tqr_factor_pairs(dA, 64, 16)
+    hA = np.array(A, order="F", copy=True)
+    hT = tqr.tqr_factor_pairs(hA, 64, 16)
+    assert np.array_equal(hA, to_host(dA)) and np.array_equal(hT, T.cpu().numpy())
+
+
+def test_full_size_sampled_pairs():
+    """16384 x 16384 N(0,1), nb 128, ib 16 (the benchmark's launch): R's leading
+    256 x 256 block equals the oracle's QR of A's first 256 columns, and Q R
+    reproduces sampled columns of A."""
+    torch = torch_cuda()
+    m = n = 16384
+    A = inputs.normal_matrix(m, n, 0)
+    dA = to_dev(A)
+    T = tqr.tqr_factor_pairs(dA, 128, 16)
+    torch.cuda.synchronize()
+    lead = dA[:256, :256].cpu().numpy()
+    Fo, _ = H.geqr2(A[:, :256])
+    assert np.linalg.norm(H.sign_normalize(np.triu(lead)) - H.sign_normalize(np.triu(Fo[:256]))) / \
+        np.linalg.norm(Fo[:256]) <= 1e-11
+    cols = [0, 1, 127, 128, 8191, 16383]
+    Rs = tqr.colmajor(torch.triu(dA)[:, cols].contiguous())
+    tqr.tqr_apply_qt_pairs("N", dA, 128, 16, T, Rs)
+    err = np.linalg.norm(to_host(Rs) - A[:, cols]) / np.linalg.norm(A[:, cols])
+    assert err <= 10 * n * U53
