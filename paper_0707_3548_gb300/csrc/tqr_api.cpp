@@ -538,8 +538,10 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
     return TQR_ERR_NOMEM;
   }
   int status = TQR_OK;
+  // slots the variant leaves unused (tree, pairs) come back as zeros
   if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess)
+                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
+      cudaMemsetAsync(dT, 0, tbytes, st) != cudaSuccess)
     status = TQR_ERR_CUDA;
   if (status == TQR_OK) status = factor_device<double>(m, n, dA, m, nb, ib, D, pair, dT, work, work_bytes, st);
   if (status == TQR_OK &&
