@@ -191,8 +191,8 @@ static void hold_until_done(const std::shared_ptr<DevPlan>& plan, cudaStream_t s
 
 static PlanKey key_of(const Inst& I, int esize, int grid, int dev, int policy) {
   const int last = I.qb > 0 ? slabs_of_col(I, I.q + I.qb - 1) : 0;
-  return PlanKey(I.mode + 16 * I.lu, I.p, I.q, I.nb, I.ib, I.cs, I.qb * 256 + last, I.trsm, esize, grid, dev, policy,
-                 I.D, 0);
+  return PlanKey(I.mode + 16 * I.lu + 32 * I.pair, I.p, I.q, I.nb, I.ib, I.cs, I.qb * 256 + last, I.trsm, esize, grid,
+                 dev, policy, I.D, 0);
 }
 
 std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int* status, int grid_cap) {

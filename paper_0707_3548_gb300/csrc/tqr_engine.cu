@@ -117,7 +117,7 @@ struct Ctl {
   int next;       // next ticket
   int error;      // 0, or TQR_ERR_TIMEOUT
   int err_task;   // task index whose wait ran out
-  int err_where;  // 1: dependency wait, 2: bulk-copy wait
+  int err_where;  // 1: dependency wait, 2: bulk-copy wait, 3: task kind not in this kernel
 };
 
 __device__ int g_status;  // sticky device status of asynchronous launches
@@ -142,6 +142,19 @@ __device__ void set_error(Ctx<real>& cx, int where) {
     cx.ctl->err_where = where;
   }
   atomicCAS(&g_status, 0, 3);
+}
+
+// A task kind this kernel does not implement (a plan built for another
+// kernel variant): stop every CTA and report TQR_ERR_UNSUPPORTED.
+template <typename real>
+__device__ void fail_kind(Ctx<real>& cx) {
+  if (threadIdx.x == 0) {
+    if (atomicCAS(&cx.ctl->error, 0, 7 /* TQR_ERR_UNSUPPORTED */) == 0) {
+      cx.ctl->err_task = cx.task;
+      cx.ctl->err_where = 3;
+    }
+    atomicCAS(&g_status, 0, 7);
+  }
 }
 
 // Wait for the current bulk-copy phase; bounded by the wait limit.
@@ -1492,7 +1505,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
         case K_SSRFB2_N: exec_ssrfb2(cx, I, t.k, t.i, t.l, t.j, t.s, false); break;
         case K_TRSM_UPD: exec_trsm_upd(cx, I, t.k, t.l, t.j, t.s); break;
         case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
-        default: break;
+        default: fail_kind(cx); break;
       }
     } else if constexpr (V == KV_LU) {
       switch (t.kind) {
@@ -1502,7 +1515,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
         case K_SSSSM: exec_ssssm(cx, I, t.k, t.i, t.j, t.s); break;
         case K_TRSM_UPD: exec_trsm_upd(cx, I, t.k, t.l, t.j, t.s); break;
         case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
-        default: break;
+        default: fail_kind(cx); break;
       }
     } else switch (t.kind) {
       case K_GEQRT: exec_geqrt(cx, I, t.k, t.i); break;
@@ -1518,7 +1531,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
       case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
       case K_TRSMT_UPD: exec_trsmt_upd(cx, I, t.k, t.l, t.j, t.s); break;
       case K_TRSMT_SOLVE: exec_trsmt_solve(cx, I, t.k, t.j, t.s); break;
-      default: break;
+      default: fail_kind(cx); break;
     }
     __syncthreads();
     if (threadIdx.x == 0) signal_done<V == KV_PAIR>(I, t);

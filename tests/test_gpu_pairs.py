@@ -95,3 +95,18 @@ def test_full_size_sampled_pairs():
     tqr.tqr_apply_qt_pairs("N", dA, 128, 16, T, Rs)
     err = np.linalg.norm(to_host(Rs) - A[:, cols]) / np.linalg.norm(A[:, cols])
     assert err <= 10 * n * U53
+
+
+def test_pair_and_flat_plans_do_not_mix():
+    """Both variants of one shape, alternately: each must run its own task
+    list (the plan cache keys on the variant)."""
+    A = inputs.normal_matrix(512, 512, 215)
+    f_flat = TL.tiled_qr(A, 128, 32)
+    f_pair = TL.tiled_qr_pairs(A, 128, 32)
+    for _ in range(2):
+        dA = to_dev(A)
+        tqr.tqr_factor_pairs(dA, 128, 32)
+        assert np.max(np.abs(to_host(dA) - f_pair.F)) <= 1e-11 * np.abs(f_pair.F).max()
+        dA = to_dev(A)
+        tqr.tqr_factor(dA, 128, 32)
+        assert np.max(np.abs(to_host(dA) - f_flat.F)) <= 1e-11 * np.abs(f_flat.F).max()
