@@ -4,10 +4,12 @@
 Default workload: one 16384 x 16384 FP64 factorization, entries N(0,1) from
 NumPy PCG64 seed 0, tile nb = 128, inner block ib = 16 -- the largest square
 of the plain-FP64 tiled QR sweep (nb = 128, ib = 16 was the fastest of the
-nb in {128, 192, 256} x ib in {16, 32, 64} grid measured at n = 8192).  A step
-restores the matrix from a pristine device copy and calls tqr_factor (pack to
+nb in {128, 192, 256} x ib in {16, 32, 64} grid measured at n = 8192) -- with
+2b x b bottoms (Section 3.2's non-square blocks: the rows below each diagonal
+tile are taken in pairs), the fastest variant at this size.  A step restores
+the matrix from a pristine device copy and calls tqr_factor_pairs (pack to
 Block Data Layout, the persistent task kernel, unpack).  The 2 GiB input is
-larger than L2.
+larger than L2.  `--workload qr16384` is Algorithm 1's flat b x b tiles.
 
 Metric: TFLOP/s counting 2 m n^2 - 2 n^3 / 3 per factorization, and its
 fraction of this GPU's FP64 FMA peak (measured in the run by a DFMA probe).
@@ -443,7 +445,8 @@ def run_ours(args, w):
     achieved = flops / (kern_avg_ms * 1e-3) / 1e12
     roofline = {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak, "traffic": measured_traffic(args.workload),
-                "kernel": "tqr::run_tasks_kernel<double> (persistent task scheduler)",
+                "kernel": ("tqr::run_pair_tasks_kernel<double>" if pairs else "tqr::run_tasks_kernel<double>") +
+                          " (persistent task scheduler)",
                 "peak_source": "FP64 DFMA probe measured in this run (tqr_debug_fp64_peak); "
                                "nominal GB300 FP64 1.25 TFLOP/s",
                 "kernel_ms_per_launch": kern_avg_ms}
@@ -905,7 +908,7 @@ def main():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="qr16384", choices=sorted(WORKLOADS))
+    ap.add_argument("--workload", default="qr16384_pairs", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--nb", type=int, default=0, help="override the workload's tile size")
