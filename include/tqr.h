@@ -418,14 +418,17 @@ int tqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int nb, int
 /*
  * Device status of the asynchronous calls made on `stream`: synchronizes the
  * stream and returns TQR_OK, TQR_ERR_TIMEOUT (a scheduler wait ran out; the
- * affected output is undefined) or TQR_ERR_CUDA.  Clears the recorded status.
+ * affected output is undefined), TQR_ERR_UNSUPPORTED (a launch met a task
+ * kind its kernel does not implement; output undefined) or TQR_ERR_CUDA.
+ * Clears the recorded status.
  */
 int tqr_stream_status(void* stream);
 
 /*
  * Dependency-wait limit of the device scheduler in milliseconds (default
- * 20000).  A wait that exceeds it makes every CTA of that launch stop and
- * the call report TQR_ERR_TIMEOUT.  Returns the previous value.
+ * 20000, or TQR_WAIT_LIMIT_MS from the environment when the library loads).
+ * A wait that exceeds it makes every CTA of that launch stop and the call
+ * report TQR_ERR_TIMEOUT.  Returns the previous value.
  */
 int64_t tqr_set_wait_limit_ms(int64_t ms);
 

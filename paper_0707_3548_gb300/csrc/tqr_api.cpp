@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cstdlib>
 #include <cmath>
 #include <list>
 #include <map>
@@ -22,7 +23,18 @@
 
 namespace tqr {
 
-static long long g_wait_limit_ms = 20000;
+// The device's bounded waits give up after this long (TQR_WAIT_LIMIT_MS in
+// the environment overrides it, e.g. for runs under a profiler's replay,
+// which slows launches by orders of magnitude).
+static long long initial_wait_limit_ms() {
+  const char* e = std::getenv("TQR_WAIT_LIMIT_MS");
+  if (e != nullptr) {
+    const long long v = std::atoll(e);
+    if (v > 0) return v;
+  }
+  return 20000;
+}
+static long long g_wait_limit_ms = initial_wait_limit_ms();
 static int g_policy = -1;
 static int g_max_ctas = 0;
 static std::mutex g_mu;
