@@ -404,10 +404,8 @@ def run_ours(args, w):
     tqr.tqr_debug_timing(0)
     status = tqr.tqr_stream_status()
     elapsed_ms = e0.elapsed_time(e1)
-    if dist is not None:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    from paper_0707_3548_gb300.ranks import max_over_ranks
+    elapsed_ms = max_over_ranks(elapsed_ms, dist, dev)
     flops = qr_flops(m, n)
     value = flops * args.steps * world / (elapsed_ms * 1e-3) / 1e12
 
@@ -430,10 +428,8 @@ def run_ours(args, w):
         if it >= args.warmup:
             e2e_times.append(t1 - t0)
     e2e_s = statistics.mean(e2e_times) if e2e_times else float("nan")
-    if dist is not None and e2e_times:
-        t = torch.tensor([e2e_s], device=dev, dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
+    if e2e_times:
+        e2e_s = max_over_ranks(e2e_s, dist, dev)
     e2e = None
     if e2e_times:
         e2e = {"value": flops * world / e2e_s / 1e12, "unit": "TFLOP/s",
@@ -741,26 +737,43 @@ def run_lu(args, w):
 
 
 def run_batch(args, w):
-    """Batched factorization: all matrices in one persistent launch (CUDA
-    graph), value = total 2mn^2 - 2n^3/3 over the batch / device time."""
+    """Batched factorization: all matrices of a rank in one persistent launch
+    (CUDA graph), value = total 2mn^2 - 2n^3/3 over the batch / device time.
+    With N ranks the matrices are sharded by flops (greedy, no collective);
+    the job's time is the slowest rank's."""
     import numpy as np
     import torch
 
     from paper_0707_3548_gb300 import build as B
     from paper_0707_3548_gb300 import inputs, tqr
+    from paper_0707_3548_gb300.ranks import max_over_ranks, shard_by_cost
 
-    torch.cuda.set_device(0)
-    B.build()
-    shapes = inputs.batch_shapes(w["count"], seed=0)
-    flops = sum(qr_flops(m, n) for m, n in shapes)
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
+    all_shapes = inputs.batch_shapes(w["count"], seed=0)
+    all_flops = [qr_flops(m, n) for m, n in all_shapes]
+    mine = shard_by_cost(all_flops, world)[rank]
+    shapes = [all_shapes[t] for t in mine]
+    flops = sum(all_flops)
     pristine = []
-    for t, (m, n) in enumerate(shapes):
+    for t in mine:
+        m, n = all_shapes[t]
         A = inputs.normal_matrix(m, n, t)
-        pristine.append(tqr.colmajor(torch.from_numpy(A).cuda()))
-    work = [torch.empty_like(a) for a in pristine]
-    work = [tqr.colmajor(x) for x in work]
+        pristine.append(tqr.colmajor(torch.from_numpy(A).to(dev)))
+    work = [tqr.colmajor(torch.empty_like(a)) for a in pristine]
     tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
-    Ts = [torch.zeros(tqr.tqr_t_size(m, n, nb, ib) // 8, dtype=torch.float64, device="cuda")
+    Ts = [torch.zeros(tqr.tqr_t_size(m, n, nb, ib) // 8, dtype=torch.float64, device=dev)
           for (m, n), (nb, ib) in zip(shapes, tiles)]
     stream = torch.cuda.current_stream()
 
@@ -776,38 +789,58 @@ def run_batch(args, w):
     for _ in range(args.warmup - 1):
         restore()
         tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tiles), len(shapes))
-    times = []
-    for _ in range(args.steps):
-        restore()
-        torch.cuda.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        t = tqr.tqr_batch_submit(work, Ts, tiles)
-        e1.record(stream)
-        rc, st = tqr.tqr_batch_wait(t, len(shapes))
-        torch.cuda.synchronize()
-        assert rc == 0 and not st.any()
-        times.append(e0.elapsed_time(e1) * 1e-3)
-    sec = statistics.mean(times)
-    cpu = None
-    if not args.no_cpu_baseline:
-        fl, tt, smp = oracle_kind_sample("batch", {"count": w["count"]}, 8.0)
-        cpu = {"value": fl / tt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
-               "sample": smp + ", %.1f s" % tt}
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    props = torch.cuda.get_device_properties(dev)
+    try:
+        bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
+    except AttributeError:
+        bus = None
+    total = 0.0
+    with ClockSampler(bus) as clk:
+        for _ in range(args.steps):
+            restore()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            t = tqr.tqr_batch_submit(work, Ts, tiles)
+            e1.record(stream)
+            rc, st = tqr.tqr_batch_wait(t, len(shapes))
+            torch.cuda.synchronize()
+            assert rc == 0 and not st.any()
+            total += e0.elapsed_time(e1) * 1e-3
+    if dist is not None:
+        dist.barrier()
+    sec = max_over_ranks(total / args.steps, dist, dev)
+    if rank != 0:
+        dist.destroy_process_group()
+        return
     classes = {}
     for nb, ib in tiles:
         classes["%d/%d" % (nb, ib)] = classes.get("%d/%d" % (nb, ib), 0) + 1
-    line = {"metric": METRIC + " (batched)", "value": flops / sec / 1e12, "unit": "TFLOP/s", "n_gpus": 1,
+    cpu = None
+    if world == 1 and not args.no_cpu_baseline:
+        fl, tt, smp = oracle_kind_sample("batch", {"count": w["count"]}, 8.0)
+        cpu = {"value": fl / tt / 1e12, "unit": "TFLOP/s", "cores": 1, "kind": "oracle",
+               "sample": smp + ", %.1f s" % tt}
+    line = {"metric": METRIC + " (batched)", "value": flops / sec / 1e12, "unit": "TFLOP/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sec, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic: N(0,1), seed per matrix",
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic: N(0,1), seed per matrix",
             "config": {"workload": "batched QR of %d matrices, m log-uniform [64, 2048], n uniform [32, m], one "
-                                   "persistent launch, autotuned nb/ib" % len(shapes),
-                       "total_flops": flops, "total_bytes": 8 * sum(m * n for m, n in shapes),
+                                   "persistent launch per rank, autotuned nb/ib" % len(all_shapes),
+                       "total_flops": flops, "total_bytes": 8 * sum(m * n for m, n in all_shapes),
                        "l2": "inputs > 129 MB L2, restored from device copies before each step",
-                       "tile_classes": classes},
-            "first_submit_s_incl_plan": t_plan, "gpu_launches": 3 * args.steps, "cpu_baseline": cpu}
+                       "parallelism": ("instances sharded over %d ranks by flops (greedy), no collective" % world)
+                                      if world > 1 else "single GPU",
+                       "tile_classes_rank0": classes},
+            "first_submit_s_incl_plan": t_plan, "gpu_launches": 3 * args.steps, "cpu_baseline": cpu,
+            "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def run_serve(args, w):
