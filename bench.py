@@ -772,7 +772,11 @@ def run_batch(args, w):
         A = inputs.normal_matrix(m, n, t)
         pristine.append(tqr.colmajor(torch.from_numpy(A).to(dev)))
     work = [tqr.colmajor(torch.empty_like(a)) for a in pristine]
-    tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
+    if "nb" in w:   # --nb/--ib: one tile shape for every matrix instead of the autotuner's
+        tiles = [(min(w["nb"], max(16, 1 << (max(m, n) - 1).bit_length())), w["ib"]) for m, n in shapes]
+        tiles = [(nb, min(ib, nb)) for nb, ib in tiles]
+    else:
+        tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
     Ts = [torch.zeros(tqr.tqr_t_size(m, n, nb, ib) // 8, dtype=torch.float64, device=dev)
           for (m, n), (nb, ib) in zip(shapes, tiles)]
     stream = torch.cuda.current_stream()
