@@ -299,10 +299,10 @@ typedef struct tqr_desc {
 } tqr_desc;
 
 /*
- * Tile sizes for one m x n factorization inside a batch, from a table of
- * half-octave size classes filled on first use by a model of the scheduler's
- * costs (padded work plus a small weight on the critical path; candidates
- * nb in {16..256}, ib in {16, 32}).  Writes *nb, *ib.  Returns 0 or -i.
+ * Tile sizes for one m x n factorization inside a batch, by a rule taken
+ * from batch measurements: nb = 128, ib = 16, except that a matrix smaller
+ * than 128 takes the smallest power of two (>= 16) that holds it.  Writes
+ * *nb, *ib.  Returns 0 or -i.
  */
 int tqr_autotune(int64_t m, int64_t n, int* nb, int* ib);
 
