@@ -26,6 +26,7 @@ constexpr size_t kNaOffCtr = kNaTileBytes;
 constexpr size_t kNaOffTask = kNaOffCtr + kNaCtrBytes;
 constexpr size_t kNaOffInst = kNaOffTask + kNaTaskBytes;
 constexpr size_t kNaOffCtl = kNaOffInst + 256;
+static_assert(sizeof(tqr::Inst) <= 256, "the instance slot of the static scratch is 256 bytes");
 constexpr size_t kNaBytes = kNaOffCtl + 256;
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kNaBytes];
