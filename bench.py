@@ -48,10 +48,10 @@ WORKLOADS = {
     "ts65536x2048_tree": dict(m=65536, n=2048, nb=128, ib=16, tree=True),
     # least squares A = U diag(sigma) V^T, kappa 1e2 / 1e5 / 1e8: plain FP64
     # against FP32 factorization + FP64-residual refinement
-    "ls16384x4096k1e2": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e2, ls=True),
-    "ls16384x4096k1e5": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e5, ls=True),
-    "ls16384x4096k1e8": dict(m=16384, n=4096, nb=128, ib=32, kappa=1e8, ls=True),
-    "ls4096x1024k1e2": dict(m=4096, n=1024, nb=128, ib=32, kappa=1e2, ls=True),
+    "ls16384x4096k1e2": dict(m=16384, n=4096, nb=128, ib=16, kappa=1e2, ls=True),
+    "ls16384x4096k1e5": dict(m=16384, n=4096, nb=128, ib=16, kappa=1e5, ls=True),
+    "ls16384x4096k1e8": dict(m=16384, n=4096, nb=128, ib=16, kappa=1e8, ls=True),
+    "ls4096x1024k1e2": dict(m=4096, n=1024, nb=128, ib=16, kappa=1e2, ls=True),
     # served least-squares stream: Poisson arrivals, m log-uniform [128, 8192],
     # n uniform [64, m/2], 1-16 right-hand sides, 30% repeat-A, FP64 and
     # refined-FP32 classes, 64 GB HBM budget

@@ -462,6 +462,113 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
 template int run_plan<double>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t, int);
 template int run_plan<float>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t, int);
 
+// ---------------------------------------------------------------- several graphs, one launch
+// Independent task graphs of one factorization's operands (say Q^T f and a
+// triangular solve of another vector) run as one persistent launch, so
+// their dependency chains overlap instead of adding up.  Cached by the
+// instances' structures.
+static std::list<std::pair<std::vector<PlanKey>, std::shared_ptr<DevPlan>>> g_mplans;
+static const size_t kMaxMultiPlans = 64;
+
+template <typename real>
+int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int ctas_per_sm, int smem,
+                   cudaStream_t st, int grid_cap) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  int policy, max_ctas;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    policy = g_policy;
+    max_ctas = g_max_ctas;
+  }
+  int max_grid = device_sms() * ctas_per_sm;
+  if (max_ctas > 0 && max_ctas < max_grid) max_grid = max_ctas;
+  if (grid_cap > 0 && grid_cap < max_grid) max_grid = grid_cap;
+  std::vector<PlanKey> want;
+  for (int a = 0; a < count; ++a) want.push_back(key_of(insts[a], sizeof(real), max_grid, dev, policy));
+  std::shared_ptr<DevPlan> plan;
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    for (auto it = g_mplans.begin(); it != g_mplans.end(); ++it)
+      if (it->first == want) {
+        plan = it->second;
+        g_mplans.splice(g_mplans.begin(), g_mplans, it);
+        break;
+      }
+  }
+  if (!plan) {
+    std::vector<Inst> hi(insts, insts + count);
+    for (Inst& I : hi)
+      if (I.D > 0) I.vtab = host_vtab(I);
+    std::vector<TaskX> seq, ordered;
+    for (int a = 0; a < count; ++a) seq_tasks(hi[a], a, seq);
+    plan = std::make_shared<DevPlan>();
+    plan->device = dev;
+    plan->ntasks = static_cast<int>(seq.size());
+    plan->grid = std::max(1, std::min<int>(max_grid, plan->ntasks));
+    if (!seq.empty()) {
+      std::string err;
+      const bool ok = (grid_cap > 0 && policy < 0)
+                          ? order_bottom_level(hi, seq, sizeof(real), ctas_per_sm, plan->grid, ordered, &plan->stats,
+                                               &err)
+                          : order_tasks(hi, seq, plan->grid, sizeof(real), ctas_per_sm, policy, ordered,
+                                        &plan->stats, &err);
+      if (!ok) {
+        set_last_error(err);
+        return TQR_ERR_UNSUPPORTED;
+      }
+      cudaStream_t ps = plan_stream(dev);
+      if (cudaMallocAsync(reinterpret_cast<void**>(&plan->d_tasks), sizeof(TaskX) * ordered.size(), ps) !=
+          cudaSuccess) {
+        cudaGetLastError();
+        plan->d_tasks = nullptr;
+        return TQR_ERR_NOMEM;
+      }
+      if (cudaMemcpyAsync(plan->d_tasks, ordered.data(), sizeof(TaskX) * ordered.size(), cudaMemcpyHostToDevice,
+                          ps) != cudaSuccess ||
+          cudaStreamSynchronize(ps) != cudaSuccess)
+        return TQR_ERR_CUDA;
+    }
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_mplans.emplace_front(want, plan);
+    while (g_mplans.size() > kMaxMultiPlans) g_mplans.pop_back();
+  }
+  if (plan->ntasks == 0) return TQR_OK;
+  // counters of every instance and the launch's control block start at zero
+  for (int a = 0; a < count; ++a) {
+    const Inst& I = insts[a];
+    const size_t nctr = static_cast<size_t>(I.p) * (I.q + I.qb) * I.NS;
+    if (cudaMemsetAsync(I.ver, 0, sizeof(int) * nctr, st) != cudaSuccess) return TQR_ERR_CUDA;
+  }
+  if (cudaMemsetAsync(d_ctl, 0, ctl_bytes(), st) != cudaSuccess ||
+      cudaMemcpyAsync(d_insts, insts, sizeof(Inst) * count, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return TQR_ERR_CUDA;
+  std::pair<cudaEvent_t, cudaEvent_t> ev(nullptr, nullptr);
+  {
+    std::lock_guard<std::mutex> lk(g_mu);
+    if (g_timing.on) {
+      ev = timing_pair();
+      cudaEventRecord(ev.first, st);
+    }
+  }
+  cudaError_t e = launch_run<real>(plan->d_tasks, plan->ntasks, d_insts, d_ctl, wait_limit_ns(), plan->grid, smem,
+                                   st, insts[0].lu ? 1 : (insts[0].pair ? 2 : 0));
+  if (ev.first) {
+    cudaEventRecord(ev.second, st);
+    std::lock_guard<std::mutex> lk(g_mu);
+    g_timing.pending.push_back(ev);
+  }
+  hold_until_done(plan, st);
+  if (e != cudaSuccess) {
+    set_last_error(cudaGetErrorString(e));
+    return TQR_ERR_CUDA;
+  }
+  return TQR_OK;
+}
+
+template int run_plan_multi<double>(const Inst*, int, Inst*, void*, int, int, cudaStream_t, int);
+template int run_plan_multi<float>(const Inst*, int, Inst*, void*, int, int, cudaStream_t, int);
+
 // ---------------------------------------------------------------- pointers
 int ptr_kind(const void* p) {
   if (p == nullptr) return PTR_NULL;

@@ -29,6 +29,13 @@ WsLayout ws_layout(const Inst& I, int esize, bool with_t);
 template <typename real>
 int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st,
              int grid_cap = 0);
+// Several instances' task graphs in one persistent launch.  insts[a].ver
+// must be disjoint counter regions (zeroed here), d_insts device room for
+// `count` instances, d_ctl the launch's control block (ctl_bytes()).  The
+// host array's Inst.vtab may be a device pointer (the host copy is rebuilt).
+template <typename real>
+int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int ctas_per_sm, int smem,
+                   cudaStream_t st, int grid_cap = 0);
 int ptr_kind(const void* p);
 int check_tiles(int nb, int ib, int arg_nb, int arg_ib);
 void clear_plans();

@@ -252,6 +252,9 @@ bool LsJob::init(int m_, int n_, int rhs_cap_, int nb_, int ib_, int prec_, int 
   o_x = o;     o += al(sizeof(double) * nr);
   o_G = o;     o += al(sizeof(double) * nr);
   o_nrm = o;   o += al(sizeof(double) * (4 * rhs_cap + 4));
+  o_b2 = o;    o += al(W.oT - W.oB);                       // as large as the first tile array
+  o_ver2 = o;  o += al(sizeof(int) * static_cast<size_t>(I.p) * (I.q + I.qb) * I.NS);
+  o_inst2 = o; o += al(2 * sizeof(Inst));
   o_acopy = o;
   bytes = o;
   return true;
@@ -278,21 +281,40 @@ int LsJob::run_mode(int mode, int trsm, int nrhs_now, cudaStream_t st) {
                     : run_plan<float>(I, ws, W, occ, smem, st, grid_cap);
 }
 
-int LsJob::pack_rhs(const double* src, long long lds, int rows, int nrhs, cudaStream_t st) {
+int LsJob::pack_rhs(const double* src, long long lds, int rows, int nrhs, cudaStream_t st, void* tiles) {
   const int sms = device_sms();
   const int qb = (nrhs + nb - 1) / nb;
+  void* B = tiles ? tiles : I.B;
   cudaError_t e = esize == 8
-                      ? launch_pack<double>(src, lds, rows, nrhs, static_cast<double*>(I.B), I.p, qb, nb, sms, st)
-                      : launch_pack<float>(src, lds, rows, nrhs, static_cast<float*>(I.B), I.p, qb, nb, sms, st);
+                      ? launch_pack<double>(src, lds, rows, nrhs, static_cast<double*>(B), I.p, qb, nb, sms, st)
+                      : launch_pack<float>(src, lds, rows, nrhs, static_cast<float*>(B), I.p, qb, nb, sms, st);
   return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
 }
 
-int LsJob::unpack_rhs(double* dst, long long ldd, int rows, int nrhs, cudaStream_t st) {
+int LsJob::unpack_rhs(double* dst, long long ldd, int rows, int nrhs, cudaStream_t st, const void* tiles) {
   const int sms = device_sms();
+  const void* B = tiles ? tiles : I.B;
   cudaError_t e = esize == 8
-                      ? launch_unpack<double>(static_cast<double*>(I.B), I.p, nb, dst, ldd, rows, nrhs, sms, st)
-                      : launch_unpack<float>(static_cast<float*>(I.B), I.p, nb, dst, ldd, rows, nrhs, sms, st);
+                      ? launch_unpack<double>(static_cast<const double*>(B), I.p, nb, dst, ldd, rows, nrhs, sms, st)
+                      : launch_unpack<float>(static_cast<const float*>(B), I.p, nb, dst, ldd, rows, nrhs, sms, st);
   return e == cudaSuccess ? TQR_OK : TQR_ERR_CUDA;
+}
+
+int LsJob::run_two(int mode_a, int mode_b, int nrhs_now, cudaStream_t st) {
+  Inst two[2] = {I, I};
+  for (Inst& x : two) {
+    x.trsm = 0;
+    x.nrhs = nrhs_now;
+    x.qb = (nrhs_now + nb - 1) / nb;
+  }
+  two[0].mode = mode_a;
+  two[1].mode = mode_b;
+  two[1].B = ws + o_b2;
+  two[1].ver = reinterpret_cast<int*>(ws + o_ver2);
+  Inst* d_insts = reinterpret_cast<Inst*>(ws + o_inst2);
+  void* d_ctl = ws + W.oCtl;
+  return esize == 8 ? run_plan_multi<double>(two, 2, d_insts, d_ctl, occ, smem, st, grid_cap)
+                    : run_plan_multi<float>(two, 2, d_insts, d_ctl, occ, smem, st, grid_cap);
 }
 
 // factor A (and keep the factors), x0 = the solution through those factors
@@ -404,26 +426,23 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
       // f = b - r - A x = e - r;  g = -A^T r
       axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, E, m, -1.0, Rr, m, F, m);
       if (atr(A, lda, m, n, Rr, m, nrhs, -1.0, Gv, n, st) != cudaSuccess) fail(TQR_ERR_CUDA);
-      // h = R^-T g
-      fail(pack_rhs(Gv, n, n, nrhs, st));
-      if (status == TQR_OK) fail(run_mode(M_TRSMT, 0, nrhs, st));
-      fail(unpack_rhs(H, n, n, nrhs, st));
-      // d = Q^T f
+      // d = Q^T f (first tiles) and h = R^-T g (second tiles): one launch
+      void* B2 = ws + o_b2;
       fail(pack_rhs(F, m, m, nrhs, st));
-      if (status == TQR_OK) fail(run_mode(M_APPLY_QT, 0, nrhs, st));
+      fail(pack_rhs(Gv, n, n, nrhs, st, B2));
+      if (status == TQR_OK) fail(run_two(M_APPLY_QT, M_TRSMT, nrhs, st));
       fail(unpack_rhs(D, m, m, nrhs, st));
-      // dx = R^-1 (d1 - h)
+      fail(unpack_rhs(H, n, n, nrhs, st, B2));
+      // dx = R^-1 (d1 - h) (second tiles) and dr = Q [h; d2] (first tiles): one launch
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, D, m, -1.0, H, n, Gv, n);
-      fail(pack_rhs(Gv, n, n, nrhs, st));
-      if (status == TQR_OK) fail(run_mode(M_TRSM, 0, nrhs, st));
-      fail(unpack_rhs(Gv, n, n, nrhs, st));
-      col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
-      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0, Gv, n, Xw, n);
-      // dr = Q [h; d2]
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, H, n, 0.0, nullptr, 0, D, m);
       fail(pack_rhs(D, m, m, nrhs, st));
-      if (status == TQR_OK) fail(run_mode(M_APPLY_Q, 0, nrhs, st));
+      fail(pack_rhs(Gv, n, n, nrhs, st, B2));
+      if (status == TQR_OK) fail(run_two(M_APPLY_Q, M_TRSM, nrhs, st));
       fail(unpack_rhs(D, m, m, nrhs, st));
+      fail(unpack_rhs(Gv, n, n, nrhs, st, B2));
+      col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
+      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0, Gv, n, Xw, n);
       axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, Rr, m, 1.0, D, m, Rr, m);
       ++iters;
       terms();
@@ -499,7 +518,7 @@ extern "C" int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A,
   if (!(tol >= 0)) return -11;
   if (maxit < 0) return -12;
   if (nb == 0) nb = n >= 1024 ? 128 : 64;
-  if (ib == 0) ib = std::min(32, nb);
+  if (ib == 0) ib = std::min(16, nb);  // measured: ib 16 beats 32 for FP64 and FP32 factors
   const int c = check_tiles(nb, ib, 15, 16);
   if (c) return c;
   cudaStream_t st = static_cast<cudaStream_t>(stream);

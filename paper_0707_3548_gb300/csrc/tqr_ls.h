@@ -23,6 +23,9 @@ struct LsJob {
   WsLayout W = {};
   LsScratch sc = {};
   size_t o_part = 0, o_e = 0, o_r = 0, o_f = 0, o_d = 0, o_g = 0, o_h = 0, o_x = 0, o_G = 0, o_nrm = 0, o_acopy = 0;
+  // a second right-hand-side tile array, its counters, and room for two
+  // instances: two independent graphs of the refinement step in one launch
+  size_t o_b2 = 0, o_ver2 = 0, o_inst2 = 0;
   size_t bytes = 0;  // workspace without the FP64 copy of A
   char* ws = nullptr;
   double* Acopy = nullptr;
@@ -38,8 +41,11 @@ struct LsJob {
   int finish(const double* A, long long lda, const double* B, long long ldb, int nrhs, double* X, long long ldx,
              double tol, int maxit, int* iters, double* berr, cudaStream_t st);
   int run_mode(int mode, int trsm, int nrhs, cudaStream_t st);
-  int pack_rhs(const double* src, long long lds, int rows, int nrhs, cudaStream_t st);
-  int unpack_rhs(double* dst, long long ldd, int rows, int nrhs, cudaStream_t st);
+  int pack_rhs(const double* src, long long lds, int rows, int nrhs, cudaStream_t st, void* tiles = nullptr);
+  int unpack_rhs(double* dst, long long ldd, int rows, int nrhs, cudaStream_t st, const void* tiles = nullptr);
+  // mode_a on the first right-hand-side tiles and mode_b on the second, as
+  // one launch (neither appends a triangular solve)
+  int run_two(int mode_a, int mode_b, int nrhs, cudaStream_t st);
 };
 
 }  // namespace tqr
