@@ -1562,38 +1562,54 @@ __global__ void __launch_bounds__(kThreads) run_pair_tasks_kernel(const TaskX* _
 
 // ---------------------------------------------------------------- BDL
 // Column-major (ld) -> Block Data Layout tiles (Section 3.4), zero padded.
-// One thread per tile element, consecutive threads on consecutive rows.
+// One warp per tile column: the column's rows are contiguous both in the
+// caller's matrix and in the tile, so lanes walk consecutive addresses on
+// both sides, and the tile coordinates cost one division per column rather
+// than per element.
 template <typename S, typename D>
 __global__ void pack_kernel(const S* __restrict__ A, long long lda, int m, int n, D* __restrict__ Ab, int p,
                             int q, int nb) {
-  const long long nb2 = static_cast<long long>(nb) * nb;
-  const long long total = nb2 * p * q;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const long long tile = e / nb2;
-    const int rem = static_cast<int>(e - tile * nb2);
-    const int r = rem % nb, c = rem / nb;
-    const int ti = static_cast<int>(tile % p), tj = static_cast<int>(tile / p);
-    const long long gi = static_cast<long long>(ti) * nb + r, gj = static_cast<long long>(tj) * nb + c;
-    D v = D(0);
-    if (gi < m && gj < n) v = static_cast<D>(A[gi + gj * lda]);
-    Ab[e] = v;
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  const long long units = static_cast<long long>(p) * q * nb;  // tile columns
+  for (long long u = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5; u < units;
+       u += nwarps) {
+    const long long t = u / nb;
+    const int c = static_cast<int>(u - t * nb);
+    const int ti = static_cast<int>(t % p), tj = static_cast<int>(t / p);
+    const long long gj = static_cast<long long>(tj) * nb + c, gi0 = static_cast<long long>(ti) * nb;
+    int valid = 0;
+    if (gj < n) {
+      const long long v = m - gi0;
+      valid = v <= 0 ? 0 : (v >= nb ? nb : static_cast<int>(v));
+    }
+    const S* src = A + gi0 + gj * lda;
+    D* dst = Ab + t * nb * static_cast<long long>(nb) + static_cast<long long>(c) * nb;
+#pragma unroll 4
+    for (int r = lane; r < nb; r += 32) dst[r] = r < valid ? static_cast<D>(src[r]) : D(0);
   }
 }
 
 template <typename S, typename D>
 __global__ void unpack_kernel(const S* __restrict__ Ab, int p, int nb, D* __restrict__ A, long long lda, int m,
                               int n) {
-  const long long total = static_cast<long long>(m) * n;
-  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
-       e += static_cast<long long>(gridDim.x) * blockDim.x) {
-    const int gi = static_cast<int>(e % m);
-    const int gj = static_cast<int>(e / m);
-    const int ti = gi / nb, r = gi - ti * nb;
-    const int tj = gj / nb, c = gj - tj * nb;
-    A[gi + static_cast<long long>(gj) * lda] =
-        static_cast<D>(Ab[(static_cast<long long>(ti) + static_cast<long long>(tj) * p) * nb * nb +
-                          static_cast<long long>(c) * nb + r]);
+  const int lane = threadIdx.x & 31;
+  const long long nwarps = (static_cast<long long>(gridDim.x) * blockDim.x) >> 5;
+  const int q = (n + nb - 1) / nb;
+  const long long units = static_cast<long long>(p) * q * nb;  // tile columns
+  for (long long u = (blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x) >> 5; u < units;
+       u += nwarps) {
+    const long long t = u / nb;
+    const int c = static_cast<int>(u - t * nb);
+    const int ti = static_cast<int>(t % p), tj = static_cast<int>(t / p);
+    const long long gj = static_cast<long long>(tj) * nb + c, gi0 = static_cast<long long>(ti) * nb;
+    if (gj >= n || gi0 >= m) continue;
+    const long long v = m - gi0;
+    const int valid = v >= nb ? nb : static_cast<int>(v);
+    const S* src = Ab + t * nb * static_cast<long long>(nb) + static_cast<long long>(c) * nb;
+    D* dst = A + gi0 + gj * lda;
+#pragma unroll 4
+    for (int r = lane; r < valid; r += 32) dst[r] = static_cast<D>(src[r]);
   }
 }
 
@@ -1721,11 +1737,20 @@ static int grid_for(long long work, int sms) {
   return static_cast<int>(g);
 }
 
+// Warp-per-tile-column copies: 8 warps per block, up to 16 blocks per SM.
+static int grid_for_columns(long long columns, int sms) {
+  long long g = (columns + 7) / 8;
+  const long long cap = static_cast<long long>(sms) * 16;
+  if (g > cap) g = cap;
+  if (g < 1) g = 1;
+  return static_cast<int>(g);
+}
+
 template <typename real>
 cudaError_t launch_pack(const double* A, long long lda, int m, int n, real* Ab, int p, int q, int nb, int sms,
                         cudaStream_t st) {
-  const long long total = static_cast<long long>(nb) * nb * p * q;
-  pack_kernel<double, real><<<grid_for(total, sms), 256, 0, st>>>(A, lda, m, n, Ab, p, q, nb);
+  const long long columns = static_cast<long long>(p) * q * nb;
+  pack_kernel<double, real><<<grid_for_columns(columns, sms), 256, 0, st>>>(A, lda, m, n, Ab, p, q, nb);
   return cudaGetLastError();
 }
 
@@ -1733,7 +1758,8 @@ template <typename real>
 cudaError_t launch_unpack(const real* Ab, int p, int nb, double* A, long long lda, int m, int n, int sms,
                           cudaStream_t st) {
   if (static_cast<long long>(m) * n == 0) return cudaSuccess;
-  unpack_kernel<real, double><<<grid_for(static_cast<long long>(m) * n, sms), 256, 0, st>>>(Ab, p, nb, A, lda, m, n);
+  const long long columns = static_cast<long long>(p) * ((n + nb - 1) / nb) * nb;
+  unpack_kernel<real, double><<<grid_for_columns(columns, sms), 256, 0, st>>>(Ab, p, nb, A, lda, m, n);
   return cudaGetLastError();
 }
 
