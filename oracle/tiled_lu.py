@@ -94,9 +94,10 @@ def tstrf(U, A, ib):
     unit lower triangles (block l in columns l*ib .. (l+1)*ib - 1, strictly
     lower part significant), piv[c] = -1 (top row c kept) or the bottom row
     swapped with top row c."""
-    b = A.shape[0]
+    b = U.shape[0]            # columns; the bottom may be taller (2b x b blocks)
     Ut = np.triu(np.array(U, dtype=np.float64, copy=True))
     Lb = np.array(A, dtype=np.float64, copy=True)
+    assert Lb.shape[1] == b
     L1 = np.zeros((ib, b))
     piv = np.full(b, -1)
     for l0 in range(0, b, ib):
@@ -138,7 +139,7 @@ def ssssm(Ct, Cb, Lb, L1, piv, ib):
     """[Ct; Cb] <- TSTRF's transformations (Lb, L1, piv) applied to them."""
     Ct = np.array(Ct, dtype=np.float64, copy=True)
     Cb = np.array(Cb, dtype=np.float64, copy=True)
-    b = Lb.shape[0]
+    b = Lb.shape[1]            # columns of the factored panel (rows of the top)
     for l0 in range(0, b, ib):
         for cc in range(ib):
             c = l0 + cc
@@ -230,5 +231,87 @@ def lu_solve(f, B):
     X = np.array(Y, dtype=np.float64, copy=True)
     n = f.n
     for r in range(n - 1, -1, -1):
+        X[r] = (X[r] - U[r, r + 1:] @ X[r + 1:]) / U[r, r]
+    return X
+
+
+
+# ---------------------------------------------------------------------------
+# 2b x b bottoms (the non-square blocks of Section 3.2's remark, applied to
+# the LU analogue): the rows below each diagonal tile are taken in pairs, so
+# each TSTRF pivots row c of U_kk against 2b rows and each SSSSM updates the
+# top tile with a 2b-row bottom.  The interchanges of a pair index its 2b
+# rows (0 .. 2b-1); its multipliers are stored in its two tiles and its L1
+# triangles under its first row.
+
+def _pair_groups(k, p):
+    out, h = [], k + 1
+    while h < p:
+        rows = (h, h + 1) if h + 1 < p else (h,)
+        out.append((h, rows))
+        h += len(rows)
+    return out
+
+
+def tiled_lu_pairs(A, nb, ib):
+    A = np.asarray(A, dtype=np.float64)
+    m, n = A.shape
+    assert nb % ib == 0
+    p, q = -(-m // nb), -(-n // nb)
+    Ap = np.zeros((p * nb, q * nb))
+    Ap[:m, :n] = A
+    f = TiledLU(m, n, nb, ib, Ap, {}, {})
+    t = f.tile
+    stack = lambda rows, j: np.vstack([t(r, j) for r in rows])
+
+    def unstack(rows, j, X):
+        for a, r in enumerate(rows):
+            t(r, j)[:] = X[a * nb:(a + 1) * nb]
+
+    for k in range(min(p, q)):
+        F, pv = getrf(t(k, k), ib)
+        t(k, k)[:] = F
+        f.piv[(k, k)] = pv
+        for j in range(k + 1, q):
+            t(k, j)[:] = gessm(t(k, j), F, pv, ib)
+        for h, rows in _pair_groups(k, p):
+            Ut, Lb, L1, pv2 = tstrf(t(k, k), stack(rows, k), ib)
+            t(k, k)[:] = np.tril(t(k, k), -1) + Ut
+            unstack(rows, k, Lb)
+            f.piv[(h, k)] = pv2
+            f.L1[(h, k)] = L1
+            for j in range(k + 1, q):
+                top, bot = ssssm(t(k, j), stack(rows, j), Lb, L1, pv2, ib)
+                t(k, j)[:] = top
+                unstack(rows, j, bot)
+    f.pairs = True
+    return f
+
+
+def pairs_apply_linv(f, B):
+    B = np.asarray(B, dtype=np.float64)
+    if B.ndim == 1:
+        B = B[:, None]
+    nb = f.nb
+    Bp = np.zeros((f.p * nb, B.shape[1]))
+    Bp[:f.m] = B
+    rows_of = lambda i: slice(i * nb, (i + 1) * nb)
+    for k in range(min(f.p, f.q)):
+        Bp[rows_of(k)] = gessm(Bp[rows_of(k)], f.tile(k, k), f.piv[(k, k)], f.ib)
+        for h, rows in _pair_groups(k, f.p):
+            Lb = np.vstack([f.tile(r, k) for r in rows])
+            bot = np.vstack([Bp[rows_of(r)] for r in rows])
+            top, bot = ssssm(Bp[rows_of(k)], bot, Lb, f.L1[(h, k)], f.piv[(h, k)], f.ib)
+            Bp[rows_of(k)] = top
+            for a, r in enumerate(rows):
+                Bp[rows_of(r)] = bot[a * nb:(a + 1) * nb]
+    return Bp[:f.m]
+
+
+def pairs_lu_solve(f, B):
+    assert f.m == f.n
+    X = pairs_apply_linv(f, B)
+    U = f.U
+    for r in range(f.n - 1, -1, -1):
         X[r] = (X[r] - U[r, r + 1:] @ X[r + 1:]) / U[r, r]
     return X

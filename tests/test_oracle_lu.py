@@ -163,3 +163,42 @@ def test_zero_diagonal_tile_takes_pivots_from_below():
     B = inputs.normal_matrix(2 * nb, 2, 18)
     X = LU.lu_solve(f, B)
     assert np.linalg.norm(A @ X - B) <= 1e-12 * np.linalg.norm(B) * np.linalg.cond(A)
+
+
+# 2b x b bottoms -------------------------------------------------------------
+
+@pytest.mark.parametrize("m,n,nb,ib", SHAPES)
+def test_pair_transformations_applied_to_a_give_u(m, n, nb, ib):
+    A = inputs.normal_matrix(m, n, m + 2 * n)
+    f = LU.tiled_lu_pairs(A, nb, ib)
+    Y = LU.pairs_apply_linv(f, A)
+    k = min(m, n)
+    U = np.triu(f.Ap[:m, :n])
+    assert _rel(Y[:k], U[:k]) <= 1e3 * n * U53
+    if m > n:
+        assert np.linalg.norm(Y[n:]) <= 1e3 * n * U53 * np.linalg.norm(A)
+
+
+@pytest.mark.parametrize("n,nb,ib", [(64, 16, 4), (70, 16, 8), (33, 8, 8), (96, 32, 8)])
+def test_pair_solve_matches_dense_solver(n, nb, ib):
+    A = inputs.normal_matrix(n, n, 21 + n)
+    B = inputs.normal_matrix(n, 3, 22)
+    f = LU.tiled_lu_pairs(A, nb, ib)
+    X = LU.pairs_lu_solve(f, B)
+    assert _rel(X, np.linalg.solve(A, B)) <= 1e3 * np.linalg.cond(A) * n * U53
+    assert np.linalg.norm(A @ X - B) / (np.linalg.norm(A) * np.linalg.norm(X)) <= 1e3 * n * U53
+
+
+def test_pair_diagonally_dominant_gives_the_unique_u():
+    n = 13
+    g = np.random.default_rng(3)
+    A = g.integers(-9, 10, size=(n, n)).astype(np.float64)
+    A += np.diag(np.abs(A).sum(axis=0) + 1.0)
+    f = LU.tiled_lu_pairs(A, 3, 1)
+    assert all((pv == -1).all() for (i, k), pv in f.piv.items() if i != k)
+    assert _rel(f.U, _doolittle_exact(A)) <= 10 * n * U53
+
+
+def test_pair_two_tile_rows_are_the_flat_factorization():
+    A = inputs.normal_matrix(32, 40, 23)
+    assert np.array_equal(LU.tiled_lu_pairs(A, 16, 4).Ap, LU.tiled_lu(A, 16, 4).Ap)
