@@ -64,6 +64,7 @@ WORKLOADS = {
     # tiled LU with pairwise pivoting (the LU analogue of Algorithm 1)
     "lu16384": dict(m=16384, n=16384, nb=128, ib=16, lu=True),
     "lu8192": dict(m=8192, n=8192, nb=128, ib=16, lu=True),
+    "lu16384_pairs": dict(m=16384, n=16384, nb=128, ib=16, lu=True, pairs=True),
     "orgqr16384": dict(m=16384, n=16384, nb=128, ib=16, qsuite="orgqr"),
     "ormqr16384r4096": dict(m=16384, n=16384, nb=128, ib=16, qsuite="ormqr", mc=4096),
     "serve": dict(rate=2000.0, window=1.0, budget=64 << 30, slots=8, pool_bytes=2 << 30, serve=True),
@@ -667,9 +668,11 @@ def run_lu(args, w):
     flops = 2.0 * k ** 3 / 3.0 + (m - k) * k * k + (n - k) * k * k   # LAPACK DGETRF (equals 2n^3/3 if square)
     stream = torch.cuda.current_stream()
 
+    pairs = bool(w.get("pairs"))
+
     def step():
         dA.copy_(dA0)
-        tqr.tqr_lu_factor(dA, nb, ib, L, piv)
+        tqr.tqr_lu_factor(dA, nb, ib, L, piv, pairs=pairs)
 
     for _ in range(args.warmup):
         step()
@@ -705,7 +708,7 @@ def run_lu(args, w):
         for it in range(args.warmup + args.steps):
             np.copyto(hA, A)
             t0 = time.perf_counter()
-            tqr.tqr_lu_factor(hA, nb, ib, hL, hp)
+            tqr.tqr_lu_factor(hA, nb, ib, hL, hp, pairs=pairs)
             if it >= args.warmup:
                 ts.append(time.perf_counter() - t0)
         sec = statistics.mean(ts)
@@ -723,8 +726,9 @@ def run_lu(args, w):
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
             "data": "synthetic: N(0,1) entries, NumPy PCG64 seed 0",
-            "config": {"workload": "tiled LU (pairwise pivoting) %dx%d FP64, N(0,1) seed 0, nb=%d ib=%d"
-                                   % (m, n, nb, ib), "m": m, "n": n, "nb": nb, "ib": ib,
+            "config": {"workload": "tiled LU (pairwise pivoting) %dx%d FP64, N(0,1) seed 0, nb=%d ib=%d%s"
+                                   % (m, n, nb, ib, ", 2b x b bottoms" if pairs else ""),
+                       "m": m, "n": n, "nb": nb, "ib": ib,
                        "l2": "input 8*m*n bytes > 129 MB L2, restored from a device copy each step"},
             "roofline": {"bound": "alu", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                          "frac": achieved / peak, "traffic": measured_traffic(args.workload),

@@ -243,10 +243,22 @@ int tqr_orgqr(int64_t m, int64_t n, const double* A, int64_t lda, int nb, int ib
  * device status (TQR_ERR_TIMEOUT).
  */
 size_t tqr_lu_piv_size(int64_t m, int64_t n, int nb);
+/*
+ * tqr_lu_factor_pairs / tqr_lu_solve_pairs: the same with 2b x b bottoms (as
+ * tqr_factor_pairs): the rows below each diagonal tile are taken in pairs, so
+ * each TSTRF pivots row c of U_kk against 2b rows (a pair's interchanges
+ * index its 2b rows, 0 .. 2b-1) and each SSSSM updates the top tile with a
+ * 2b-row bottom.  Arguments, sizes and errors as tqr_lu_factor /
+ * tqr_lu_solve; the factors of one variant are solved by the same variant.
+ */
 int tqr_lu_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* L,
                   int32_t* piv, void* stream);
 int tqr_lu_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
                  const double* L, const int32_t* piv, double* B, int64_t ldb, void* stream);
+int tqr_lu_factor_pairs(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* L,
+                        int32_t* piv, void* stream);
+int tqr_lu_solve_pairs(int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib,
+                       const double* L, const int32_t* piv, double* B, int64_t ldb, void* stream);
 
 /*
  * Least squares  min ||A x - b||_2  for full-rank A, m >= n, through the

@@ -26,7 +26,8 @@ extern "C" {
  *                     SSSSM kinds 13-16, D must be 0); add 32 to modes 0-4
  *                     for 2b x b bottoms (pairs of tile rows below the
  *                     diagonal: TSQRT2 / SSRFB2 / SSRFB2_N kinds 17-19 with
- *                     l = the group's row count, D must be 0)
+ *                     l = the group's row count, D must be 0; with 16 as
+ *                     well: the LU's TSTRF2 / SSSSM2, kinds 20-21)
  *   m, n     (args 2, 3), nb, ib (args 4, 5) as for tqr_factor
  *   cs       (arg 6)  slab width (columns) of the column-slab tasks; must
  *                     divide nb

@@ -20,7 +20,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   mode &= ~48;
   if (mode < 0 || mode > M_FORM_Q) return -1;
   if (lu && mode != M_FACTOR && mode != M_APPLY_QT && mode != M_TRSM) return -1;
-  if (pair && (lu || mode == M_FORM_Q)) return -1;
+  if (pair && mode == M_FORM_Q) return -1;
   if ((lu || pair) && D > 0) return -9;
   if (m < 1) return -2;
   if (n < 1) return -3;

@@ -1301,13 +1301,14 @@ __device__ void exec_gessm(Ctx<real>& cx, const Inst& I, int k, int j, int s) {
   __syncthreads();
 }
 
-// TSTRF(k, i): pairwise-pivoted LU of [U_kk; A_ik] in ib blocks.  Writes
-// U_kk's upper triangle, the multipliers in (i, k), the pivots and L11^-1.
+// TSTRF(k, i): pairwise-pivoted LU of [U_kk; A_ik] in ib blocks; with
+// rows = 2 the bottom is the 2b x b block of tiles (i, k), (i+1, k) and the
+// interchanges index its 2b rows.  Writes U_kk's upper triangle, the
+// multipliers in the bottom tiles, the pivots and L11^-1 under row i.
 template <typename real>
-__device__ void exec_tstrf(Ctx<real>& cx, const Inst& I, int k, int i) {
-  const int nb = I.nb, ib = I.ib, cs = I.cs;
+__device__ void exec_tstrf(Ctx<real>& cx, const Inst& I, int k, int i, int rows = 1) {
+  const int nb = I.nb, ib = I.ib, cs = I.cs, nv = rows * nb;
   real* Ut = tile_ptr<real>(I, k, k);
-  real* Ai = tile_ptr<real>(I, i, k);
   real* Lg = t_ptr<real>(I, i, k);
   int32_t* pg = piv_ptr<real>(I, i, k);
   int* pv = reinterpret_cast<int*>(cx.red + 2 * kThreads);
@@ -1317,14 +1318,16 @@ __device__ void exec_tstrf(Ctx<real>& cx, const Inst& I, int k, int i) {
       const int r = e % ib, c = e / ib;
       Rb[r + c * ib] = (r <= c) ? ldg_cg(Ut + (l0 + r) + static_cast<long long>(l0 + c) * nb) : real(0);
     }
-    bulk_cols(cx, cx.P, cx.ldP, Ai + static_cast<long long>(l0) * nb, nb, nb, ib);
+    for (int a = 0; a < rows; ++a)
+      bulk_cols(cx, cx.P + a * nb, cx.ldP, tile_ptr<real>(I, i + a, k) + static_cast<long long>(l0) * nb, nb, nb, ib);
     __syncthreads();
-    panel_tslu<real>(Rb, cx.P, cx.ldP, nb, ib, pv);
+    panel_tslu<real>(Rb, cx.P, cx.ldP, nv, ib, pv);
     for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
       const int r = e % ib, c = e / ib;
       if (r <= c) Ut[(l0 + r) + static_cast<long long>(l0 + c) * nb] = Rb[r + c * ib];
     }
-    store_block(Ai + static_cast<long long>(l0) * nb, nb, cx.P, cx.ldP, nb, ib);
+    for (int a = 0; a < rows; ++a)
+      store_block(tile_ptr<real>(I, i + a, k) + static_cast<long long>(l0) * nb, nb, cx.P + a * nb, cx.ldP, nb, ib);
     if (threadIdx.x < ib) pg[l0 + threadIdx.x] = pv[threadIdx.x];
     unit_lower_inverse_t<real>(Rb, ib, ib, cx.T, cx.ldT);
     __syncthreads();
@@ -1332,46 +1335,47 @@ __device__ void exec_tstrf(Ctx<real>& cx, const Inst& I, int k, int i) {
     for (int c0 = l0 + ib; c0 < nb; c0 += cs) {
       const int w = nb - c0 < cs ? nb - c0 : cs;
       load_block(cx.Top, ib, Ut + l0 + static_cast<long long>(c0) * nb, nb, ib, w);
-      bulk_cols(cx, cx.S, cx.ldS, Ai + static_cast<long long>(c0) * nb, nb, nb, w);
+      for (int a = 0; a < rows; ++a)
+        bulk_cols(cx, cx.S + a * nb, cx.ldS, tile_ptr<real>(I, i + a, k) + static_cast<long long>(c0) * nb, nb, nb, w);
       __syncthreads();
-      swap_rows_pair<real>(cx.Top, ib, cx.S, cx.ldS, nb, w, pv, ib);
+      swap_rows_pair<real>(cx.Top, ib, cx.S, cx.ldS, nv, w, pv, ib);
       __syncthreads();
-      apply_block_lu<real>(cx.P, cx.ldP, nb, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W);
+      apply_block_lu<real>(cx.P, cx.ldP, nv, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W);
       store_block(Ut + l0 + static_cast<long long>(c0) * nb, nb, cx.Top, ib, ib, w);
-      store_block(Ai + static_cast<long long>(c0) * nb, nb, cx.S, cx.ldS, nb, w);
+      for (int a = 0; a < rows; ++a)
+        store_block(tile_ptr<real>(I, i + a, k) + static_cast<long long>(c0) * nb, nb, cx.S + a * nb, cx.ldS, nb, w);
       __syncthreads();
     }
     __syncthreads();
   }
 }
 
-// SSSSM(k, i, j, s): slab s of [(k, j); (i, j)] <- TSTRF(k, i)'s
+// SSSSM(k, i, j, s): slab s of [(k, j); (i .. i+rows-1, j)] <- TSTRF(k, i)'s
 // transformations applied to it.
 template <typename real>
-__device__ void exec_ssssm(Ctx<real>& cx, const Inst& I, int k, int i, int j, int s) {
-  const int nb = I.nb, ib = I.ib;
-  const real* Lb = tile_ptr<real>(I, i, k);
+__device__ void exec_ssssm(Ctx<real>& cx, const Inst& I, int k, int i, int j, int s, int rows = 1) {
+  const int nb = I.nb, ib = I.ib, nv = rows * nb;
   const real* Lg = t_ptr<real>(I, i, k);
   const int32_t* pg = piv_ptr<real>(I, i, k);
   int* pv = reinterpret_cast<int*>(cx.red + 2 * kThreads);
   const long long soff = static_cast<long long>(s) * I.cs * nb;
   real* Ct = tile_ptr<real>(I, k, j) + soff;
-  real* Cb = tile_ptr<real>(I, i, j) + soff;
   const int w = slab_width(I, j, s);
-  bulk_cols(cx, cx.S, cx.ldS, Cb, nb, nb, w);
+  for (int a = 0; a < rows; ++a) bulk_cols(cx, cx.S + a * nb, cx.ldS, tile_ptr<real>(I, i + a, j) + soff, nb, nb, w);
   for (int l0 = 0; l0 < nb; l0 += ib) {
     load_block(cx.T, cx.ldT, Lg + static_cast<long long>(l0) * ib, ib, ib, ib);
     load_block(cx.Top, ib, Ct + l0, nb, ib, w);
     if (threadIdx.x < ib) pv[threadIdx.x] = ldg_cg(pg + l0 + threadIdx.x);
-    bulk_cols(cx, cx.P, cx.ldP, Lb + static_cast<long long>(l0) * nb, nb, nb, ib);
+    for (int a = 0; a < rows; ++a)
+      bulk_cols(cx, cx.P + a * nb, cx.ldP, tile_ptr<real>(I, i + a, k) + static_cast<long long>(l0) * nb, nb, nb, ib);
     __syncthreads();
-    swap_rows_pair<real>(cx.Top, ib, cx.S, cx.ldS, nb, w, pv, ib);
+    swap_rows_pair<real>(cx.Top, ib, cx.S, cx.ldS, nv, w, pv, ib);
     __syncthreads();
-    apply_block_lu<real>(cx.P, cx.ldP, nb, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W);
+    apply_block_lu<real>(cx.P, cx.ldP, nv, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W);
     store_block(Ct + l0, nb, cx.Top, ib, ib, w);
     __syncthreads();
   }
-  store_block(Cb, nb, cx.S, cx.ldS, nb, w);
+  for (int a = 0; a < rows; ++a) store_block(tile_ptr<real>(I, i + a, j) + soff, nb, cx.S + a * nb, cx.ldS, nb, w);
   __syncthreads();
 }
 
@@ -1465,7 +1469,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
           s_task = tasks[t];
           s_inst = insts[s_task.inst];
           cx.task = t;
-          go = wait_deps<real, V == KV_PAIR>(cx, s_inst, s_task) ? 1 : 0;
+          go = wait_deps<real, V != KV_QR>(cx, s_inst, s_task) ? 1 : 0;
         }
       }
       s_go = go;
@@ -1513,6 +1517,8 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
         case K_GESSM: exec_gessm(cx, I, t.k, t.j, t.s); break;
         case K_TSTRF: exec_tstrf(cx, I, t.k, t.i); break;
         case K_SSSSM: exec_ssssm(cx, I, t.k, t.i, t.j, t.s); break;
+        case K_TSTRF2: exec_tstrf(cx, I, t.k, t.i, t.l); break;
+        case K_SSSSM2: exec_ssssm(cx, I, t.k, t.i, t.j, t.s, t.l); break;
         case K_TRSM_UPD: exec_trsm_upd(cx, I, t.k, t.l, t.j, t.s); break;
         case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
         default: fail_kind(cx); break;
@@ -1534,7 +1540,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
       default: fail_kind(cx); break;
     }
     __syncthreads();
-    if (threadIdx.x == 0) signal_done<V == KV_PAIR>(I, t);
+    if (threadIdx.x == 0) signal_done<V != KV_QR>(I, t);
   }
 }
 

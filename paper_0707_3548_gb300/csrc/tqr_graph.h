@@ -66,7 +66,9 @@ enum Kind : int {
   K_TSQRT2 = 17,
   K_SSRFB2 = 18,
   K_SSRFB2_N = 19,   // (apply Q)
-  K_NKINDS = 20
+  K_TSTRF2 = 20,     // the tiled LU's TSTRF / SSSSM on 2b x b bottoms
+  K_SSSSM2 = 21,
+  K_NKINDS = 22
 };
 
 // Most waits / signals a task has (SSRFB2: 4 waits, 3 signals).
@@ -79,6 +81,8 @@ TQR_HD int qr_kind(int kind) {
     case K_TSQRT2: return K_TSQRT;
     case K_SSRFB2: return K_SSRFB;
     case K_SSRFB2_N: return K_SSRFB_N;
+    case K_TSTRF2: return K_TSQRT;
+    case K_SSSSM2: return K_SSRFB;
     case K_GETRF: return K_GEQRT;
     case K_GESSM: return K_LARFB;
     case K_TSTRF: return K_TSQRT;
@@ -94,6 +98,8 @@ TQR_HD int lu_kind(int kind) {
     case K_LARFB: return K_GESSM;
     case K_TSQRT: return K_TSTRF;
     case K_SSRFB: return K_SSSSM;
+    case K_TSQRT2: return K_TSTRF2;
+    case K_SSRFB2: return K_SSSSM2;
     default: return kind;
   }
 }
@@ -437,8 +443,15 @@ TQR_HD int task_rules_base(const Inst& I, const TaskX& t0, Wait* w, Signal* sg, 
 }
 
 TQR_HD int task_rules(const Inst& I, const TaskX& t0, Wait* w, Signal* sg, int* nsig) {
-  if (I.pair && (t0.kind == K_TSQRT2 || t0.kind == K_SSRFB2 || t0.kind == K_SSRFB2_N || t0.kind == K_LARFB_N))
-    return pair_rules(I, t0, w, sg, nsig);
+  if (I.pair) {
+    // the LU pair kinds share the QR pair kinds' data flow
+    const int k2 = t0.kind == K_TSTRF2 ? K_TSQRT2 : (t0.kind == K_SSSSM2 ? K_SSRFB2 : t0.kind);
+    if (k2 == K_TSQRT2 || k2 == K_SSRFB2 || k2 == K_SSRFB2_N || k2 == K_LARFB_N) {
+      TaskX t = t0;
+      t.kind = k2;
+      return pair_rules(I, t, w, sg, nsig);
+    }
+  }
   return task_rules_base(I, t0, w, sg, nsig);
 }
 

@@ -22,12 +22,13 @@ namespace {
 // the factors of a square n x n matrix and B (n x nrhs) is overwritten with
 // A^-1 B.
 int lu_device(int mode, int64_t m, int64_t n, int64_t nrhs, double* A, int64_t lda, int nb, int ib, double* L,
-              int32_t* piv, double* B, int64_t ldb, cudaStream_t st) {
+              int32_t* piv, double* B, int64_t ldb, int pair, cudaStream_t st) {
   int cs, occ, smem;
-  if (!choose_shape(nb, ib, sizeof(double), &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
+  if (!choose_shape(nb, ib, sizeof(double), &cs, &occ, &smem, pair ? 2 * nb : 0)) return TQR_ERR_UNSUPPORTED;
   const bool solve = mode == M_APPLY_QT;
   Inst I = make_inst(mode, m, n, nb, ib, cs, solve ? static_cast<int>(nrhs) : 0, solve ? 1 : 0);
   I.lu = 1;
+  I.pair = pair;
   const WsLayout W = ws_layout(I, sizeof(double), false);
   char* ws = nullptr;
   if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
@@ -58,7 +59,7 @@ int lu_device(int mode, int64_t m, int64_t n, int64_t nrhs, double* A, int64_t l
 
 // Host operands: staged through device copies; synchronizes the stream.
 int lu_staged(int mode, int64_t m, int64_t n, int64_t nrhs, double* A, int64_t lda, int nb, int ib, double* L,
-              int32_t* piv, double* B, int64_t ldb, cudaStream_t st) {
+              int32_t* piv, double* B, int64_t ldb, int pair, cudaStream_t st) {
   const bool solve = mode == M_APPLY_QT;
   const size_t lbytes = tqr_t_size(m, n, nb, ib), pbytes = tqr_lu_piv_size(m, n, nb);
   double *dA = nullptr, *dL = nullptr, *dB = nullptr;
@@ -83,7 +84,11 @@ int lu_staged(int mode, int64_t m, int64_t n, int64_t nrhs, double* A, int64_t l
        cudaMemcpy2DAsync(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
                          cudaMemcpyHostToDevice, st) != cudaSuccess))
     status = TQR_ERR_CUDA;
-  if (status == TQR_OK) status = lu_device(mode, m, n, nrhs, dA, m, nb, ib, dL, dP, dB, m, st);
+  // slots a pair factorization leaves unused come back as zeros
+  if (status == TQR_OK && !solve &&
+      (cudaMemsetAsync(dL, 0, lbytes, st) != cudaSuccess || cudaMemsetAsync(dP, 0, pbytes, st) != cudaSuccess))
+    status = TQR_ERR_CUDA;
+  if (status == TQR_OK) status = lu_device(mode, m, n, nrhs, dA, m, nb, ib, dL, dP, dB, m, pair, st);
   if (status == TQR_OK) {
     cudaError_t e = cudaSuccess;
     if (solve) {
@@ -119,8 +124,8 @@ size_t tqr_lu_piv_size(int64_t m, int64_t n, int nb) {
   return sizeof(int32_t) * static_cast<size_t>(piv_offset(p, nb, kt, kt));
 }
 
-int tqr_lu_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* L, int32_t* piv,
-                  void* stream) {
+static int lu_factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* L, int32_t* piv,
+                            int pair, void* stream) {
   if (m < 0) return -1;
   if (n < 0) return -2;
   if (m > (1LL << 30) || n > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
@@ -135,12 +140,12 @@ int tqr_lu_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, 
   if (ptr_kind(L) != ka) return -7;
   if (ptr_kind(piv) != ka) return -8;
   cudaStream_t st = static_cast<cudaStream_t>(stream);
-  if (ka == PTR_DEVICE) return lu_device(M_FACTOR, m, n, 0, A, lda, nb, ib, L, piv, nullptr, 0, st);
-  return lu_staged(M_FACTOR, m, n, 0, A, lda, nb, ib, L, piv, nullptr, 0, st);
+  if (ka == PTR_DEVICE) return lu_device(M_FACTOR, m, n, 0, A, lda, nb, ib, L, piv, nullptr, 0, pair, st);
+  return lu_staged(M_FACTOR, m, n, 0, A, lda, nb, ib, L, piv, nullptr, 0, pair, st);
 }
 
-int tqr_lu_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib, const double* L,
-                 const int32_t* piv, double* B, int64_t ldb, void* stream) {
+static int lu_solve_common(int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib, const double* L,
+                           const int32_t* piv, double* B, int64_t ldb, int pair, void* stream) {
   if (n < 0) return -1;
   if (nrhs < 0) return -2;
   if (n > (1LL << 30) || nrhs > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
@@ -161,8 +166,28 @@ int tqr_lu_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, 
   double* a = const_cast<double*>(A);
   double* l = const_cast<double*>(L);
   int32_t* pv = const_cast<int32_t*>(piv);
-  if (ka == PTR_DEVICE) return lu_device(M_APPLY_QT, n, n, nrhs, a, lda, nb, ib, l, pv, B, ldb, st);
-  return lu_staged(M_APPLY_QT, n, n, nrhs, a, lda, nb, ib, l, pv, B, ldb, st);
+  if (ka == PTR_DEVICE) return lu_device(M_APPLY_QT, n, n, nrhs, a, lda, nb, ib, l, pv, B, ldb, pair, st);
+  return lu_staged(M_APPLY_QT, n, n, nrhs, a, lda, nb, ib, l, pv, B, ldb, pair, st);
+}
+
+int tqr_lu_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* L, int32_t* piv,
+                  void* stream) {
+  return lu_factor_common(m, n, A, lda, nb, ib, L, piv, 0, stream);
+}
+
+int tqr_lu_solve(int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib, const double* L,
+                 const int32_t* piv, double* B, int64_t ldb, void* stream) {
+  return lu_solve_common(n, nrhs, A, lda, nb, ib, L, piv, B, ldb, 0, stream);
+}
+
+int tqr_lu_factor_pairs(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* L, int32_t* piv,
+                        void* stream) {
+  return lu_factor_common(m, n, A, lda, nb, ib, L, piv, 1, stream);
+}
+
+int tqr_lu_solve_pairs(int64_t n, int64_t nrhs, const double* A, int64_t lda, int nb, int ib, const double* L,
+                       const int32_t* piv, double* B, int64_t ldb, void* stream) {
+  return lu_solve_common(n, nrhs, A, lda, nb, ib, L, piv, B, ldb, 1, stream);
 }
 
 }  // extern "C"

@@ -344,6 +344,14 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
       f = (nb / ib) * (4.0 * t.l * nb * ib * w + ib * ib * w);
       lat = (nb / ib) * blk_lat;
       break;
+    case K_TSTRF2:
+      f = t.l * nb * nb * nb;
+      lat = 2.0 * nb * col_lat;
+      break;
+    case K_SSSSM2:
+      f = (nb / ib) * (2.0 * t.l * nb * ib * w + ib * ib * w);
+      lat = (nb / ib) * blk_lat;
+      break;
     case K_GETRF:
       f = 2.0 * nb * nb * nb / 3.0;
       lat = 2.0 * nb * col_lat;

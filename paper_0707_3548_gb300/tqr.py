@@ -88,6 +88,8 @@ SIGNATURES = {
     "tqr_debug_critical_path": (_int, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _vp]),
     "tqr_lu_factor": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp]),
     "tqr_lu_solve": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp, _i64, _vp]),
+    "tqr_lu_factor_pairs": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp]),
+    "tqr_lu_solve_pairs": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _vp, _i64, _vp]),
     "tqr_stream_status": (_int, [_vp]),
     "tqr_set_wait_limit_ms": (_i64, [_i64]),
     "tqr_debug_plan": (_i64, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _int, _int, _vp, _i64, _vp]),
@@ -293,9 +295,10 @@ def tqr_lu_piv_size(m, n, nb):
     return lib().tqr_lu_piv_size(m, n, nb)
 
 
-def tqr_lu_factor(A, nb, ib, L=None, piv=None, stream=None):
+def tqr_lu_factor(A, nb, ib, L=None, piv=None, stream=None, pairs=False):
     """Tiled LU (pairwise pivoting) of column-major A in place; returns
-    (L, piv), allocated on A's device (or host) if not given."""
+    (L, piv), allocated on A's device (or host) if not given.  pairs: 2b x b
+    bottoms (tqr_lu_factor_pairs)."""
     pa, m, n, lda, cuda = _mat(A, "A")
     if L is None:
         L = new_t(m, n, nb, ib, A)
@@ -303,16 +306,17 @@ def tqr_lu_factor(A, nb, ib, L=None, piv=None, stream=None):
         cnt = tqr_lu_piv_size(m, n, nb) // 4
         piv = np.zeros(cnt, dtype=np.int32) if isinstance(A, np.ndarray) else \
             _torch().zeros(cnt, dtype=_torch().int32, device=A.device)
-    _check("tqr_lu_factor", lib().tqr_lu_factor(m, n, pa, lda, nb, ib, _ptr(L), _ptr(piv), _stream(cuda, stream)))
+    fn = "tqr_lu_factor_pairs" if pairs else "tqr_lu_factor"
+    _check(fn, getattr(lib(), fn)(m, n, pa, lda, nb, ib, _ptr(L), _ptr(piv), _stream(cuda, stream)))
     return L, piv
 
 
-def tqr_lu_solve(A, nb, ib, L, piv, B, stream=None):
+def tqr_lu_solve(A, nb, ib, L, piv, B, stream=None, pairs=False):
     """B <- A^-1 B in place from tqr_lu_factor's (A, L, piv); returns B."""
     pa, n, n2, lda, cuda = _mat(A, "A")
     pb, nb_rows, nrhs, ldb, _ = _mat(B, "B")
-    _check("tqr_lu_solve", lib().tqr_lu_solve(n, nrhs, pa, lda, nb, ib, _ptr(L), _ptr(piv), pb, ldb,
-                                              _stream(cuda, stream)))
+    fn = "tqr_lu_solve_pairs" if pairs else "tqr_lu_solve"
+    _check(fn, getattr(lib(), fn)(n, nrhs, pa, lda, nb, ib, _ptr(L), _ptr(piv), pb, ldb, _stream(cuda, stream)))
     return B
 
 

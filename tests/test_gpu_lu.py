@@ -157,3 +157,50 @@ def test_full_size_sampled_lu():
     tqr.tqr_lu_solve(dA, nb, ib, L, piv, b)
     res = torch.linalg.norm(dA0 @ b - r0).item()
     assert res / (torch.linalg.norm(dA0).item() * torch.linalg.norm(b).item()) <= 1e3 * n * U53
+
+
+# 2b x b bottoms -------------------------------------------------------------
+
+@pytest.mark.parametrize("m,n,nb,ib", [(512, 512, 128, 32), (700, 500, 128, 32), (1000, 1000, 128, 16),
+                                       (300, 600, 64, 16), (33, 17, 8, 4)])
+def test_lu_pairs_match_oracle(m, n, nb, ib):
+    torch_cuda()
+    A = inputs.normal_matrix(m, n, 301 + m + n)
+    dA = to_dev(A)
+    L, piv = tqr.tqr_lu_factor(dA, nb, ib, pairs=True)
+    f = LU.tiled_lu_pairs(A, nb, ib)
+    ref = f.Ap[:m, :n]
+    assert np.max(np.abs(to_host(dA) - ref)) <= 1e-10 * max(1.0, np.abs(ref).max())
+    pv = piv.cpu().numpy()
+    slots = _slots(m, n, nb)
+    for key, p_ref in f.piv.items():
+        idx = slots.index(key)
+        assert np.array_equal(pv[idx * nb:(idx + 1) * nb], p_ref), key
+
+
+@pytest.mark.parametrize("n,nb,ib,nrhs", [(512, 128, 32, 3), (700, 64, 16, 40)])
+def test_lu_pairs_solve(n, nb, ib, nrhs):
+    A = inputs.normal_matrix(n, n, 311 + n)
+    B = inputs.normal_matrix(n, nrhs, 312)
+    dA = to_dev(A)
+    L, piv = tqr.tqr_lu_factor(dA, nb, ib, pairs=True)
+    dB = to_dev(B)
+    tqr.tqr_lu_solve(dA, nb, ib, L, piv, dB, pairs=True)
+    X = to_host(dB)
+    ref = LU.pairs_lu_solve(LU.tiled_lu_pairs(A, nb, ib), B)
+    assert np.max(np.abs(X - ref)) <= 1e-12 * np.linalg.cond(A) * max(1.0, np.abs(ref).max())
+    assert np.linalg.norm(A @ X - B) / (np.linalg.norm(A) * np.linalg.norm(X)) <= 1e3 * n * U53
+
+
+def test_lu_pairs_host_path_and_plan_separation():
+    A = inputs.normal_matrix(400, 400, 313)
+    dA = to_dev(A)
+    L, piv = tqr.tqr_lu_factor(dA, 64, 16, pairs=True)
+    hA = np.array(A, order="F", copy=True)
+    hL, hp = tqr.tqr_lu_factor(hA, 64, 16, pairs=True)
+    assert np.array_equal(hA, to_host(dA)) and np.array_equal(hp, piv.cpu().numpy())
+    # the flat LU of the same shape right after must run its own task list
+    dA2 = to_dev(A)
+    tqr.tqr_lu_factor(dA2, 64, 16)
+    f = LU.tiled_lu(A, 64, 16)
+    assert np.max(np.abs(to_host(dA2) - f.Ap[:400, :400])) <= 1e-10 * np.abs(f.Ap).max()

@@ -142,3 +142,61 @@ def test_lu_plan_rejects_tree_and_other_modes():
         tqr.tqr_debug_plan(LUF | FACTOR, 64, 64, 16, 4, 8, 0, 0, 7, -1, D=2)
     with pytest.raises(RuntimeError):
         tqr.tqr_debug_plan(LUF | 2, 64, 64, 16, 4, 8, 4, 0, 7, -1)
+
+
+# 2b x b bottoms -------------------------------------------------------------
+PAIR = 32
+TSTRF2, SSSSM2 = 20, 21
+
+
+def execute_pairs(g, task):
+    kind, s, _, k, h, j, l = (int(v) for v in task[:7])
+    if kind not in (TSTRF2, SSSSM2):
+        return execute(g, task)
+    ib = g.ib
+    rows = list(range(h, h + l))
+    if kind == TSTRF2:
+        Ut, Lb, L1, pv = LU.tstrf(g.tile(k, k), np.vstack([g.tile(r, k) for r in rows]), ib)
+        g.tile(k, k)[:] = np.tril(g.tile(k, k), -1) + Ut
+        for a, r in enumerate(rows):
+            g.tile(r, k)[:] = Lb[a * g.nb:(a + 1) * g.nb]
+        g.piv[(h, k)] = pv
+        g.L1[(h, k)] = L1
+    else:
+        top = g.slab(k, j, s)
+        bots = [g.slab(r, j, s) for r in rows]
+        Lb = np.vstack([g.tile(r, k) for r in rows])
+        t2, b2 = LU.ssssm(top, np.vstack(bots), Lb, g.L1[(h, k)], g.piv[(h, k)], ib)
+        top[:] = t2
+        for a, b in enumerate(bots):
+            b[:] = b2[a * g.nb:(a + 1) * g.nb]
+
+
+@pytest.mark.parametrize("m,n,nb,ib,cs", SHAPES)
+def test_lu_pair_factor_plan_replays_the_oracle(m, n, nb, ib, cs):
+    A = inputs.normal_matrix(m, n, 3 * m + n)
+    f = LU.tiled_lu_pairs(A, nb, ib)
+    for seed in (None, 6):
+        g = LuGrid(m, n, nb, ib, cs)
+        g.A[:m, :n] = A
+        plan, _ = tqr.tqr_debug_plan(PAIR | LUF | FACTOR, m, n, nb, ib, cs, 0, 0, 7, -1)
+        check_order_satisfies_waits(PAIR | LUF | FACTOR, g, plan)
+        kinds = {int(t[0]) for t in plan}
+        assert kinds <= {13, 14, TSTRF2, SSSSM2} and (TSTRF2 in kinds or g.p == 1)
+        for t in (plan if seed is None else random_valid_order(PAIR | LUF | FACTOR, g, plan, seed)):
+            execute_pairs(g, t)
+        assert np.array_equal(g.A, f.Ap)
+
+
+@pytest.mark.parametrize("n,nb,ib,cs,nrhs", [(64, 16, 4, 8, 3), (45, 16, 8, 8, 17)])
+def test_lu_pair_factor_and_solve_in_one_plan(n, nb, ib, cs, nrhs):
+    A = inputs.normal_matrix(n, n, 24)
+    B = inputs.normal_matrix(n, nrhs, 25)
+    g = LuGrid(n, n, nb, ib, cs, nrhs)
+    g.A[:n, :n] = A
+    g.B[:n, :nrhs] = B
+    plan, _ = tqr.tqr_debug_plan(PAIR | LUF | FACTOR, n, n, nb, ib, cs, nrhs, 1, 7, -1)
+    check_order_satisfies_waits(PAIR | LUF | FACTOR, g, plan)
+    for t in random_valid_order(PAIR | LUF | FACTOR, g, plan, 2):
+        execute_pairs(g, t)
+    assert np.allclose(g.B[:n, :nrhs], np.linalg.solve(A, B), atol=1e-9 * np.linalg.cond(A))
