@@ -1509,6 +1509,8 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
         case K_SSRFB2_N: exec_ssrfb2(cx, I, t.k, t.i, t.l, t.j, t.s, false); break;
         case K_TRSM_UPD: exec_trsm_upd(cx, I, t.k, t.l, t.j, t.s); break;
         case K_TRSM_SOLVE: exec_trsm_solve(cx, I, t.k, t.j, t.s); break;
+        case K_TRSMT_UPD: exec_trsmt_upd(cx, I, t.k, t.l, t.j, t.s); break;
+        case K_TRSMT_SOLVE: exec_trsmt_solve(cx, I, t.k, t.j, t.s); break;
         default: fail_kind(cx); break;
       }
     } else if constexpr (V == KV_LU) {
