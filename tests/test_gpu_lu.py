@@ -204,3 +204,15 @@ def test_lu_pairs_host_path_and_plan_separation():
     tqr.tqr_lu_factor(dA2, 64, 16)
     f = LU.tiled_lu(A, 64, 16)
     assert np.max(np.abs(to_host(dA2) - f.Ap[:400, :400])) <= 1e-10 * np.abs(f.Ap).max()
+
+
+@pytest.mark.parametrize("m,n,nb,ib", [(1, 1, 8, 8), (5, 3, 8, 4), (8, 8, 8, 2), (17, 40, 8, 4), (24, 1, 8, 8),
+                                       (40, 17, 8, 8)])
+@pytest.mark.parametrize("pairs", [False, True])
+def test_lu_tiny_and_degenerate_shapes(m, n, nb, ib, pairs):
+    torch_cuda()
+    A = inputs.uniform_matrix(m, n, 321 + m + n)
+    dA = to_dev(A)
+    tqr.tqr_lu_factor(dA, nb, ib, pairs=pairs)
+    f = LU.tiled_lu_pairs(A, nb, ib) if pairs else LU.tiled_lu(A, nb, ib)
+    assert np.max(np.abs(to_host(dA) - f.Ap[:m, :n])) <= 1e-11 * max(1.0, np.abs(f.Ap).max())

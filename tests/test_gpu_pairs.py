@@ -110,3 +110,18 @@ def test_pair_and_flat_plans_do_not_mix():
         dA = to_dev(A)
         tqr.tqr_factor(dA, 128, 32)
         assert np.max(np.abs(to_host(dA) - f_flat.F)) <= 1e-11 * np.abs(f_flat.F).max()
+
+
+@pytest.mark.parametrize("m,n,nb,ib", [(1, 1, 8, 8), (5, 3, 8, 4), (8, 8, 8, 2), (17, 40, 8, 4), (24, 1, 8, 8),
+                                       (40, 17, 8, 8), (100, 7, 16, 4)])
+def test_pair_tiny_and_degenerate_shapes(m, n, nb, ib):
+    torch_cuda()
+    A = inputs.uniform_matrix(m, n, 221 + m + n)
+    dA = to_dev(A)
+    T = tqr.tqr_factor_pairs(dA, nb, ib)
+    f = TL.tiled_qr_pairs(A, nb, ib)
+    assert np.max(np.abs(to_host(dA) - f.F)) <= 1e-12 * max(1.0, np.abs(f.F).max())
+    B = inputs.uniform_matrix(m, 2, 222)
+    dB = to_dev(B)
+    tqr.tqr_apply_qt_pairs("T", dA, nb, ib, T, dB)
+    assert np.max(np.abs(to_host(dB) - TL.pairs_apply_qt(f, B))) <= 1e-12 * max(1.0, np.abs(B).max())
