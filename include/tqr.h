@@ -190,11 +190,11 @@ int tqr_apply_qt_pairs(char trans, int64_t m, int64_t n, int64_t nrhs, const dou
  * tqr_orgqr(m, n, A, lda, nb, ib, D, T, ncols, Q, ldq, stream)
  *   Writes the first ncols (0 <= ncols <= m, arg 9) columns of Q to Q (arg 10,
  *   m x ncols, ldq >= max(1, m), arg 11); ncols = n gives the thin Q of
- *   A = Q R.  Other arguments as for tqr_ormqr (A is arg 3, T arg 8).  With
- *   the flat panel (D = 0) step k of the reverse accumulation skips the
- *   identity's tile columns < k, which its reflectors cannot reach (they
- *   touch rows >= k*nb only), so the work is that of the factorization's
- *   updates, not of a full m x ncols product.
+ *   A = Q R.  Other arguments as for tqr_ormqr (A is arg 3, T arg 8).  Step
+ *   k of the reverse accumulation skips the identity's tile columns < k,
+ *   which its reflectors (flat or tree) cannot reach -- they touch rows
+ *   >= k*nb only -- so the work is that of the factorization's updates, not
+ *   of a full m x ncols product.
  *
  * Both calls: A, T, C / Q all on the device (asynchronous on stream) or all
  * on the host (staged through device copies; the call synchronizes).  They

@@ -21,7 +21,7 @@ extern "C" {
  *                     4 forward substitution with R^T, 5 apply Q to the
  *                     leading columns of the identity (explicit Q; step k
  *                     skips right-hand-side tile columns < k; flat panel
- *                     only, D must be 0); add 16 to modes 0, 1 and 3 for
+ *                     or tree); add 16 to modes 0, 1 and 3 for
  *                     the tiled LU's task lists (GETRF / GESSM / TSTRF /
  *                     SSSSM kinds 13-16, D must be 0); add 32 to modes 0-4
  *                     for 2b x b bottoms (pairs of tile rows below the

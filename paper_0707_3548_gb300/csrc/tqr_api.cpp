@@ -890,9 +890,8 @@ int tqr_orgqr(int64_t m, int64_t n, const double* A, int64_t lda, int nb, int ib
   if (n > 0 && A == nullptr) return -3;
   if (n > 0 && T == nullptr) return -8;
   if (Q == nullptr) return -10;
-  // flat panel: identity columns skip the steps that cannot touch them
-  return apply_staged(D == 0 ? M_FORM_Q : M_APPLY_Q, RHS_IDENTITY, m, n, ncols, A, lda, nb, ib, D, 0, T, Q, ldq, 3, 8,
-                      10, stream);
+  // identity columns skip the steps that cannot touch them
+  return apply_staged(M_FORM_Q, RHS_IDENTITY, m, n, ncols, A, lda, nb, ib, D, 0, T, Q, ldq, 3, 8, 10, stream);
 }
 
 int tqr_factor_pairs(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib, double* T, void* stream) {

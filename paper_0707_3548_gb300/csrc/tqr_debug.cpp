@@ -29,7 +29,7 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
   if (nrhs < 0) return -7;
   if (mode != 0 && nrhs == 0) return -7;
   if (trsm && (nrhs == 0 || m < n || (mode != 0 && mode != 1))) return -8;
-  if (D < 0 || (D > 0 && mode == M_FORM_Q)) return -9;
+  if (D < 0) return -9;
   if (workers < 1) return -10;
   if (policy < -1 || policy > 2) return -11;
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);

@@ -208,12 +208,22 @@ TQR_HD int tree_rules(const Inst& I, const TaskX& t, Wait* w, Signal* sg, int* n
   const int kt = I.kt, NS = I.NS;
   const int k = t.k, i = t.i, j = t.j, s = t.s, l = t.l;
   const bool a_final = I.mode != M_FACTOR;
-  const bool rev = I.mode == M_APPLY_Q;
+  const bool rev = I.mode == M_APPLY_Q || I.mode == M_FORM_Q;
   int nw = 0;
   *nsig = 0;
+  // reverse modes replay the writers backwards: the version is the number of
+  // writes after this one in forward order.  M_FORM_Q only runs steps <= jb
+  // on right-hand-side tile column jb = j - q, so a tile's forward writes end
+  // with step min(jb + 1, kt).
   auto ver = [&](int r, int pos) {
     const int f = tree_base(I, k, r) + pos;
-    return rev ? tree_fin(I, r) - 1 - f : f;
+    if (!rev) return f;
+    int fin = tree_fin(I, r);
+    if (I.mode == M_FORM_Q) {
+      const int last = j - I.q + 1 < kt ? j - I.q + 1 : kt;
+      fin = I.vtab[last * I.p + r];
+    }
+    return fin - 1 - f;
   };
   switch (t.kind) {
     case K_GEQRT:

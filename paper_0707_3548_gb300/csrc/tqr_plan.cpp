@@ -72,12 +72,15 @@ static bool tree_seq(const Inst& I, int x, std::vector<TaskX>& out) {
       for (int k = 0; k < I.kt; ++k) tree_step(I, x, k, false, out);
       if (I.trsm) trsm_tasks(I, x, out);
       return true;
-    case M_APPLY_Q: {
-      // the transposed updates in exactly the reverse order
+    case M_APPLY_Q:
+    case M_FORM_Q: {
+      // the transposed updates in exactly the reverse order; explicit Q
+      // columns skip the steps after their own tile column
       std::vector<TaskX> fw;
       for (int k = 0; k < I.kt; ++k) tree_step(I, x, k, false, fw);
       for (size_t a = fw.size(); a-- > 0;) {
         TaskX t = fw[a];
+        if (I.mode == M_FORM_Q && t.j - I.q < t.k) continue;
         t.kind = t.kind == K_LARFB ? K_LARFB_N : t.kind == K_SSRFB ? K_SSRFB_N : K_TTMQR_N;
         out.push_back(t);
       }

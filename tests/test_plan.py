@@ -266,9 +266,9 @@ def test_form_q_plan_skips_identity_columns(m, n, nb, ib, cs, ncols):
     assert len(plan) < len(full) or g.kt == 1
 
 
-def test_form_q_plan_rejects_tree_panel():
+def test_form_q_plan_rejects_pair_variant():
     with pytest.raises(Exception):
-        tqr.tqr_debug_plan(FORM_Q, 64, 64, 16, 4, 8, 16, 0, 7, -1, D=2)
+        tqr.tqr_debug_plan(32 | FORM_Q, 64, 64, 16, 4, 8, 16, 0, 7, -1)
 
 
 @pytest.mark.parametrize("m,n,nb,ib,cs,nrhs", [(70, 45, 16, 8, 8, 3), (64, 64, 16, 4, 16, 17), (50, 16, 8, 8, 8, 1)])

@@ -28,7 +28,7 @@ def _cases(seed, count):
         D = int(g.integers(1, 5)) if variant == "tree" else 0
         if variant in ("lu", "lupair") and mode not in (FACTOR, APPLY_QT, TRSM):
             continue
-        if mode == FORM_Q and variant != "flat":
+        if mode == FORM_Q and variant not in ("flat", "tree"):
             continue
         trsm = int(g.integers(0, 2)) if mode in (FACTOR, APPLY_QT) and m >= n else 0
         if mode == FACTOR and not trsm:

@@ -187,3 +187,22 @@ def test_tree_shortens_simulated_critical_path_for_tall_skinny():
     tree = tqr.tqr_debug_plan(FACTOR, 65536, 2048, 128, 16, 32, 0, 0, workers=304, D=32)[1]
     assert tree[4] < 0.6 * flat[4]       # critical path
     assert tree[0] < flat[0]             # simulated makespan
+
+
+@pytest.mark.parametrize("m,n,nb,ib,cs,ncols,D", [(160, 48, 16, 4, 8, 48, 1), (150, 40, 16, 8, 8, 150, 3),
+                                                  (96, 96, 16, 4, 16, 96, 2), (200, 60, 16, 8, 16, 37, 4)])
+def test_tree_explicit_q_plan_skips_identity_columns(m, n, nb, ib, cs, ncols, D):
+    A = inputs.normal_matrix(m, n, 5)
+    f = TL.tree_qr(A, nb, ib, D)
+    g = TreeGrid(m, n, nb, ib, cs, ncols)
+    g.A[:] = f.Ap
+    g.T = dict(f.T)
+    g.T2 = dict(f.T2)
+    g.B[:m, :ncols] = np.eye(m, ncols)
+    plan, _ = tqr.tqr_debug_plan(5, m, n, nb, ib, cs, ncols, 0, workers=5, D=D)
+    full, _ = tqr.tqr_debug_plan(APPLY_Q, m, n, nb, ib, cs, ncols, 0, workers=5, D=D)
+    assert len(plan) < len(full) or g.kt == 1
+    check_order(5, g, plan, D)
+    for t in random_order(5, g, plan, D, 2):
+        execute(g, t)
+    assert np.allclose(g.B[:m, :ncols], TL.orgqr(f, ncols), rtol=0, atol=1e-13)
