@@ -437,6 +437,15 @@ int tqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int nb, int
 int tqr_stream_status(void* stream);
 
 /*
+ * Workspaces and staging buffers of the calls come from a stream-ordered pool
+ * per device that keeps freed memory for the next call (so calls do not map
+ * fresh device memory each time).  tqr_release_memory() synchronizes the
+ * devices the library used and returns that cached memory to the driver.
+ * Returns 0 or TQR_ERR_CUDA.
+ */
+int tqr_release_memory(void);
+
+/*
  * Dependency-wait limit of the device scheduler in milliseconds (default
  * 20000, or TQR_WAIT_LIMIT_MS from the environment when the library loads).
  * A wait that exceeds it makes every CTA of that launch stop and the call

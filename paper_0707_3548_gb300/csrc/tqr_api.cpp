@@ -7,6 +7,7 @@
 
 #include <algorithm>
 #include <cstdlib>
+#include <cstring>
 #include <cmath>
 #include <list>
 #include <map>
@@ -116,6 +117,62 @@ Inst make_inst(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs,
   I.mode = mode;
   I.trsm = trsm;
   return I;
+}
+
+// ---------------------------------------------------------------- memory
+// Library workspaces and staging buffers come from a stream-ordered pool per
+// device that keeps freed memory for reuse.  The device's default pool gives
+// freed memory back to the driver at every synchronization, so a call that
+// follows a synchronization (every call on host buffers) would map its
+// gigabytes of workspace afresh.  tqr_release_memory() hands it back.
+static std::mutex g_pool_mu;
+static std::map<int, cudaMemPool_t> g_pools;
+
+static cudaMemPool_t lib_pool(int dev) {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  auto it = g_pools.find(dev);
+  if (it != g_pools.end()) return it->second;
+  cudaMemPoolProps props;
+  std::memset(&props, 0, sizeof(props));
+  props.allocType = cudaMemAllocationTypePinned;
+  props.location.type = cudaMemLocationTypeDevice;
+  props.location.id = dev;
+  cudaMemPool_t pool = nullptr;
+  if (cudaMemPoolCreate(&pool, &props) == cudaSuccess) {
+    uint64_t keep = UINT64_MAX;
+    cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &keep);
+  } else {
+    cudaGetLastError();
+    pool = nullptr;  // the device's default pool then
+  }
+  g_pools[dev] = pool;
+  return pool;
+}
+
+cudaError_t lib_malloc(void** p, size_t bytes, cudaStream_t st) {
+  int dev = 0;
+  cudaGetDevice(&dev);
+  cudaMemPool_t pool = lib_pool(dev);
+  const cudaError_t e = pool ? cudaMallocFromPoolAsync(p, bytes, pool, st) : cudaMallocAsync(p, bytes, st);
+  if (e != cudaSuccess) cudaGetLastError();
+  return e;
+}
+
+int release_memory() {
+  std::lock_guard<std::mutex> lk(g_pool_mu);
+  int cur = 0;
+  cudaGetDevice(&cur);
+  for (auto& kv : g_pools) {
+    if (!kv.second) continue;
+    if (cudaSetDevice(kv.first) != cudaSuccess || cudaDeviceSynchronize() != cudaSuccess ||
+        cudaMemPoolTrimTo(kv.second, 0) != cudaSuccess) {
+      cudaGetLastError();
+      cudaSetDevice(cur);
+      return TQR_ERR_CUDA;
+    }
+  }
+  cudaSetDevice(cur);
+  return TQR_OK;
 }
 
 // ---------------------------------------------------------------- plan cache
@@ -265,7 +322,7 @@ std::shared_ptr<DevPlan> get_plan(const Inst& I, int esize, int ctas_per_sm, int
       plan->grid = std::max(1, std::min(plan->grid, want));
     }
     cudaStream_t ps = plan_stream(dev);
-    if (cudaMallocAsync(reinterpret_cast<void**>(&plan->d_tasks), sizeof(TaskX) * ordered.size(), ps) !=
+    if (lib_malloc(reinterpret_cast<void**>(&plan->d_tasks), sizeof(TaskX) * ordered.size(), ps) !=
         cudaSuccess) {
       cudaGetLastError();
       plan->d_tasks = nullptr;
@@ -518,7 +575,7 @@ int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int
         return TQR_ERR_UNSUPPORTED;
       }
       cudaStream_t ps = plan_stream(dev);
-      if (cudaMallocAsync(reinterpret_cast<void**>(&plan->d_tasks), sizeof(TaskX) * ordered.size(), ps) !=
+      if (lib_malloc(reinterpret_cast<void**>(&plan->d_tasks), sizeof(TaskX) * ordered.size(), ps) !=
           cudaSuccess) {
         cudaGetLastError();
         plan->d_tasks = nullptr;
@@ -605,7 +662,7 @@ static int factor_device(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   char* ws = static_cast<char*>(work);
   bool own = false;
   if (ws == nullptr) {
-    if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
+    if (lib_malloc(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
       cudaGetLastError();
       return TQR_ERR_NOMEM;
     }
@@ -650,8 +707,8 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   // host buffers: stage through the device, synchronously
   const size_t tbytes = tqr_t_size(m, n, nb, ib) * (D > 0 ? 2 : 1);
   double *dA = nullptr, *dT = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dT), tbytes, st) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
+      lib_malloc(reinterpret_cast<void**>(&dT), tbytes, st) != cudaSuccess) {
     cudaGetLastError();
     if (dA) cudaFreeAsync(dA, st);
     return TQR_ERR_NOMEM;
@@ -694,7 +751,7 @@ static int apply_device(int mode, int form, int64_t m, int64_t n, int64_t nrhs, 
   I.pair = pair;
   const WsLayout W = ws_layout(I, sizeof(real), false);
   char* ws = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return TQR_ERR_NOMEM;
   }
@@ -738,9 +795,9 @@ static int apply_staged(int mode, int form, int64_t m, int64_t n, int64_t nrhs, 
   if (ka == PTR_DEVICE) return apply_device<double>(mode, form, m, n, nrhs, A, lda, nb, ib, D, pair, T, B, ldb, st);
   const size_t tbytes = tqr_t_size(m, n, nb, ib) * (D > 0 ? 2 : 1);
   double *dA = nullptr, *dT = nullptr, *dB = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * std::max<int64_t>(1, m * n), st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dT), std::max<size_t>(8, tbytes), st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * brows * bcols, st) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&dA), sizeof(double) * std::max<int64_t>(1, m * n), st) != cudaSuccess ||
+      lib_malloc(reinterpret_cast<void**>(&dT), std::max<size_t>(8, tbytes), st) != cudaSuccess ||
+      lib_malloc(reinterpret_cast<void**>(&dB), sizeof(double) * brows * bcols, st) != cudaSuccess) {
     cudaGetLastError();
     if (dA) cudaFreeAsync(dA, st);
     if (dT) cudaFreeAsync(dT, st);
@@ -908,6 +965,8 @@ int tqr_stream_status(void* stream) {
   if (read_status(&s, static_cast<cudaStream_t>(stream)) != cudaSuccess) return TQR_ERR_CUDA;
   return s;
 }
+
+int tqr_release_memory(void) { return release_memory(); }
 
 int64_t tqr_set_wait_limit_ms(int64_t ms) {
   const int64_t old = g_wait_limit_ms;

@@ -36,6 +36,9 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
 template <typename real>
 int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int ctas_per_sm, int smem,
                    cudaStream_t st, int grid_cap = 0);
+// Stream-ordered allocation from the library's pool (keeps freed memory).
+cudaError_t lib_malloc(void** p, size_t bytes, cudaStream_t st);
+int release_memory();
 int ptr_kind(const void* p);
 int check_tiles(int nb, int ib, int arg_nb, int arg_ib);
 void clear_plans();

@@ -126,7 +126,7 @@ int tqr_debug_stalled_launch(int64_t limit_ms, void* stream) {
   Inst I = make_inst(M_FACTOR, 32, 16, 16, 8, cs, 0, 0);
   const WsLayout W = ws_layout(I, 8, true);
   char* ws = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes + 256, st) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&ws), W.bytes + 256, st) != cudaSuccess) {
     cudaGetLastError();
     return TQR_ERR_NOMEM;
   }

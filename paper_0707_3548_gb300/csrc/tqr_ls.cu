@@ -484,7 +484,7 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
   if (!job.init(static_cast<int>(m64), static_cast<int>(n64), static_cast<int>(nrhs64), nb, ib, prec, 0))
     return TQR_ERR_UNSUPPORTED;
   char* ws = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), job.bytes, st) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&ws), job.bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return TQR_ERR_NOMEM;
   }
@@ -530,9 +530,9 @@ extern "C" int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A,
   if (ka == PTR_DEVICE)
     return solve_device(m, n, nrhs, A, lda, B, ldb, X, ldx, prec, tol, maxit, iters, berr, nb, ib, st);
   double *dA = nullptr, *dB = nullptr, *dX = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dX), sizeof(double) * n * nrhs, st) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
+      lib_malloc(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess ||
+      lib_malloc(reinterpret_cast<void**>(&dX), sizeof(double) * n * nrhs, st) != cudaSuccess) {
     cudaGetLastError();
     if (dA) cudaFreeAsync(dA, st);
     if (dB) cudaFreeAsync(dB, st);

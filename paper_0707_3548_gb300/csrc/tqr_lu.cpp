@@ -31,7 +31,7 @@ int lu_device(int mode, int64_t m, int64_t n, int64_t nrhs, double* A, int64_t l
   I.pair = pair;
   const WsLayout W = ws_layout(I, sizeof(double), false);
   char* ws = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
+  if (lib_malloc(reinterpret_cast<void**>(&ws), W.bytes, st) != cudaSuccess) {
     cudaGetLastError();
     return TQR_ERR_NOMEM;
   }
@@ -64,10 +64,10 @@ int lu_staged(int mode, int64_t m, int64_t n, int64_t nrhs, double* A, int64_t l
   const size_t lbytes = tqr_t_size(m, n, nb, ib), pbytes = tqr_lu_piv_size(m, n, nb);
   double *dA = nullptr, *dL = nullptr, *dB = nullptr;
   int32_t* dP = nullptr;
-  if (cudaMallocAsync(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dL), lbytes, st) != cudaSuccess ||
-      cudaMallocAsync(reinterpret_cast<void**>(&dP), pbytes, st) != cudaSuccess ||
-      (solve && cudaMallocAsync(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess)) {
+  if (lib_malloc(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
+      lib_malloc(reinterpret_cast<void**>(&dL), lbytes, st) != cudaSuccess ||
+      lib_malloc(reinterpret_cast<void**>(&dP), pbytes, st) != cudaSuccess ||
+      (solve && lib_malloc(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess)) {
     cudaGetLastError();
     if (dA) cudaFreeAsync(dA, st);
     if (dL) cudaFreeAsync(dL, st);

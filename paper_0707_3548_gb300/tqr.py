@@ -83,6 +83,7 @@ SIGNATURES = {
                          _i64, _vp]),
     "tqr_orgqr": (_int, [_i64, _i64, _vp, _i64, _int, _int, _int, _vp, _i64, _vp, _i64, _vp]),
     "tqr_lu_piv_size": (ctypes.c_size_t, [_i64, _i64, _int]),
+    "tqr_release_memory": (_int, []),
     "tqr_factor_pairs": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp]),
     "tqr_apply_qt_pairs": (_int, [ctypes.c_char, _i64, _i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _i64, _vp]),
     "tqr_debug_critical_path": (_int, [_int, _i64, _i64, _int, _int, _int, _int, _int, _int, _vp]),
@@ -289,6 +290,11 @@ def tqr_apply_qt_pairs(trans, A, nb, ib, T, B, stream=None):
     _check("tqr_apply_qt_pairs", lib().tqr_apply_qt_pairs(_ch(trans), m, n, nrhs, pa, lda, nb, ib, _ptr(T), pb, ldb,
                                                            _stream(cuda, stream)))
     return B
+
+
+def tqr_release_memory():
+    """Return the library's cached workspace memory to the driver."""
+    _check("tqr_release_memory", lib().tqr_release_memory())
 
 
 def tqr_lu_piv_size(m, n, nb):

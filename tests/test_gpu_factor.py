@@ -166,3 +166,16 @@ def test_full_size_sampled_parity():
     tqr.tqr_apply_qt("N", dA, 128, 32, T, Rs)
     err = np.linalg.norm(to_host(Rs) - A[:, cols]) / np.linalg.norm(A[:, cols])
     assert err <= 10 * n * U53
+
+
+def test_release_cached_memory_then_factor_again():
+    """The library's workspace pool can be handed back; later calls allocate
+    again and give the same bits."""
+    A = inputs.normal_matrix(600, 500, 41)
+    F1, T1 = _factor(A, 128, 32)
+    tqr.tqr_release_memory()
+    F2, T2 = _factor(A, 128, 32)
+    assert np.array_equal(F1, F2) and np.array_equal(T1, T2)
+    hA = np.array(A, order="F", copy=True)
+    hT = tqr.tqr_factor(hA, 128, 32)
+    assert np.array_equal(hA, F1)
