@@ -158,6 +158,12 @@ cudaError_t lib_malloc(void** p, size_t bytes, cudaStream_t st) {
   return e;
 }
 
+cudaError_t copy_cols(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t height,
+                      cudaMemcpyKind kind, cudaStream_t st) {
+  if (dpitch == width && spitch == width) return cudaMemcpyAsync(dst, src, width * height, kind, st);
+  return cudaMemcpy2DAsync(dst, dpitch, src, spitch, width, height, kind, st);
+}
+
 int release_memory() {
   std::lock_guard<std::mutex> lk(g_pool_mu);
   int cur = 0;
@@ -715,13 +721,13 @@ static int factor_common(int64_t m, int64_t n, double* A, int64_t lda, int nb, i
   }
   int status = TQR_OK;
   // slots the variant leaves unused (tree, pairs) come back as zeros
-  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+  if (copy_cols(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
       cudaMemsetAsync(dT, 0, tbytes, st) != cudaSuccess)
     status = TQR_ERR_CUDA;
   if (status == TQR_OK) status = factor_device<double>(m, n, dA, m, nb, ib, D, pair, dT, work, work_bytes, st);
   if (status == TQR_OK &&
-      (cudaMemcpy2DAsync(A, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
+      (copy_cols(A, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
                          cudaMemcpyDeviceToHost, st) != cudaSuccess ||
        cudaMemcpyAsync(T, dT, tbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess))
     status = TQR_ERR_CUDA;
@@ -804,17 +810,17 @@ static int apply_staged(int mode, int form, int64_t m, int64_t n, int64_t nrhs, 
     return TQR_ERR_NOMEM;
   }
   int status = TQR_OK;
-  if ((n > 0 && (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+  if ((n > 0 && (copy_cols(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
                                    cudaMemcpyHostToDevice, st) != cudaSuccess ||
                  cudaMemcpyAsync(dT, T, tbytes, cudaMemcpyHostToDevice, st) != cudaSuccess)) ||
-      (form != RHS_IDENTITY && cudaMemcpy2DAsync(dB, sizeof(double) * brows, B, sizeof(double) * ldb,
+      (form != RHS_IDENTITY && copy_cols(dB, sizeof(double) * brows, B, sizeof(double) * ldb,
                                                  sizeof(double) * brows, bcols, cudaMemcpyHostToDevice,
                                                  st) != cudaSuccess))
     status = TQR_ERR_CUDA;
   if (status == TQR_OK)
     status = apply_device<double>(mode, form, m, n, nrhs, dA, std::max<int64_t>(1, m), nb, ib, D, pair, dT, dB,
                                   brows, st);
-  if (status == TQR_OK && cudaMemcpy2DAsync(B, sizeof(double) * ldb, dB, sizeof(double) * brows,
+  if (status == TQR_OK && copy_cols(B, sizeof(double) * ldb, dB, sizeof(double) * brows,
                                             sizeof(double) * brows, bcols, cudaMemcpyDeviceToHost,
                                             st) != cudaSuccess)
     status = TQR_ERR_CUDA;

@@ -39,6 +39,10 @@ int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int
 // Stream-ordered allocation from the library's pool (keeps freed memory).
 cudaError_t lib_malloc(void** p, size_t bytes, cudaStream_t st);
 int release_memory();
+// Column-major matrix copy (cudaMemcpy2DAsync arguments): one flat copy when
+// both sides are contiguous -- a 2-D copy of many columns is much slower.
+cudaError_t copy_cols(void* dst, size_t dpitch, const void* src, size_t spitch, size_t width, size_t height,
+                      cudaMemcpyKind kind, cudaStream_t st);
 int ptr_kind(const void* p);
 int check_tiles(int nb, int ib, int arg_nb, int arg_ib);
 void clear_plans();

@@ -324,7 +324,7 @@ int LsJob::factor_solve(const double* A, long long lda, const double* B, long lo
   const int sms = device_sms();
   if (upload_vtab(I, ws, W, st) != TQR_OK) return TQR_ERR_CUDA;
   if (Acopy != nullptr &&
-      cudaMemcpy2DAsync(Acopy, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+      copy_cols(Acopy, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
                         cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return TQR_ERR_CUDA;
   cudaError_t e = esize == 8 ? launch_pack<double>(A, lda, m, n, static_cast<double*>(I.A), I.p, I.q, nb, sms, st)
@@ -469,7 +469,7 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     if (status == TQR_OK && !(berr <= tol)) status = TQR_ERR_NOCONV;
   }
   if (X != nullptr &&
-      cudaMemcpy2DAsync(X, sizeof(double) * ldx, Xw, sizeof(double) * n, sizeof(double) * n, nrhs,
+      copy_cols(X, sizeof(double) * ldx, Xw, sizeof(double) * n, sizeof(double) * n, nrhs,
                         cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     fail(TQR_ERR_CUDA);
   if (iters_out) *iters_out = iters;
@@ -539,14 +539,14 @@ extern "C" int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A,
     return TQR_ERR_NOMEM;
   }
   int status = TQR_OK;
-  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+  if (copy_cols(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
                         cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      cudaMemcpy2DAsync(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
+      copy_cols(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
     status = TQR_ERR_CUDA;
   if (status == TQR_OK) status = solve_device(m, n, nrhs, dA, m, dB, m, dX, n, prec, tol, maxit, iters, berr, nb, ib, st);
   if ((status == TQR_OK || status == TQR_ERR_NOCONV || status == TQR_ERR_RANK) &&
-      cudaMemcpy2DAsync(X, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n, nrhs,
+      copy_cols(X, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n, nrhs,
                         cudaMemcpyDeviceToHost, st) != cudaSuccess)
     status = TQR_ERR_CUDA;
   cudaFreeAsync(dA, st);

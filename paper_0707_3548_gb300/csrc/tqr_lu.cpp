@@ -75,13 +75,13 @@ int lu_staged(int mode, int64_t m, int64_t n, int64_t nrhs, double* A, int64_t l
     return TQR_ERR_NOMEM;
   }
   int status = TQR_OK;
-  if (cudaMemcpy2DAsync(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+  if (copy_cols(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
                         cudaMemcpyHostToDevice, st) != cudaSuccess)
     status = TQR_ERR_CUDA;
   if (status == TQR_OK && solve &&
       (cudaMemcpyAsync(dL, L, lbytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
        cudaMemcpyAsync(dP, piv, pbytes, cudaMemcpyHostToDevice, st) != cudaSuccess ||
-       cudaMemcpy2DAsync(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
+       copy_cols(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
                          cudaMemcpyHostToDevice, st) != cudaSuccess))
     status = TQR_ERR_CUDA;
   // slots a pair factorization leaves unused come back as zeros
@@ -92,10 +92,10 @@ int lu_staged(int mode, int64_t m, int64_t n, int64_t nrhs, double* A, int64_t l
   if (status == TQR_OK) {
     cudaError_t e = cudaSuccess;
     if (solve) {
-      e = cudaMemcpy2DAsync(B, sizeof(double) * ldb, dB, sizeof(double) * m, sizeof(double) * m, nrhs,
+      e = copy_cols(B, sizeof(double) * ldb, dB, sizeof(double) * m, sizeof(double) * m, nrhs,
                             cudaMemcpyDeviceToHost, st);
     } else {
-      e = cudaMemcpy2DAsync(A, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
+      e = copy_cols(A, sizeof(double) * lda, dA, sizeof(double) * m, sizeof(double) * m, n,
                             cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(L, dL, lbytes, cudaMemcpyDeviceToHost, st);
       if (e == cudaSuccess) e = cudaMemcpyAsync(piv, dP, pbytes, cudaMemcpyDeviceToHost, st);
