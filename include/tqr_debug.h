@@ -60,7 +60,8 @@ int64_t tqr_debug_plan(int mode, int64_t m, int64_t n, int nb, int ib, int cs, i
  */
 /*
  * Critical path and total work (seconds of the scheduler's cost model, FP64,
- * 2 CTAs per SM) of the launch described as for tqr_debug_plan, computed in
+ * or FP32 with the mode flag 64; 2 CTAs per SM) of the launch described as
+ * for tqr_debug_plan, computed in
  * one pass over the sequential task order (the estimate the library uses to
  * choose the tree variant's domain size).  out: double[2].  Returns 0, or -1
  * / -2 for invalid arguments.
@@ -78,6 +79,16 @@ int tqr_debug_rules(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int 
  * not depend on either.  Returns 0, or -1 / -2 for an invalid argument.
  */
 int tqr_debug_set_schedule(int policy, int max_ctas);
+
+/*
+ * Tuning overrides for later launches: cs (0: automatic, else 8, 16 or 32)
+ * forces the slab width where the shared-memory layout allows it; D (-1:
+ * automatic, 0: flat panel, else the domain size in tile rows) replaces the
+ * library's choice of reduction tree wherever it makes one (tqr_factor_tree
+ * with D = 0, tqr_solve_ls, the server).  Returns 0, or -1 / -2 for an
+ * invalid argument.
+ */
+int tqr_debug_set_shape(int cs, int D);
 
 /*
  * Launches the device scheduler on a task whose input is never produced
@@ -103,6 +114,19 @@ int tqr_debug_timing_read(double* ms, int64_t* launches);
  * Returns 0 or TQR_ERR_CUDA.
  */
 int tqr_debug_fp64_peak(double* tflops, void* stream);
+
+/*
+ * Task trace of later task-kernel launches on the current device: for every
+ * ticket t < capacity, thread 0 of the CTA that ran it writes eight uint64
+ * words at buffer + 8 t -- global-timer ns when the ticket was taken, when
+ * its dependencies were met and when it finished; smid | kind << 16 |
+ * inst << 32; k; i; j; s | l << 32.  Tickets are positions in the launch's
+ * ordered task list, so concurrent launches overwrite each other's records.
+ * buffer: device memory of 64 * capacity bytes owned by the caller, or NULL
+ * to stop tracing (capacity is then ignored).  Synchronous.  Returns 0, -2
+ * for a negative capacity, or TQR_ERR_CUDA.
+ */
+int tqr_debug_trace(void* buffer, int64_t capacity);
 
 /* Last error message of this thread ("" if none). */
 const char* tqr_debug_last_error(void);

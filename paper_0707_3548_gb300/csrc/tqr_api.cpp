@@ -6,6 +6,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <atomic>
 #include <cstdlib>
 #include <cstring>
 #include <cmath>
@@ -45,6 +46,16 @@ void set_schedule(int policy, int max_ctas) {
   g_policy = policy;
   g_max_ctas = max_ctas;
 }
+
+// Tuning overrides of the slab width (0: automatic) and of the reduction-tree
+// domain size (-1: automatic, 0: flat panel).
+static std::atomic<int> g_force_cs{0};
+static std::atomic<int> g_force_d{-1};
+
+void set_shape_override(int cs, int D) {
+  g_force_cs.store(cs);
+  g_force_d.store(D);
+}
 static thread_local std::string g_last_error;
 
 void set_last_error(const std::string& s) { g_last_error = s; }
@@ -70,8 +81,10 @@ long long wait_limit_ns() { return g_wait_limit_ms * 1000000LL; }
 bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem, int rows) {
   const int kSmemPerSM = 233472, kSmemPerBlock = 232448, kReserved = 1024;
   int best_cs = 0, best_occ = 0, best_smem = 0;
+  const int forced = g_force_cs.load();
   for (int c : {32, 16, 8}) {
     if (c > nb || nb % c != 0) continue;
+    if (forced > 0 && c != forced) continue;
     if (ib * c > kThreads * kMaxOutPerThread) continue;
     const SmemLayout L = smem_layout(nb, ib, c, esize, rows);
     if (L.bytes > kSmemPerBlock) continue;
@@ -415,6 +428,8 @@ int choose_domain(int64_t m, int64_t n, int nb, int ib, int esize) {
   static std::mutex mu;
   static std::map<std::tuple<int64_t, int64_t, int, int, int>, int> cache;
   const int64_t p = std::max<int64_t>(1, (m + nb - 1) / nb), q = std::max<int64_t>(1, (n + nb - 1) / nb);
+  const int forced = g_force_d.load();
+  if (forced >= 0) return forced < p ? forced : 0;
   const auto key = std::make_tuple(p, q, nb, ib, esize);
   {
     std::lock_guard<std::mutex> lk(mu);

@@ -53,6 +53,7 @@ const int32_t* host_vtab(const Inst& I);
 int choose_domain(int64_t m, int64_t n, int nb, int ib, int esize);
 int upload_vtab(Inst& I, char* ws, const WsLayout& W, cudaStream_t st);
 void set_schedule(int policy, int max_ctas);
+void set_shape_override(int cs, int D);
 int timing_enable(int on);
 int timing_read(double* ms, int64_t* launches);
 

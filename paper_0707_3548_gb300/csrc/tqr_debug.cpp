@@ -71,7 +71,8 @@ int tqr_debug_critical_path(int mode, int64_t m, int64_t n, int nb, int ib, int 
                             double* out) {
   const int lu = (mode & 16) ? 1 : 0;
   const int pair = (mode & 32) ? 1 : 0;
-  mode &= ~48;
+  const int esize = (mode & 64) ? 4 : 8;
+  mode &= ~112;
   if (mode < 0 || mode > M_FORM_Q || out == nullptr) return -1;
   if (m < 1 || n < 1 || check_tiles(nb, ib, 4, 5) != 0 || cs < 1 || nb % cs != 0) return -2;
   Inst I = make_inst(mode, m, n, nb, ib, cs, nrhs, trsm);
@@ -79,7 +80,7 @@ int tqr_debug_critical_path(int mode, int64_t m, int64_t n, int nb, int ib, int 
   I.lu = lu;
   I.pair = pair;
   if (D > 0) I.vtab = host_vtab(I);
-  critical_path_estimate(I, 8, 2, &out[0], &out[1]);
+  critical_path_estimate(I, esize, 2, &out[0], &out[1]);
   return 0;
 }
 
@@ -112,6 +113,14 @@ int tqr_debug_set_schedule(int policy, int max_ctas) {
   if (policy < -1 || policy > 1) return -1;
   if (max_ctas < 0) return -2;
   set_schedule(policy, max_ctas);
+  clear_plans();
+  return 0;
+}
+
+int tqr_debug_set_shape(int cs, int D) {
+  if (cs != 0 && cs != 8 && cs != 16 && cs != 32) return -1;
+  if (D < -1) return -2;
+  set_shape_override(cs, D);
   clear_plans();
   return 0;
 }
@@ -159,6 +168,11 @@ int tqr_debug_timing_read(double* ms, int64_t* launches) { return timing_read(ms
 int tqr_debug_fp64_peak(double* tflops, void* stream) {
   if (tflops == nullptr) return -1;
   return fp64_peak(tflops, static_cast<cudaStream_t>(stream)) == cudaSuccess ? 0 : TQR_ERR_CUDA;
+}
+
+int tqr_debug_trace(void* buffer, int64_t capacity) {
+  if (buffer != nullptr && capacity < 0) return -2;
+  return set_trace(buffer, buffer != nullptr ? capacity : 0) == cudaSuccess ? 0 : TQR_ERR_CUDA;
 }
 
 const char* tqr_debug_last_error(void) { return last_error(); }

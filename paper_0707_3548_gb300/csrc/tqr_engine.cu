@@ -112,6 +112,18 @@ __device__ __forceinline__ unsigned long long abs_bits<float>(float x) {
          0x7fffffffffffffffull;
 }
 
+// max |x| over x[0..len) across the warp, exact (the ordering of IEEE
+// magnitudes is the ordering of their bit patterns, NaN above infinity).
+__device__ __forceinline__ double warp_amax(const double* x, int len, int lane) {
+  unsigned long long mx = 0;
+  for (int r = lane; r < len; r += 32) {
+    const unsigned long long b = abs_bits(x[r]);
+    mx = b > mx ? b : mx;
+  }
+  mx = warp_max_u64(mx);
+  return __longlong_as_double(static_cast<long long>(mx));
+}
+
 // ---------------------------------------------------------------- context
 struct Ctl {
   int next;       // next ticket
@@ -122,9 +134,41 @@ struct Ctl {
 
 __device__ int g_status;  // sticky device status of asynchronous launches
 
+// Task trace (a debugging aid, off unless a buffer is set): thread 0 of each
+// CTA writes, for every ticket t < g_trace_cap, eight words at
+// g_trace + 8 t: the global-timer ns when the ticket was taken, when its
+// dependencies were met and when the task finished; smid | kind << 16 |
+// inst << 32; k; i; j; s | l << 32.
+__device__ unsigned long long* g_trace;
+__device__ long long g_trace_cap;
+
+__device__ __forceinline__ void trace_begin(int t, unsigned long long t_ticket, const TaskX& x) {
+  unsigned long long* tr = g_trace;
+  if (tr == nullptr || t >= g_trace_cap) return;
+  unsigned smid;
+  asm volatile("mov.u32 %0, %%smid;" : "=r"(smid));
+  unsigned long long* r = tr + 8LL * t;
+  r[0] = t_ticket;
+  r[1] = gtimer();
+  r[3] = static_cast<unsigned long long>(smid) | (static_cast<unsigned long long>(x.kind & 0xffff) << 16) |
+         (static_cast<unsigned long long>(static_cast<unsigned>(x.inst)) << 32);
+  r[4] = static_cast<unsigned long long>(x.k);
+  r[5] = static_cast<unsigned long long>(x.i);
+  r[6] = static_cast<unsigned long long>(x.j);
+  r[7] = static_cast<unsigned long long>(static_cast<unsigned>(x.s)) |
+         (static_cast<unsigned long long>(static_cast<unsigned>(x.l)) << 32);
+}
+
+__device__ __forceinline__ void trace_end(int t) {
+  unsigned long long* tr = g_trace;
+  if (tr == nullptr || t >= g_trace_cap) return;
+  tr[8LL * t + 2] = gtimer();
+}
+
 template <typename real>
 struct Ctx {
-  real *P, *T, *S, *Top, *W, *Rb, *Part;
+  real *P, *P2, *T, *S, *Top, *W, *Rb, *Part;  // P2: nullptr when the layout has none
+  real *TopS, *Tst;                              // FP32 update staging, or nullptr
   double* red;       // reduction scratch (>= 2*kThreads + 160 doubles)
   uint32_t bar;
   uint32_t phase;
@@ -194,6 +238,40 @@ __device__ void bulk_cols(Ctx<real>& cx, real* dst, int sld, const real* src, lo
       bulk_g2s(smem_u32(dst + c * sld), src + c * gld, bytes, cx.bar);
   }
   bulk_wait(cx);
+}
+
+// Pieces of one bulk phase, issued by warp 0: bulk_expect (lane 0 announces
+// the phase's total bytes), __syncwarp, then bulk_issue_cols per column set.
+template <typename real>
+__device__ __forceinline__ void bulk_expect(Ctx<real>& cx, uint32_t bytes) {
+  if (threadIdx.x == 0) {
+    fence_proxy_async();
+    mbar_arrive_expect_tx(cx.bar, bytes);
+  }
+}
+
+template <typename real>
+__device__ __forceinline__ void bulk_issue_cols(Ctx<real>& cx, real* dst, int sld, const real* src, long long gld,
+                                                int rows, int ncols) {
+  const uint32_t b = static_cast<uint32_t>(rows) * sizeof(real);
+  for (int c = threadIdx.x; c < ncols; c += 32) bulk_g2s(smem_u32(dst + c * sld), src + c * gld, b, cx.bar);
+}
+
+// Asynchronous form for warp 0 only: one bulk phase that fills two column
+// sets (n1 columns of r1 rows, then n2 of r2; n2 may be 0).  Completes at the
+// next bulk_wait of every thread; nothing else may use the barrier before.
+template <typename real>
+__device__ void bulk_cols2_issue(Ctx<real>& cx, real* d1, int sld1, const real* s1, long long gld1, int r1, int n1,
+                                 real* d2, int sld2, const real* s2, long long gld2, int r2, int n2) {
+  const int lane = threadIdx.x;
+  const uint32_t b1 = static_cast<uint32_t>(r1) * sizeof(real), b2 = static_cast<uint32_t>(r2) * sizeof(real);
+  if (lane == 0) {
+    fence_proxy_async();
+    mbar_arrive_expect_tx(cx.bar, b1 * n1 + b2 * n2);
+  }
+  __syncwarp();
+  for (int c = lane; c < n1; c += 32) bulk_g2s(smem_u32(d1 + c * sld1), s1 + c * gld1, b1, cx.bar);
+  for (int c = lane; c < n2; c += 32) bulk_g2s(smem_u32(d2 + c * sld2), s2 + c * gld2, b2, cx.bar);
 }
 
 // Plain strided copies (L2 only; data may come from other SMs).
@@ -321,12 +399,16 @@ __device__ void apply_block(const real* __restrict__ V, int ldv, int nv, const r
 // FP32 form of apply_block with 4 x 4 register micro-tiles (the FP32 pipe is
 // ~58x the FP64 one, so here shared-memory traffic, not arithmetic, is the
 // limit).  Requires ib, w, nv multiples of 4, leading dimensions multiples of
-// 4 and 16-byte aligned V, S (checked by the caller).
+// 4, 16-byte aligned V, S and ib (w + 4) <= 17 kThreads (checked by the
+// caller).
 //   Phase 1: W = Top + L^T Top + V^T S.  The (ib/4) x (w/4) micro-tiles are
 //            split over the rows of V and S (split-K); each thread writes its
 //            16 partial sums to Part, then every output sums its partials in
 //            a fixed order (deterministic).
 //   Phase 3: S -= V W with one 4 x 4 micro-tile per thread per pass.
+// Partial sums sit at stride 17 (one bank per lane when a warp stores them),
+// and T W goes row-major (ld w + 4) into the partial-sum area, so phase 3
+// reads four of its columns with one 16-byte load.
 __device__ void apply_block_f32(const float* __restrict__ V, int ldv, int nv, const float* __restrict__ L, int ldl,
                                 float* Top, int ldt, float* S, int lds, const float* __restrict__ Tm, int ldT,
                                 int ib, int w, float* W, float* Part, bool trans) {
@@ -361,7 +443,7 @@ __device__ void apply_block_f32(const float* __restrict__ V, int ldv, int nv, co
             acc[i][j] = fmaf(vq[i].w, sq[j].w, acc[i][j]);
           }
       }
-      float* pp = Part + (ks * MT + tile) * 16;
+      float* pp = Part + (ks * MT + tile) * 17;
 #pragma unroll
       for (int i = 0; i < 4; ++i)
 #pragma unroll
@@ -375,39 +457,33 @@ __device__ void apply_block_f32(const float* __restrict__ V, int ldv, int nv, co
     float a = Top[r + c * ldt];
     if (L != nullptr)
       for (int t = r + 1; t < ib; ++t) a = fmaf(L[t + r * ldl], Top[t + c * ldt], a);
-    for (int ks = 0; ks < KS; ++ks) a += Part[(ks * MT + tile) * 16 + (r % 4) * 4 + (c % 4)];
+    for (int ks = 0; ks < KS; ++ks) a += Part[(ks * MT + tile) * 17 + (r % 4) * 4 + (c % 4)];
     W[o] = a;
   }
   __syncthreads();
-  float tmp[kMaxOutPerThread];
-  {
-    int cnt = 0;
-    for (int o = tid; o < nout; o += kThreads, ++cnt) {
-      const int r = o % ib, c = o / ib;
-      const float* wc = W + c * ib;
-      float a;
-      if (trans) {
-        a = Tm[r * ldT] * wc[0];
-        for (int q = 1; q <= r; ++q) a = fmaf(Tm[q + r * ldT], wc[q], a);
-      } else {
-        a = Tm[r + r * ldT] * wc[r];
-        for (int q = r + 1; q < ib; ++q) a = fmaf(Tm[r + q * ldT], wc[q], a);
-      }
-      tmp[cnt] = a;
+  // T W (or T^T W), row-major with ld w + 4, into the partial-sum area (free
+  // once W is summed): no in-place rewrite, one barrier less
+  const int ldw = w + 4;
+  float* W2 = Part;
+  for (int o = tid; o < nout; o += kThreads) {
+    const int r = o % ib, c = o / ib;
+    const float* wc = W + c * ib;
+    float a;
+    if (trans) {
+      a = Tm[r * ldT] * wc[0];
+      for (int q = 1; q <= r; ++q) a = fmaf(Tm[q + r * ldT], wc[q], a);
+    } else {
+      a = Tm[r + r * ldT] * wc[r];
+      for (int q = r + 1; q < ib; ++q) a = fmaf(Tm[r + q * ldT], wc[q], a);
     }
-  }
-  __syncthreads();
-  {
-    int cnt = 0;
-    for (int o = tid; o < nout; o += kThreads, ++cnt) W[o] = tmp[cnt];
+    W2[c + r * ldw] = a;
   }
   __syncthreads();
   for (int o = tid; o < nout; o += kThreads) {
     const int r = o % ib, c = o / ib;
-    const float* wc = W + c * ib;
-    float a = Top[r + c * ldt] - wc[r];
+    float a = Top[r + c * ldt] - W2[c + r * ldw];
     if (L != nullptr)
-      for (int t = 0; t < r; ++t) a = fmaf(-L[r + t * ldl], wc[t], a);
+      for (int t = 0; t < r; ++t) a = fmaf(-L[r + t * ldl], W2[c + t * ldw], a);
     Top[r + c * ldt] = a;
   }
   const int ntile = (nv / 4) * (w / 4);
@@ -418,13 +494,14 @@ __device__ void apply_block_f32(const float* __restrict__ V, int ldv, int nv, co
     for (int j = 0; j < 4; ++j) acc[j] = *reinterpret_cast<const float4*>(S + t0 + (c0 + j) * lds);
     for (int r = 0; r < ib; ++r) {
       const float4 vq = *reinterpret_cast<const float4*>(V + t0 + r * ldv);
+      const float4 wq = *reinterpret_cast<const float4*>(W2 + c0 + r * ldw);
+      const float wv[4] = {wq.x, wq.y, wq.z, wq.w};
 #pragma unroll
       for (int j = 0; j < 4; ++j) {
-        const float wv = W[r + (c0 + j) * ib];
-        acc[j].x = fmaf(-vq.x, wv, acc[j].x);
-        acc[j].y = fmaf(-vq.y, wv, acc[j].y);
-        acc[j].z = fmaf(-vq.z, wv, acc[j].z);
-        acc[j].w = fmaf(-vq.w, wv, acc[j].w);
+        acc[j].x = fmaf(-vq.x, wv[j], acc[j].x);
+        acc[j].y = fmaf(-vq.y, wv[j], acc[j].y);
+        acc[j].z = fmaf(-vq.z, wv[j], acc[j].z);
+        acc[j].w = fmaf(-vq.w, wv[j], acc[j].w);
       }
     }
 #pragma unroll
@@ -441,7 +518,7 @@ __device__ __forceinline__ void apply_any(const real* V, int ldv, int nv, const 
   if constexpr (sizeof(real) == 4) {
     const bool ok = (ib % 4 == 0) && (w % 4 == 0) && (nv % 4 == 0) && (ldv % 4 == 0) && (lds % 4 == 0) &&
                     ((reinterpret_cast<uintptr_t>(V) | reinterpret_cast<uintptr_t>(S)) & 15) == 0 &&
-                    (ib / 4) * (w / 4) <= kThreads;
+                    (ib / 4) * (w / 4) <= kThreads && ib * (w + 4) <= kThreads * 17;
     if (ok) {
       apply_block_f32(V, ldv, nv, L, ldl, Top, ldt, S, lds, Tm, ldT, ib, w, W, Part, trans);
       return;
@@ -450,40 +527,48 @@ __device__ __forceinline__ void apply_any(const real* V, int ldv, int nv, const 
   apply_block<real>(V, ldv, nv, L, ldl, Top, ldt, S, lds, Tm, ldT, ib, w, W, trans);
 }
 
-// ||x|| over x[0..len) (stride 1) by one warp, in FP64; every lane returns
-// the same bits (xor-butterfly reductions).  The sum of squares is taken
-// directly when max|x| lies in [2^-500, 2^500] (no intermediate can overflow
-// or lose the result to underflow there); otherwise it is recomputed on x
-// scaled by an exact power of two.
+// Column measure for the reflector, by one warp (every lane returns the same
+// bits: xor-butterfly reductions).
+//   FP64 columns: ||x|| over x[0..len), taken directly when max|x| lies in
+//   [2^-500, 2^500] (no intermediate can overflow or lose the result to
+//   underflow there), otherwise recomputed on x scaled by an exact power of
+//   two.
+//   FP32 columns: the FP64 sum of squares ||x||^2 itself.  Each square is
+//   exact in FP64 and lies in [2^-298, 2^256], so no scaling is ever needed,
+//   and the square root is left to make_refl (one FP64 square root per
+//   column instead of two: on this GPU each FP64 instruction of a lone warp
+//   costs tens of cycles, and the panel's column chain is serial).
 template <typename real>
 __device__ double warp_norm(const real* x, int len) {
   const int lane = threadIdx.x & 31;
   double ssq = 0.0;
-  unsigned long long mx = 0;
   for (int r = lane; r < len; r += 32) {
     const double v = static_cast<double>(x[r]);
     ssq = fma(v, v, ssq);
-    const unsigned long long b = abs_bits(x[r]);
-    mx = b > mx ? b : mx;
   }
   ssq = warp_sum(ssq);
-  mx = warp_max_u64(mx);
-  const double amax = __longlong_as_double(static_cast<long long>(mx));
-  if (amax != 0.0 && isfinite(amax) && (amax < 0x1p-500 || amax > 0x1p500)) {
-    const int e = ilogb(amax);
-    const double sc = scalbn(1.0, -e);
-    double s2 = 0.0;
-    for (int r = lane; r < len; r += 32) {
-      const double v = static_cast<double>(x[r]) * sc;
-      s2 = fma(v, v, s2);
+  if constexpr (sizeof(real) == 4) {
+    return ssq;
+  } else {
+    const double amax = warp_amax(x, len, lane);
+    if (amax != 0.0 && isfinite(amax) && (amax < 0x1p-500 || amax > 0x1p500)) {
+      const int e = ilogb(amax);
+      const double sc = scalbn(1.0, -e);
+      double s2 = 0.0;
+      for (int r = lane; r < len; r += 32) {
+        const double v = static_cast<double>(x[r]) * sc;
+        s2 = fma(v, v, s2);
+      }
+      s2 = warp_sum(s2);
+      return scalbn(sqrt(s2), e);
     }
-    s2 = warp_sum(s2);
-    return scalbn(sqrt(s2), e);
+    return sqrt(ssq);
   }
-  return sqrt(ssq);
 }
 
-// Householder reflector (LAPACK convention, FP64) from alpha and ||x2||:
+// Householder reflector (LAPACK convention, FP64) from alpha and the
+// column measure of x2 (warp_norm: ||x2|| for FP64 columns, ||x2||^2 for
+// FP32 ones):
 //   beta = -sign(alpha) ||[alpha; x2]||, tau = (beta - alpha)/beta and the
 //   scale 1/(alpha - beta) of v.  Pure function of its inputs, so threads
 //   that call it on the same values agree bit for bit.
@@ -491,14 +576,27 @@ struct Refl {
   double tau, beta, scal;
 };
 
-__device__ __forceinline__ Refl make_refl(double alpha, double xnorm) {
+// FP32 columns: ||[alpha; x2]|| = sqrt(alpha^2 + ||x2||^2) needs no overflow
+// guard (all terms lie far inside FP64's range), and tau and the scale share
+// one FP64 reciprocal: with d = alpha - beta, 1/d = beta/(d beta) and
+// tau = -d/beta = -d^2/(d beta) (a few FP64 ulps apart from the two
+// divisions, far below the FP32 rounding they are followed by).
+template <typename real>
+__device__ __forceinline__ Refl make_refl(double alpha, double xm) {
   Refl f;
-  if (xnorm == 0.0) {
+  if (xm == 0.0) {
     f.tau = 0.0;
     f.beta = alpha;
     f.scal = 0.0;
+  } else if constexpr (sizeof(real) == 4) {
+    const double h = sqrt(fma(alpha, alpha, xm));
+    f.beta = (alpha >= 0.0) ? -h : h;  // sign(0) = +1, also for -0.0
+    const double d = alpha - f.beta;
+    const double rc = 1.0 / (d * f.beta);
+    f.scal = f.beta * rc;
+    f.tau = -(d * d) * rc;
   } else {
-    const double h = hypot(alpha, xnorm);
+    const double h = hypot(alpha, xm);
     f.beta = (alpha >= 0.0) ? -h : h;  // sign(0) = +1, also for -0.0
     f.tau = (f.beta - alpha) / f.beta;
     f.scal = 1.0 / (alpha - f.beta);
@@ -512,50 +610,59 @@ __device__ __forceinline__ Refl make_refl(double alpha, double xnorm) {
 //   TS == true  (TSQRT): the top is the ib x ib triangle R (ld ldr) and P is
 //                        nr x ib below it; reflector c has v = [e_c; s x],
 //                        x = P(:, c).
-// One barrier per column.  The norm of column c's x2 was computed during
-// step c-1 by the warp that updated column c (warp 0), in the same pass, and
-// left in red[c & 1]; every thread derives the reflector from it.  The warps
-// owning columns d > c apply it with v formed on the fly from the unscaled x:
+// One barrier per column.  Reflector c is derived once, by the warp that
+// owns column c (warp 0): during step c-1 it applies reflector c-1 to
+// column c, then takes the FP64 norm of column c's x2 and the reflector
+// (tau, beta, scale) from it, and publishes them in red[4 (c & 1) ...] (FP64)
+// and, rounded to the tile precision, after red + 8.  The warps owning
+// columns d > c apply it with v formed on the fly from the unscaled x:
 // w = top + s (x^T p_d), p_d -= (tau w s) x, top -= tau w.  Column c itself
 // (v = s x, beta, tau) is written by warp 0 during the next step, when no
 // warp reads it.
 template <typename real, bool TS>
+__device__ __forceinline__ void publish_refl(double* red, int c, double alpha, double xn) {
+  const Refl f = make_refl<real>(alpha, xn);
+  double* d = red + 4 * (c & 1);
+  d[0] = f.tau;
+  d[1] = f.beta;
+  d[2] = f.scal;
+  real* r = reinterpret_cast<real*>(red + 8) + 2 * (c & 1);
+  r[0] = static_cast<real>(f.tau);
+  r[1] = static_cast<real>(f.scal);
+}
+
+template <typename real, bool TS>
 __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, double* red, double* taus) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int nwarps = kThreads / 32;
-  // norm of column 0's x2
+  // reflector of column 0
   if (wid == 0) {
     const double xn = TS ? warp_norm<real>(P, nr) : warp_norm<real>(P + 1, nr - 1);
-    if (lane == 0) red[0] = xn;
+    if (lane == 0) publish_refl<real, TS>(red, 0, static_cast<double>(TS ? R[0] : P[0]), xn);
   }
   __syncthreads();
-  Refl prev = {0.0, 0.0, 0.0};
   for (int c = 0; c <= ib; ++c) {
     // deferred writes of column c-1
     if (wid == 0 && c > 0) {
+      const double* pf = red + 4 * ((c - 1) & 1);
       real* pp = P + (c - 1) * ldP;
       const int r0p = TS ? 0 : c;
-      const real sp = static_cast<real>(prev.scal);
+      const real sp = static_cast<real>(pf[2]);
       for (int r = r0p + lane; r < nr; r += 32) pp[r] *= sp;
       if (lane == 0) {
         if constexpr (TS)
-          R[(c - 1) + (c - 1) * ldr] = static_cast<real>(prev.beta);
+          R[(c - 1) + (c - 1) * ldr] = static_cast<real>(pf[1]);
         else
-          pp[c - 1] = static_cast<real>(prev.beta);
-        taus[c - 1] = prev.tau;
+          pp[c - 1] = static_cast<real>(pf[1]);
+        taus[c - 1] = pf[0];
       }
     }
     if (c == ib) break;
     real* pc = P + c * ldP;
     const int r0 = TS ? 0 : c + 1;
-    real alpha_r;
-    if constexpr (TS)
-      alpha_r = R[c + c * ldr];
-    else
-      alpha_r = pc[c];
-    const Refl f = make_refl(static_cast<double>(alpha_r), red[c & 1]);
-    const real tau = static_cast<real>(f.tau);
-    const real scal = static_cast<real>(f.scal);
+    const real* rf = reinterpret_cast<const real*>(red + 8) + 2 * (c & 1);
+    const real tau = rf[0];
+    const real scal = rf[1];
     for (int d = c + 1 + wid; d < ib; d += nwarps) {
       real* pd = P + d * ldP;
       if (tau != real(0)) {
@@ -578,13 +685,15 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
         }
       }
       if (d == c + 1) {
-        // this warp owns the next column: its norm, for step c + 1
+        // this warp owns the next column: its reflector, for step c + 1
         __syncwarp();
         const double xn = TS ? warp_norm<real>(pd, nr) : warp_norm<real>(pd + c + 2, nr - c - 2);
-        if (lane == 0) red[(c + 1) & 1] = xn;
+        if (lane == 0) {
+          const double alpha = static_cast<double>(TS ? R[(c + 1) + (c + 1) * ldr] : pd[c + 1]);
+          publish_refl<real, TS>(red, c + 1, alpha, xn);
+        }
       }
     }
-    prev = f;
     __syncthreads();
   }
   __syncthreads();
@@ -793,6 +902,87 @@ __device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int head, int i,
   real* Cb = tile_ptr<real>(I, i, j) + soff;
   const int w = slab_width(I, j, s);
   const int nblk = nb / ib;
+  if (cx.TopS != nullptr) {
+    // FP32: the bottom slab, the whole top slab, all T blocks and the first
+    // V block arrive in one bulk phase; block l+1's V is copied into the
+    // other buffer while block l is applied; both slabs go back at the end
+    // (same arithmetic, same order as below).
+    const int lf = trans ? 0 : nblk - 1;
+    if (threadIdx.x < 32) {
+      const uint32_t cb = static_cast<uint32_t>(nb) * sizeof(real);
+      bulk_expect(cx, cb * (2 * w + ib) + static_cast<uint32_t>(ib) * nb * sizeof(real));
+      __syncwarp();
+      bulk_issue_cols(cx, cx.S, cx.ldS, Cb, nb, nb, w);
+      bulk_issue_cols(cx, cx.TopS, cx.ldS, Ct, nb, nb, w);
+      bulk_issue_cols(cx, cx.Tst, 0, Tg, 0, ib * nb, 1);
+      bulk_issue_cols(cx, cx.P, cx.ldP, Vt + static_cast<long long>(lf) * ib * nb, nb, nb, ib);
+    }
+    bulk_wait(cx);
+    for (int bb = 0; bb < nblk; ++bb) {
+      const int l = trans ? bb : nblk - 1 - bb;
+      const int l0 = l * ib;
+      real* Pc = (bb & 1) ? cx.P2 : cx.P;
+      if (bb + 1 < nblk && threadIdx.x < 32) {
+        const int ln = trans ? bb + 1 : nblk - 2 - bb;
+        bulk_expect(cx, static_cast<uint32_t>(nb) * ib * sizeof(real));
+        __syncwarp();
+        bulk_issue_cols(cx, (bb & 1) ? cx.P : cx.P2, cx.ldP, Vt + static_cast<long long>(ln) * ib * nb, nb, nb, ib);
+      }
+      for (int e = threadIdx.x; e < ib * ib; e += kThreads) {
+        const int r = e % ib, c = e / ib;
+        cx.T[r + c * cx.ldT] = cx.Tst[l0 * ib + r + c * ib];
+      }
+      const int nv = tt ? l0 + ib : nb;
+      if (tt)
+        for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
+          const int r = e % nv, c = e / nv;
+          if (r > l0 + c) Pc[r + c * cx.ldP] = real(0);
+        }
+      __syncthreads();
+      apply_any<real>(Pc, cx.ldP, nv, nullptr, 0, cx.TopS + l0, cx.ldS, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W,
+                      cx.Part, trans);
+      if (bb + 1 < nblk) bulk_wait(cx);
+    }
+    store_block(Cb, nb, cx.S, cx.ldS, nb, w);
+    store_block(Ct, nb, cx.TopS, cx.ldS, nb, w);
+    __syncthreads();
+    return;
+  }
+  if (cx.P2 != nullptr) {
+    // Pipelined: block l+1's V is copied into the other buffer while block l
+    // is applied (same arithmetic, same order as below).
+    const int lf = trans ? 0 : nblk - 1;
+    if (threadIdx.x < 32)
+      bulk_cols2_issue(cx, cx.S, cx.ldS, Cb, nb, nb, w, cx.P, cx.ldP, Vt + static_cast<long long>(lf) * ib * nb, nb,
+                       nb, ib);
+    bulk_wait(cx);
+    for (int bb = 0; bb < nblk; ++bb) {
+      const int l = trans ? bb : nblk - 1 - bb;
+      const int l0 = l * ib;
+      real* Pc = (bb & 1) ? cx.P2 : cx.P;
+      if (bb + 1 < nblk && threadIdx.x < 32) {
+        const int ln = trans ? bb + 1 : nblk - 2 - bb;
+        bulk_cols2_issue(cx, (bb & 1) ? cx.P : cx.P2, cx.ldP, Vt + static_cast<long long>(ln) * ib * nb, nb, nb, ib,
+                         static_cast<real*>(nullptr), 0, static_cast<const real*>(nullptr), 0, 0, 0);
+      }
+      load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
+      load_block(cx.Top, ib, Ct + l0, nb, ib, w);
+      const int nv = tt ? l0 + ib : nb;
+      if (tt)
+        for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
+          const int r = e % nv, c = e / nv;
+          if (r > l0 + c) Pc[r + c * cx.ldP] = real(0);
+        }
+      __syncthreads();
+      apply_any<real>(Pc, cx.ldP, nv, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, trans);
+      store_block(Ct + l0, nb, cx.Top, ib, ib, w);
+      __syncthreads();
+      if (bb + 1 < nblk) bulk_wait(cx);
+    }
+    store_block(Cb, nb, cx.S, cx.ldS, nb, w);
+    __syncthreads();
+    return;
+  }
   bulk_cols(cx, cx.S, cx.ldS, Cb, nb, nb, w);
   for (int bb = 0; bb < nblk; ++bb) {
     const int l = trans ? bb : nblk - 1 - bb;
@@ -1445,6 +1635,7 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
   cx.limit_ns = limit_ns;
   cx.phase = 0;
   int cur_nb = -1, cur_ib = -1, cur_cs = -1, cur_pair = -1;
+  int cur_inst = -1;  // thread 0: index of the descriptor held in s_inst (fixed during a launch)
   if (threadIdx.x == 0) {
     // the barrier sits at the end of the largest layout; its offset is passed
     // through the kernel's dynamic size
@@ -1466,10 +1657,15 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
       if (ld_relaxed(&ctl->error) == 0) {
         const int t = atomicAdd(&ctl->next, 1);
         if (t < ntasks) {
+          const unsigned long long t_ticket = g_trace != nullptr ? gtimer() : 0ull;
           s_task = tasks[t];
-          s_inst = insts[s_task.inst];
+          if (s_task.inst != cur_inst) {
+            s_inst = insts[s_task.inst];
+            cur_inst = s_task.inst;
+          }
           cx.task = t;
           go = wait_deps<real, V != KV_QR>(cx, s_inst, s_task) ? 1 : 0;
+          if (go) trace_begin(t, t_ticket, s_task);
         }
       }
       s_go = go;
@@ -1481,6 +1677,9 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
     if (I.nb != cur_nb || I.ib != cur_ib || I.cs != cur_cs || I.pair != cur_pair) {
       const SmemLayout L = smem_layout(I.nb, I.ib, I.cs, sizeof(real), I.pair ? 2 * I.nb : 0);
       cx.P = reinterpret_cast<real*>(smem + L.oP);
+      cx.P2 = L.oP2 >= 0 ? reinterpret_cast<real*>(smem + L.oP2) : nullptr;
+      cx.TopS = L.oTopS >= 0 ? reinterpret_cast<real*>(smem + L.oTopS) : nullptr;
+      cx.Tst = L.oTst >= 0 ? reinterpret_cast<real*>(smem + L.oTst) : nullptr;
       cx.T = reinterpret_cast<real*>(smem + L.oT);
       cx.S = reinterpret_cast<real*>(smem + L.oS);
       cx.Top = reinterpret_cast<real*>(smem + L.oTop);
@@ -1542,12 +1741,15 @@ __device__ __forceinline__ void task_loop(const TaskX* __restrict__ tasks, int n
       default: fail_kind(cx); break;
     }
     __syncthreads();
-    if (threadIdx.x == 0) signal_done<V != KV_QR>(I, t);
+    if (threadIdx.x == 0) {
+      trace_end(cx.task);
+      signal_done<V != KV_QR>(I, t);
+    }
   }
 }
 
 template <typename real>
-__global__ void __launch_bounds__(kThreads) run_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
+__global__ void __launch_bounds__(kThreads, 2) run_tasks_kernel(const TaskX* __restrict__ tasks, int ntasks,
                                                              const Inst* __restrict__ insts, Ctl* ctl,
                                                              long long limit_ns) {
   task_loop<real, KV_QR>(tasks, ntasks, insts, ctl, limit_ns);
@@ -1735,6 +1937,14 @@ __global__ void identity_kernel(int m, int ncols, D* __restrict__ Ab, int p, int
 }
 
 __global__ void status_reset_kernel() { g_status = 0; }
+
+cudaError_t set_trace(void* buffer, long long capacity) {
+  unsigned long long* b = static_cast<unsigned long long*>(buffer);
+  const long long cap = buffer != nullptr ? capacity : 0;
+  cudaError_t e = cudaMemcpyToSymbol(g_trace, &b, sizeof(b));
+  if (e == cudaSuccess) e = cudaMemcpyToSymbol(g_trace_cap, &cap, sizeof(cap));
+  return e;
+}
 
 // ---------------------------------------------------------------- host launchers
 static int grid_for(long long work, int sms) {

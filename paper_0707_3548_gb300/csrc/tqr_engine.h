@@ -49,5 +49,8 @@ cudaError_t read_status(int* status, cudaStream_t st);
 size_t ctl_bytes();
 // FP64 FMA throughput probe (TFLOP/s).
 cudaError_t fp64_peak(double* tflops, cudaStream_t st);
+// Points the task kernels' trace at buffer (8 words per task, device memory
+// of the current device; nullptr turns the trace off).  Synchronous.
+cudaError_t set_trace(void* buffer, long long capacity);
 
 }  // namespace tqr

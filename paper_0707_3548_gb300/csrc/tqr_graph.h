@@ -509,7 +509,8 @@ constexpr int kMaxOutPerThread = 8;
 //   Part           FP32 only: split-K partials of the blocked W = V^T S
 //   Bar 8 bytes    mbarrier for the bulk (TMA) copies
 struct SmemLayout {
-  int oP, oT, oS, oTop, oW, oRed, oPart, oBar, bytes;
+  int oP, oP2, oT, oS, oTop, oW, oRed, oPart, oBar, bytes;  // oP2 < 0: no second panel buffer
+  int oTopS, oTst;  // FP32 update staging (top slab, all T blocks); < 0: absent
   bool r_in_s;
 };
 
@@ -529,13 +530,31 @@ TQR_HD SmemLayout smem_layout(int nb, int ib, int cs, int esize, int rows = 0) {
   if (!L.r_in_s && ib * ib > top_elems) top_elems = ib * ib;
   int o = 0;
   L.oP = o;   o += align16(ld * ib * esize);
+  // second reflector-block buffer (b x b layouts, blocks up to 32 KB): the
+  // update tasks load block l+1's V while applying block l
+  L.oP2 = -1;
+  if (rows <= nb && ld * ib * esize <= 32768) {
+    L.oP2 = o;
+    o += align16(ld * ib * esize);
+  }
+  // FP32 with the second buffer: the update tasks also stage the whole top
+  // slab and all ib x ib T blocks of the tile once per task
+  L.oTopS = -1;
+  L.oTst = -1;
+  if (esize == 4 && L.oP2 >= 0) {
+    L.oTopS = o;
+    o += align16(ld * cs * esize);
+    L.oTst = o;
+    o += align16(ib * nb * esize);
+  }
   L.oT = o;   o += align16(ib * (ib + 1) * esize);
   L.oS = o;   o += align16(ld * cs * esize);
   L.oTop = o; o += align16(top_elems * esize);
   L.oW = o;   o += align16(ib * cs * esize);
   L.oRed = o; o += align16((2 * kThreads + 2 * 64 + 32) * 8);
-  // FP32 only: split-K partial sums of the register-blocked update (16 per thread)
-  L.oPart = o; if (esize == 4) o += align16(kThreads * 16 * esize);
+  // FP32 only: split-K partial sums of the register-blocked update (16 per
+  // thread, stride 17 so a warp's stores fall in distinct banks)
+  L.oPart = o; if (esize == 4) o += align16(kThreads * 17 * esize);
   L.oBar = o; o += 16;
   L.bytes = o;
   return L;

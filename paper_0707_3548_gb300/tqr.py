@@ -100,6 +100,8 @@ SIGNATURES = {
     "tqr_debug_timing": (_int, [_int]),
     "tqr_debug_timing_read": (_int, [ctypes.POINTER(_dbl), ctypes.POINTER(_i64)]),
     "tqr_debug_fp64_peak": (_int, [ctypes.POINTER(_dbl), _vp]),
+    "tqr_debug_trace": (_int, [_vp, _i64]),
+    "tqr_debug_set_shape": (_int, [_int, _int]),
     "tqr_debug_last_error": (ctypes.c_char_p, []),
 }
 
@@ -455,6 +457,10 @@ def tqr_debug_set_schedule(policy=-1, max_ctas=0):
     return lib().tqr_debug_set_schedule(policy, max_ctas)
 
 
+def tqr_debug_set_shape(cs=0, D=-1):
+    return lib().tqr_debug_set_shape(cs, D)
+
+
 def tqr_debug_stalled_launch(limit_ms, stream=None):
     return lib().tqr_debug_stalled_launch(limit_ms, _stream(True, stream))
 
@@ -475,6 +481,31 @@ def tqr_debug_fp64_peak(stream=None):
     t = _dbl(0)
     _check("tqr_debug_fp64_peak", lib().tqr_debug_fp64_peak(ctypes.byref(t), _stream(True, stream)))
     return t.value
+
+
+def tqr_debug_trace(buffer):
+    """Traces later task-kernel launches into a device int64 tensor of shape
+    (capacity, 8) (None stops tracing); decode with trace_records."""
+    if buffer is None:
+        _check("tqr_debug_trace", lib().tqr_debug_trace(None, 0))
+        return
+    if buffer.dim() != 2 or buffer.shape[1] != 8 or buffer.element_size() != 8 or not buffer.is_contiguous():
+        raise ValueError("trace buffer must be a contiguous (capacity, 8) 64-bit device tensor")
+    _check("tqr_debug_trace", lib().tqr_debug_trace(_vp(buffer.data_ptr()), buffer.shape[0]))
+
+
+def trace_records(words):
+    """Decodes an (n, 8) array of trace words into a dict of columns, keeping
+    the rows that were written (nonzero end time)."""
+    w = np.asarray(words).astype(np.uint64)
+    w = w[w[:, 2] != 0]
+    return {
+        "ticket_ns": w[:, 0].astype(np.int64), "start_ns": w[:, 1].astype(np.int64),
+        "end_ns": w[:, 2].astype(np.int64), "sm": (w[:, 3] & 0xffff).astype(np.int64),
+        "kind": ((w[:, 3] >> 16) & 0xffff).astype(np.int64), "inst": (w[:, 3] >> 32).astype(np.int64),
+        "k": w[:, 4].astype(np.int64), "i": w[:, 5].astype(np.int64), "j": w[:, 6].astype(np.int64),
+        "s": (w[:, 7] & 0xffffffff).astype(np.int64), "l": (w[:, 7] >> 32).astype(np.int64),
+    }
 
 
 class Server:

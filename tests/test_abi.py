@@ -94,3 +94,15 @@ def test_debug_schedule_validation(lib):
     assert lib.tqr_debug_set_schedule(3, 0) == -1
     assert lib.tqr_debug_set_schedule(0, -1) == -2
     assert lib.tqr_debug_set_schedule(-1, 0) == 0
+
+
+def test_debug_shape_override_validation(lib):
+    assert lib.tqr_debug_set_shape(12, -1) == -1
+    assert lib.tqr_debug_set_shape(0, -2) == -2
+    assert lib.tqr_debug_set_shape(16, 4) == 0
+    assert lib.tqr_debug_set_shape(0, -1) == 0
+
+
+def test_debug_trace_rejects_a_negative_capacity():
+    import ctypes
+    assert tqr.lib().tqr_debug_trace(ctypes.c_void_p(256), -1) == -2

@@ -97,6 +97,21 @@ def test_deterministic_across_schedules():
         assert np.array_equal(F, outs[0][0]) and np.array_equal(T, outs[0][1])
 
 
+def test_fp64_bits_do_not_depend_on_the_slab_width():
+    """Every FP64 output of an update is one FMA chain over its own column,
+    so the slab width (8, 16 or 32 columns per task) changes no bit."""
+    A = inputs.normal_matrix(700, 650, 6)
+    outs = []
+    try:
+        for cs in (0, 8, 16, 32):
+            tqr.tqr_debug_set_shape(cs, -1)
+            outs.append(_factor(A, 64, 16))
+    finally:
+        tqr.tqr_debug_set_shape(0, -1)
+    for F, T in outs[1:]:
+        assert np.array_equal(F, outs[0][0]) and np.array_equal(T, outs[0][1])
+
+
 def test_host_pointer_path_equals_device_path():
     A = inputs.uniform_matrix(300, 200, 8)
     F_dev, T_dev = _factor(A, 64, 16)
