@@ -11,8 +11,18 @@ Backward error (the paper is silent; normwise reading recorded with the
 design notes):
     eta(x) = ||A^T r||_2 / (||A||_F (||A||_F ||x||_2 + ||b||_2)),  r = b - A x.
 
-Refinement (the paper is silent): Bjorck's iterative refinement of the
-augmented system
+Refinement (the paper is silent), two forms:
+
+(1) corrected semi-normal equations (Bjorck): with R from a (possibly lower
+accuracy) QR factorization, R^T R ~ A^T A, and float64 residuals
+    e = b - A x,  dx = R^{-1} (R^{-T} (A^T e)),  x += dx.
+Its fixed point is the LS solution (A^T (b - A x) = 0).  When R is the
+exact factor of A + E with ||E|| = eps ||A||, the iteration matrix
+I - (R^T R)^{-1} A^T A is similar to I - M^T M, M = A R^{-1} = Q - E R^{-1},
+so the error contracts by about 2 kappa(A) eps per step: it needs
+kappa eps well below 1;
+
+(2) Bjorck's iterative refinement of the augmented system
     [ I   A ] [r]   [b]
     [ A^T 0 ] [x] = [0]
 with residuals in float64 and each correction solved through a QR
@@ -136,3 +146,29 @@ def augmented_refinement(A, b, solver, tol=1e-12, maxit=30, x0=None):
         it += 1
         history.append(backward_error(A, x, b))
     return x, r, it, history
+
+
+def seminormal_refinement(A, b, R, tol=1e-12, maxit=30, x0=None):
+    """Corrected semi-normal equations with float64 residuals:
+    x += R^{-1} R^{-T} A^T (b - A x) until the backward error is at most tol.
+
+    ``R`` is the n x n upper triangle of a possibly lower-accuracy QR
+    factorization of A.  Starts from x0 (default: the semi-normal solution
+    R^{-1} R^{-T} A^T b).  Returns (x, iterations, backward errors per
+    iteration).
+    """
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64).ravel()
+    R = np.asarray(R, dtype=np.float64)
+
+    def correction(v):
+        return back_substitution(R, forward_substitution_rt(R, (A.T @ v)[:, None]))[:, 0]
+
+    x = correction(b) if x0 is None else np.array(x0, dtype=np.float64)
+    history = [backward_error(A, x, b)]
+    it = 0
+    while history[-1] > tol and it < maxit:
+        x = x + correction(b - A @ x)
+        it += 1
+        history.append(backward_error(A, x, b))
+    return x, it, history

@@ -1022,6 +1022,39 @@ __device__ void gemm_sub(real* S, int lds, int nv, int w, const real* V, int ldv
   }
 }
 
+// Triangular solves of one ib x ib diagonal block for w right-hand-side
+// columns in shared memory (x = S + c ldS + b0), one warp per column, in
+// column (axpy) order: once x_r is final it is broadcast and every lane
+// removes its multiple from the rows still open.  Reciprocals of the
+// diagonal are taken once per block, all lanes at once (an FP64 division
+// costs hundreds of cycles on this GPU), into rinv (ib entries).  Rows at or
+// past nvalid (zero padding) get x = 0.
+//   upper = true:  T x = c (T upper, ld ldT), r = ib-1 .. 0
+//   upper = false: T^T x = c,                  r = 0 .. ib-1
+template <typename real, bool upper>
+__device__ void tri_block_solve(real* S, int ldS, int b0, int w, const real* T, int ldT, int ib, int nvalid,
+                                real* rinv) {
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  for (int t = threadIdx.x; t < ib; t += kThreads)
+    rinv[t] = (b0 + t < nvalid) ? real(1) / T[t + t * ldT] : real(0);
+  __syncthreads();
+  for (int c = wid; c < w; c += kThreads / 32) {
+    real* x = S + c * ldS + b0;
+    for (int q = 0; q < ib; ++q) {
+      const int r = upper ? ib - 1 - q : q;
+      const real xr = x[r] * rinv[r];
+      __syncwarp();
+      if (lane == 0) x[r] = xr;
+      if constexpr (upper) {
+        for (int t = lane; t < r; t += 32) x[t] = fma(-T[t + r * ldT], xr, x[t]);
+      } else {
+        for (int t = r + 1 + lane; t < ib; t += 32) x[t] = fma(-T[r + t * ldT], xr, x[t]);
+      }
+      __syncwarp();
+    }
+  }
+}
+
 // TRSM_UPD(k, l, j, s): C_k -= R_kl X_l on slab s of right-hand-side column j.
 template <typename real>
 __device__ void exec_trsm_upd(Ctx<real>& cx, const Inst& I, int k, int l, int j, int s) {
@@ -1060,14 +1093,7 @@ __device__ void exec_trsm_solve(Ctx<real>& cx, const Inst& I, int k, int j, int 
       cx.T[r + c * cx.ldT] = (r <= c) ? ldg_cg(R + (b0 + r) + static_cast<long long>(b0 + c) * nb) : real(0);
     }
     __syncthreads();
-    if (threadIdx.x < w) {
-      real* x = cx.S + threadIdx.x * cx.ldS + b0;
-      for (int r = ib - 1; r >= 0; --r) {
-        real v = x[r];
-        for (int t = r + 1; t < ib; ++t) v -= cx.T[r + t * cx.ldT] * x[t];
-        x[r] = (b0 + r < nvalid) ? v / cx.T[r + r * cx.ldT] : real(0);
-      }
-    }
+    tri_block_solve<real, true>(cx.S, cx.ldS, b0, w, cx.T, cx.ldT, ib, nvalid, cx.W);
     __syncthreads();
     if (b0 > 0) {
       load_block(cx.P, cx.ldP, R + static_cast<long long>(b0) * nb, nb, b0, ib);
@@ -1129,14 +1155,7 @@ __device__ void exec_trsmt_solve(Ctx<real>& cx, const Inst& I, int k, int j, int
       cx.T[r + c * cx.ldT] = (r <= c) ? ldg_cg(R + (b0 + r) + static_cast<long long>(b0 + c) * nb) : real(0);
     }
     __syncthreads();
-    if (threadIdx.x < w) {
-      real* x = cx.S + threadIdx.x * cx.ldS + b0;
-      for (int r = 0; r < ib; ++r) {
-        real v = x[r];
-        for (int t = 0; t < r; ++t) v -= cx.T[t + r * cx.ldT] * x[t];
-        x[r] = (b0 + r < nvalid) ? v / cx.T[r + r * cx.ldT] : real(0);
-      }
-    }
+    tri_block_solve<real, false>(cx.S, cx.ldS, b0, w, cx.T, cx.ldT, ib, nvalid, cx.W);
     __syncthreads();
     const int nbelow = nb - b0 - ib;
     if (nbelow > 0) {

@@ -69,3 +69,45 @@ def test_conditioned_problem_has_requested_condition_number():
         A, b, x = inputs.conditioned_ls_problem(200, 30, kappa, seed=2)
         s = np.linalg.svd(A, compute_uv=False)
         assert s[0] / s[-1] == pytest.approx(kappa, rel=1e-3 if kappa < 1e8 else 1e-1)
+
+
+def test_seminormal_refinement_with_exact_r_is_the_ls_solution():
+    """With the exact R, R^T R = A^T A, so the first semi-normal solve is the
+    normal-equations solution: one correction reaches the FP64 LS answer."""
+    A, b, _ = inputs.conditioned_ls_problem(200, 30, 1e3, seed=4)
+    R = np.linalg.qr(A, mode="r")
+    x, it, hist = L.seminormal_refinement(A, b, R, tol=1e-15, maxit=3)
+    x_ref = np.linalg.lstsq(A, b, rcond=None)[0]
+    assert it <= 2 and hist[-1] <= 1e-15
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-14 * 1e3
+
+
+@pytest.mark.parametrize("kappa", [1e1, 1e2])
+def test_seminormal_refinement_converges_for_well_conditioned_problems(kappa):
+    """An R perturbed by eps ~ 1e-7 relative (an FP32 factorization's size of
+    error) contracts the error by ~ 2 kappa eps per step."""
+    A, b, _ = inputs.conditioned_ls_problem(300, 40, kappa, seed=1)
+    E = 1e-7 * np.linalg.norm(A, 2) * inputs.normal_matrix(300, 40, 9) / np.sqrt(300)
+    R = _PerturbedSolver(A + E).R
+    x, it, hist = L.seminormal_refinement(A, b, R, tol=1e-14, maxit=20)
+    assert hist[-1] <= 1e-14 and it <= 6
+    x_ref = L.lstsq(A, b)
+    assert np.linalg.norm(x - x_ref) / np.linalg.norm(x_ref) <= 1e-12 * kappa
+    # geometric decrease while far from rounding level
+    for a, c in zip(hist[:-1], hist[1:]):
+        if c > 1e-15:
+            assert c < 0.1 * a
+
+
+def test_seminormal_refinement_diverges_when_kappa_eps_exceeds_one():
+    """R is the exact factor of A + E, so R^T R = (A+E)^T (A+E) and the
+    iteration matrix is similar to M^T M - I with M = A R^-1 = Q - E R^-1:
+    the contraction is about 2 kappa eps.  kappa eps = 1e5 * 1e-3 = 100: the
+    corrections grow (the regime the device leaves for the augmented-system
+    refinement)."""
+    A, b, _ = inputs.conditioned_ls_problem(300, 40, 1e5, seed=1)
+    E = 1e-3 * np.linalg.norm(A, 2) * inputs.normal_matrix(300, 40, 9) / np.sqrt(300)
+    R = _PerturbedSolver(A + E).R
+    x_ref = L.lstsq(A, b)
+    x, it, hist = L.seminormal_refinement(A, b, R, tol=0.0, maxit=4)
+    assert np.linalg.norm(x - x_ref) > np.linalg.norm(x_ref)
