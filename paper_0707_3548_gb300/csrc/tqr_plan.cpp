@@ -324,13 +324,17 @@ bool build_dag(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, st
 }
 
 // Seconds for one task on one CTA.  FP64: 1.19e12 flop/s over 152 SMs shared
-// by ctas_per_sm CTAs (measured DFMA rate); FP32 ~58x more.  Panels pay a
-// per-column latency (reductions and barriers).
+// by ctas_per_sm CTAs (measured DFMA rate).  FP32, from the device task
+// trace at nb = 128, ib = 16: update tasks run at ~60 GFLOP/s per CTA (two
+// per SM) after ~10 us of fixed cost (staging, descriptor, dependency
+// handshake), panels ~3.5 us per column.  Panels pay a per-column latency
+// (reductions and barriers).
 double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
-  const double sm_rate = (esize == 8 ? 1.19e12 : 69.0e12) / 152.0;
+  const double sm_rate = esize == 8 ? 1.19e12 / 152.0 : 2 * 60.0e9;
   const double rate = sm_rate / (ctas_per_sm > 0 ? ctas_per_sm : 1);
   const double nb = I.nb, ib = I.ib;
-  const double col_lat = 2.0e-6, blk_lat = 1.0e-6;
+  const double col_lat = esize == 8 ? 2.0e-6 : 3.5e-6, blk_lat = 1.0e-6;
+  const double fixed = esize == 8 ? 0.0 : 10.0e-6;
   double w = I.cs;
   if (t.j >= I.q) {
     const double c0 = static_cast<double>(t.j - I.q) * I.nb + static_cast<double>(t.s) * I.cs;
@@ -415,7 +419,7 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
     default:
       break;
   }
-  return f / rate + lat;
+  return f / rate + lat + fixed;
 }
 
 static int kind_rank(int kind) {
