@@ -1228,14 +1228,26 @@ __device__ void exec_ssrfb2(Ctx<real>& cx, const Inst& I, int k, int h, int rows
   real* Ct = tile_ptr<real>(I, k, j) + soff;
   const int w = slab_width(I, j, s);
   const int nblk = nb / ib;
-  for (int a = 0; a < rows; ++a) bulk_cols(cx, cx.S + a * nb, cx.ldS, tile_ptr<real>(I, h + a, j) + soff, nb, nb, w);
+  const uint32_t cb = static_cast<uint32_t>(nb) * sizeof(real);
+  // each block's V pieces go out as one bulk phase before its T and Top
+  // loads, so the copy and the loads overlap (the first phase also carries
+  // the bottom slabs)
   for (int bb = 0; bb < nblk; ++bb) {
     const int blk = trans ? bb : nblk - 1 - bb;
     const int l0 = blk * ib;
+    if (threadIdx.x < 32) {
+      bulk_expect(cx, cb * rows * (ib + (bb == 0 ? w : 0)));
+      __syncwarp();
+      if (bb == 0)
+        for (int a = 0; a < rows; ++a)
+          bulk_issue_cols(cx, cx.S + a * nb, cx.ldS, tile_ptr<real>(I, h + a, j) + soff, nb, nb, w);
+      for (int a = 0; a < rows; ++a)
+        bulk_issue_cols(cx, cx.P + a * nb, cx.ldP, tile_ptr<real>(I, h + a, k) + static_cast<long long>(l0) * nb,
+                        nb, nb, ib);
+    }
     load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
     load_block(cx.Top, ib, Ct + l0, nb, ib, w);
-    for (int a = 0; a < rows; ++a)
-      bulk_cols(cx, cx.P + a * nb, cx.ldP, tile_ptr<real>(I, h + a, k) + static_cast<long long>(l0) * nb, nb, nb, ib);
+    bulk_wait(cx);
     __syncthreads();
     apply_any<real>(cx.P, cx.ldP, nv, nullptr, 0, cx.Top, ib, cx.S, cx.ldS, cx.T, cx.ldT, ib, w, cx.W, cx.Part, trans);
     store_block(Ct + l0, nb, cx.Top, ib, ib, w);
@@ -1570,13 +1582,25 @@ __device__ void exec_ssssm(Ctx<real>& cx, const Inst& I, int k, int i, int j, in
   const long long soff = static_cast<long long>(s) * I.cs * nb;
   real* Ct = tile_ptr<real>(I, k, j) + soff;
   const int w = slab_width(I, j, s);
-  for (int a = 0; a < rows; ++a) bulk_cols(cx, cx.S + a * nb, cx.ldS, tile_ptr<real>(I, i + a, j) + soff, nb, nb, w);
+  const uint32_t cb = static_cast<uint32_t>(nb) * sizeof(real);
+  // each block's L pieces go out as one bulk phase before its other loads,
+  // so the copy and the loads overlap (the first phase also carries the
+  // bottom slabs)
   for (int l0 = 0; l0 < nb; l0 += ib) {
+    if (threadIdx.x < 32) {
+      bulk_expect(cx, cb * rows * (ib + (l0 == 0 ? w : 0)));
+      __syncwarp();
+      if (l0 == 0)
+        for (int a = 0; a < rows; ++a)
+          bulk_issue_cols(cx, cx.S + a * nb, cx.ldS, tile_ptr<real>(I, i + a, j) + soff, nb, nb, w);
+      for (int a = 0; a < rows; ++a)
+        bulk_issue_cols(cx, cx.P + a * nb, cx.ldP, tile_ptr<real>(I, i + a, k) + static_cast<long long>(l0) * nb,
+                        nb, nb, ib);
+    }
     load_block(cx.T, cx.ldT, Lg + static_cast<long long>(l0) * ib, ib, ib, ib);
     load_block(cx.Top, ib, Ct + l0, nb, ib, w);
     if (threadIdx.x < ib) pv[threadIdx.x] = ldg_cg(pg + l0 + threadIdx.x);
-    for (int a = 0; a < rows; ++a)
-      bulk_cols(cx, cx.P + a * nb, cx.ldP, tile_ptr<real>(I, i + a, k) + static_cast<long long>(l0) * nb, nb, nb, ib);
+    bulk_wait(cx);
     __syncthreads();
     swap_rows_pair<real>(cx.Top, ib, cx.S, cx.ldS, nv, w, pv, ib);
     __syncthreads();
