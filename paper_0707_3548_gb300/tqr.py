@@ -508,6 +508,47 @@ def trace_records(words):
     }
 
 
+TASK_KIND_NAMES = ("GEQRT", "TSQRT", "LARFB", "SSRFB", "LARFB_N", "SSRFB_N", "TRSM_UPD", "TRSM_SOLVE",
+                   "TRSMT_UPD", "TRSMT_SOLVE", "TTQRT", "TTMQR", "TTMQR_N", "GETRF", "GESSM", "TSTRF", "SSSSM",
+                   "TSQRT2", "SSRFB2", "SSRFB2_N", "TSTRF2", "SSSSM2")
+
+
+def trace_chrome(words, path=None):
+    """Chrome-trace ("traceEvents") form of a task trace: one complete event
+    per task on a row of its SM (tasks that overlap on one SM -- its two CTAs
+    -- go to separate rows), times in microseconds from the first ticket, the
+    task's indices and its dependency wait in args.  Written as JSON to path
+    when given; returns the dict."""
+    import json
+
+    r = trace_records(words)
+    n = len(r["kind"])
+    t0 = int(r["ticket_ns"].min()) if n else 0
+    rows_end = {}
+    events = []
+    for a in np.argsort(r["start_ns"], kind="stable"):
+        sm, st, en = int(r["sm"][a]), int(r["start_ns"][a]), int(r["end_ns"][a])
+        lanes = rows_end.setdefault(sm, [])
+        lane = next((x for x, e in enumerate(lanes) if e <= st), len(lanes))
+        if lane == len(lanes):
+            lanes.append(en)
+        else:
+            lanes[lane] = en
+        kind = int(r["kind"][a])
+        events.append({
+            "name": TASK_KIND_NAMES[kind] if kind < len(TASK_KIND_NAMES) else str(kind), "ph": "X",
+            "ts": (st - t0) / 1e3, "dur": (en - st) / 1e3, "pid": 0, "tid": sm * 4 + lane,
+            "args": {"k": int(r["k"][a]), "i": int(r["i"][a]), "j": int(r["j"][a]), "s": int(r["s"][a]),
+                     "l": int(r["l"][a]), "inst": int(r["inst"][a]),
+                     "wait_us": (st - int(r["ticket_ns"][a])) / 1e3},
+        })
+    out = {"traceEvents": events, "displayTimeUnit": "ms"}
+    if path is not None:
+        with open(path, "w") as f:
+            json.dump(out, f)
+    return out
+
+
 class Server:
     """Thin wrapper of the tqr_server_* calls (device tensors only)."""
 

@@ -106,3 +106,21 @@ def test_debug_shape_override_validation(lib):
 def test_debug_trace_rejects_a_negative_capacity():
     import ctypes
     assert tqr.lib().tqr_debug_trace(ctypes.c_void_p(256), -1) == -2
+
+
+def test_trace_decoding_and_chrome_form():
+    """Trace words as the kernel writes them (host-built here): decoding keeps
+    the written rows, and the Chrome form puts overlapping tasks of one SM on
+    separate rows with times from the first ticket."""
+    w = np.zeros((4, 8), dtype=np.int64)
+    w[0] = [1000, 2000, 5000, 7 | (3 << 16) | (1 << 32), 2, 5, 4, 1 | (6 << 32)]
+    w[1] = [1500, 3000, 4000, 7 | (1 << 16), 2, 3, 2, 0]
+    w[2] = [1200, 6000, 9000, 8 | (0 << 16), 3, 3, 3, 0]
+    r = tqr.trace_records(w)
+    assert list(r["sm"]) == [7, 7, 8] and list(r["kind"]) == [3, 1, 0]
+    assert list(r["inst"]) == [1, 0, 0] and list(r["s"]) == [1, 0, 0] and list(r["l"]) == [6, 0, 0]
+    ev = tqr.trace_chrome(w)["traceEvents"]
+    by_name = {e["name"]: e for e in ev}
+    assert by_name["SSRFB"]["ts"] == 1.0 and by_name["SSRFB"]["dur"] == 3.0
+    assert by_name["SSRFB"]["tid"] != by_name["TSQRT"]["tid"]      # overlap on SM 7
+    assert by_name["GEQRT"]["tid"] == 8 * 4 and by_name["GEQRT"]["args"]["wait_us"] == 4.8

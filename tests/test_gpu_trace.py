@@ -37,6 +37,7 @@ def test_trace_covers_algorithm_1_and_respects_the_dag(m, n, nb, ib):
     assert np.array_equal(F, to_host(dA)) and np.array_equal(T, T2.cpu().numpy())
 
     r = tqr.trace_records(words)
+    assert len(tqr.trace_chrome(words)["traceEvents"]) == len(r["kind"])
     p, q = -(-m // nb), -(-n // nb)
     kt = min(p, q)
     assert np.all(r["ticket_ns"] <= r["start_ns"]) and np.all(r["start_ns"] <= r["end_ns"])
