@@ -23,7 +23,7 @@ def test_opcount_tends_to_five_halves():
         assert ratio == pytest.approx(1.25, rel=0.02)
 
 
-def _survey_edges(p, q):
+def _listed_edges(p, q):
     """The dependency list written independently from the kernels' read/write
     sets: GEQRT(k) <- SSRFB(k-1,k,k); LARFB(k,j) <- GEQRT(k), SSRFB(k-1,k,j);
     TSQRT(k,i) <- TSQRT(k,i-1) or GEQRT(k), SSRFB(k-1,i,k);
@@ -53,7 +53,7 @@ def _survey_edges(p, q):
 @pytest.mark.parametrize("p,q", [(2, 2), (3, 3), (4, 2), (2, 4), (4, 4)])
 def test_dataflow_dag_matches_dependency_list(p, q):
     red = D.reduced_edges(p, q)
-    listed = _survey_edges(p, q)
+    listed = _listed_edges(p, q)
     # every listed edge is implied by the data-flow DAG, and the data-flow
     # DAG's minimal edges are all listed
     full = D.edges(p, q)

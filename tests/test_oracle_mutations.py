@@ -119,3 +119,46 @@ def test_mutation_reflector_missing_scaling(monkeypatch):
         return tau, v2 * 1.0000001, beta
     monkeypatch.setattr(TL, "householder", bad)
     assert not _pins_hold()
+
+
+# ---- least-squares refinement ------------------------------------------------
+from oracle import lstsq as LSQ  # noqa: E402
+
+
+def _seminormal_pins_hold():
+    """The semi-normal pins: with the exact R one correction reaches the LS
+    solution, and with an R perturbed by 1e-7 the backward error falls
+    geometrically to the rounding level."""
+    A, b, _ = inputs.conditioned_ls_problem(120, 20, 1e2, seed=3)
+    x_ref = np.linalg.lstsq(A, b, rcond=None)[0]
+    R = np.linalg.qr(A, mode="r")
+    try:
+        x, it, hist = LSQ.seminormal_refinement(A, b, R, tol=1e-15, maxit=3)
+        ok_exact = hist[-1] <= 1e-15 and np.linalg.norm(x - x_ref) <= 1e-10 * np.linalg.norm(x_ref)
+        E = 1e-7 * np.linalg.norm(A, 2) * inputs.normal_matrix(120, 20, 4) / np.sqrt(120)
+        Rp = np.linalg.qr(A + E, mode="r")
+        x, it, hist = LSQ.seminormal_refinement(A, b, Rp, tol=1e-14, maxit=20)
+        ok_pert = hist[-1] <= 1e-14 and it <= 6
+    except (ValueError, np.linalg.LinAlgError, FloatingPointError):
+        return False
+    return bool(ok_exact and ok_pert)
+
+
+def test_unmutated_seminormal_refinement_passes():
+    assert _seminormal_pins_hold()
+
+
+def test_mutation_seminormal_without_the_transposed_solve(monkeypatch):
+    # R^-1 R^-1 A^T e in place of R^-1 R^-T A^T e
+    monkeypatch.setattr(LSQ, "forward_substitution_rt", LSQ.back_substitution)
+    assert not _seminormal_pins_hold()
+
+
+def test_mutation_seminormal_with_the_residual_sign_flipped(monkeypatch):
+    orig = LSQ.back_substitution
+
+    def flipped(R, C):
+        return -orig(R, C)
+
+    monkeypatch.setattr(LSQ, "back_substitution", flipped)
+    assert not _seminormal_pins_hold()
