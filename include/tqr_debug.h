@@ -123,8 +123,9 @@ int tqr_debug_fp64_peak(double* tflops, void* stream);
  * inst << 32; k; i; j; s | l << 32.  Tickets are positions in the launch's
  * ordered task list, so concurrent launches overwrite each other's records.
  * buffer: device memory of 64 * capacity bytes owned by the caller, or NULL
- * to stop tracing (capacity is then ignored).  Synchronous.  Returns 0, -2
- * for a negative capacity, or TQR_ERR_CUDA.
+ * to stop tracing (capacity is then ignored).  Synchronous.  Returns 0, -1
+ * when buffer is not 8-byte aligned device memory, -2 for a negative
+ * capacity, or TQR_ERR_CUDA.
  */
 int tqr_debug_trace(void* buffer, int64_t capacity);
 

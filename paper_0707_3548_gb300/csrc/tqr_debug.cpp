@@ -172,6 +172,10 @@ int tqr_debug_fp64_peak(double* tflops, void* stream) {
 
 int tqr_debug_trace(void* buffer, int64_t capacity) {
   if (buffer != nullptr && capacity < 0) return -2;
+  // the kernels write the records: only device memory, 8-byte aligned
+  if (buffer != nullptr &&
+      (ptr_kind(buffer) != PTR_DEVICE || (reinterpret_cast<uintptr_t>(buffer) & 7) != 0))
+    return -1;
   return set_trace(buffer, buffer != nullptr ? capacity : 0) == cudaSuccess ? 0 : TQR_ERR_CUDA;
 }
 

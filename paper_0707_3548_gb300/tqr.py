@@ -489,7 +489,8 @@ def tqr_debug_trace(buffer):
     if buffer is None:
         _check("tqr_debug_trace", lib().tqr_debug_trace(None, 0))
         return
-    if buffer.dim() != 2 or buffer.shape[1] != 8 or buffer.element_size() != 8 or not buffer.is_contiguous():
+    if (not getattr(buffer, "is_cuda", False) or buffer.dim() != 2 or buffer.shape[1] != 8
+            or buffer.element_size() != 8 or not buffer.is_contiguous()):
         raise ValueError("trace buffer must be a contiguous (capacity, 8) 64-bit device tensor")
     _check("tqr_debug_trace", lib().tqr_debug_trace(_vp(buffer.data_ptr()), buffer.shape[0]))
 

@@ -108,6 +108,14 @@ def test_debug_trace_rejects_a_negative_capacity():
     assert tqr.lib().tqr_debug_trace(ctypes.c_void_p(256), -1) == -2
 
 
+def test_debug_trace_rejects_host_memory():
+    import torch
+    host = np.zeros((4, 8), dtype=np.int64)
+    assert tqr.lib().tqr_debug_trace(host.ctypes.data, 4) == -1
+    with pytest.raises(ValueError):
+        tqr.tqr_debug_trace(torch.zeros((4, 8), dtype=torch.int64))
+
+
 def test_trace_decoding_and_chrome_form():
     """Trace words as the kernel writes them (host-built here): decoding keeps
     the written rows, and the Chrome form puts overlapping tasks of one SM on
