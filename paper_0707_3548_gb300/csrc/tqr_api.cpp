@@ -81,19 +81,22 @@ long long wait_limit_ns() { return g_wait_limit_ms * 1000000LL; }
 bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* smem, int rows) {
   const int kSmemPerSM = 233472, kSmemPerBlock = 232448, kReserved = 1024;
   int best_cs = 0, best_occ = 0, best_smem = 0;
+  // a forced width (tuning override) where it fits, else the automatic choice
   const int forced = g_force_cs.load();
-  for (int c : {32, 16, 8}) {
-    if (c > nb || nb % c != 0) continue;
-    if (forced > 0 && c != forced) continue;
-    if (ib * c > kThreads * kMaxOutPerThread) continue;
-    const SmemLayout L = smem_layout(nb, ib, c, esize, rows);
-    if (L.bytes > kSmemPerBlock) continue;
-    int occ = kSmemPerSM / (L.bytes + kReserved);
-    if (occ > 2) occ = 2;
-    if (occ > best_occ) {
-      best_occ = occ;
-      best_cs = c;
-      best_smem = L.bytes;
+  for (int pass = forced > 0 ? 0 : 1; pass < 2 && best_occ == 0; ++pass) {
+    for (int c : {32, 16, 8}) {
+      if (c > nb || nb % c != 0) continue;
+      if (pass == 0 && c != forced) continue;
+      if (ib * c > kThreads * kMaxOutPerThread) continue;
+      const SmemLayout L = smem_layout(nb, ib, c, esize, rows);
+      if (L.bytes > kSmemPerBlock) continue;
+      int occ = kSmemPerSM / (L.bytes + kReserved);
+      if (occ > 2) occ = 2;
+      if (occ > best_occ) {
+        best_occ = occ;
+        best_cs = c;
+        best_smem = L.bytes;
+      }
     }
   }
   if (best_occ == 0) return false;
