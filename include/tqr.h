@@ -50,7 +50,8 @@ enum {
   TQR_ERR_NOCONV = 5,      /* least squares: refinement did not reach tol */
   TQR_ERR_BUSY = 6,        /* batch / server: no free slot right now */
   TQR_ERR_UNSUPPORTED = 7, /* valid arguments outside what this build supports */
-  TQR_ERR_TOO_LARGE = 8    /* tqr_factor_noalloc: problem exceeds its static scratch */
+  TQR_ERR_TOO_LARGE = 8,   /* tqr_factor_noalloc: problem exceeds its static scratch */
+  TQR_ERR_NONFINITE = 9    /* least squares: A or B holds a NaN or an infinity */
 };
 
 enum { TQR_PREC_FP64 = 0, TQR_PREC_FP32 = 1 };
@@ -284,10 +285,11 @@ int tqr_lu_solve_pairs(int64_t n, int64_t nrhs, const double* A, int64_t lda, in
  * Tall problems use the reduction-tree variant when the library's model of
  * the task graph predicts a shorter run (see tqr_factor_tree).
  * Synchronizes the stream (the refinement loop needs the backward error on
- * the host).  Returns TQR_ERR_RANK for a numerically rank-deficient R and
- * TQR_ERR_NOCONV when refinement stalls (neither the backward error nor the
- * correction halves in 3 steps) or reaches maxit with the backward error
- * above tol; X then holds the best iterate.
+ * the host).  Returns TQR_ERR_NONFINITE when A or B holds a NaN or an
+ * infinity (they propagate into X), TQR_ERR_RANK for a numerically
+ * rank-deficient R and TQR_ERR_NOCONV when refinement stalls (neither the
+ * backward error nor the correction halves in 3 steps) or reaches maxit with
+ * the backward error above tol; X then holds the best iterate.
  */
 int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda,
                  const double* B, int64_t ldb, double* X, int64_t ldx, int prec,

@@ -137,6 +137,21 @@ __global__ void __launch_bounds__(kLsThreads) col_sumsq(const double* __restrict
   }
 }
 
+// out[0] = x[0] + ... + x[n-1] (one block, fixed order).
+__global__ void __launch_bounds__(kLsThreads) vec_sum(const double* __restrict__ x, int n, double* __restrict__ out) {
+  __shared__ double red[kLsThreads / 32];
+  double s = 0.0;
+  for (int r = threadIdx.x; r < n; r += kLsThreads) s += x[r];
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int w = 0; w < kLsThreads / 32; ++w) t += red[w];
+    out[0] = t;
+  }
+}
+
 // min and max |R(i, i)| over i < n of the tiled factor (diagonal tiles).
 template <typename real>
 __global__ void diag_minmax(const real* __restrict__ Ab, int p, int nb, int n, double* __restrict__ out) {
@@ -345,8 +360,9 @@ int LsJob::factor_solve(const double* A, long long lda, const double* B, long lo
       diag_minmax<float><<<1, kLsThreads, 0, st>>>(static_cast<float*>(I.A), I.p, nb, n, dmm);
     double* nA2 = reinterpret_cast<double*>(ws + o_nrm) + 4 * rhs_cap;
     double* colsq = reinterpret_cast<double*>(ws + o_g);
+    // ||A||_F^2: the columns' sums of squares, then their sum
     col_sumsq<<<n, kLsThreads, 0, st>>>(A, lda, m, colsq);
-    col_sumsq<<<1, kLsThreads, 0, st>>>(colsq, n, n, nA2);
+    vec_sum<<<1, kLsThreads, 0, st>>>(colsq, n, nA2);
     if (cudaGetLastError() != cudaSuccess) s = TQR_ERR_CUDA;
   }
   factored = (s == TQR_OK);
@@ -412,6 +428,12 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
   };
   terms();
   read_back();
+  if (status == TQR_OK) {
+    // a NaN or an infinity in A or B shows in their FP64 norms
+    bool finite = std::isfinite(hn[4 * R]);
+    for (int c = 0; c < nrhs; ++c) finite = finite && std::isfinite(hn[2 * R + c]);
+    if (!finite) status = TQR_ERR_NONFINITE;
+  }
   if (status == TQR_OK) {
     // numerical rank test on R with the FP64 unit roundoff in both precisions:
     // an FP32 factor with a small pivot may still refine to an FP64 answer,

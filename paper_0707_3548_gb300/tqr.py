@@ -31,11 +31,13 @@ TQR_ERR_NOCONV = 5
 TQR_ERR_BUSY = 6
 TQR_ERR_UNSUPPORTED = 7
 TQR_ERR_TOO_LARGE = 8
+TQR_ERR_NONFINITE = 9
 TQR_PREC_FP64 = 0
 TQR_PREC_FP32 = 1
 
 _ERRNAMES = {1: "TQR_ERR_CUDA", 2: "TQR_ERR_NOMEM", 3: "TQR_ERR_TIMEOUT", 4: "TQR_ERR_RANK",
-             5: "TQR_ERR_NOCONV", 6: "TQR_ERR_BUSY", 7: "TQR_ERR_UNSUPPORTED", 8: "TQR_ERR_TOO_LARGE"}
+             5: "TQR_ERR_NOCONV", 6: "TQR_ERR_BUSY", 7: "TQR_ERR_UNSUPPORTED", 8: "TQR_ERR_TOO_LARGE",
+             9: "TQR_ERR_NONFINITE"}
 
 _lib = None
 

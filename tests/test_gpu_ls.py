@@ -22,6 +22,34 @@ def test_solve_fp64_matches_oracle(m, n, nrhs, nb, ib):
     assert abs(berr - LS.backward_error(A, to_host(X), B)) <= 1e-15 + 0.05 * berr
 
 
+def test_reported_backward_error_is_the_oracles():
+    """Without refinement (maxit = 0) the FP32 solution's backward error is
+    well above rounding noise, so the device's value (FP64 residual, ||A||_F,
+    ||x||, ||b||) must equal the oracle's for the returned x closely."""
+    torch_cuda()
+    A, b, _ = inputs.conditioned_ls_problem(1500, 400, 1e3, seed=2)
+    X, it, berr, rc = tqr.tqr_solve_ls(to_dev(A), to_dev(b[:, None]), prec=tqr.TQR_PREC_FP32, tol=1e-12,
+                                       maxit=0, nb=64, ib=16, check=False)
+    assert rc == tqr.TQR_ERR_NOCONV and it == 0
+    ref = LS.backward_error(A, to_host(X)[:, 0], b)
+    assert ref > 1e-12
+    assert abs(berr - ref) <= 1e-6 * ref
+
+
+def test_nonfinite_input_is_reported():
+    torch_cuda()
+    A = inputs.normal_matrix(200, 60, 7)
+    B = inputs.normal_matrix(200, 2, 8)
+    A_nan = A.copy()
+    A_nan[17, 5] = np.nan
+    _, _, _, rc = tqr.tqr_solve_ls(to_dev(A_nan), to_dev(B), nb=32, ib=8, check=False)
+    assert rc == tqr.TQR_ERR_NONFINITE
+    B_inf = B.copy()
+    B_inf[3, 1] = np.inf
+    _, _, _, rc = tqr.tqr_solve_ls(to_dev(A), to_dev(B_inf), prec=tqr.TQR_PREC_FP32, nb=32, ib=8, check=False)
+    assert rc == tqr.TQR_ERR_NONFINITE
+
+
 @pytest.mark.parametrize("kappa", [1e2, 1e5])
 def test_solve_fp32_refined_reaches_fp64_accuracy(kappa):
     torch_cuda()
