@@ -370,6 +370,10 @@ int tqr_batch_wait(uint64_t ticket, int* status_per_item);
  *   tqr_server_poll(server, request, &done, &status, &iters, &berr,
  *                   &latency_ms, &reused)   non-blocking; once done the
  *       request is forgotten.  latency_ms counts from submit to completion.
+ *       status: that of tqr_solve_ls, or TQR_ERR_NOMEM for a request whose
+ *       workspace exceeds the whole budget (refused at admission, not
+ *       queued forever), TQR_ERR_UNSUPPORTED for a shape the kernels cannot
+ *       take.
  *   tqr_server_wait(...)                     blocking form
  *   tqr_server_stats(server, out[8])         completed, p50 and p99 latency
  *       (ms) over completed requests, resident+running bytes, requests that

@@ -171,15 +171,26 @@ static void worker(tqr_server* S) {
       auto job = std::make_shared<Entry>();
       int nb = 0, ib = 0;
       autotune((*it)->m, (*it)->n, &nb, &ib);
-      if (!job->job.init(static_cast<int>((*it)->m), static_cast<int>((*it)->n), 16, nb, ib, (*it)->prec,
-                         S->grid_cap)) {
-        (*it)->status = TQR_ERR_UNSUPPORTED;
+      auto refuse = [&](int code) {
+        (*it)->status = code;
+        (*it)->t_start = (*it)->t_end = Clock::now();
         (*it)->done = true;
+        S->completed++;
+        S->failed++;
         S->pending.erase(it);
         S->cv_done.notify_all();
+      };
+      if (!job->job.init(static_cast<int>((*it)->m), static_cast<int>((*it)->n), 16, nb, ib, (*it)->prec,
+                         S->grid_cap)) {
+        refuse(TQR_ERR_UNSUPPORTED);
         break;
       }
       job->bytes = job->job.bytes_with_acopy();
+      if (job->bytes > S->budget) {
+        // can never be admitted: refuse it instead of waiting for room
+        refuse(TQR_ERR_NOMEM);
+        break;
+      }
       const bool head = (it == S->pending.begin());
       if (S->in_use + job->bytes > S->budget && !(head && make_room(S, job->bytes, st))) {
         if (head) break;  // wait for memory to free up

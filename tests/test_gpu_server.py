@@ -89,3 +89,29 @@ def test_server_budget_eviction_keeps_working():
         assert st["bytes_in_use"] <= 24 << 20
     finally:
         s.close()
+
+
+def test_request_larger_than_the_budget_is_refused():
+    """A request whose workspace exceeds the whole HBM budget finishes with
+    TQR_ERR_NOMEM instead of waiting for room; a request that fits still runs."""
+    import time
+
+    torch = torch_cuda()
+    s = tqr.Server(16 << 20, slots=1)
+    try:
+        big = inputs.normal_matrix(3000, 1000, 90)          # 24 MB of A alone
+        Xb = tqr.colmajor(torch.zeros((1000, 1), dtype=torch.float64, device="cuda"))
+        rid = s.submit(0, to_dev(big), to_dev(inputs.normal_matrix(3000, 1, 91)), Xb)
+        info, deadline = None, time.time() + 60
+        while info is None and time.time() < deadline:
+            info = s.poll(rid)
+            time.sleep(0.01)
+        assert info is not None and info["status"] == tqr.TQR_ERR_NOMEM
+        A = inputs.normal_matrix(300, 100, 92)
+        B = inputs.normal_matrix(300, 2, 93)
+        X = tqr.colmajor(torch.zeros((100, 2), dtype=torch.float64, device="cuda"))
+        info = s.wait(s.submit(1, to_dev(A), to_dev(B), X))
+        assert info["status"] == 0
+        assert np.allclose(to_host(X), LS.lstsq(A, B), atol=1e-10)
+    finally:
+        s.close()
