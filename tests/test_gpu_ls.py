@@ -79,3 +79,21 @@ def test_rank_deficient_reports_rank():
     B = inputs.normal_matrix(200, 1, 6)
     X, it, berr, rc = tqr.tqr_solve_ls(to_dev(A), to_dev(B), nb=32, ib=8, check=False)
     assert rc == tqr.TQR_ERR_RANK
+
+
+def test_full_size_least_squares_16384x4096():
+    """The benchmark's least-squares launch (A 16384 x 4096 = U diag(sigma) V^T,
+    kappa 1e2, nb 128, ib 16): the FP32-refined solution reaches backward
+    error <= 1e-12, recomputed here in FP64 from the returned x, and agrees
+    with the FP64 solve, which meets the same bound."""
+    torch_cuda()
+    A, b, _ = inputs.conditioned_ls_problem(16384, 4096, 1e2, seed=0)
+    dA, db = to_dev(A), to_dev(b[:, None])
+    X64, _, _, rc64 = tqr.tqr_solve_ls(dA, db, nb=128, ib=16, check=False)
+    X32, it, berr, rc32 = tqr.tqr_solve_ls(dA, db, prec=tqr.TQR_PREC_FP32, tol=1e-12, maxit=30, nb=128, ib=16,
+                                           check=False)
+    assert rc64 == tqr.TQR_OK and rc32 == tqr.TQR_OK and it >= 1
+    x64, x32 = to_host(X64)[:, 0], to_host(X32)[:, 0]
+    assert LS.backward_error(A, x64, b) <= 1e-12
+    assert LS.backward_error(A, x32, b) <= 1e-12
+    assert np.linalg.norm(x32 - x64) <= 1e-12 * np.linalg.norm(x64)
