@@ -75,3 +75,28 @@ def test_tall_least_squares_through_tree(prec):
     X, it, berr, rc = tqr.tqr_solve_ls(to_dev(A), to_dev(b), prec=prec, nb=32, ib=16)
     assert rc == 0 and berr <= 1e-12
     assert np.allclose(to_host(X), LS.lstsq(A, b), atol=1e-11)
+
+
+def test_full_size_sampled_tall_skinny_tree():
+    """65536 x 2048 N(0,1), nb 128, ib 16, the library's domain choice (the
+    benchmark's tall-skinny launch): R's leading 256 x 256 block equals the
+    oracle's QR of A's first 256 columns up to row signs, and Q R reproduces
+    sampled columns of A."""
+    torch = torch_cuda()
+    m, n = 65536, 2048
+    A = inputs.normal_matrix(m, n, 0)
+    dA = to_dev(A)
+    T, D = tqr.tqr_factor_tree(dA, 128, 16, 0)
+    torch.cuda.synchronize()
+    assert D > 0
+    lead = dA[:256, :256].cpu().numpy()
+    Fo, _ = H.geqr2(A[:, :256])
+    assert np.linalg.norm(H.sign_normalize(np.triu(lead)) - H.sign_normalize(np.triu(Fo[:256]))) / \
+        np.linalg.norm(Fo[:256]) <= 1e-11
+    cols = [0, 1, 127, 128, 1023, 2047]
+    Rs = torch.zeros((m, len(cols)), dtype=torch.float64, device="cuda")
+    Rs[:n] = torch.triu(dA[:n, :n])[:, cols]
+    Rs = tqr.colmajor(Rs)
+    tqr.tqr_apply_qt_tree("N", dA, 128, 16, D, T, Rs)
+    err = np.linalg.norm(to_host(Rs) - A[:, cols]) / np.linalg.norm(A[:, cols])
+    assert err <= 10 * m * 2.0 ** -53
