@@ -552,6 +552,31 @@ def trace_chrome(words, path=None):
     return out
 
 
+def trace_summary(words, ctas=None):
+    """Per task kind: count, mean / total execution time and mean dependency
+    wait (microseconds), plus the launch's span (first ticket to last end)
+    and, given the number of CTAs, the fraction of CTA time spent
+    executing."""
+    r = trace_records(words)
+    n = len(r["kind"])
+    if n == 0:
+        return {"tasks": 0, "span_us": 0.0, "kinds": {}}
+    t0 = int(r["ticket_ns"].min())
+    span = (int(r["end_ns"].max()) - t0) / 1e3
+    ex = (r["end_ns"] - r["start_ns"]) / 1e3
+    wt = (r["start_ns"] - r["ticket_ns"]) / 1e3
+    kinds = {}
+    for k in np.unique(r["kind"]):
+        sel = r["kind"] == k
+        name = TASK_KIND_NAMES[int(k)] if int(k) < len(TASK_KIND_NAMES) else str(int(k))
+        kinds[name] = {"count": int(sel.sum()), "mean_us": float(ex[sel].mean()), "total_us": float(ex[sel].sum()),
+                       "mean_wait_us": float(wt[sel].mean())}
+    out = {"tasks": n, "span_us": span, "kinds": kinds}
+    if ctas:
+        out["busy_fraction"] = float(ex.sum() / (span * ctas)) if span > 0 else 0.0
+    return out
+
+
 class Server:
     """Thin wrapper of the tqr_server_* calls (device tensors only)."""
 

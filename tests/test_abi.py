@@ -132,3 +132,15 @@ def test_trace_decoding_and_chrome_form():
     assert by_name["SSRFB"]["ts"] == 1.0 and by_name["SSRFB"]["dur"] == 3.0
     assert by_name["SSRFB"]["tid"] != by_name["TSQRT"]["tid"]      # overlap on SM 7
     assert by_name["GEQRT"]["tid"] == 8 * 4 and by_name["GEQRT"]["args"]["wait_us"] == 4.8
+
+
+def test_trace_summary():
+    w = np.zeros((3, 8), dtype=np.int64)
+    w[0] = [0, 1000, 5000, 0 | (3 << 16), 0, 1, 1, 0]
+    w[1] = [0, 2000, 4000, 1 | (3 << 16), 0, 2, 1, 0]
+    w[2] = [500, 5000, 6000, 0 | (0 << 16), 1, 1, 1, 0]
+    sm = tqr.trace_summary(w, ctas=2)
+    assert sm["tasks"] == 3 and sm["span_us"] == 6.0
+    assert sm["kinds"]["SSRFB"] == {"count": 2, "mean_us": 3.0, "total_us": 6.0, "mean_wait_us": 1.5}
+    assert sm["kinds"]["GEQRT"]["mean_wait_us"] == 4.5
+    assert sm["busy_fraction"] == 7.0 / 12.0
