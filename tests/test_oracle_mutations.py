@@ -162,3 +162,38 @@ def test_mutation_seminormal_with_the_residual_sign_flipped(monkeypatch):
 
     monkeypatch.setattr(LSQ, "back_substitution", flipped)
     assert not _seminormal_pins_hold()
+
+
+def _augmented_pins_hold(solver_cls=LSQ.QRSolver):
+    """The augmented-system pins: with an R and Q perturbed by 1e-7 the
+    refinement reaches backward error 1e-14 and the LS solution."""
+    A, b, _ = inputs.conditioned_ls_problem(150, 25, 1e2, seed=5)
+    x_ref = np.linalg.lstsq(A, b, rcond=None)[0]
+    E = 1e-7 * np.linalg.norm(A, 2) * inputs.normal_matrix(150, 25, 6) / np.sqrt(150)
+    try:
+        x, r, it, hist = LSQ.augmented_refinement(A, b, solver_cls(A + E), tol=1e-14, maxit=20)
+    except (ValueError, np.linalg.LinAlgError, FloatingPointError):
+        return False
+    return bool(hist[-1] <= 1e-14 and np.linalg.norm(x - x_ref) <= 1e-10 * np.linalg.norm(x_ref))
+
+
+def test_unmutated_augmented_refinement_passes():
+    assert _augmented_pins_hold()
+
+
+def test_mutation_augmented_with_h_added(monkeypatch):
+    # dx = R^-1 (d1 + h) in place of R^-1 (d1 - h)
+    orig = LSQ.forward_substitution_rt
+    monkeypatch.setattr(LSQ, "forward_substitution_rt", lambda R, G: -orig(R, G))
+    assert not _augmented_pins_hold()
+
+
+def test_mutation_augmented_with_q_and_qt_swapped():
+    class Swapped(LSQ.QRSolver):
+        def qt(self, B):
+            return super().q(B)
+
+        def q(self, B):
+            return super().qt(B)
+
+    assert not _augmented_pins_hold(Swapped)
