@@ -11,7 +11,7 @@ Backward error (the paper is silent; normwise reading recorded with the
 design notes):
     eta(x) = ||A^T r||_2 / (||A||_F (||A||_F ||x||_2 + ||b||_2)),  r = b - A x.
 
-Refinement (the paper is silent), two forms:
+Refinement (the paper is silent), three forms:
 
 (1) corrected semi-normal equations (Bjorck): with R from a (possibly lower
 accuracy) QR factorization, R^T R ~ A^T A, and float64 residuals
@@ -31,6 +31,21 @@ factorization (possibly of lower accuracy):
     h  = R^{-T} g,  d = Q^T f = [d1; d2]
     dx = R^{-1} (d1 - h),  dr = Q [h; d2]
     x += dx, r += dr.
+
+(3) GMRES-based refinement of the same augmented system (Carson, Higham and
+Pranesh, "Three-precision GMRES-based iterative refinement for least squares
+problems", SIAM J. Sci. Comput. 2020), for problems too ill-conditioned for
+(2) to contract: each outer step solves the correction equation
+    [I A; A^T 0] [dr; dx] = [f; g]
+by GMRES (Saad and Schultz 1986) applied to the left-preconditioned system
+M^{-1} [I A; A^T 0] z = M^{-1} [f; g], where M is the augmented matrix with
+the factorization's Q R in place of A, so that M^{-1} [f; g] is exactly the
+correction of (2).  The preconditioned matrix stays well conditioned when
+kappa(A) u_f is near or above 1, where (2) stalls.  Readings (the method's
+paper leaves them to the user): the augmented system is not scaled
+(alpha = 1, as in (2)); the inner solve stops at a relative residual
+inner_tol or after `restart` steps, and the outer step applies whatever it
+reached.
 """
 
 import numpy as np
@@ -172,3 +187,113 @@ def seminormal_refinement(A, b, R, tol=1e-12, maxit=30, x0=None):
         it += 1
         history.append(backward_error(A, x, b))
     return x, it, history
+
+
+def gmres(op, s, tol, restart):
+    """GMRES for op(z) = s from z = 0 (Saad and Schultz 1986).
+
+    Arnoldi with modified Gram-Schmidt builds an orthonormal basis V_k of the
+    Krylov space K_k(op, s) and the (k+1) x k Hessenberg H_k with
+    op(V_k) = V_{k+1} H_k; the iterate z_k = V_k y_k takes the y_k that
+    minimises ||beta e_1 - H_k y|| (beta = ||s||), which minimises the
+    residual ||s - op(z)|| over the Krylov space.  Stops once that residual is
+    at most tol * beta, at a breakdown (h_{k+1,k} = 0: the space is invariant
+    and z_k solves the system), or after `restart` steps.
+
+    Returns (z, steps, relative residual)."""
+    s = np.asarray(s, dtype=np.float64)
+    beta = np.linalg.norm(s)
+    if beta == 0.0:
+        return np.zeros_like(s), 0, 0.0
+    V = [s / beta]
+    H = np.zeros((restart + 1, restart))
+    for j in range(restart):
+        w = np.asarray(op(V[j]), dtype=np.float64)
+        for i in range(j + 1):
+            H[i, j] = V[i] @ w
+            w = w - H[i, j] * V[i]
+        H[j + 1, j] = np.linalg.norm(w)
+        e1 = np.zeros(j + 2)
+        e1[0] = beta
+        y = np.linalg.lstsq(H[:j + 2, :j + 1], e1, rcond=None)[0]
+        res = np.linalg.norm(e1 - H[:j + 2, :j + 1] @ y) / beta
+        if res <= tol or H[j + 1, j] == 0.0 or j + 1 == restart:
+            break
+        V.append(w / H[j + 1, j])
+    z = np.zeros_like(s)
+    for i in range(j + 1):
+        z = z + y[i] * V[i]
+    return z, j + 1, res
+
+
+def augmented_preconditioner(solver):
+    """M^{-1} for the augmented system [I A; A^T 0] with A replaced by the
+    factorization Q R of ``solver`` (methods qt, q and attribute R):
+    M^{-1} [f; g] = [Q [h; d2]; R^{-1} (d1 - h)],  h = R^{-T} g,  d = Q^T f
+    (the correction of Bjorck's refinement, form (2))."""
+    R = np.asarray(solver.R, dtype=np.float64)
+    n = R.shape[0]
+
+    def apply(f, g):
+        h = forward_substitution_rt(R, np.asarray(g, dtype=np.float64)[:, None])[:, 0]
+        d = np.asarray(solver.qt(np.asarray(f, dtype=np.float64)[:, None]), dtype=np.float64)[:, 0]
+        v = back_substitution(R, (d[:n] - h)[:, None])[:, 0]
+        u = np.asarray(solver.q(np.concatenate([h, d[n:]])[:, None]), dtype=np.float64)[:, 0]
+        return u, v
+
+    return apply
+
+
+def gmres_ir(A, b, solver, tol=1e-12, inner_tol=1e-3, restart=30, maxit=20, x0=None, settle=True):
+    """GMRES-based iterative refinement of the augmented system, left-
+    preconditioned by the factorization in ``solver`` (form (3) above).
+
+    Starts from x0 (default: the solution through the factorization) and
+    r = b - A x; each outer step forms in float64
+        f = b - r - A x,  g = -A^T r,
+    solves [I A; A^T 0] [dr; dx] = [f; g] by GMRES on the left-preconditioned
+    system to a relative residual inner_tol (at most `restart` steps), and
+    updates r += dr, x += dx, until the backward error is at most tol and,
+    with ``settle``, x has settled: the last correction is below FP64
+    rounding (||dx|| <= 2^-50 ||x||) or no longer halves the one before (the
+    corrections have reached the rounding noise of the float64 residuals).
+    A backward error at tol alone does not make x accurate when kappa(A) is
+    large; the settled x is as accurate as a backward-stable FP64 solve.
+    Stops after maxit outer steps in any case.
+
+    Returns (x, r, outer steps, total GMRES steps, backward errors per outer
+    step)."""
+    A = np.asarray(A, dtype=np.float64)
+    b = np.asarray(b, dtype=np.float64).ravel()
+    m, n = A.shape
+    precond = augmented_preconditioner(solver)
+    if x0 is None:
+        c = np.asarray(solver.qt(b[:, None]), dtype=np.float64)[:, 0]
+        x = back_substitution(np.asarray(solver.R, dtype=np.float64), c[:n])[:, 0]
+    else:
+        x = np.array(x0, dtype=np.float64)
+    r = b - A @ x
+
+    def op(z):
+        u, v = precond(z[:m] + A @ z[m:], A.T @ z[:m])
+        return np.concatenate([u, v])
+
+    history = [backward_error(A, x, b)]
+    it = 0
+    inner = 0
+    dx_prev = np.inf
+    settled = not settle
+    while (history[-1] > tol or not settled) and it < maxit:
+        f = b - r - A @ x
+        g = -(A.T @ r)
+        u, v = precond(f, g)
+        z, steps, _ = gmres(op, np.concatenate([u, v]), inner_tol, restart)
+        inner += steps
+        r = r + z[:m]
+        x = x + z[m:]
+        it += 1
+        history.append(backward_error(A, x, b))
+        dx = np.linalg.norm(z[m:])
+        settled = (not settle) or dx <= 2.0 ** -50 * np.linalg.norm(x) or not (dx < 0.5 * dx_prev)
+        dx_prev = min(dx_prev, dx)
+    return x, r, it, inner, history
