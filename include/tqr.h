@@ -271,13 +271,26 @@ int tqr_lu_solve_pairs(int64_t n, int64_t nrhs, const double* A, int64_t lda, in
  *   X, ldx     (args 8, 9)  n x nrhs solutions, ldx >= n
  *   prec       (arg 10)     TQR_PREC_FP64: plain FP64.  TQR_PREC_FP32: the
  *                           factorization in FP32 (norms and tau in FP64),
- *                           then iterative refinement of the augmented
- *                           system with FP64 residuals until the backward
- *                           error is <= tol and the last correction changes
- *                           x by at most 2^-50 ||x|| (FP64 accuracy)
+ *                           then refinement with FP64 residuals until the
+ *                           backward error is <= tol and x has settled (the
+ *                           last correction is at most 2^-50 ||x|| or no
+ *                           longer halves): first the corrected semi-normal
+ *                           equations x += R^-1 R^-T A^T (b - A x) while the
+ *                           spread of R's diagonal puts kappa u_fp32 below
+ *                           0.01 and each step halves the backward error;
+ *                           then Bjorck's refinement of the augmented system
+ *                           [I A; A^T 0][r; x] = [b; 0] (while kappa u_fp32
+ *                           seems below 0.02 and it keeps converging); then
+ *                           GMRES-IR on the same system, left-preconditioned
+ *                           by the FP32 factors (Carson, Higham and Pranesh
+ *                           2020).  A problem none of them finishes -- or
+ *                           whose ||A||_F lies outside [2^-100, 2^100] -- is
+ *                           solved again in plain FP64 (tqr_ls_last_info
+ *                           tells which path gave the result)
  *   tol        (arg 11)     backward-error target for refinement (e.g. 1e-12)
  *   maxit      (arg 12)     refinement iteration limit
- *   iters      (arg 13)     out (may be NULL): refinement steps taken
+ *   iters      (arg 13)     out (may be NULL): refinement steps taken (outer
+ *                           steps of every form, FP32 attempt)
  *   berr       (arg 14)     out (may be NULL): final normwise backward error
  *                           max_c ||A^T r_c|| / (||A||_F (||A||_F ||x_c|| + ||b_c||))
  *   nb, ib     (args 15-16) tile and inner block size (0, 0 = library choice)
@@ -285,16 +298,84 @@ int tqr_lu_solve_pairs(int64_t n, int64_t nrhs, const double* A, int64_t lda, in
  * Tall problems use the reduction-tree variant when the library's model of
  * the task graph predicts a shorter run (see tqr_factor_tree).
  * Synchronizes the stream (the refinement loop needs the backward error on
- * the host).  Returns TQR_ERR_NONFINITE when A or B holds a NaN or an
- * infinity (they propagate into X), TQR_ERR_RANK for a numerically
- * rank-deficient R and TQR_ERR_NOCONV when refinement stalls (neither the
- * backward error nor the correction halves in 3 steps) or reaches maxit with
- * the backward error above tol; X then holds the best iterate.
+ * the host).  Norms are taken with power-of-two scaling, so finite entries
+ * of any magnitude give finite norms.  Returns TQR_ERR_NONFINITE when A or
+ * B holds a NaN or an infinity (they propagate into X), TQR_ERR_RANK for a
+ * numerically rank-deficient R and TQR_ERR_NOCONV when the FP32 class
+ * reaches maxit with the backward error above tol (X then holds the last
+ * iterate; maxit = 0 returns the unrefined FP32 solution this way).
+ * Refinement that stagnates before maxit is not an error: the problem is
+ * solved again in FP64.  The FP64 class is not refined and never returns
+ * TQR_ERR_NOCONV.
  */
 int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t lda,
                  const double* B, int64_t ldb, double* X, int64_t ldx, int prec,
                  double tol, int maxit, int* iters, double* berr, int nb, int ib,
                  void* stream);
+
+/*
+ * How a least-squares result was reached.  path: the last form that ran --
+ *   TQR_LS_PATH_FP64            plain FP64 factorization and solve
+ *   TQR_LS_PATH_FP32            FP32 factorization, no refinement step ran
+ *   TQR_LS_PATH_FP32_SEMINORMAL corrected semi-normal refinement
+ *   TQR_LS_PATH_FP32_AUGMENTED  augmented-system refinement
+ *   TQR_LS_PATH_FP32_GMRES      GMRES-IR
+ *   TQR_LS_PATH_FP64_FALLBACK   the FP32 class gave up and FP64 solved it
+ *                               (fp32_status: TQR_ERR_NOCONV, or
+ *                               TQR_ERR_UNSUPPORTED for ||A||_F outside
+ *                               FP32's range)
+ * iters: outer refinement steps; inner_iters: GMRES steps; berr: the final
+ * backward error; berr_fp32: the one the FP32 refinement reached.
+ * tqr_ls_last_info(&info) returns this for the calling thread's last
+ * tqr_solve_ls or tqr_ls_solve (0, or -1 for a NULL pointer).
+ */
+enum {
+  TQR_LS_PATH_FP64 = 0,
+  TQR_LS_PATH_FP32 = 1,
+  TQR_LS_PATH_FP32_SEMINORMAL = 2,
+  TQR_LS_PATH_FP32_AUGMENTED = 3,
+  TQR_LS_PATH_FP32_GMRES = 4,
+  TQR_LS_PATH_FP64_FALLBACK = 5
+};
+typedef struct tqr_ls_info {
+  int32_t path, iters, inner_iters, fp32_status;
+  double berr, berr_fp32;
+} tqr_ls_info;
+int tqr_ls_last_info(tqr_ls_info* info);
+
+/*
+ * A least-squares factorization kept resident for repeated right-hand sides
+ * (solves with new B skip the factorization: Q^T B and the back
+ * substitution, plus refinement for the FP32 class).
+ *
+ * tqr_ls_factor(m, n, A, lda, prec, nb, ib, rhs_cap, stream, &h)
+ *   m >= n >= 1 (args 1, 2); A (arg 3, device, m x n, lda >= m, arg 4) is
+ *   copied: the handle keeps an FP64 copy for the refinement residuals and
+ *   the backward error, so A may change afterwards; prec (arg 5) as for
+ *   tqr_solve_ls; nb, ib (args 6, 7; 0, 0 = library choice); rhs_cap (arg 8)
+ *   the most right-hand sides one solve may take.  Device memory: the tiles,
+ *   the copy of A and work arrays for rhs_cap columns.  Asynchronous on
+ *   stream, except that the FP32 class synchronizes once to check ||A||_F
+ *   (outside [2^-100, 2^100] the handle factors in FP64 instead).  Returns
+ *   0 and *h, -i, TQR_ERR_NOMEM, TQR_ERR_UNSUPPORTED or TQR_ERR_CUDA.
+ * tqr_ls_solve(h, nrhs, B, ldb, X, ldx, tol, maxit, info, stream)
+ *   B (device, m x nrhs, 1 <= nrhs <= rhs_cap), X (device, n x nrhs);
+ *   tol, maxit and the result codes as tqr_solve_ls; info (may be NULL) as
+ *   tqr_ls_info.  An FP32 handle whose refinement cannot finish factors its
+ *   copy of A in FP64 once and answers this and every later solve from that
+ *   (path TQR_LS_PATH_FP64_FALLBACK).  Synchronizes the stream.
+ * tqr_ls_release(h, stream)
+ *   frees the handle's device memory stream-ordered on `stream` (give the
+ *   stream of its last solve, or a later point); 0 or TQR_ERR_CUDA.
+ * One handle serves one thread at a time, on the device that was current
+ * when it was made.
+ */
+typedef struct tqr_ls tqr_ls;
+int tqr_ls_factor(int64_t m, int64_t n, const double* A, int64_t lda, int prec, int nb, int ib,
+                  int64_t rhs_cap, void* stream, tqr_ls** h);
+int tqr_ls_solve(tqr_ls* h, int64_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                 double tol, int maxit, tqr_ls_info* info, void* stream);
+int tqr_ls_release(tqr_ls* h, void* stream);
 
 /*
  * One matrix of a batch (tqr_batch_submit).
@@ -375,6 +456,13 @@ int tqr_batch_wait(uint64_t ticket, int* status_per_item);
  *       queued forever), TQR_ERR_UNSUPPORTED for a shape the kernels cannot
  *       take.
  *   tqr_server_wait(...)                     blocking form
+ *   tqr_server_wait_info(server, request, &status, &info, &latency_ms,
+ *                        &reused)            blocking, with the tqr_ls_info
+ *       of the solve.  An FP32-class request whose refinement cannot finish
+ *       is answered from an FP64 factorization of the resident copy of A,
+ *       which the entry keeps for its later requests (path
+ *       TQR_LS_PATH_FP64_FALLBACK; its bytes join the budget's accounting
+ *       when it is made, even if that overshoots the budget)
  *   tqr_server_stats(server, out[8])         completed, p50 and p99 latency
  *       (ms) over completed requests, resident+running bytes, requests that
  *       reused a resident factorization, failed, queued, resident entries
@@ -390,6 +478,8 @@ int tqr_server_poll(tqr_server* server, uint64_t request, int* done, int* status
                     double* berr, double* latency_ms, int* reused);
 int tqr_server_wait(tqr_server* server, uint64_t request, int* status, int* iters, double* berr,
                     double* latency_ms, int* reused);
+int tqr_server_wait_info(tqr_server* server, uint64_t request, int* status, tqr_ls_info* info,
+                         double* latency_ms, int* reused);
 int tqr_server_stats(tqr_server* server, double* out);
 int tqr_server_destroy(tqr_server* server);
 
@@ -415,7 +505,9 @@ int tqr_server_destroy(tqr_server* server);
  * at most TQR_NOALLOC_MAX_COUNTERS slab counters and TQR_NOALLOC_MAX_TASKS
  * tasks; larger problems return TQR_ERR_TOO_LARGE and enqueue nothing.
  * Tasks run in Algorithm 1's sequential order (no schedule simulation); the
- * result is bit-identical to tqr_factor's.
+ * result is bit-identical to tqr_factor's.  The GPU work of a call reads no
+ * host memory: the instance descriptor travels as a kernel parameter and a
+ * set-up kernel writes the task list into the array.
  *
  * Set-up: the first call on each device looks up the array's device address
  * (cudaGetSymbolAddress) with that device current; make that first call

@@ -1,4 +1,5 @@
-// tqr_ls.cu -- least squares on top of the tiled QR (tqr_solve_ls).
+// tqr_ls.cu -- least squares on top of the tiled QR (tqr_solve_ls and the
+// resident handle tqr_ls_factor / tqr_ls_solve / tqr_ls_release).
 //
 // FP64: one task graph factors A, applies Q^T to the right-hand sides (they
 // ride along as extra tile columns of Algorithm 1) and back-substitutes with
@@ -6,17 +7,21 @@
 // companion).
 //
 // FP32 + refinement: the same graph in FP32 (column norms and tau in FP64)
-// gives x0; for well-conditioned A the corrected semi-normal equations
-//     dx = R^-1 R^-T A^T (b - A x)
-// refine it (two triangular solves per step, FP64 residuals); otherwise, or
-// once they stop halving the backward error, Bjorck's iterative refinement
-// of the augmented system
-//     [I A; A^T 0] [r; x] = [b; 0]
-// runs with FP64 residuals  f = b - r - A x,  g = -A^T r  and corrections from
-// the FP32 factors:  h = R^-T g,  d = Q^T f,  dx = R^-1 (d1 - h),
-// dr = Q [h; d2],  until the normwise backward error
+// gives x0, refined with FP64 residuals in up to three forms, each taking
+// over when the one before cannot finish:
+//  (1) the corrected semi-normal equations dx = R^-1 R^-T A^T (b - A x), for
+//      well-conditioned A (two triangular solves per step);
+//  (2) Bjorck's iterative refinement of the augmented system
+//          [I A; A^T 0] [r; x] = [b; 0]
+//      with f = b - r - A x, g = -A^T r and corrections from the FP32
+//      factors:  h = R^-T g,  d = Q^T f,  dx = R^-1 (d1 - h),  dr = Q [h; d2];
+//  (3) GMRES-IR (Carson, Higham and Pranesh 2020): the same correction
+//      equation solved by GMRES, left-preconditioned with (2)'s correction,
+//      for kappa(A) u_fp32 near or above 1, where (2) no longer contracts.
+// The normwise backward error
 //     max_c ||A^T (b_c - A x_c)|| / (||A||_F (||A||_F ||x_c|| + ||b_c||))
-// is at most tol.  The FP64 work (residuals, A^T products, norms) runs in the
+// must reach tol and x must settle; a problem that does not is solved again
+// in FP64.  The FP64 work (residuals, A^T products, norms, GMRES) runs in the
 // kernels below; they are bound by the FP64 pipe or by HBM.
 #include <cuda_runtime.h>
 
@@ -71,11 +76,12 @@ __global__ void __launch_bounds__(kLsThreads) gemm_nn_partial(const double* __re
   }
 }
 
-// Y = alpha * Z + beta * W - sum_s P[s]   (all m x nrhs; Z, W may be null)
+// Y = alpha * Z + beta * W + gamma * sum_s P[s]   (all m x nrhs; Z, W may be
+// null; gamma = -1 gives a residual, +1 the product A X added)
 __global__ void combine_partials(const double* __restrict__ P, int nsplit, int m, int nrhs,
                                  const double* __restrict__ Z, long long ldz, double alpha,
-                                 const double* __restrict__ Wm, long long ldw, double beta, double* __restrict__ Y,
-                                 long long ldy) {
+                                 const double* __restrict__ Wm, long long ldw, double beta, double gamma,
+                                 double* __restrict__ Y, long long ldy) {
   const long long total = static_cast<long long>(m) * nrhs;
   for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
        e += static_cast<long long>(gridDim.x) * blockDim.x) {
@@ -83,8 +89,9 @@ __global__ void combine_partials(const double* __restrict__ P, int nsplit, int m
     double v = 0.0;
     if (Z) v = alpha * Z[r + c * ldz];
     if (Wm) v += beta * Wm[r + c * ldw];
-    for (int s = 0; s < nsplit; ++s) v -= P[(static_cast<long long>(s) * nrhs + c) * m + r];
-    Y[r + c * ldy] = v;
+    double ax = 0.0;
+    for (int s = 0; s < nsplit; ++s) ax += P[(static_cast<long long>(s) * nrhs + c) * m + r];
+    Y[r + c * ldy] = fma(gamma, ax, v);
   }
 }
 
@@ -116,39 +123,103 @@ __global__ void __launch_bounds__(kLsThreads) gemm_tn(const double* __restrict__
   }
 }
 
-// Per-column sums of squares of an m x ncols column-major matrix into
-// out[c] (deterministic: one block per column, fixed reduction tree).
-__global__ void __launch_bounds__(kLsThreads) col_sumsq(const double* __restrict__ X, long long ldx, int m,
-                                                        double* __restrict__ out) {
+// Block-wide reductions over kLsThreads threads (fixed order: deterministic).
+__device__ double block_max(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_xor_sync(0xffffffffu, v, o));
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kLsThreads / 32; ++w) t = fmax(t, red[w]);
+  return t;
+}
+
+__device__ double block_sum(double v, double* red) {
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  __syncthreads();
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = v;
+  __syncthreads();
+  double t = 0.0;
+  for (int w = 0; w < kLsThreads / 32; ++w) t += red[w];
+  return t;
+}
+
+// 2-norm of each column of an m x ncols column-major matrix into out[c], one
+// block per column, without overflow or underflow: the column is scaled by
+// the power of two 2^-e nearest below 1/max|x| (exact in binary), its sum
+// of squares taken, and the root scaled back (the scaling in the manner of
+// LAPACK's dnrm2, with a power of two so the scaling itself is exact).  A
+// NaN or an infinity in the column gives a non-finite norm.
+__global__ void __launch_bounds__(kLsThreads) col_nrm2(const double* __restrict__ X, long long ldx, int m,
+                                                       double* __restrict__ out) {
   __shared__ double red[kLsThreads / 32];
-  const int c = blockIdx.x;
+  const double* x = X + static_cast<long long>(blockIdx.x) * ldx;
+  double mx = 0.0;
+  bool bad = false;
+  for (int r = threadIdx.x; r < m; r += kLsThreads) {
+    const double a = fabs(x[r]);
+    bad = bad || !(a <= 1.7976931348623157e308);  // NaN or infinity
+    mx = fmax(mx, a);
+  }
+  mx = block_max(bad ? INFINITY : mx, red);
+  if (!(mx <= 1.7976931348623157e308)) {
+    if (threadIdx.x == 0) out[blockIdx.x] = NAN;
+    return;
+  }
+  if (mx == 0.0) {
+    if (threadIdx.x == 0) out[blockIdx.x] = 0.0;
+    return;
+  }
+  const int e = ilogb(mx);  // mx in [2^e, 2^(e+1)): x * 2^-e is below 2 in magnitude
   double s = 0.0;
   for (int r = threadIdx.x; r < m; r += kLsThreads) {
-    const double v = X[r + static_cast<long long>(c) * ldx];
+    const double v = scalbn(x[r], -e);
     s = fma(v, v, s);
   }
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kLsThreads / 32; ++w) t += red[w];
-    out[c] = t;
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[blockIdx.x] = scalbn(sqrt(s), e);
+}
+
+// GMRES (Arnoldi) helpers.  The basis vectors of all right-hand sides live
+// in one array: vector i of right-hand side c is the N-vector at
+// V + (i * nrhs + c) * N (N = m + n: [u; v] of the augmented system).
+// out[i + c * ldo] = V_i(:, c)^T w(:, c) for i < nvec: one block per (i, c).
+__global__ void __launch_bounds__(kLsThreads) gmres_dots(const double* __restrict__ V, int nvec, long long N,
+                                                         int nrhs, const double* __restrict__ w,
+                                                         double* __restrict__ out, int ldo) {
+  __shared__ double red[kLsThreads / 32];
+  const int i = blockIdx.x, c = blockIdx.y;
+  if (i >= nvec) return;
+  const double* v = V + (static_cast<long long>(i) * nrhs + c) * N;
+  const double* x = w + static_cast<long long>(c) * N;
+  double s = 0.0;
+  for (long long r = threadIdx.x; r < N; r += kLsThreads) s = fma(v[r], x[r], s);
+  s = block_sum(s, red);
+  if (threadIdx.x == 0) out[i + c * ldo] = s;
+}
+
+// w(:, c) -= sum_{i < nvec} coef[i + c * ldc] V_i(:, c)
+__global__ void gmres_axpy(const double* __restrict__ V, int nvec, long long N, int nrhs,
+                           const double* __restrict__ coef, int ldc, double* __restrict__ w) {
+  const long long total = N * nrhs;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(e / N);
+    const long long r = e - static_cast<long long>(c) * N;
+    double acc = w[e];
+    for (int i = 0; i < nvec; ++i) acc = fma(-coef[i + c * ldc], V[(static_cast<long long>(i) * nrhs + c) * N + r], acc);
+    w[e] = acc;
   }
 }
 
-// out[0] = x[0] + ... + x[n-1] (one block, fixed order).
-__global__ void __launch_bounds__(kLsThreads) vec_sum(const double* __restrict__ x, int n, double* __restrict__ out) {
-  __shared__ double red[kLsThreads / 32];
-  double s = 0.0;
-  for (int r = threadIdx.x; r < n; r += kLsThreads) s += x[r];
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_xor_sync(0xffffffffu, s, o);
-  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
-  __syncthreads();
-  if (threadIdx.x == 0) {
-    double t = 0.0;
-    for (int w = 0; w < kLsThreads / 32; ++w) t += red[w];
-    out[0] = t;
+// w(:, c) *= 1 / nrm[c]  (a zero norm -- a breakdown -- leaves a zero vector)
+__global__ void col_scale_inv(double* __restrict__ w, long long N, int nrhs, const double* __restrict__ nrm) {
+  const long long total = N * nrhs;
+  for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
+       e += static_cast<long long>(gridDim.x) * blockDim.x) {
+    const int c = static_cast<int>(e / N);
+    const double d = nrm[c];
+    w[e] = d > 0.0 ? w[e] / d : 0.0;
   }
 }
 
@@ -216,14 +287,14 @@ static LsScratch ls_scratch_shape(int m, int n, int nrhs) {
   return s;
 }
 
-// Y = alpha Z + beta W - A X
+// Y = alpha Z + beta W + gamma A X
 static cudaError_t resid(const LsScratch& sc, const double* A, long long lda, int m, int n, const double* X,
                          long long ldx, int nrhs, const double* Z, long long ldz, double alpha, const double* Wm,
-                         long long ldw, double beta, double* Y, long long ldy, cudaStream_t st) {
+                         long long ldw, double beta, double gamma, double* Y, long long ldy, cudaStream_t st) {
   dim3 grid((m + kLsThreads - 1) / kLsThreads, sc.nsplit);
   gemm_nn_partial<<<grid, kLsThreads, 0, st>>>(A, lda, m, n, X, ldx, nrhs, sc.split_len, sc.part);
   combine_partials<<<ew_grid(static_cast<long long>(m) * nrhs), 256, 0, st>>>(sc.part, sc.nsplit, m, nrhs, Z, ldz,
-                                                                            alpha, Wm, ldw, beta, Y, ldy);
+                                                                            alpha, Wm, ldw, beta, gamma, Y, ldy);
   return cudaGetLastError();
 }
 
@@ -234,12 +305,30 @@ static cudaError_t atr(const double* A, long long lda, int m, int n, const doubl
   return cudaGetLastError();
 }
 
+// ||A||_F (and the column norms on the way) into nA, overflow-free
+static cudaError_t fro_norm(const double* A, long long lda, int m, int n, double* colnrm, double* nA,
+                            cudaStream_t st) {
+  col_nrm2<<<n, kLsThreads, 0, st>>>(A, lda, m, colnrm);
+  col_nrm2<<<1, kLsThreads, 0, st>>>(colnrm, n, n, nA);
+  return cudaGetLastError();
+}
+
 struct BerrBufs {
   double* G;     // n x nrhs
-  double* nrm;   // 3 * nrhs
+  double* nrm;   // 4 * nrhs + 4
 };
 
 static size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// GMRES-IR constants: Krylov steps per outer step (restart length), relative
+// residual the inner solve stops at, and the limit on inner steps in total.
+constexpr int kGmresRestart = 30;
+constexpr double kGmresInnerTol = 1e-3;
+constexpr int kGmresMaxInner = 300;
+// The FP32 factorization is used only for A with 2^-100 <= ||A||_F <= 2^100
+// (its entries, R and the reflectors then stay far inside FP32's range);
+// other problems are solved in FP64.
+constexpr double kFp32NormLo = 0x1p-100, kFp32NormHi = 0x1p100;
 
 // ---------------------------------------------------------------------------
 // LsJob: device state of one least-squares problem.  The tiles of A (and T)
@@ -254,6 +343,7 @@ bool LsJob::init(int m_, int n_, int rhs_cap_, int nb_, int ib_, int prec_, int 
   prec = prec_;
   esize = prec == TQR_PREC_FP64 ? 8 : 4;
   grid_cap = grid_cap_;
+  factored = false;
   if (!choose_shape(nb, ib, esize, &cs, &occ, &smem)) return false;
   I = make_inst(M_FACTOR, m, n, nb, ib, cs, rhs_cap, 1);
   I.D = choose_domain(m, n, nb, ib, esize);  // reduction tree when it shortens the run
@@ -338,31 +428,77 @@ int LsJob::run_two(int mode_a, int mode_b, int nrhs_now, cudaStream_t st) {
                     : run_plan_multi<float>(two, 2, d_insts, d_ctl, occ, smem, st, grid_cap);
 }
 
-// factor A (and keep the factors), x0 = the solution through those factors
+// [U; V] = M^-1 [F; G] with M = [I, QR; (QR)^T, 0] from the factors in the
+// tiles: d = Q^T F and h = R^-T G (one launch), then V = R^-1 (d1 - h) and
+// U = Q [h; d2] (one launch) -- the correction of the augmented-system
+// refinement, and the preconditioner of GMRES-IR.  F: m x nrhs (ldf), G:
+// n x nrhs (ldg), U: m x nrhs (ldu), V: n x nrhs (ldv).  The inputs are
+// packed into the tiles before the scratch D, H and the G buffer are
+// written, so F and G may be those buffers.
+int LsJob::precond(const double* F, long long ldf, const double* G, long long ldg, double* U, long long ldu,
+                   double* V, long long ldv, int nrhs, cudaStream_t st) {
+  double* D = reinterpret_cast<double*>(ws + o_d);
+  double* H = reinterpret_cast<double*>(ws + o_h);
+  double* Gv = reinterpret_cast<double*>(ws + o_g);
+  void* B2 = ws + o_b2;
+  const size_t nr = static_cast<size_t>(n) * nrhs;
+  int s = pack_rhs(F, ldf, m, nrhs, st);
+  if (s == TQR_OK) s = pack_rhs(G, ldg, n, nrhs, st, B2);
+  if (s == TQR_OK) s = run_two(M_APPLY_QT, M_TRSMT, nrhs, st);
+  if (s == TQR_OK) s = unpack_rhs(D, m, m, nrhs, st);
+  if (s == TQR_OK) s = unpack_rhs(H, n, n, nrhs, st, B2);
+  if (s != TQR_OK) return s;
+  axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, D, m, -1.0, H, n, Gv, n);
+  axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, H, n, 0.0, nullptr, 0, D, m);
+  if (cudaGetLastError() != cudaSuccess) return TQR_ERR_CUDA;
+  s = pack_rhs(D, m, m, nrhs, st);
+  if (s == TQR_OK) s = pack_rhs(Gv, n, n, nrhs, st, B2);
+  if (s == TQR_OK) s = run_two(M_APPLY_Q, M_TRSM, nrhs, st);
+  if (s == TQR_OK) s = unpack_rhs(U, ldu, m, nrhs, st);
+  if (s == TQR_OK) s = unpack_rhs(V, ldv, n, nrhs, st, B2);
+  return s;
+}
+
+// Factors A (and keeps the factors) and, with nrhs > 0, runs Q^T B and the
+// back substitution in the same graph: x0 through those factors.  Also
+// ||A||_F and R's extreme diagonal entries for the solve's checks.  The FP32
+// class first checks that A suits FP32 (kLsFp32Range if not).
 int LsJob::factor_solve(const double* A, long long lda, const double* B, long long ldb, int nrhs, cudaStream_t st) {
   const int sms = device_sms();
+  factored = false;
+  double* nrm = reinterpret_cast<double*>(ws + o_nrm);
+  double* colnrm = reinterpret_cast<double*>(ws + o_g);
+  if (fro_norm(A, lda, m, n, colnrm, nrm + 4 * rhs_cap, st) != cudaSuccess) return TQR_ERR_CUDA;
+  if (esize == 4) {
+    double h = 0.0;
+    if (cudaMemcpyAsync(&h, nrm + 4 * rhs_cap, sizeof(double), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+        cudaStreamSynchronize(st) != cudaSuccess)
+      return TQR_ERR_CUDA;
+    if (!std::isfinite(h)) return TQR_ERR_NONFINITE;
+    if (!(h >= kFp32NormLo && h <= kFp32NormHi)) return kLsFp32Range;
+  }
   if (upload_vtab(I, ws, W, st) != TQR_OK) return TQR_ERR_CUDA;
   if (Acopy != nullptr &&
       copy_cols(Acopy, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
-                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     return TQR_ERR_CUDA;
   cudaError_t e = esize == 8 ? launch_pack<double>(A, lda, m, n, static_cast<double*>(I.A), I.p, I.q, nb, sms, st)
                              : launch_pack<float>(A, lda, m, n, static_cast<float*>(I.A), I.p, I.q, nb, sms, st);
   if (e != cudaSuccess) return TQR_ERR_CUDA;
-  int s = pack_rhs(B, ldb, m, nrhs, st);
-  if (s == TQR_OK) s = run_mode(M_FACTOR, 1, nrhs, st);
-  if (s == TQR_OK) s = unpack_rhs(reinterpret_cast<double*>(ws + o_x), n, n, nrhs, st);
+  int s = TQR_OK;
+  if (nrhs > 0) {
+    s = pack_rhs(B, ldb, m, nrhs, st);
+    if (s == TQR_OK) s = run_mode(M_FACTOR, 1, nrhs, st);
+    if (s == TQR_OK) s = unpack_rhs(reinterpret_cast<double*>(ws + o_x), n, n, nrhs, st);
+  } else {
+    s = run_mode(M_FACTOR, 0, 0, st);
+  }
   if (s == TQR_OK) {
-    double* dmm = reinterpret_cast<double*>(ws + o_nrm) + 4 * rhs_cap + 2;
+    double* dmm = nrm + 4 * rhs_cap + 2;
     if (esize == 8)
       diag_minmax<double><<<1, kLsThreads, 0, st>>>(static_cast<double*>(I.A), I.p, nb, n, dmm);
     else
       diag_minmax<float><<<1, kLsThreads, 0, st>>>(static_cast<float*>(I.A), I.p, nb, n, dmm);
-    double* nA2 = reinterpret_cast<double*>(ws + o_nrm) + 4 * rhs_cap;
-    double* colsq = reinterpret_cast<double*>(ws + o_g);
-    // ||A||_F^2: the columns' sums of squares, then their sum
-    col_sumsq<<<n, kLsThreads, 0, st>>>(A, lda, m, colsq);
-    vec_sum<<<1, kLsThreads, 0, st>>>(colsq, n, nA2);
     if (cudaGetLastError() != cudaSuccess) s = TQR_ERR_CUDA;
   }
   factored = (s == TQR_OK);
@@ -380,23 +516,24 @@ int LsJob::solve(const double* B, long long ldb, int nrhs, cudaStream_t st) {
 // Backward error of x, FP32 refinement, copy of x to X.  A is the FP64
 // matrix (caller's or the resident copy).
 int LsJob::finish(const double* A, long long lda, const double* B, long long ldb, int nrhs, double* X, long long ldx,
-                  double tol, int maxit, int* iters_out, double* berr_out, cudaStream_t st) {
+                  double tol, int maxit, tqr_ls_info* info, cudaStream_t st) {
   const size_t mr = static_cast<size_t>(m) * nrhs, nr = static_cast<size_t>(n) * nrhs;
   double* E = reinterpret_cast<double*>(ws + o_e);
   double* Rr = reinterpret_cast<double*>(ws + o_r);
   double* F = reinterpret_cast<double*>(ws + o_f);
   double* D = reinterpret_cast<double*>(ws + o_d);
   double* Gv = reinterpret_cast<double*>(ws + o_g);
-  double* H = reinterpret_cast<double*>(ws + o_h);
   double* Xw = reinterpret_cast<double*>(ws + o_x);
   BerrBufs bb;
   bb.G = reinterpret_cast<double*>(ws + o_G);
   bb.nrm = reinterpret_cast<double*>(ws + o_nrm);
-  const int R = rhs_cap;  // nrm layout: [0,R) |A^T e|^2, [R,2R) |x|^2, [2R,3R) |b|^2, [4R] |A|^2, [4R+2,4R+3] diag
+  // nrm layout (norms, not squares): [0,R) ||A^T e||, [R,2R) ||x||, [2R,3R) ||b||,
+  // [3R,4R) ||dx||, [4R] ||A||_F, [4R+2], [4R+3] min and max |r_ii|
+  const int R = rhs_cap;
   double* dx2 = bb.nrm + 3 * R;
   std::vector<double> hn(4 * R + 4);
   int status = TQR_OK;
-  int iters = 0;
+  int iters = 0, inner = 0, path = esize == 8 ? TQR_LS_PATH_FP64 : TQR_LS_PATH_FP32;
   double berr = INFINITY;
   auto fail = [&](int s) {
     if (status == TQR_OK && s != TQR_OK) status = s;
@@ -408,22 +545,23 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
   };
   auto berr_of = [&]() {
     double worst = 0.0;
-    const double nA = std::sqrt(hn[4 * R]);
+    const double nA = hn[4 * R];
     for (int c = 0; c < nrhs; ++c) {
-      const double num = std::sqrt(hn[c]);
-      const double den = nA * (nA * std::sqrt(hn[R + c]) + std::sqrt(hn[2 * R + c]));
+      const double num = hn[c];
+      const double den = nA * (nA * hn[R + c] + hn[2 * R + c]);
       const double eta = den > 0 ? num / den : (num > 0 ? INFINITY : 0.0);
       if (!(eta <= worst)) worst = eta;
     }
     return worst;
   };
+  // e = b - A x, A^T e and the norms of the backward error
   auto terms = [&]() {
-    if (resid(sc, A, lda, m, n, Xw, n, nrhs, B, ldb, 1.0, nullptr, 0, 0.0, E, m, st) != cudaSuccess ||
+    if (resid(sc, A, lda, m, n, Xw, n, nrhs, B, ldb, 1.0, nullptr, 0, 0.0, -1.0, E, m, st) != cudaSuccess ||
         atr(A, lda, m, n, E, m, nrhs, 1.0, bb.G, n, st) != cudaSuccess)
       fail(TQR_ERR_CUDA);
-    col_sumsq<<<nrhs, kLsThreads, 0, st>>>(bb.G, n, n, bb.nrm);
-    col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Xw, n, n, bb.nrm + R);
-    col_sumsq<<<nrhs, kLsThreads, 0, st>>>(B, ldb, m, bb.nrm + 2 * R);
+    col_nrm2<<<nrhs, kLsThreads, 0, st>>>(bb.G, n, n, bb.nrm);
+    col_nrm2<<<nrhs, kLsThreads, 0, st>>>(Xw, n, n, bb.nrm + R);
+    col_nrm2<<<nrhs, kLsThreads, 0, st>>>(B, ldb, m, bb.nrm + 2 * R);
     if (cudaGetLastError() != cudaSuccess) fail(TQR_ERR_CUDA);
   };
   terms();
@@ -442,47 +580,50 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     if (!(hn[4 * R + 2] > n * eps * hn[4 * R + 3])) status = TQR_ERR_RANK;
     berr = berr_of();
   }
+  double prev = berr, prev_dx = INFINITY, dxrel = INFINITY;
+  bool settled = false;
+  auto dx_rel = [&](double scale) {
+    double worst = 0.0;
+    for (int c = 0; c < nrhs; ++c) {
+      const double xr = hn[R + c];
+      const double d = hn[3 * R + c] / scale;
+      const double rel = xr > 0 ? d / xr : d;
+      if (!(rel <= worst)) worst = rel;
+    }
+    return worst;
+  };
+  // Refinement runs until the backward error meets tol AND x has settled at
+  // FP64 accuracy: the last correction is below FP64 rounding (||dx|| <=
+  // 2^-50 ||x||) or, with the backward error already met, no longer halves
+  // (the corrections have reached the rounding noise of the FP64
+  // residuals), so the answer matches an FP64 solve; a form gives way to the
+  // next on stagnation (neither the backward error nor the correction halves
+  // for 3 steps), and the whole refinement stops at maxit.
+  auto more = [&]() { return status == TQR_OK && !settled && (berr > tol || dxrel > 0x1p-50) && iters < maxit; };
+  // spread of R's diagonal: a lower bound on kappa(A) (R from A + E)
+  const double spread = hn[4 * R + 3] / hn[4 * R + 2];
   if (status == TQR_OK && esize == 4) {
-    // Refine until the backward error meets tol AND x has settled at FP64
-    // accuracy: the last correction is below FP64 rounding (||dx|| <=
-    // 2^-50 ||x||) or, with the backward error already met, no longer halves
-    // (the corrections have reached the rounding noise of the FP64
-    // residuals), so the answer matches an FP64 solve; stop early on
-    // stagnation (neither the backward error nor the correction halves for 3
-    // steps) or at maxit.
-    double prev = berr, prev_dx = INFINITY, dxrel = INFINITY;
-    bool settled = false;
-    auto dx_rel = [&](double scale) {
-      double worst = 0.0;
-      for (int c = 0; c < nrhs; ++c) {
-        const double xr = std::sqrt(hn[R + c]);
-        const double d = std::sqrt(hn[3 * R + c]) / scale;
-        const double rel = xr > 0 ? d / xr : d;
-        if (!(rel <= worst)) worst = rel;
-      }
-      return worst;
-    };
-    // Corrected semi-normal equations first: dx = R^-1 R^-T A^T e with
-    // e = b - A x and A^T e already on the device from the backward-error
-    // terms -- two triangular-solve graphs per step and no Q application.
-    // With R the factor of A + E (||E|| ~ eps ||A||) the error contracts by
-    // about 2 kappa eps per step, so they run only while the spread of R's
-    // diagonal (a lower bound on kappa) keeps kappa u_fp32 small, and give
-    // way to the augmented-system refinement as soon as a step fails to
-    // halve the backward error (a step that made it worse is undone).
-    const double spread = hn[4 * R + 3] / hn[4 * R + 2];
+    // (1) Corrected semi-normal equations: dx = R^-1 R^-T A^T e with e = b -
+    // A x and A^T e already on the device from the backward-error terms --
+    // two triangular-solve graphs per step and no Q application.  With R the
+    // factor of A + E (||E|| ~ eps ||A||) the error contracts by about
+    // 2 kappa eps per step, so they run only while the spread of R's
+    // diagonal keeps kappa u_fp32 small, and give way to the augmented-system
+    // refinement as soon as a step fails to halve the backward error (a step
+    // that made it worse is undone).
     bool semi = spread * 0x1p-24 < 0.01;
-    while (status == TQR_OK && semi && !settled && (berr > tol || dxrel > 0x1p-50) && iters < maxit) {
+    if (semi) path = TQR_LS_PATH_FP32_SEMINORMAL;
+    while (semi && more()) {
       // scale A^T e by a power of two near 1/max ||.|| so FP32 keeps it normal
       double gmax = 0.0;
-      for (int c = 0; c < nrhs; ++c) gmax = std::max(gmax, std::sqrt(hn[c]));
+      for (int c = 0; c < nrhs; ++c) gmax = std::max(gmax, hn[c]);
       const double scale = gmax > 0 && std::isfinite(gmax) ? std::ldexp(1.0, -std::ilogb(gmax)) : 1.0;
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, scale, bb.G, n, 0.0, nullptr, 0, Gv, n);
       fail(pack_rhs(Gv, n, n, nrhs, st));
       if (status == TQR_OK) fail(run_mode(M_TRSMT, 0, nrhs, st));
       if (status == TQR_OK) fail(run_mode(M_TRSM, 0, nrhs, st));
       fail(unpack_rhs(Gv, n, n, nrhs, st));
-      col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
+      col_nrm2<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0 / scale, Gv, n, Xw, n);
       ++iters;
       terms();
@@ -514,27 +655,20 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     if (!settled &&
         cudaMemcpyAsync(Rr, E, sizeof(double) * mr, cudaMemcpyDeviceToDevice, st) != cudaSuccess)
       fail(TQR_ERR_CUDA);
+    // (2) Bjorck's refinement of the augmented system [I A; A^T 0][r; x] =
+    // [b; 0], corrections through the factors (precond).  It contracts by
+    // about kappa u_fp32 per step, so it is skipped when R's diagonal spread
+    // already puts kappa u_fp32 above 0.02, and gives way to GMRES-IR when
+    // it stagnates.
     int stall = 0;
-    while (status == TQR_OK && !settled && (berr > tol || dxrel > 0x1p-50) && iters < maxit) {
-      // f = b - r - A x = e - r;  g = -A^T r
+    const bool aug = spread * 0x1p-24 < 0.02;
+    if (aug && more()) path = TQR_LS_PATH_FP32_AUGMENTED;
+    while (aug && more()) {
+      // f = b - r - A x = e - r;  g = -A^T r;  [dr; dx] = M^-1 [f; g]
       axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, E, m, -1.0, Rr, m, F, m);
       if (atr(A, lda, m, n, Rr, m, nrhs, -1.0, Gv, n, st) != cudaSuccess) fail(TQR_ERR_CUDA);
-      // d = Q^T f (first tiles) and h = R^-T g (second tiles): one launch
-      void* B2 = ws + o_b2;
-      fail(pack_rhs(F, m, m, nrhs, st));
-      fail(pack_rhs(Gv, n, n, nrhs, st, B2));
-      if (status == TQR_OK) fail(run_two(M_APPLY_QT, M_TRSMT, nrhs, st));
-      fail(unpack_rhs(D, m, m, nrhs, st));
-      fail(unpack_rhs(H, n, n, nrhs, st, B2));
-      // dx = R^-1 (d1 - h) (second tiles) and dr = Q [h; d2] (first tiles): one launch
-      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, D, m, -1.0, H, n, Gv, n);
-      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, H, n, 0.0, nullptr, 0, D, m);
-      fail(pack_rhs(D, m, m, nrhs, st));
-      fail(pack_rhs(Gv, n, n, nrhs, st, B2));
-      if (status == TQR_OK) fail(run_two(M_APPLY_Q, M_TRSM, nrhs, st));
-      fail(unpack_rhs(D, m, m, nrhs, st));
-      fail(unpack_rhs(Gv, n, n, nrhs, st, B2));
-      col_sumsq<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
+      if (status == TQR_OK) fail(precond(F, m, Gv, n, D, m, Gv, n, nrhs, st));
+      col_nrm2<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0, Gv, n, Xw, n);
       axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, Rr, m, 1.0, D, m, Rr, m);
       ++iters;
@@ -543,7 +677,10 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
       if (status != TQR_OK) break;
       berr = berr_of();
       dxrel = dx_rel(1.0);
-      if (berr <= tol && !(dxrel < 0.5 * prev_dx)) break;
+      if (berr <= tol && !(dxrel < 0.5 * prev_dx)) {
+        settled = true;
+        break;
+      }
       if (!(berr < 0.5 * prev) && !(dxrel < 0.5 * prev_dx)) {
         if (++stall >= 3) break;
       } else {
@@ -552,20 +689,191 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
       prev = std::min(prev, berr);
       prev_dx = std::min(prev_dx, dxrel);
     }
-    if (status == TQR_OK && !(berr <= tol)) status = TQR_ERR_NOCONV;
+    // (3) GMRES-IR (Carson, Higham and Pranesh 2020): each outer step solves
+    // the correction equation [I A; A^T 0][dr; dx] = [f; g] by GMRES on the
+    // system left-preconditioned with precond (M^-1 applied in the factors'
+    // precision, the augmented operator and all GMRES arithmetic in FP64).
+    if (more()) {
+      path = TQR_LS_PATH_FP32_GMRES;
+      const long long N = static_cast<long long>(m) + n;
+      const int K = kGmresRestart;
+      const size_t basis = sizeof(double) * static_cast<size_t>(K + 1) * N * nrhs;
+      const size_t zbytes = sizeof(double) * static_cast<size_t>(N) * nrhs;
+      const size_t hbytes = sizeof(double) * static_cast<size_t>(2 * (K + 1) + 1) * nrhs;
+      char* gm = nullptr;
+      if (lib_malloc(reinterpret_cast<void**>(&gm), al(basis) + al(zbytes) + al(hbytes), st) != cudaSuccess) {
+        cudaGetLastError();
+        gm = nullptr;
+        fail(TQR_ERR_NOMEM);
+      }
+      double* Vb = reinterpret_cast<double*>(gm);
+      double* Z = reinterpret_cast<double*>(gm + al(basis));
+      double* h1 = reinterpret_cast<double*>(gm + al(basis) + al(zbytes));  // (K+1) x nrhs, then h2, then ||w||
+      double* h2 = h1 + static_cast<size_t>(K + 1) * nrhs;
+      double* hw = h2 + static_cast<size_t>(K + 1) * nrhs;
+      // host side of GMRES per right-hand side c: Hessenberg columns after
+      // the Givens rotations (upper triangle, column-major (K+1) x K), the
+      // rotations, the rotated right-hand side g and the step count k_c at
+      // which the column converged
+      std::vector<double> Hh(static_cast<size_t>(K + 1) * K * nrhs), cs(static_cast<size_t>(K) * nrhs),
+          sn(static_cast<size_t>(K) * nrhs), g(static_cast<size_t>(K + 1) * nrhs), beta(nrhs), hh(2 * (K + 1) * nrhs + nrhs),
+          y(static_cast<size_t>(K + 1) * nrhs);
+      std::vector<int> kc(nrhs);
+      auto vec = [&](int i) { return Vb + static_cast<size_t>(i) * nrhs * N; };
+      auto normalize = [&](double* w) {
+        col_nrm2<<<nrhs, kLsThreads, 0, st>>>(w, N, static_cast<int>(N), hw);
+        col_scale_inv<<<ew_grid(N * nrhs), 256, 0, st>>>(w, N, nrhs, hw);
+        if (cudaGetLastError() != cudaSuccess) fail(TQR_ERR_CUDA);
+      };
+      int stall = 0;
+      prev = berr;
+      prev_dx = INFINITY;
+      while (more() && inner < kGmresMaxInner) {
+        // s = M^-1 [f; g] with f = e - r, g = -A^T r: the first basis vector
+        axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, E, m, -1.0, Rr, m, F, m);
+        if (atr(A, lda, m, n, Rr, m, nrhs, -1.0, Gv, n, st) != cudaSuccess) fail(TQR_ERR_CUDA);
+        if (status == TQR_OK) fail(precond(F, m, Gv, n, vec(0), N, vec(0) + m, N, nrhs, st));
+        normalize(vec(0));
+        if (status == TQR_OK && (cudaMemcpyAsync(beta.data(), hw, sizeof(double) * nrhs, cudaMemcpyDeviceToHost, st) !=
+                                     cudaSuccess ||
+                                 cudaStreamSynchronize(st) != cudaSuccess))
+          fail(TQR_ERR_CUDA);
+        if (status != TQR_OK) break;
+        int open = 0;
+        for (int c = 0; c < nrhs; ++c) {
+          std::fill(g.begin() + static_cast<size_t>(c) * (K + 1), g.begin() + static_cast<size_t>(c + 1) * (K + 1), 0.0);
+          g[static_cast<size_t>(c) * (K + 1)] = beta[c];
+          kc[c] = (beta[c] > 0.0 && std::isfinite(beta[c])) ? -1 : 0;  // -1: still iterating
+          open += kc[c] < 0;
+        }
+        int steps = 0;
+        for (int j = 0; j < K && open > 0 && inner < kGmresMaxInner; ++j) {
+          double* vj = vec(j);
+          double* w = vec(j + 1);
+          // [u_j + A v_j; A^T u_j], then M^-1 of it into w
+          if (resid(sc, A, lda, m, n, vj + m, N, nrhs, vj, N, 1.0, nullptr, 0, 0.0, 1.0, F, m, st) != cudaSuccess ||
+              atr(A, lda, m, n, vj, N, nrhs, 1.0, Gv, n, st) != cudaSuccess)
+            fail(TQR_ERR_CUDA);
+          if (status == TQR_OK) fail(precond(F, m, Gv, n, w, N, w + m, N, nrhs, st));
+          // classical Gram-Schmidt, twice (as stable as modified Gram-Schmidt
+          // and two reductions per step instead of j + 1)
+          gmres_dots<<<dim3(j + 1, nrhs), kLsThreads, 0, st>>>(Vb, j + 1, N, nrhs, w, h1, K + 1);
+          gmres_axpy<<<ew_grid(N * nrhs), 256, 0, st>>>(Vb, j + 1, N, nrhs, h1, K + 1, w);
+          gmres_dots<<<dim3(j + 1, nrhs), kLsThreads, 0, st>>>(Vb, j + 1, N, nrhs, w, h2, K + 1);
+          gmres_axpy<<<ew_grid(N * nrhs), 256, 0, st>>>(Vb, j + 1, N, nrhs, h2, K + 1, w);
+          normalize(w);
+          if (status == TQR_OK && (cudaMemcpyAsync(hh.data(), h1, hbytes, cudaMemcpyDeviceToHost, st) != cudaSuccess ||
+                                   cudaStreamSynchronize(st) != cudaSuccess))
+            fail(TQR_ERR_CUDA);
+          if (status != TQR_OK) break;
+          ++inner;
+          steps = j + 1;
+          for (int c = 0; c < nrhs; ++c) {
+            if (kc[c] >= 0) continue;
+            double* Hc = Hh.data() + static_cast<size_t>(c) * (K + 1) * K;
+            double* col = Hc + static_cast<size_t>(j) * (K + 1);
+            for (int i = 0; i <= j; ++i)
+              col[i] = hh[i + static_cast<size_t>(c) * (K + 1)] + hh[(K + 1) * static_cast<size_t>(nrhs) + i + static_cast<size_t>(c) * (K + 1)];
+            col[j + 1] = hh[2 * (K + 1) * static_cast<size_t>(nrhs) + c];
+            // earlier rotations, then the one that zeroes col[j + 1]
+            double* csc = cs.data() + static_cast<size_t>(c) * K;
+            double* snc = sn.data() + static_cast<size_t>(c) * K;
+            for (int i = 0; i < j; ++i) {
+              const double a = col[i], b2 = col[i + 1];
+              col[i] = csc[i] * a + snc[i] * b2;
+              col[i + 1] = -snc[i] * a + csc[i] * b2;
+            }
+            const double rho = std::hypot(col[j], col[j + 1]);
+            const double cj = rho > 0 ? col[j] / rho : 1.0, sj = rho > 0 ? col[j + 1] / rho : 0.0;
+            csc[j] = cj;
+            snc[j] = sj;
+            col[j] = rho;
+            col[j + 1] = 0.0;
+            double* gc = g.data() + static_cast<size_t>(c) * (K + 1);
+            gc[j + 1] = -sj * gc[j];
+            gc[j] = cj * gc[j];
+            const double res = std::fabs(gc[j + 1]) / beta[c];
+            const bool breakdown = !(hh[2 * (K + 1) * static_cast<size_t>(nrhs) + c] > 0.0);
+            if (res <= kGmresInnerTol || breakdown || !std::isfinite(res)) {
+              kc[c] = j + 1;
+              --open;
+            }
+          }
+        }
+        if (status != TQR_OK) break;
+        // y_c from the rotated triangle (k_c steps), z = sum_i y_i v_i
+        int kmax = 0;
+        for (int c = 0; c < nrhs; ++c) {
+          if (kc[c] < 0) kc[c] = steps;
+          kmax = std::max(kmax, kc[c]);
+          const double* Hc = Hh.data() + static_cast<size_t>(c) * (K + 1) * K;
+          const double* gc = g.data() + static_cast<size_t>(c) * (K + 1);
+          double* yc = y.data() + static_cast<size_t>(c) * (K + 1);
+          std::fill(yc, yc + K + 1, 0.0);
+          for (int i = kc[c] - 1; i >= 0; --i) {
+            double t = gc[i];
+            for (int l = i + 1; l < kc[c]; ++l) t -= Hc[i + static_cast<size_t>(l) * (K + 1)] * yc[l];
+            const double d = Hc[i + static_cast<size_t>(i) * (K + 1)];
+            yc[i] = d != 0.0 ? t / d : 0.0;
+          }
+          for (int i = 0; i < kc[c]; ++i) yc[i] = -yc[i];  // gmres_axpy subtracts
+        }
+        if (cudaMemcpyAsync(h1, y.data(), sizeof(double) * y.size(), cudaMemcpyHostToDevice, st) != cudaSuccess ||
+            cudaMemsetAsync(Z, 0, zbytes, st) != cudaSuccess)
+          fail(TQR_ERR_CUDA);
+        gmres_axpy<<<ew_grid(N * nrhs), 256, 0, st>>>(Vb, kmax, N, nrhs, h1, K + 1, Z);
+        // x += dz_v, r += dz_u
+        col_nrm2<<<nrhs, kLsThreads, 0, st>>>(Z + m, N, n, dx2);
+        axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0, Z + m, N, Xw, n);
+        axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, Rr, m, 1.0, Z, N, Rr, m);
+        if (cudaGetLastError() != cudaSuccess) fail(TQR_ERR_CUDA);
+        ++iters;
+        terms();
+        read_back();
+        if (status != TQR_OK) break;
+        berr = berr_of();
+        dxrel = dx_rel(1.0);
+        if (berr <= tol && !(dxrel < 0.5 * prev_dx)) {
+          settled = true;
+          break;
+        }
+        if (!(berr < 0.5 * prev) && !(dxrel < 0.5 * prev_dx)) {
+          if (++stall >= 3) break;
+        } else {
+          stall = 0;
+        }
+        prev = std::min(prev, berr);
+        prev_dx = std::min(prev_dx, dxrel);
+      }
+      if (gm) cudaFreeAsync(gm, st);
+    }
+    // short of tol: maxit (the caller's limit) ends the solve with
+    // TQR_ERR_NOCONV; stagnation hands the problem to an FP64 solve
+    if (status == TQR_OK && !(berr <= tol)) status = iters >= maxit ? TQR_ERR_NOCONV : kLsStalled;
   }
   if (X != nullptr &&
       copy_cols(X, sizeof(double) * ldx, Xw, sizeof(double) * n, sizeof(double) * n, nrhs,
-                        cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+                cudaMemcpyDeviceToDevice, st) != cudaSuccess)
     fail(TQR_ERR_CUDA);
-  if (iters_out) *iters_out = iters;
-  if (berr_out) *berr_out = berr;
+  if (info) {
+    info->path = path;
+    info->iters = iters;
+    info->inner_iters = inner;
+    info->berr = berr;
+  }
   return status;
 }
 
-static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* A, int64_t lda, const double* B,
-                        int64_t ldb, double* X, int64_t ldx, int prec, double tol, int maxit, int* iters_out,
-                        double* berr_out, int nb, int ib, cudaStream_t st) {
+// The FP32 class's way out: a problem FP32 refinement cannot finish (no
+// convergence, or A outside FP32's comfortable range) is solved again in
+// FP64 from its FP64 data.
+static bool wants_fp64(int status) { return status == kLsStalled || status == kLsFp32Range; }
+
+static thread_local tqr_ls_info t_last_info = {};
+
+static int solve_device_prec(int64_t m64, int64_t n64, int64_t nrhs64, const double* A, int64_t lda,
+                             const double* B, int64_t ldb, double* X, int64_t ldx, int prec, double tol, int maxit,
+                             tqr_ls_info* info, int nb, int ib, cudaStream_t st) {
   LsJob job;
   if (!job.init(static_cast<int>(m64), static_cast<int>(n64), static_cast<int>(nrhs64), nb, ib, prec, 0))
     return TQR_ERR_UNSUPPORTED;
@@ -577,11 +885,32 @@ static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* 
   job.bind(ws, false);
   int status = job.factor_solve(A, lda, B, ldb, static_cast<int>(nrhs64), st);
   if (status == TQR_OK)
-    status = job.finish(A, lda, B, ldb, static_cast<int>(nrhs64), X, ldx, tol, maxit, iters_out, berr_out, st);
+    status = job.finish(A, lda, B, ldb, static_cast<int>(nrhs64), X, ldx, tol, maxit, info, st);
   cudaFreeAsync(ws, st);
   int dev_status = TQR_OK;
   if (read_status(&dev_status, st) != cudaSuccess && status == TQR_OK) status = TQR_ERR_CUDA;
   if (dev_status != TQR_OK) status = dev_status;
+  return status;
+}
+
+static int solve_device(int64_t m64, int64_t n64, int64_t nrhs64, const double* A, int64_t lda, const double* B,
+                        int64_t ldb, double* X, int64_t ldx, int prec, double tol, int maxit, tqr_ls_info* info,
+                        int nb, int ib, cudaStream_t st) {
+  tqr_ls_info first = {};
+  first.path = prec == TQR_PREC_FP64 ? TQR_LS_PATH_FP64 : TQR_LS_PATH_FP32;
+  int status = solve_device_prec(m64, n64, nrhs64, A, lda, B, ldb, X, ldx, prec, tol, maxit, &first, nb, ib, st);
+  *info = first;
+  info->fp32_status = TQR_OK;
+  info->berr_fp32 = prec == TQR_PREC_FP32 ? first.berr : 0.0;
+  if (prec == TQR_PREC_FP32 && wants_fp64(status)) {
+    tqr_ls_info second = {};
+    const int s32 = status;
+    status = solve_device_prec(m64, n64, nrhs64, A, lda, B, ldb, X, ldx, TQR_PREC_FP64, tol, 0, &second, nb, ib, st);
+    info->fp32_status = s32 == kLsFp32Range ? TQR_ERR_UNSUPPORTED : TQR_ERR_NOCONV;
+    info->path = TQR_LS_PATH_FP64_FALLBACK;
+    info->berr = second.berr;
+  }
+  if (status == kLsStalled || status == kLsFp32Range) status = TQR_ERR_NOCONV;
   return status;
 }
 
@@ -613,31 +942,184 @@ extern "C" int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A,
   const int ka = ptr_kind(A);
   if (ptr_kind(B) != ka) return -6;
   if (ptr_kind(X) != ka) return -8;
-  if (ka == PTR_DEVICE)
-    return solve_device(m, n, nrhs, A, lda, B, ldb, X, ldx, prec, tol, maxit, iters, berr, nb, ib, st);
-  double *dA = nullptr, *dB = nullptr, *dX = nullptr;
-  if (lib_malloc(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
-      lib_malloc(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess ||
-      lib_malloc(reinterpret_cast<void**>(&dX), sizeof(double) * n * nrhs, st) != cudaSuccess) {
+  tqr_ls_info info = {};
+  int status = TQR_OK;
+  if (ka == PTR_DEVICE) {
+    status = solve_device(m, n, nrhs, A, lda, B, ldb, X, ldx, prec, tol, maxit, &info, nb, ib, st);
+  } else {
+    double *dA = nullptr, *dB = nullptr, *dX = nullptr;
+    if (lib_malloc(reinterpret_cast<void**>(&dA), sizeof(double) * m * n, st) != cudaSuccess ||
+        lib_malloc(reinterpret_cast<void**>(&dB), sizeof(double) * m * nrhs, st) != cudaSuccess ||
+        lib_malloc(reinterpret_cast<void**>(&dX), sizeof(double) * n * nrhs, st) != cudaSuccess) {
+      cudaGetLastError();
+      if (dA) cudaFreeAsync(dA, st);
+      if (dB) cudaFreeAsync(dB, st);
+      return TQR_ERR_NOMEM;
+    }
+    if (copy_cols(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n, cudaMemcpyHostToDevice,
+                  st) != cudaSuccess ||
+        copy_cols(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs, cudaMemcpyHostToDevice,
+                  st) != cudaSuccess)
+      status = TQR_ERR_CUDA;
+    if (status == TQR_OK)
+      status = solve_device(m, n, nrhs, dA, m, dB, m, dX, n, prec, tol, maxit, &info, nb, ib, st);
+    if ((status == TQR_OK || status == TQR_ERR_NOCONV || status == TQR_ERR_RANK) &&
+        copy_cols(X, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n, nrhs, cudaMemcpyDeviceToHost,
+                  st) != cudaSuccess)
+      status = TQR_ERR_CUDA;
+    cudaFreeAsync(dA, st);
+    cudaFreeAsync(dB, st);
+    cudaFreeAsync(dX, st);
+    if (cudaStreamSynchronize(st) != cudaSuccess) return TQR_ERR_CUDA;
+  }
+  if (iters) *iters = info.iters;
+  if (berr) *berr = info.berr;
+  t_last_info = info;
+  return status;
+}
+
+extern "C" int tqr_ls_last_info(tqr_ls_info* info) {
+  if (info == nullptr) return -1;
+  *info = t_last_info;
+  return TQR_OK;
+}
+
+// ---------------------------------------------------------------------------
+// Resident factorization handle: tqr_ls_factor / tqr_ls_solve / tqr_ls_release.
+struct tqr_ls {
+  tqr::LsJob job;             // the requested class's factorization, with the FP64 copy of A
+  char* ws = nullptr;
+  tqr::LsJob job64;           // FP64 factorization made after an FP32 fallback
+  char* ws64 = nullptr;
+  bool has64 = false;
+  int prec = 0;
+  int device = 0;
+};
+
+namespace tqr {
+
+// FP64 factorization of the handle's resident copy of A (for the FP32
+// class's fallback).
+static int ls_make_fp64(tqr_ls* h, cudaStream_t st) {
+  if (h->has64) return TQR_OK;
+  if (!h->job64.init(h->job.m, h->job.n, h->job.rhs_cap, h->job.nb, h->job.ib, TQR_PREC_FP64, 0))
+    return TQR_ERR_UNSUPPORTED;
+  if (lib_malloc(reinterpret_cast<void**>(&h->ws64), h->job64.bytes, st) != cudaSuccess) {
     cudaGetLastError();
-    if (dA) cudaFreeAsync(dA, st);
-    if (dB) cudaFreeAsync(dB, st);
+    h->ws64 = nullptr;
     return TQR_ERR_NOMEM;
   }
+  h->job64.bind(h->ws64, false);
+  const int s = h->job64.factor_solve(h->job.Acopy, h->job.m, nullptr, 0, 0, st);
+  if (s != TQR_OK) {
+    cudaFreeAsync(h->ws64, st);
+    h->ws64 = nullptr;
+    return s;
+  }
+  h->has64 = true;
+  return TQR_OK;
+}
+
+}  // namespace tqr
+
+extern "C" int tqr_ls_factor(int64_t m, int64_t n, const double* A, int64_t lda, int prec, int nb, int ib,
+                             int64_t rhs_cap, void* stream, tqr_ls** out) {
+  if (m < 1) return -1;
+  if (n < 1 || n > m) return -2;
+  if (A == nullptr || ptr_kind(A) != PTR_DEVICE) return -3;
+  if (lda < m) return -4;
+  if (prec != TQR_PREC_FP64 && prec != TQR_PREC_FP32) return -5;
+  if (rhs_cap < 1 || rhs_cap > (1 << 20)) return -8;
+  if (out == nullptr) return -10;
+  *out = nullptr;
+  if (m > (1LL << 30)) return TQR_ERR_UNSUPPORTED;
+  if (nb == 0) nb = n >= 1024 ? 128 : 64;
+  if (ib == 0) ib = std::min(16, nb);
+  const int c = check_tiles(nb, ib, 6, 7);
+  if (c) return c;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  tqr_ls* h = new tqr_ls();
+  h->prec = prec;
+  cudaGetDevice(&h->device);
+  if (!h->job.init(static_cast<int>(m), static_cast<int>(n), static_cast<int>(rhs_cap), nb, ib, prec, 0)) {
+    delete h;
+    return TQR_ERR_UNSUPPORTED;
+  }
+  if (lib_malloc(reinterpret_cast<void**>(&h->ws), h->job.bytes_with_acopy(), st) != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return TQR_ERR_NOMEM;
+  }
+  h->job.bind(h->ws, true);
+  int s = h->job.factor_solve(A, lda, nullptr, 0, 0, st);
+  if (s == kLsFp32Range) {
+    // A outside FP32's range: keep the FP64 copy, factor it in FP64
+    if (copy_cols(h->job.Acopy, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
+                  cudaMemcpyDeviceToDevice, st) != cudaSuccess)
+      s = TQR_ERR_CUDA;
+    else
+      s = ls_make_fp64(h, st);
+  }
+  if (s != TQR_OK) {
+    if (h->ws64) cudaFreeAsync(h->ws64, st);
+    cudaFreeAsync(h->ws, st);
+    delete h;
+    return s;
+  }
+  *out = h;
+  return TQR_OK;
+}
+
+extern "C" int tqr_ls_solve(tqr_ls* h, int64_t nrhs, const double* B, int64_t ldb, double* X, int64_t ldx,
+                            double tol, int maxit, tqr_ls_info* info, void* stream) {
+  if (h == nullptr) return -1;
+  if (nrhs < 1 || nrhs > h->job.rhs_cap) return -2;
+  if (B == nullptr || ptr_kind(B) != PTR_DEVICE) return -3;
+  if (ldb < h->job.m) return -4;
+  if (X == nullptr || ptr_kind(X) != PTR_DEVICE) return -5;
+  if (ldx < h->job.n) return -6;
+  if (!(tol >= 0)) return -7;
+  if (maxit < 0) return -8;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  const int k = static_cast<int>(nrhs);
+  tqr_ls_info inf = {};
   int status = TQR_OK;
-  if (copy_cols(dA, sizeof(double) * m, A, sizeof(double) * lda, sizeof(double) * m, n,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess ||
-      copy_cols(dB, sizeof(double) * m, B, sizeof(double) * ldb, sizeof(double) * m, nrhs,
-                        cudaMemcpyHostToDevice, st) != cudaSuccess)
-    status = TQR_ERR_CUDA;
-  if (status == TQR_OK) status = solve_device(m, n, nrhs, dA, m, dB, m, dX, n, prec, tol, maxit, iters, berr, nb, ib, st);
-  if ((status == TQR_OK || status == TQR_ERR_NOCONV || status == TQR_ERR_RANK) &&
-      copy_cols(X, sizeof(double) * ldx, dX, sizeof(double) * n, sizeof(double) * n, nrhs,
-                        cudaMemcpyDeviceToHost, st) != cudaSuccess)
-    status = TQR_ERR_CUDA;
-  cudaFreeAsync(dA, st);
-  cudaFreeAsync(dB, st);
-  cudaFreeAsync(dX, st);
-  if (cudaStreamSynchronize(st) != cudaSuccess) return TQR_ERR_CUDA;
+  const bool use32 = h->prec == TQR_PREC_FP32 && !h->has64;
+  LsJob& J = use32 || !h->has64 ? h->job : h->job64;
+  inf.path = J.esize == 8 ? TQR_LS_PATH_FP64 : TQR_LS_PATH_FP32;
+  status = J.solve(B, ldb, k, st);
+  if (status == TQR_OK) status = J.finish(h->job.Acopy, h->job.m, B, ldb, k, X, ldx, tol, maxit, &inf, st);
+  inf.berr_fp32 = use32 ? inf.berr : 0.0;
+  if (use32 && wants_fp64(status)) {
+    // refinement cannot finish from the FP32 factors: factor in FP64 once,
+    // keep it for the handle's later solves, and solve this one again
+    const int s32 = status;
+    tqr_ls_info second = {};
+    status = ls_make_fp64(h, st);
+    if (status == TQR_OK) status = h->job64.solve(B, ldb, k, st);
+    if (status == TQR_OK)
+      status = h->job64.finish(h->job.Acopy, h->job.m, B, ldb, k, X, ldx, tol, 0, &second, st);
+    inf.fp32_status = s32 == kLsFp32Range ? TQR_ERR_UNSUPPORTED : TQR_ERR_NOCONV;
+    inf.path = TQR_LS_PATH_FP64_FALLBACK;
+    inf.berr = second.berr;
+  } else if (h->prec == TQR_PREC_FP32 && h->has64) {
+    inf.path = TQR_LS_PATH_FP64_FALLBACK;
+  }
+  if (status == kLsStalled || status == kLsFp32Range) status = TQR_ERR_NOCONV;
+  int dev_status = TQR_OK;
+  if (read_status(&dev_status, st) != cudaSuccess && status == TQR_OK) status = TQR_ERR_CUDA;
+  if (dev_status != TQR_OK) status = dev_status;
+  if (info) *info = inf;
+  t_last_info = inf;
+  return status;
+}
+
+extern "C" int tqr_ls_release(tqr_ls* h, void* stream) {
+  if (h == nullptr) return -1;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  int status = TQR_OK;
+  if (h->ws64 && cudaFreeAsync(h->ws64, st) != cudaSuccess) status = TQR_ERR_CUDA;
+  if (h->ws && cudaFreeAsync(h->ws, st) != cudaSuccess) status = TQR_ERR_CUDA;
+  delete h;
   return status;
 }

@@ -5,10 +5,18 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include "tqr.h"
 #include "tqr_api_internal.h"
 #include "tqr_graph.h"
 
 namespace tqr {
+
+// factor_solve of the FP32 class: A lies outside the range the FP32
+// factorization handles (the caller solves in FP64 instead).  Internal only.
+constexpr int kLsFp32Range = 1000;
+// finish of the FP32 class: every refinement form stagnated (or GMRES used
+// up its steps) before maxit -- the caller solves in FP64 instead.  Internal.
+constexpr int kLsStalled = 1001;
 
 struct LsScratch {
   double* part;  // nsplit * m * nrhs partial products
@@ -36,10 +44,16 @@ struct LsJob {
   bool init(int m, int n, int rhs_cap, int nb, int ib, int prec, int grid_cap);
   size_t bytes_with_acopy() const;
   void bind(char* base, bool with_acopy);
+  // factor A (nrhs = 0: factor only) and with nrhs > 0 solve through it
   int factor_solve(const double* A, long long lda, const double* B, long long ldb, int nrhs, cudaStream_t st);
   int solve(const double* B, long long ldb, int nrhs, cudaStream_t st);
+  // backward error, refinement (FP32 class) and the copy of x to X; info
+  // (may be null) receives the path, steps and backward error
   int finish(const double* A, long long lda, const double* B, long long ldb, int nrhs, double* X, long long ldx,
-             double tol, int maxit, int* iters, double* berr, cudaStream_t st);
+             double tol, int maxit, tqr_ls_info* info, cudaStream_t st);
+  // [U; V] = M^-1 [F; G] through the factors (augmented-system correction)
+  int precond(const double* F, long long ldf, const double* G, long long ldg, double* U, long long ldu, double* V,
+              long long ldv, int nrhs, cudaStream_t st);
   int run_mode(int mode, int trsm, int nrhs, cudaStream_t st);
   int pack_rhs(const double* src, long long lds, int rows, int nrhs, cudaStream_t st, void* tiles = nullptr);
   int unpack_rhs(double* dst, long long ldd, int rows, int nrhs, cudaStream_t st, const void* tiles = nullptr);

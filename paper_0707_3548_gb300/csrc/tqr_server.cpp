@@ -40,9 +40,14 @@ struct Entry {                 // a resident factorization
   int prec = 0;
   LsJob job;
   char* ws = nullptr;
-  size_t bytes = 0;
+  size_t bytes = 0;              // ws plus ws64
   bool busy = false;
   int device = 0;
+  // FP32 class only: the FP64 factorization of the resident copy of A, made
+  // when FP32 refinement could not finish; later requests use it directly
+  LsJob job64;
+  char* ws64 = nullptr;
+  bool has64 = false;
 };
 
 struct Request {
@@ -57,6 +62,7 @@ struct Request {
   bool done = false;
   int status = 0, iters = 0, reused = 0;
   double berr = 0;
+  tqr_ls_info info = {};
 };
 
 }  // namespace tqr
@@ -99,10 +105,30 @@ static bool make_room(tqr_server* S, size_t need, cudaStream_t st) {
       if (!(*it)->busy) victim = it;
     if (victim == S->cache.end()) return false;
     cudaFreeAsync((*victim)->ws, st);
+    if ((*victim)->ws64) cudaFreeAsync((*victim)->ws64, st);
     S->in_use -= (*victim)->bytes;
     S->cache.erase(victim);
   }
   return true;
+}
+
+// FP64 factorization of an FP32 entry's resident copy of A (its fallback);
+// the extra bytes are returned for the budget's accounting.
+static int make_fp64(tqr_server* S, Entry& E, cudaStream_t st, size_t* extra) {
+  *extra = 0;
+  if (!E.job64.init(E.job.m, E.job.n, E.job.rhs_cap, E.job.nb, E.job.ib, TQR_PREC_FP64, S->grid_cap))
+    return TQR_ERR_UNSUPPORTED;
+  if ((S->pool ? cudaMallocFromPoolAsync(reinterpret_cast<void**>(&E.ws64), E.job64.bytes, S->pool, st)
+               : cudaMallocAsync(reinterpret_cast<void**>(&E.ws64), E.job64.bytes, st)) != cudaSuccess) {
+    cudaGetLastError();
+    E.ws64 = nullptr;
+    return TQR_ERR_NOMEM;
+  }
+  E.job64.bind(E.ws64, false);
+  *extra = E.job64.bytes;
+  const int s = E.job64.factor_solve(E.job.Acopy, E.job.m, nullptr, 0, 0, st);
+  if (s == TQR_OK) E.has64 = true;
+  return s;
 }
 
 static void run_request(tqr_server* S, Request& R, cudaStream_t st, std::unique_lock<std::mutex>& lk,
@@ -110,19 +136,57 @@ static void run_request(tqr_server* S, Request& R, cudaStream_t st, std::unique_
   lk.unlock();
   int status = TQR_OK;
   Entry& E = *entry;
+  const int nrhs = static_cast<int>(R.nrhs);
+  size_t extra = 0;
+  bool fp32_tried = false;
   if (fresh) {
-    status = E.job.factor_solve(R.A, R.lda, R.B, R.ldb, static_cast<int>(R.nrhs), st);
+    status = E.job.factor_solve(R.A, R.lda, R.B, R.ldb, nrhs, st);
+    if (status == kLsFp32Range) {
+      // A outside FP32's range: the entry keeps an FP64 factorization
+      R.info.fp32_status = TQR_ERR_UNSUPPORTED;
+      status = copy_cols(E.job.Acopy, sizeof(double) * R.m, R.A, sizeof(double) * R.lda, sizeof(double) * R.m, R.n,
+                         cudaMemcpyDeviceToDevice, st) == cudaSuccess
+                   ? make_fp64(S, E, st, &extra)
+                   : TQR_ERR_CUDA;
+      if (status == TQR_OK) status = E.job64.solve(R.B, R.ldb, nrhs, st);
+    } else {
+      fp32_tried = true;
+    }
+  } else if (E.has64) {
+    status = E.job64.solve(R.B, R.ldb, nrhs, st);
   } else {
-    status = E.job.solve(R.B, R.ldb, static_cast<int>(R.nrhs), st);
+    status = E.job.solve(R.B, R.ldb, nrhs, st);
+    fp32_tried = true;
   }
-  if (status == TQR_OK)
-    status = E.job.finish(E.job.Acopy, R.m, R.B, R.ldb, static_cast<int>(R.nrhs), R.X, R.ldx, R.tol, 40, &R.iters,
-                          &R.berr, st);
+  LsJob& J = fp32_tried ? E.job : E.job64;
+  if (status == TQR_OK) status = J.finish(E.job.Acopy, R.m, R.B, R.ldb, nrhs, R.X, R.ldx, R.tol, 40, &R.info, st);
+  if (fp32_tried && E.prec == TQR_PREC_FP32 && status == kLsStalled) {
+    // FP32 refinement could not finish: solve from an FP64 factorization of
+    // the resident copy, kept for the entry's later requests
+    const int s32 = status;
+    const double b32 = R.info.berr;
+    const int it32 = R.info.iters, in32 = R.info.inner_iters;
+    status = make_fp64(S, E, st, &extra);
+    if (status == TQR_OK) status = E.job64.solve(R.B, R.ldb, nrhs, st);
+    if (status == TQR_OK) status = E.job64.finish(E.job.Acopy, R.m, R.B, R.ldb, nrhs, R.X, R.ldx, R.tol, 0, &R.info, st);
+    R.info.fp32_status = s32 == kLsStalled ? TQR_ERR_NOCONV : s32;
+    R.info.berr_fp32 = b32;
+    R.info.iters = it32;
+    R.info.inner_iters = in32;
+  }
+  if (E.prec == TQR_PREC_FP32 && E.has64) R.info.path = TQR_LS_PATH_FP64_FALLBACK;
+  if (status == kLsStalled || status == kLsFp32Range) status = TQR_ERR_NOCONV;
+  R.iters = R.info.iters;
+  R.berr = R.info.berr;
   int dev_status = TQR_OK;
   if (read_status(&dev_status, st) != cudaSuccess && status == TQR_OK) status = TQR_ERR_CUDA;
   if (dev_status != TQR_OK) status = dev_status;
   if (cudaStreamSynchronize(st) != cudaSuccess && status == TQR_OK) status = TQR_ERR_CUDA;
   lk.lock();
+  if (extra) {
+    E.bytes += extra;
+    S->in_use += extra;
+  }
   R.status = status;
   R.reused = fresh ? 0 : 1;
   R.t_end = Clock::now();
@@ -133,6 +197,7 @@ static void run_request(tqr_server* S, Request& R, cudaStream_t st, std::unique_
     for (auto it = S->cache.begin(); it != S->cache.end(); ++it)
       if (it->get() == &E) {
         cudaFreeAsync(E.ws, st);
+        if (E.ws64) cudaFreeAsync(E.ws64, st);
         S->in_use -= E.bytes;
         S->cache.erase(it);
         break;
@@ -280,7 +345,10 @@ int tqr_server_destroy(tqr_server* S) {
   }
   S->cv_work.notify_all();
   for (auto& t : S->workers) t.join();
-  for (auto& e : S->cache) cudaFreeAsync(e->ws, nullptr);
+  for (auto& e : S->cache) {
+    cudaFreeAsync(e->ws, nullptr);
+    if (e->ws64) cudaFreeAsync(e->ws64, nullptr);
+  }
   cudaDeviceSynchronize();
   if (S->pool) cudaMemPoolDestroy(S->pool);
   delete S;
@@ -329,7 +397,7 @@ int tqr_server_submit(tqr_server* S, uint64_t matrix_id, int64_t m, int64_t n, i
 }
 
 static int report(tqr_server* S, uint64_t request, bool wait, int* done, int* status, int* iters, double* berr,
-                  double* latency_ms, int* reused) {
+                  double* latency_ms, int* reused, tqr_ls_info* info = nullptr) {
   std::unique_lock<std::mutex> lk(S->mu);
   auto it = S->reqs.find(request);
   if (it == S->reqs.end()) return -2;
@@ -342,6 +410,7 @@ static int report(tqr_server* S, uint64_t request, bool wait, int* done, int* st
   if (iters) *iters = R->iters;
   if (berr) *berr = R->berr;
   if (reused) *reused = R->reused;
+  if (info) *info = R->info;
   if (latency_ms) *latency_ms = std::chrono::duration<double, std::milli>(R->t_end - R->t_submit).count();
   S->reqs.erase(it);
   return TQR_OK;
@@ -359,6 +428,13 @@ int tqr_server_wait(tqr_server* S, uint64_t request, int* status, int* iters, do
   if (S == nullptr) return -1;
   int done = 0;
   return report(S, request, true, &done, status, iters, berr, latency_ms, reused);
+}
+
+int tqr_server_wait_info(tqr_server* S, uint64_t request, int* status, tqr_ls_info* info, double* latency_ms,
+                         int* reused) {
+  if (S == nullptr) return -1;
+  int done = 0;
+  return report(S, request, true, &done, status, nullptr, nullptr, latency_ms, reused, info);
 }
 
 int tqr_server_stats(tqr_server* S, double* out) {

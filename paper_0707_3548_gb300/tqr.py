@@ -34,6 +34,14 @@ TQR_ERR_TOO_LARGE = 8
 TQR_ERR_NONFINITE = 9
 TQR_PREC_FP64 = 0
 TQR_PREC_FP32 = 1
+TQR_LS_PATH_FP64 = 0
+TQR_LS_PATH_FP32 = 1
+TQR_LS_PATH_FP32_SEMINORMAL = 2
+TQR_LS_PATH_FP32_AUGMENTED = 3
+TQR_LS_PATH_FP32_GMRES = 4
+TQR_LS_PATH_FP64_FALLBACK = 5
+LS_PATH_NAMES = {0: "fp64", 1: "fp32", 2: "fp32_seminormal", 3: "fp32_augmented", 4: "fp32_gmres",
+                 5: "fp64_fallback"}
 
 _ERRNAMES = {1: "TQR_ERR_CUDA", 2: "TQR_ERR_NOMEM", 3: "TQR_ERR_TIMEOUT", 4: "TQR_ERR_RANK",
              5: "TQR_ERR_NOCONV", 6: "TQR_ERR_BUSY", 7: "TQR_ERR_UNSUPPORTED", 8: "TQR_ERR_TOO_LARGE",
@@ -46,6 +54,17 @@ class TqrDesc(ctypes.Structure):
     """tqr_desc of include/tqr.h."""
     _fields_ = [("m", ctypes.c_int64), ("n", ctypes.c_int64), ("A", ctypes.c_void_p), ("lda", ctypes.c_int64),
                 ("T", ctypes.c_void_p), ("nb", ctypes.c_int32), ("ib", ctypes.c_int32)]
+
+class TqrLsInfo(ctypes.Structure):
+    """tqr_ls_info of include/tqr.h."""
+    _fields_ = [("path", ctypes.c_int32), ("iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
+                ("fp32_status", ctypes.c_int32), ("berr", ctypes.c_double), ("berr_fp32", ctypes.c_double)]
+
+    def as_dict(self):
+        return dict(path=LS_PATH_NAMES.get(self.path, str(self.path)), iters=self.iters,
+                    inner_iters=self.inner_iters, fp32_status=self.fp32_status, berr=self.berr,
+                    berr_fp32=self.berr_fp32)
+
 
 _i64 = ctypes.c_int64
 _int = ctypes.c_int
@@ -63,6 +82,10 @@ SIGNATURES = {
     "tqr_apply_qt": (_int, [ctypes.c_char, _i64, _i64, _i64, _vp, _i64, _int, _int, _vp, _vp, _i64, _vp]),
     "tqr_solve_ls": (_int, [_i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int, _dbl, _int,
                             ctypes.POINTER(_int), ctypes.POINTER(_dbl), _int, _int, _vp]),
+    "tqr_ls_last_info": (_int, [ctypes.POINTER(TqrLsInfo)]),
+    "tqr_ls_factor": (_int, [_i64, _i64, _vp, _i64, _int, _int, _int, _i64, _vp, ctypes.POINTER(_vp)]),
+    "tqr_ls_solve": (_int, [_vp, _i64, _vp, _i64, _vp, _i64, _dbl, _int, ctypes.POINTER(TqrLsInfo), _vp]),
+    "tqr_ls_release": (_int, [_vp, _vp]),
     "tqr_factor_noalloc": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp]),
     "tqr_autotune": (_int, [_i64, _i64, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "tqr_server_create": (_int, [_size, _int, _int, ctypes.POINTER(_vp)]),
@@ -73,6 +96,8 @@ SIGNATURES = {
                                ctypes.POINTER(_int)]),
     "tqr_server_wait": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_int), ctypes.POINTER(_int),
                                ctypes.POINTER(_dbl), ctypes.POINTER(_dbl), ctypes.POINTER(_int)]),
+    "tqr_server_wait_info": (_int, [_vp, ctypes.c_uint64, ctypes.POINTER(_int), ctypes.POINTER(TqrLsInfo),
+                                    ctypes.POINTER(_dbl), ctypes.POINTER(_int)]),
     "tqr_server_stats": (_int, [_vp, _vp]),
     "tqr_server_destroy": (_int, [_vp]),
     "tqr_batch_submit": (_int, [_int, _vp, ctypes.POINTER(ctypes.c_uint64), _vp]),
@@ -414,6 +439,53 @@ def tqr_solve_ls(A, B, X=None, prec=TQR_PREC_FP64, tol=1e-12, maxit=30, nb=0, ib
     return X, iters.value, berr.value, rc
 
 
+def tqr_ls_last_info():
+    """tqr_ls_info (as a dict) of this thread's last tqr_solve_ls / LsHandle.solve."""
+    info = TqrLsInfo()
+    _check("tqr_ls_last_info", lib().tqr_ls_last_info(ctypes.byref(info)))
+    return info.as_dict()
+
+
+class LsHandle:
+    """A resident least-squares factorization (tqr_ls_factor / tqr_ls_solve /
+    tqr_ls_release); A is a CUDA tensor, copied by the library."""
+
+    def __init__(self, A, prec=TQR_PREC_FP64, rhs_cap=16, nb=0, ib=0, stream=None):
+        pa, m, n, lda, cuda = _mat(A, "A")
+        if not cuda:
+            raise ValueError("LsHandle takes device tensors")
+        self.m, self.n, self.rhs_cap = m, n, rhs_cap
+        h = _vp()
+        self.stream = stream
+        _check("tqr_ls_factor", lib().tqr_ls_factor(m, n, pa, lda, prec, nb, ib, rhs_cap, _stream(True, stream),
+                                                     ctypes.byref(h)))
+        self.h = h
+
+    def solve(self, B, X=None, tol=1e-12, maxit=30, check=True):
+        """Returns (X, info dict, status)."""
+        pb, mb, nrhs, ldb, _ = _mat(B, "B")
+        if X is None:
+            X = colmajor(_torch().zeros((self.n, nrhs), dtype=_torch().float64, device=B.device))
+        px, _, _, ldx, _ = _mat(X, "X")
+        info = TqrLsInfo()
+        rc = lib().tqr_ls_solve(self.h, nrhs, pb, ldb, px, ldx, tol, maxit, ctypes.byref(info),
+                                _stream(True, self.stream))
+        if check and rc != TQR_OK:
+            raise TqrError("tqr_ls_solve", rc)
+        return X, info.as_dict(), rc
+
+    def release(self):
+        if self.h:
+            _check("tqr_ls_release", lib().tqr_ls_release(self.h, _stream(True, self.stream)))
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.release()
+        except Exception:
+            pass
+
+
 def tqr_stream_status(stream=None):
     return lib().tqr_stream_status(_stream(True, stream))
 
@@ -615,6 +687,16 @@ class Server:
         if rc != 0:
             raise TqrError("tqr_server_wait", rc)
         return dict(status=st.value, iters=it.value, berr=be.value, latency_ms=lat.value, reused=ru.value)
+
+    def wait_info(self, request):
+        """Blocking; (status, tqr_ls_info dict, latency_ms, reused)."""
+        st, lat, ru = _int(0), _dbl(0), _int(0)
+        info = TqrLsInfo()
+        rc = lib().tqr_server_wait_info(self.h, request, ctypes.byref(st), ctypes.byref(info), ctypes.byref(lat),
+                                        ctypes.byref(ru))
+        if rc != 0:
+            raise TqrError("tqr_server_wait_info", rc)
+        return st.value, info.as_dict(), lat.value, ru.value
 
     def stats(self):
         out = np.zeros(8)

@@ -4,11 +4,13 @@ start-up, or code that may not risk an allocation's latency or failure).  Its
 scratch is a static device array inside libtqr.
 
 The checks call the new entry point through the C ABI and compare it with
-tqr_factor, within the tolerance the other parity tests use, over calls in a
-row (the array keeps the previous call's contents, so stale counters would
-show).  The file name makes pytest collect it last, so a run that stops at the
-first failure has already run every other test; it also passes on its own in
-a fresh process."""
+tqr_factor over calls in a row (the array keeps the previous call's contents,
+so stale counters would show).  Each tile's sequence of updates is fixed by
+the task DAG, so the sequential task order of this entry point and the
+scheduled order of tqr_factor give the same bits: F and T must be equal.
+The file name makes pytest collect it last, so a run that stops at the first
+failure has already run every other test; it also passes on its own in a
+fresh process."""
 import numpy as np
 import pytest
 
@@ -43,8 +45,8 @@ def test_noalloc_matches_tqr_factor_on_calls_in_a_row():
         assert rc == tqr.TQR_OK
         assert tqr.tqr_stream_status() == tqr.TQR_OK
         Fr, Tr = _reference(A, nb, ib)
-        assert np.max(np.abs(F - Fr)) <= 1e-11 * np.abs(Fr).max(), (m, n, seed)
-        assert np.max(np.abs(T - Tr)) <= 1e-11 * max(1.0, np.abs(Tr).max()), (m, n, seed)
+        assert np.array_equal(F, Fr), (m, n, seed, np.max(np.abs(F - Fr)))
+        assert np.array_equal(T, Tr), (m, n, seed, np.max(np.abs(T - Tr)))
 
 
 def test_noalloc_rejects_what_does_not_fit():
