@@ -453,6 +453,14 @@ def run_ours(args, w):
             dist.barrier()
             dist.destroy_process_group()
         return
+    # the least-squares half of the metric: plain FP64 against FP32 +
+    # refinement on the 16384 x 4096, kappa = 1e2 problem, equal error 1e-12
+    ls = None
+    if world == 1 and not args.no_ls:
+        dA = dA0 = T = None
+        torch.cuda.empty_cache()
+        ls = ls_measure(16384, 4096, 1e2, 128, 16, 1, 2)
+        ls["workload"] = "least squares 16384x4096, A = U diag(sigma) V^T, kappa 1e2, nrhs 1, nb 128 ib 16, seed 0"
     cpu = None
     if world == 1 and not args.no_cpu_baseline:
         rates, c, times = oracle_sample(m, n, 6.0, 2)
@@ -476,6 +484,7 @@ def run_ours(args, w):
         "gpu_launches": 3 * args.steps,
         "clocks": clk.summary(),
         "status": status,
+        "ls": ls,
     }
     print(json.dumps(line), flush=True)
     if dist is not None:
@@ -483,43 +492,65 @@ def run_ours(args, w):
         dist.destroy_process_group()
 
 
-def run_ls(args, w):
-    """Least-squares solves/s, plain FP64 vs FP32 + refinement, same problem,
-    same backward-error target (1e-12)."""
+def ls_measure(m, n, kappa, nb, ib, warmup, steps, problem=None):
+    """One least-squares problem (A = U diag(sigma) V^T, seed 0, one right-hand
+    side) solved by tqr_solve_ls in plain FP64 and in FP32 + refinement, both
+    to backward error 1e-12: wall time per solve (device buffers, stream
+    synchronized), the device-reported and the host-recomputed backward
+    errors, and the refinement path."""
     import numpy as np
     import torch
 
-    from paper_0707_3548_gb300 import build as B
     from paper_0707_3548_gb300 import inputs, tqr
 
-    torch.cuda.set_device(0)
-    B.build()
-    m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
-    A, b, x_true = inputs.conditioned_ls_problem(m, n, w["kappa"], seed=0)
+    A, b, _ = problem if problem is not None else inputs.conditioned_ls_problem(m, n, kappa, seed=0)
     dA = tqr.colmajor(torch.from_numpy(A).cuda())
     db = tqr.colmajor(torch.from_numpy(b[:, None]).cuda())
     out = {}
     xs = {}
     for name, prec in (("fp64", tqr.TQR_PREC_FP64), ("fp32_refined", tqr.TQR_PREC_FP32)):
         times, its, berrs, rcs = [], [], [], []
-        for step in range(args.warmup + args.steps):
+        info = {}
+        for step in range(warmup + steps):
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             X, it, berr, rc = tqr.tqr_solve_ls(dA, db, prec=prec, tol=1e-12, maxit=40, nb=nb, ib=ib, check=False)
             torch.cuda.synchronize()
             t1 = time.perf_counter()
-            if step >= args.warmup:
+            info = tqr.tqr_ls_last_info()
+            if step >= warmup:
                 times.append(t1 - t0)
                 its.append(it)
                 berrs.append(berr)
                 rcs.append(rc)
         xs[name] = X.cpu().numpy()[:, 0]
+        r = b - A @ xs[name]
+        nA = float(np.linalg.norm(A))
+        host_berr = float(np.linalg.norm(A.T @ r) / (nA * (nA * np.linalg.norm(xs[name]) + np.linalg.norm(b))))
         lat = sorted(times)
-        out[name] = {"solves_per_s": 1.0 / statistics.mean(times), "p50_ms": 1e3 * lat[len(lat) // 2],
+        out[name] = {"ms": 1e3 * statistics.mean(times), "solves_per_s": 1.0 / statistics.mean(times),
+                     "p50_ms": 1e3 * lat[len(lat) // 2],
                      "p99_ms": 1e3 * lat[min(len(lat) - 1, int(0.99 * len(lat)))], "iters": its[-1],
-                     "berr": max(berrs), "status": rcs[-1]}
+                     "inner_iters": info.get("inner_iters"), "path": info.get("path"),
+                     "berr": max(berrs), "berr_host": host_berr, "status": rcs[-1]}
     ref = xs["fp64"]
     out["fp32_refined"]["rel_diff_vs_fp64"] = float(np.linalg.norm(xs["fp32_refined"] - ref) / np.linalg.norm(ref))
+    out["speedup_vs_fp64"] = out["fp64"]["ms"] / out["fp32_refined"]["ms"]
+    out["equal_error"] = bool(out["fp64"]["berr_host"] <= 1e-12 and out["fp32_refined"]["berr_host"] <= 1e-12)
+    return out
+
+
+def run_ls(args, w):
+    """Least-squares solves/s, plain FP64 vs FP32 + refinement, same problem,
+    same backward-error target (1e-12)."""
+    import torch
+
+    from paper_0707_3548_gb300 import build as B
+
+    torch.cuda.set_device(0)
+    B.build()
+    m, n, nb, ib = w["m"], w["n"], w["nb"], w["ib"]
+    out = ls_measure(m, n, w["kappa"], nb, ib, args.warmup, args.steps)
     cpu = None
     if not args.no_cpu_baseline:
         fl, tt, smp = oracle_kind_sample("ls", {"m": m, "n": n, "kappa": w["kappa"]}, 8.0)
@@ -531,7 +562,7 @@ def run_ls(args, w):
             "steps": args.steps, "warmup": args.warmup, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic: A = U diag(sigma) V^T, seed 0",
             "config": {"workload": "least squares %dx%d kappa=%g, nrhs=1, nb=%d ib=%d" % (m, n, w["kappa"], nb, ib)},
-            "ls": out, "speedup_vs_fp64": out["fp32_refined"]["solves_per_s"] / out["fp64"]["solves_per_s"],
+            "ls": out, "speedup_vs_fp64": out["speedup_vs_fp64"],
             "cpu_baseline": cpu}
     print(json.dumps(line), flush=True)
 
@@ -952,6 +983,7 @@ def main():
     ap.add_argument("--workload", default="qr16384_pairs", choices=sorted(WORKLOADS))
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
+    ap.add_argument("--no-ls", action="store_true", help="skip the least-squares comparison of the default line")
     ap.add_argument("--nb", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--ib", type=int, default=0, help="override the workload's inner block size")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: arrival rate (req/s)")
