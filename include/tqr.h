@@ -284,7 +284,7 @@ int tqr_lu_solve_pairs(int64_t n, int64_t nrhs, const double* A, int64_t lda, in
  *                           GMRES-IR on the same system, left-preconditioned
  *                           by the FP32 factors (Carson, Higham and Pranesh
  *                           2020).  A problem none of them finishes -- or
- *                           whose ||A||_F lies outside [2^-100, 2^100] -- is
+ *                           whose ||A||_F lies outside [2^-40, 2^40] -- is
  *                           solved again in plain FP64 (tqr_ls_last_info
  *                           tells which path gave the result)
  *   tol        (arg 11)     backward-error target for refinement (e.g. 1e-12)
@@ -325,7 +325,9 @@ int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t ld
  *                               TQR_ERR_UNSUPPORTED for ||A||_F outside
  *                               FP32's range)
  * iters: outer refinement steps; inner_iters: GMRES steps; berr: the final
- * backward error; berr_fp32: the one the FP32 refinement reached.
+ * backward error; berr_fp32: the one the FP32 refinement reached;
+ * gmres_res: the relative residual the last GMRES cycle reached (max over
+ * right-hand sides; 0 if GMRES did not run).
  * tqr_ls_last_info(&info) returns this for the calling thread's last
  * tqr_solve_ls or tqr_ls_solve (0, or -1 for a NULL pointer).
  */
@@ -339,7 +341,7 @@ enum {
 };
 typedef struct tqr_ls_info {
   int32_t path, iters, inner_iters, fp32_status;
-  double berr, berr_fp32;
+  double berr, berr_fp32, gmres_res;
 } tqr_ls_info;
 int tqr_ls_last_info(tqr_ls_info* info);
 
@@ -356,7 +358,7 @@ int tqr_ls_last_info(tqr_ls_info* info);
  *   the most right-hand sides one solve may take.  Device memory: the tiles,
  *   the copy of A and work arrays for rhs_cap columns.  Asynchronous on
  *   stream, except that the FP32 class synchronizes once to check ||A||_F
- *   (outside [2^-100, 2^100] the handle factors in FP64 instead).  Returns
+ *   (outside [2^-40, 2^40] the handle factors in FP64 instead).  Returns
  *   0 and *h, -i, TQR_ERR_NOMEM, TQR_ERR_UNSUPPORTED or TQR_ERR_CUDA.
  * tqr_ls_solve(h, nrhs, B, ldb, X, ldx, tol, maxit, info, stream)
  *   B (device, m x nrhs, 1 <= nrhs <= rhs_cap), X (device, n x nrhs);

@@ -16,7 +16,12 @@ so), written for a reader who checks it against the paper by eye:
 * ``dag``          -- the task set of Algorithm 1, its dependency edges
   (Section 3.3) and the per-step operation count (Section 3.2, Eq. opcount).
 * ``lstsq``        -- least squares through the QR factors, the normwise
-  backward error, and augmented-system iterative refinement (Bjorck).
+  backward error, and iterative refinement: semi-normal, augmented-system
+  (Bjorck) and GMRES-based (Carson, Higham and Pranesh).
+* ``ctiled``       -- the paper's multicore design in plain C (ctiled.c): the
+  Section 3.1 tile kernels under Section 3.3's dynamic DAG scheduling on
+  POSIX threads; the benchmark's multithreaded CPU baseline, checked against
+  ``tiled``.
 
 Parity status: every function here is pinned by a ``-m "not gpu"`` test
 against something other than itself (closed forms, 50-digit brute force,

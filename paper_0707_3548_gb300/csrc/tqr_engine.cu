@@ -631,10 +631,33 @@ __device__ __forceinline__ void publish_refl(double* red, int c, double alpha, d
   r[1] = static_cast<real>(f.scal);
 }
 
+//
+// The dot products x^T p_d use the unscaled x, which is exact in range while
+// the panel's entries stay within [2^-480, 2^480]: products then neither
+// overflow nor underflow to nothing.  A FP64 panel with a larger or a
+// nonzero smaller max |entry| takes the dot products on v = s x instead
+// (one more multiply per element), so entries up to the FP64 limits
+// factor without overflow (decided once per panel, uniformly per block).
 template <typename real, bool TS>
 __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, double* red, double* taus) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
   constexpr int nwarps = kThreads / 32;
+  bool extreme = false;
+  if constexpr (sizeof(real) == 8) {
+    __shared__ unsigned long long s_amax;
+    if (tid == 0) s_amax = 0;
+    __syncthreads();
+    unsigned long long mx = 0;
+    for (int e = tid; e < nr * ib; e += kThreads) {
+      const unsigned long long b = abs_bits(P[(e % nr) + (e / nr) * ldP]);
+      mx = b > mx ? b : mx;
+    }
+    mx = warp_max_u64(mx);
+    if (lane == 0 && mx != 0) atomicMax(&s_amax, mx);
+    __syncthreads();
+    const double amax = __longlong_as_double(static_cast<long long>(s_amax));
+    extreme = amax > 0x1p480 || (amax != 0.0 && amax < 0x1p-480);
+  }
   // reflector of column 0
   if (wid == 0) {
     const double xn = TS ? warp_norm<real>(P, nr) : warp_norm<real>(P + 1, nr - 1);
@@ -667,14 +690,18 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
       real* pd = P + d * ldP;
       if (tau != real(0)) {
         real acc = real(0);
-        for (int r = r0 + lane; r < nr; r += 32) acc = fma(pc[r], pd[r], acc);
+        if (!extreme) {
+          for (int r = r0 + lane; r < nr; r += 32) acc = fma(pc[r], pd[r], acc);
+        } else {
+          for (int r = r0 + lane; r < nr; r += 32) acc = fma(pc[r] * scal, pd[r], acc);
+        }
         acc = warp_sum(acc);
         real top;
         if constexpr (TS)
           top = R[c + d * ldr];
         else
           top = pd[c];
-        const real wv = tau * fma(scal, acc, top);
+        const real wv = extreme ? tau * (acc + top) : tau * fma(scal, acc, top);
         const real coef = -(wv * scal);
         for (int r = r0 + lane; r < nr; r += 32) pd[r] = fma(coef, pc[r], pd[r]);
         if (lane == 0) {

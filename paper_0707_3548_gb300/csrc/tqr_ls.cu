@@ -325,10 +325,11 @@ static size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 constexpr int kGmresRestart = 30;
 constexpr double kGmresInnerTol = 1e-3;
 constexpr int kGmresMaxInner = 300;
-// The FP32 factorization is used only for A with 2^-100 <= ||A||_F <= 2^100
-// (its entries, R and the reflectors then stay far inside FP32's range);
-// other problems are solved in FP64.
-constexpr double kFp32NormLo = 0x1p-100, kFp32NormHi = 0x1p100;
+// The FP32 factorization is used only for A with 2^-40 <= ||A||_F <= 2^40:
+// every entry is then at most 2^40, so the FP32 products of the panel and
+// update kernels stay below 2^80, far from FP32's overflow at 2^128; other
+// problems are solved in FP64.
+constexpr double kFp32NormLo = 0x1p-40, kFp32NormHi = 0x1p40;
 
 // ---------------------------------------------------------------------------
 // LsJob: device state of one least-squares problem.  The tiles of A (and T)
@@ -534,7 +535,7 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
   std::vector<double> hn(4 * R + 4);
   int status = TQR_OK;
   int iters = 0, inner = 0, path = esize == 8 ? TQR_LS_PATH_FP64 : TQR_LS_PATH_FP32;
-  double berr = INFINITY;
+  double berr = INFINITY, gres = 0.0;
   auto fail = [&](int s) {
     if (status == TQR_OK && s != TQR_OK) status = s;
   };
@@ -549,7 +550,11 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     for (int c = 0; c < nrhs; ++c) {
       const double num = hn[c];
       const double den = nA * (nA * hn[R + c] + hn[2 * R + c]);
-      const double eta = den > 0 ? num / den : (num > 0 ? INFINITY : 0.0);
+      // a NaN anywhere (x included) makes the backward error NaN
+      const double eta = std::isnan(num) || std::isnan(den) ? NAN
+                         : den > 0                          ? num / den
+                         : (num > 0 ? INFINITY : 0.0);
+      if (std::isnan(eta)) return static_cast<double>(NAN);
       if (!(eta <= worst)) worst = eta;
     }
     return worst;
@@ -803,9 +808,11 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
         if (status != TQR_OK) break;
         // y_c from the rotated triangle (k_c steps), z = sum_i y_i v_i
         int kmax = 0;
+        gres = 0.0;
         for (int c = 0; c < nrhs; ++c) {
           if (kc[c] < 0) kc[c] = steps;
           kmax = std::max(kmax, kc[c]);
+          if (kc[c] > 0) gres = std::max(gres, std::fabs(g[static_cast<size_t>(c) * (K + 1) + kc[c]]) / beta[c]);
           const double* Hc = Hh.data() + static_cast<size_t>(c) * (K + 1) * K;
           const double* gc = g.data() + static_cast<size_t>(c) * (K + 1);
           double* yc = y.data() + static_cast<size_t>(c) * (K + 1);
@@ -860,6 +867,7 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     info->iters = iters;
     info->inner_iters = inner;
     info->berr = berr;
+    info->gmres_res = gres;
   }
   return status;
 }

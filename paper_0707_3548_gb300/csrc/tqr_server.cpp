@@ -166,6 +166,7 @@ static void run_request(tqr_server* S, Request& R, cudaStream_t st, std::unique_
     const int s32 = status;
     const double b32 = R.info.berr;
     const int it32 = R.info.iters, in32 = R.info.inner_iters;
+    const double g32 = R.info.gmres_res;
     status = make_fp64(S, E, st, &extra);
     if (status == TQR_OK) status = E.job64.solve(R.B, R.ldb, nrhs, st);
     if (status == TQR_OK) status = E.job64.finish(E.job.Acopy, R.m, R.B, R.ldb, nrhs, R.X, R.ldx, R.tol, 0, &R.info, st);
@@ -173,6 +174,7 @@ static void run_request(tqr_server* S, Request& R, cudaStream_t st, std::unique_
     R.info.berr_fp32 = b32;
     R.info.iters = it32;
     R.info.inner_iters = in32;
+    R.info.gmres_res = g32;
   }
   if (E.prec == TQR_PREC_FP32 && E.has64) R.info.path = TQR_LS_PATH_FP64_FALLBACK;
   if (status == kLsStalled || status == kLsFp32Range) status = TQR_ERR_NOCONV;
