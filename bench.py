@@ -1045,6 +1045,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-ls", action="store_true", help="skip the least-squares comparison of the default line")
+    ap.add_argument("--variant", default="", choices=["", "flat", "pairs", "tree"],
+                    help="override the factorization variant of a QR workload")
     ap.add_argument("--nb", type=int, default=0, help="override the workload's tile size")
     ap.add_argument("--ib", type=int, default=0, help="override the workload's inner block size")
     ap.add_argument("--rate", type=float, default=0.0, help="serve: arrival rate (req/s)")
@@ -1057,6 +1059,11 @@ def main():
         w["nb"] = args.nb
     if args.ib:
         w["ib"] = args.ib
+    if args.variant:
+        w.pop("pairs", None)
+        w.pop("tree", None)
+        if args.variant != "flat":
+            w[args.variant] = True
     if args.slots:
         w["slots"] = args.slots
     if args.impl == "reference":

@@ -528,18 +528,18 @@ __device__ __forceinline__ void apply_any(const real* V, int ldv, int nv, const 
 }
 
 // Column measure for the reflector, by one warp (every lane returns the same
-// bits: xor-butterfly reductions).
-//   FP64 columns: ||x|| over x[0..len), taken directly when max|x| lies in
-//   [2^-500, 2^500] (no intermediate can overflow or lose the result to
-//   underflow there), otherwise recomputed on x scaled by an exact power of
-//   two.
-//   FP32 columns: the FP64 sum of squares ||x||^2 itself.  Each square is
-//   exact in FP64 and lies in [2^-298, 2^256], so no scaling is ever needed,
-//   and the square root is left to make_refl (one FP64 square root per
-//   column instead of two: on this GPU each FP64 instruction of a lone warp
-//   costs tens of cycles, and the panel's column chain is serial).
+// bits: xor-butterfly reductions).  Sets *squared and returns
+//   ||x||^2 (*squared = true) for FP32 columns (each square is exact in FP64
+//   and lies in [2^-298, 2^256]) and for FP64 columns of a normal-range
+//   panel whose sum of squares lies in [2^-900, 2^900] (no square that
+//   matters can have been lost to underflow, none can overflow); the square
+//   root is then left to make_refl -- one FP64 square root per column
+//   instead of two (on this GPU each FP64 instruction of a lone warp costs
+//   tens of cycles, and the panel's column chain is serial);
+//   ||x|| (*squared = false) otherwise, taken on x scaled by an exact power
+//   of two when max|x| is outside [2^-500, 2^500].
 template <typename real>
-__device__ double warp_norm(const real* x, int len) {
+__device__ double warp_norm(const real* x, int len, bool extreme, bool* squared) {
   const int lane = threadIdx.x & 31;
   double ssq = 0.0;
   for (int r = lane; r < len; r += 32) {
@@ -547,9 +547,12 @@ __device__ double warp_norm(const real* x, int len) {
     ssq = fma(v, v, ssq);
   }
   ssq = warp_sum(ssq);
+  *squared = true;
   if constexpr (sizeof(real) == 4) {
     return ssq;
   } else {
+    if (!extreme && ssq >= 0x1p-900 && ssq <= 0x1p900) return ssq;
+    *squared = false;
     const double amax = warp_amax(x, len, lane);
     if (amax != 0.0 && isfinite(amax) && (amax < 0x1p-500 || amax > 0x1p500)) {
       const int e = ilogb(amax);
@@ -567,8 +570,7 @@ __device__ double warp_norm(const real* x, int len) {
 }
 
 // Householder reflector (LAPACK convention, FP64) from alpha and the
-// column measure of x2 (warp_norm: ||x2|| for FP64 columns, ||x2||^2 for
-// FP32 ones):
+// column measure of x2 (warp_norm):
 //   beta = -sign(alpha) ||[alpha; x2]||, tau = (beta - alpha)/beta and the
 //   scale 1/(alpha - beta) of v.  Pure function of its inputs, so threads
 //   that call it on the same values agree bit for bit.
@@ -576,19 +578,20 @@ struct Refl {
   double tau, beta, scal;
 };
 
-// FP32 columns: ||[alpha; x2]|| = sqrt(alpha^2 + ||x2||^2) needs no overflow
-// guard (all terms lie far inside FP64's range), and tau and the scale share
-// one FP64 reciprocal: with d = alpha - beta, 1/d = beta/(d beta) and
-// tau = -d/beta = -d^2/(d beta) (a few FP64 ulps apart from the two
-// divisions, far below the FP32 rounding they are followed by).
+// xm = ||x2||^2 (squared): ||[alpha; x2]|| = sqrt(alpha^2 + ||x2||^2) needs
+// no overflow guard (|alpha| stays below 2^490 in a normal-range panel, and
+// FP32 data is far inside FP64's range), and tau and the scale share one
+// FP64 reciprocal: with d = alpha - beta, 1/d = beta/(d beta) and
+// tau = -d/beta = -d^2/(d beta) (a few ulps from the two divisions).
+// xm = ||x2||: hypot and two divisions, safe for any finite entries.
 template <typename real>
-__device__ __forceinline__ Refl make_refl(double alpha, double xm) {
+__device__ __forceinline__ Refl make_refl(double alpha, double xm, bool squared) {
   Refl f;
   if (xm == 0.0) {
     f.tau = 0.0;
     f.beta = alpha;
     f.scal = 0.0;
-  } else if constexpr (sizeof(real) == 4) {
+  } else if (squared) {
     const double h = sqrt(fma(alpha, alpha, xm));
     f.beta = (alpha >= 0.0) ? -h : h;  // sign(0) = +1, also for -0.0
     const double d = alpha - f.beta;
@@ -604,24 +607,9 @@ __device__ __forceinline__ Refl make_refl(double alpha, double xm) {
   return f;
 }
 
-// Unblocked QR of an ib-wide panel (DGEQR2 on the panel, Section 2).
-//   TS == false (GEQRT): P is nr x ib; reflector c has v = [1; s x], x =
-//                        P(c+1:nr, c), s = 1/(alpha - beta).
-//   TS == true  (TSQRT): the top is the ib x ib triangle R (ld ldr) and P is
-//                        nr x ib below it; reflector c has v = [e_c; s x],
-//                        x = P(:, c).
-// One barrier per column.  Reflector c is derived once, by the warp that
-// owns column c (warp 0): during step c-1 it applies reflector c-1 to
-// column c, then takes the FP64 norm of column c's x2 and the reflector
-// (tau, beta, scale) from it, and publishes them in red[4 (c & 1) ...] (FP64)
-// and, rounded to the tile precision, after red + 8.  The warps owning
-// columns d > c apply it with v formed on the fly from the unscaled x:
-// w = top + s (x^T p_d), p_d -= (tau w s) x, top -= tau w.  Column c itself
-// (v = s x, beta, tau) is written by warp 0 during the next step, when no
-// warp reads it.
 template <typename real, bool TS>
-__device__ __forceinline__ void publish_refl(double* red, int c, double alpha, double xn) {
-  const Refl f = make_refl<real>(alpha, xn);
+__device__ __forceinline__ void publish_refl(double* red, int c, double alpha, double xn, bool squared) {
+  const Refl f = make_refl<real>(alpha, xn, squared);
   double* d = red + 4 * (c & 1);
   d[0] = f.tau;
   d[1] = f.beta;
@@ -652,6 +640,14 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
       const unsigned long long b = abs_bits(P[(e % nr) + (e / nr) * ldP]);
       mx = b > mx ? b : mx;
     }
+    if (TS)  // the top triangle's entries enter alpha and the updates too
+      for (int e = tid; e < ib * ib; e += kThreads) {
+        const int i = e % ib, j = e / ib;
+        if (i <= j) {
+          const unsigned long long b = abs_bits(R[i + j * ldr]);
+          mx = b > mx ? b : mx;
+        }
+      }
     mx = warp_max_u64(mx);
     if (lane == 0 && mx != 0) atomicMax(&s_amax, mx);
     __syncthreads();
@@ -660,8 +656,9 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
   }
   // reflector of column 0
   if (wid == 0) {
-    const double xn = TS ? warp_norm<real>(P, nr) : warp_norm<real>(P + 1, nr - 1);
-    if (lane == 0) publish_refl<real, TS>(red, 0, static_cast<double>(TS ? R[0] : P[0]), xn);
+    bool sq;
+    const double xn = TS ? warp_norm<real>(P, nr, extreme, &sq) : warp_norm<real>(P + 1, nr - 1, extreme, &sq);
+    if (lane == 0) publish_refl<real, TS>(red, 0, static_cast<double>(TS ? R[0] : P[0]), xn, sq);
   }
   __syncthreads();
   for (int c = 0; c <= ib; ++c) {
@@ -714,10 +711,12 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
       if (d == c + 1) {
         // this warp owns the next column: its reflector, for step c + 1
         __syncwarp();
-        const double xn = TS ? warp_norm<real>(pd, nr) : warp_norm<real>(pd + c + 2, nr - c - 2);
+        bool sq;
+        const double xn = TS ? warp_norm<real>(pd, nr, extreme, &sq)
+                             : warp_norm<real>(pd + c + 2, nr - c - 2, extreme, &sq);
         if (lane == 0) {
           const double alpha = static_cast<double>(TS ? R[(c + 1) + (c + 1) * ldr] : pd[c + 1]);
-          publish_refl<real, TS>(red, c + 1, alpha, xn);
+          publish_refl<real, TS>(red, c + 1, alpha, xn, sq);
         }
       }
     }

@@ -95,13 +95,24 @@ __global__ void combine_partials(const double* __restrict__ P, int nsplit, int m
   }
 }
 
-// G(j, c) = alpha * sum_r A(r, j) R(r, c): one warp per column j.
+// Power of two near 1 / nA (1 for zero or non-finite nA): the exact scale
+// that keeps products of A's entries with vectors of A's size finite.
+__host__ __device__ inline double norm_scale(double nA) {
+  return nA > 0.0 && nA <= 1.7976931348623157e308 ? ldexp(1.0, -ilogb(nA)) : 1.0;
+}
+
+// G(j, c) = alpha * sum_r (s A(r, j)) R(r, c): one warp per column j, with
+// s = norm_scale(*nA) when nA is given (else 1) -- the backward error's
+// A^T r, whose true size ||A|| ||r|| may exceed FP64's range, is formed as
+// s A^T r.
 __global__ void __launch_bounds__(kLsThreads) gemm_tn(const double* __restrict__ A, long long lda, int m, int n,
                                                       const double* __restrict__ R, long long ldr, int nrhs,
-                                                      double alpha, double* __restrict__ G, long long ldg) {
+                                                      double alpha, double* __restrict__ G, long long ldg,
+                                                      const double* __restrict__ nA) {
   const int lane = threadIdx.x & 31;
   const int j = blockIdx.x * (kLsThreads / 32) + (threadIdx.x >> 5);
   if (j >= n) return;
+  const double s = nA ? norm_scale(*nA) : 1.0;
   const double* a = A + static_cast<long long>(j) * lda;
   for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
     const int cw = min(kRhsChunk, nrhs - c0);
@@ -109,7 +120,7 @@ __global__ void __launch_bounds__(kLsThreads) gemm_tn(const double* __restrict__
 #pragma unroll
     for (int c = 0; c < kRhsChunk; ++c) acc[c] = 0.0;
     for (int r = lane; r < m; r += 32) {
-      const double av = a[r];
+      const double av = a[r] * s;
 #pragma unroll
       for (int c = 0; c < kRhsChunk; ++c)
         if (c < cw) acc[c] = fma(av, R[r + static_cast<long long>(c0 + c) * ldr], acc[c]);
@@ -298,10 +309,11 @@ static cudaError_t resid(const LsScratch& sc, const double* A, long long lda, in
   return cudaGetLastError();
 }
 
+// G = alpha s A^T R, s = norm_scale(*nA) (nA null: s = 1)
 static cudaError_t atr(const double* A, long long lda, int m, int n, const double* R, long long ldr, int nrhs,
-                       double alpha, double* G, long long ldg, cudaStream_t st) {
+                       double alpha, double* G, long long ldg, cudaStream_t st, const double* nA = nullptr) {
   const int wpb = kLsThreads / 32;
-  gemm_tn<<<(n + wpb - 1) / wpb, kLsThreads, 0, st>>>(A, lda, m, n, R, ldr, nrhs, alpha, G, ldg);
+  gemm_tn<<<(n + wpb - 1) / wpb, kLsThreads, 0, st>>>(A, lda, m, n, R, ldr, nrhs, alpha, G, ldg, nA);
   return cudaGetLastError();
 }
 
@@ -325,6 +337,14 @@ static size_t al(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 constexpr int kGmresRestart = 30;
 constexpr double kGmresInnerTol = 1e-3;
 constexpr int kGmresMaxInner = 300;
+// GMRES-IR runs only while R's diagonal spread puts kappa u_fp32 below 0.1,
+// and stops after a cycle that left the relative residual above 0.1: beyond
+// that the FP32 factors, applied in FP32, no longer precondition the
+// augmented system well enough for GMRES to converge in a few steps (their
+// rounding acts as a perturbation of the operator), and an FP64 solve is
+// the faster way to the answer.
+constexpr double kGmresSpreadLimit = 0.1;
+constexpr double kGmresGiveUp = 0.1;
 // The FP32 factorization is used only for A with 2^-40 <= ||A||_F <= 2^40:
 // every entry is then at most 2^40, so the FP32 products of the panel and
 // update kernels stay below 2^80, far from FP32's overflow at 2^128; other
@@ -544,12 +564,16 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
         cudaStreamSynchronize(st) != cudaSuccess)
       fail(TQR_ERR_CUDA);
   };
+  // hn[c] holds s ||A^T e|| with s = norm_scale(||A||_F) (exact power of
+  // two), so the ratio is formed as s||A^T e|| / ((s ||A||) (||A|| ||x|| + ||b||))
+  // -- every factor finite for any finite data
   auto berr_of = [&]() {
     double worst = 0.0;
     const double nA = hn[4 * R];
+    const double sA = norm_scale(nA);
     for (int c = 0; c < nrhs; ++c) {
       const double num = hn[c];
-      const double den = nA * (nA * hn[R + c] + hn[2 * R + c]);
+      const double den = (sA * nA) * (nA * hn[R + c] + hn[2 * R + c]);
       // a NaN anywhere (x included) makes the backward error NaN
       const double eta = std::isnan(num) || std::isnan(den) ? NAN
                          : den > 0                          ? num / den
@@ -562,7 +586,7 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
   // e = b - A x, A^T e and the norms of the backward error
   auto terms = [&]() {
     if (resid(sc, A, lda, m, n, Xw, n, nrhs, B, ldb, 1.0, nullptr, 0, 0.0, -1.0, E, m, st) != cudaSuccess ||
-        atr(A, lda, m, n, E, m, nrhs, 1.0, bb.G, n, st) != cudaSuccess)
+        atr(A, lda, m, n, E, m, nrhs, 1.0, bb.G, n, st, bb.nrm + 4 * R) != cudaSuccess)
       fail(TQR_ERR_CUDA);
     col_nrm2<<<nrhs, kLsThreads, 0, st>>>(bb.G, n, n, bb.nrm);
     col_nrm2<<<nrhs, kLsThreads, 0, st>>>(Xw, n, n, bb.nrm + R);
@@ -619,11 +643,14 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     bool semi = spread * 0x1p-24 < 0.01;
     if (semi) path = TQR_LS_PATH_FP32_SEMINORMAL;
     while (semi && more()) {
-      // scale A^T e by a power of two near 1/max ||.|| so FP32 keeps it normal
+      // the device holds s A^T e (s = norm_scale(||A||_F)); scale it by a
+      // power of two near 1/max ||.|| so FP32 keeps it normal: Gv = g A^T e
+      // with g = gs s, and the correction is R^-1 R^-T Gv / g
       double gmax = 0.0;
       for (int c = 0; c < nrhs; ++c) gmax = std::max(gmax, hn[c]);
-      const double scale = gmax > 0 && std::isfinite(gmax) ? std::ldexp(1.0, -std::ilogb(gmax)) : 1.0;
-      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, scale, bb.G, n, 0.0, nullptr, 0, Gv, n);
+      const double gs = gmax > 0 && std::isfinite(gmax) ? std::ldexp(1.0, -std::ilogb(gmax)) : 1.0;
+      const double scale = gs * norm_scale(hn[4 * R]);
+      axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, gs, bb.G, n, 0.0, nullptr, 0, Gv, n);
       fail(pack_rhs(Gv, n, n, nrhs, st));
       if (status == TQR_OK) fail(run_mode(M_TRSMT, 0, nrhs, st));
       if (status == TQR_OK) fail(run_mode(M_TRSM, 0, nrhs, st));
@@ -698,7 +725,7 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     // the correction equation [I A; A^T 0][dr; dx] = [f; g] by GMRES on the
     // system left-preconditioned with precond (M^-1 applied in the factors'
     // precision, the augmented operator and all GMRES arithmetic in FP64).
-    if (more()) {
+    if (more() && spread * 0x1p-24 < kGmresSpreadLimit) {
       path = TQR_LS_PATH_FP32_GMRES;
       const long long N = static_cast<long long>(m) + n;
       const int K = kGmresRestart;
@@ -844,6 +871,7 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
           settled = true;
           break;
         }
+        if (!(gres <= kGmresGiveUp)) break;
         if (!(berr < 0.5 * prev) && !(dxrel < 0.5 * prev_dx)) {
           if (++stall >= 3) break;
         } else {
