@@ -868,52 +868,75 @@ def run_batch(args, w):
         A = inputs.normal_matrix(m, n, t)
         pristine.append(tqr.colmajor(torch.from_numpy(A).to(dev)))
     work = [tqr.colmajor(torch.empty_like(a)) for a in pristine]
+    tune_s = 0.0
+    rule_tiles = None
+    tqr.tqr_autotune_clear()
     if "nb" in w:   # --nb/--ib: one tile shape for every matrix instead of the autotuner's
         tiles = [(min(w["nb"], max(16, 1 << (max(m, n) - 1).bit_length())), w["ib"]) for m, n in shapes]
         tiles = [(nb, min(ib, nb)) for nb, ib in tiles]
     else:
+        rule_tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
+        # the measured autotuner: every size class present in this rank's share
+        t0 = time.perf_counter()
+        if args.tune_cache and os.path.exists(args.tune_cache):
+            tqr.tqr_autotune_load(args.tune_cache)
+        seen = set()
+        for m, n in shapes:
+            c = tqr.tqr_debug_autotune_class(m, n)
+            if c not in seen:
+                seen.add(c)
+                tqr.tqr_autotune_run(m, n)
+        if args.tune_cache:
+            tqr.tqr_autotune_save(args.tune_cache)
+        tune_s = time.perf_counter() - t0
         tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
-    Ts = [torch.zeros(tqr.tqr_t_size(m, n, nb, ib) // 8, dtype=torch.float64, device=dev)
-          for (m, n), (nb, ib) in zip(shapes, tiles)]
     stream = torch.cuda.current_stream()
-
-    def restore():
-        for a, b in zip(work, pristine):
-            a.copy_(b)
-
-    t_plan = time.perf_counter()
-    restore()
-    rc, st = tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tiles), len(shapes))
-    t_plan = time.perf_counter() - t_plan
-    assert rc == 0
-    for _ in range(args.warmup - 1):
-        restore()
-        tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tiles), len(shapes))
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
     props = torch.cuda.get_device_properties(dev)
     try:
         bus = "%08x:%02x:%02x.0" % (props.pci_domain_id, props.pci_bus_id, props.pci_device_id)
     except AttributeError:
         bus = None
-    total = 0.0
-    with ClockSampler(bus) as clk:
-        for _ in range(args.steps):
+
+    def restore():
+        for a, b in zip(work, pristine):
+            a.copy_(b)
+
+    def timed(tl, clk_sampler):
+        Ts = [torch.zeros(tqr.tqr_t_size(m, n, nb, ib) // 8, dtype=torch.float64, device=dev)
+              for (m, n), (nb, ib) in zip(shapes, tl)]
+        t_plan = time.perf_counter()
+        restore()
+        rc, st = tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tl), len(shapes))
+        t_plan = time.perf_counter() - t_plan
+        assert rc == 0
+        for _ in range(args.warmup - 1):
             restore()
-            torch.cuda.synchronize()
-            e0 = torch.cuda.Event(enable_timing=True)
-            e1 = torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            t = tqr.tqr_batch_submit(work, Ts, tiles)
-            e1.record(stream)
-            rc, st = tqr.tqr_batch_wait(t, len(shapes))
-            torch.cuda.synchronize()
-            assert rc == 0 and not st.any()
-            total += e0.elapsed_time(e1) * 1e-3
-    if dist is not None:
-        dist.barrier()
-    sec = max_over_ranks(total / args.steps, dist, dev)
+            tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tl), len(shapes))
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        total = 0.0
+        with clk_sampler as clk:
+            for _ in range(args.steps):
+                restore()
+                torch.cuda.synchronize()
+                e0 = torch.cuda.Event(enable_timing=True)
+                e1 = torch.cuda.Event(enable_timing=True)
+                e0.record(stream)
+                t = tqr.tqr_batch_submit(work, Ts, tl)
+                e1.record(stream)
+                rc, st = tqr.tqr_batch_wait(t, len(shapes))
+                torch.cuda.synchronize()
+                assert rc == 0 and not st.any()
+                total += e0.elapsed_time(e1) * 1e-3
+        if dist is not None:
+            dist.barrier()
+        return max_over_ranks(total / args.steps, dist, dev), t_plan, clk
+
+    rule_sec = None
+    if rule_tiles is not None and rule_tiles != tiles:
+        rule_sec, _, _ = timed(rule_tiles, ClockSampler(None))
+    sec, t_plan, clk = timed(tiles, ClockSampler(bus))
     if rank != 0:
         dist.destroy_process_group()
         return
@@ -935,7 +958,10 @@ def run_batch(args, w):
                        "l2": "inputs > 129 MB L2, restored from device copies before each step",
                        "parallelism": ("instances sharded over %d ranks by flops (greedy), no collective" % world)
                                       if world > 1 else "single GPU",
-                       "tile_classes_rank0": classes},
+                       "tile_classes_rank0": classes,
+                       "autotune": "measured per size class (tqr_autotune_run), %.1f s" % tune_s
+                                   if rule_tiles is not None else "fixed by --nb/--ib"},
+            "rule_tiles_value": flops / rule_sec / 1e12 if rule_sec else None,
             "first_submit_s_incl_plan": t_plan, "gpu_launches": 3 * args.steps, "cpu_baseline": cpu,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
@@ -1045,6 +1071,7 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-ls", action="store_true", help="skip the least-squares comparison of the default line")
+    ap.add_argument("--tune-cache", default="", help="batch: autotuner table file to load before and save after")
     ap.add_argument("--variant", default="", choices=["", "flat", "pairs", "tree"],
                     help="override the factorization variant of a QR workload")
     ap.add_argument("--nb", type=int, default=0, help="override the workload's tile size")

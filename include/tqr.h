@@ -398,12 +398,38 @@ typedef struct tqr_desc {
 } tqr_desc;
 
 /*
- * Tile sizes for one m x n factorization inside a batch, by a rule taken
- * from batch measurements: nb = 128, ib = 16, except that a matrix smaller
+ * Tile sizes for one m x n factorization inside a batch (and for the
+ * server's requests).  Size classes are ceil(log2 m) x ceil(log2 n).  A class
+ * measured by tqr_autotune_run answers with its measured winner; any other
+ * class takes the fixed rule nb = 128, ib = 16, except that a matrix smaller
  * than 128 takes the smallest power of two (>= 16) that holds it.  Writes
  * *nb, *ib.  Returns 0 or -i.
  */
 int tqr_autotune(int64_t m, int64_t n, int* nb, int* ib);
+
+/*
+ * The measured autotuner (the paper's b and inner blocking, Sections 3.1-3.2,
+ * chosen per size class by timing them on this GPU).
+ *   tqr_autotune_run(m, n, stream): unless the class of m x n is already in
+ *     the table, factors batches of copies of one representative matrix of
+ *     the class (its geometric middle; enough copies for ~2e10 flops, 8 to
+ *     1024) in one persistent launch each, for every candidate nb in
+ *     {16, 32, 64, 96, 128, 192, 256} (up to the smallest that holds the
+ *     matrix) and ib in {8, 16, 32} dividing nb; keeps the (nb, ib) with the
+ *     least device time per matrix (best of two timed runs after one that
+ *     builds the plan).  Allocates its matrices from the library's pool and
+ *     synchronizes the stream.  Returns 0, -i, TQR_ERR_NOMEM or a batch
+ *     status.
+ *   tqr_autotune_save(path) / tqr_autotune_load(path): the table as text,
+ *     one class per line ("mb nbin nb ib us_per_matrix", '#' comments); load
+ *     merges, and rejects a malformed file as a whole (TQR_ERR_UNSUPPORTED,
+ *     as for a file that cannot be opened).
+ *   tqr_autotune_clear(): empties the table (every class back to the rule).
+ */
+int tqr_autotune_run(int64_t m, int64_t n, void* stream);
+int tqr_autotune_save(const char* path);
+int tqr_autotune_load(const char* path);
+int tqr_autotune_clear(void);
 
 /*
  * Factor `count` independent matrices in ONE persistent launch whose global

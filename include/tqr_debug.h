@@ -129,6 +129,16 @@ int tqr_debug_fp64_peak(double* tflops, void* stream);
  */
 int tqr_debug_trace(void* buffer, int64_t capacity);
 
+/*
+ * Autotuner table without a GPU (tests of the class map, the lookup and the
+ * file format): tqr_debug_autotune_class writes the size class of m x n
+ * (ceil(log2 m), ceil(log2 n)); tqr_debug_autotune_put stores (nb, ib, us)
+ * for the class of m x n as if tqr_autotune_run had measured it.  Return 0
+ * or -3 (invalid output pointer, or nb / ib outside what the kernels take).
+ */
+int tqr_debug_autotune_class(int64_t m, int64_t n, int* mb, int* nbin);
+int tqr_debug_autotune_put(int64_t m, int64_t n, int nb, int ib, double us);
+
 /* Last error message of this thread ("" if none). */
 const char* tqr_debug_last_error(void);
 

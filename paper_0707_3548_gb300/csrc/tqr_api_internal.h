@@ -47,6 +47,9 @@ int ptr_kind(const void* p);
 int check_tiles(int nb, int ib, int arg_nb, int arg_ib);
 void clear_plans();
 void autotune(int64_t m, int64_t n, int* nb, int* ib);
+// The measured autotuner's table (tqr_tune.cu): true and (nb, ib) if the
+// size class of m x n has been tuned.
+bool tune_lookup(int64_t m, int64_t n, int* nb, int* ib);
 // Host copy of the tree variant's prefix table for planning (Inst.D > 0).
 const int32_t* host_vtab(const Inst& I);
 // Tree variant: chosen domain size (0 = flat) and the device table upload.

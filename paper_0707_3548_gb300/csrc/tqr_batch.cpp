@@ -36,7 +36,10 @@ namespace tqr {
 // size class (0.829 against 0.757 .. 0.821 and 0.790 TFLOP/s): the update
 // kernels lose more to small tiles than padding costs.  Matrices smaller
 // than 128 take the smallest power of two that holds them (at least 16).
+// A class measured by tqr_autotune_run (tqr_tune.cu) answers from the
+// tuner's table instead.
 void autotune(int64_t m, int64_t n, int* nb_out, int* ib_out) {
+  if (tune_lookup(m, n, nb_out, ib_out)) return;
   const int64_t mx = std::max(m, n);
   int nb = 16;
   while (nb < 128 && nb < mx) nb *= 2;

@@ -89,6 +89,12 @@ SIGNATURES = {
     "tqr_ls_release": (_int, [_vp, _vp]),
     "tqr_factor_noalloc": (_int, [_i64, _i64, _vp, _i64, _int, _int, _vp, _vp]),
     "tqr_autotune": (_int, [_i64, _i64, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "tqr_autotune_run": (_int, [_i64, _i64, _vp]),
+    "tqr_autotune_save": (_int, [ctypes.c_char_p]),
+    "tqr_autotune_load": (_int, [ctypes.c_char_p]),
+    "tqr_autotune_clear": (_int, []),
+    "tqr_debug_autotune_class": (_int, [_i64, _i64, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
+    "tqr_debug_autotune_put": (_int, [_i64, _i64, _int, _int, _dbl]),
     "tqr_server_create": (_int, [_size, _int, _int, ctypes.POINTER(_vp)]),
     "tqr_server_submit": (_int, [_vp, ctypes.c_uint64, _i64, _i64, _i64, _vp, _i64, _vp, _i64, _vp, _i64, _int,
                                  _dbl, ctypes.POINTER(ctypes.c_uint64)]),
@@ -371,6 +377,33 @@ def tqr_autotune(m, n):
     ib = _int(0)
     _check("tqr_autotune", lib().tqr_autotune(m, n, ctypes.byref(nb), ctypes.byref(ib)))
     return nb.value, ib.value
+
+
+def tqr_autotune_run(m, n, stream=None):
+    """Measure the size class of m x n on the device (no-op if tuned)."""
+    _check("tqr_autotune_run", lib().tqr_autotune_run(m, n, _stream(True, stream)))
+
+
+def tqr_autotune_save(path):
+    _check("tqr_autotune_save", lib().tqr_autotune_save(os.fsencode(path)))
+
+
+def tqr_autotune_load(path):
+    _check("tqr_autotune_load", lib().tqr_autotune_load(os.fsencode(path)))
+
+
+def tqr_autotune_clear():
+    _check("tqr_autotune_clear", lib().tqr_autotune_clear())
+
+
+def tqr_debug_autotune_class(m, n):
+    a, b = _int(0), _int(0)
+    _check("tqr_debug_autotune_class", lib().tqr_debug_autotune_class(m, n, ctypes.byref(a), ctypes.byref(b)))
+    return a.value, b.value
+
+
+def tqr_debug_autotune_put(m, n, nb, ib, us=1.0):
+    _check("tqr_debug_autotune_put", lib().tqr_debug_autotune_put(m, n, nb, ib, us))
 
 
 def tqr_batch_submit(mats, Ts, tiles=None, stream=None):

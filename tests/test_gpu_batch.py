@@ -63,3 +63,34 @@ def test_batch_graph_replay_with_new_data_and_poll():
             F, _ = _alone(A, nb, ib)
             assert np.array_equal(to_host(dA), F)
     assert tqr.lib().tqr_batch_poll(987654321, tqr.ctypes.byref(tqr.ctypes.c_int(0)), None) == -1
+
+
+def test_measured_autotuner_picks_a_candidate_and_the_batch_uses_it(tmp_path):
+    """tqr_autotune_run times the candidates of one size class on the device
+    and stores the winner; tqr_autotune and a batch with the library's
+    choice then use it, and the factors equal those of factoring each
+    matrix alone with that (nb, ib) and the oracle's."""
+    torch_cuda()
+    tqr.tqr_autotune_clear()
+    try:
+        tqr.tqr_autotune_run(300, 200)
+        nb, ib = tqr.tqr_autotune(300, 200)
+        assert nb in (16, 32, 64, 96, 128, 192, 256) and ib in (8, 16, 32) and nb % ib == 0
+        assert tqr.tqr_autotune(257, 129) == (nb, ib)          # same class (9, 8)
+        path = tmp_path / "tune.txt"
+        tqr.tqr_autotune_save(str(path))
+        assert ("9 8 %d %d" % (nb, ib)) in path.read_text()
+        shapes = [(300, 200), (280, 150), (257, 256)]
+        mats = [inputs.normal_matrix(m, n, 80 + a) for a, (m, n) in enumerate(shapes)]
+        tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
+        assert all(t == (nb, ib) for t in tiles)
+        t, dev, Ts = _submit(mats, tiles)
+        rc, st = tqr.tqr_batch_wait(t, len(mats))
+        assert rc == 0 and not st.any()
+        for A, dA in zip(mats, dev):
+            F, _ = _alone(A, nb, ib)
+            assert np.array_equal(to_host(dA), F)
+            f = TL.tiled_qr(A, nb, ib)
+            assert np.max(np.abs(F - f.F)) <= 1e-11 * np.abs(f.F).max()
+    finally:
+        tqr.tqr_autotune_clear()
