@@ -981,11 +981,33 @@ def run_serve(args, w):
     from paper_0707_3548_gb300 import build as B
     from paper_0707_3548_gb300 import inputs, tqr
 
-    torch.cuda.set_device(0)
-    B.build()
+    from paper_0707_3548_gb300.ranks import max_over_ranks, route_requests
+
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+    if rank == 0 or world == 1:
+        B.build()
+    if dist is not None:
+        dist.barrier()
     rate = args.rate or w["rate"]
     window = args.window or w["window"]
-    reqs, mats = inputs.serving_stream(rate, window, seed=0)
+    all_reqs, mats = inputs.serving_stream(rate, window, seed=0)
+    if args.classes != "mixed":    # the whole stream in one precision class
+        for q in all_reqs:
+            q["prec"] = args.classes
+    # requests are routed to ranks by matrix affinity / least load (every
+    # rank computes the same routing; no data moves between ranks)
+    route, _ = route_requests(all_reqs, world)
+    reqs = [q for q, r in zip(all_reqs, route) if r == rank]
+    mine_ids = {q["matrix"] for q in reqs}
+    mats = [x for x in mats if x[2] in mine_ids]
     # distinct matrix data is drawn into a bounded pool; a later matrix id
     # reuses the leading m x n block of the smallest pool matrix that covers
     # it (its own identity is kept: a new id is factored again)
@@ -997,23 +1019,25 @@ def run_serve(args, w):
             view_of[mid] = pool[k][:m, :n]
             continue
         A = inputs.normal_matrix(m, n, 10_000 + mid)
-        pool.append(tqr.colmajor(torch.from_numpy(A).cuda()))
+        pool.append(tqr.colmajor(torch.from_numpy(A).to(dev)))
         used += 8 * m * n
         view_of[mid] = pool[-1]
     rhs = []
     for r, q in enumerate(reqs):
         Bh = inputs.normal_matrix(q["m"], q["nrhs"], 50_000 + r)
-        rhs.append(tqr.colmajor(torch.from_numpy(Bh).cuda()))
-    outs = [tqr.colmajor(torch.zeros((q["n"], q["nrhs"]), dtype=torch.float64, device="cuda")) for q in reqs]
+        rhs.append(tqr.colmajor(torch.from_numpy(Bh).to(dev)))
+    outs = [tqr.colmajor(torch.zeros((q["n"], q["nrhs"]), dtype=torch.float64, device=dev)) for q in reqs]
     torch.cuda.synchronize()
     srv = tqr.Server(w["budget"], slots=w["slots"], grid_cap=args.grid_cap)
     # warm the plan cache and kernels with a few requests outside the window
     for k, q in enumerate(reqs[:3]):
-        Xw = tqr.colmajor(torch.zeros((q["n"], q["nrhs"]), dtype=torch.float64, device="cuda"))
+        Xw = tqr.colmajor(torch.zeros((q["n"], q["nrhs"]), dtype=torch.float64, device=dev))
         srv.wait(srv.submit(10**9 + q["matrix"], view_of[q["matrix"]], rhs[k], Xw,
                             prec=tqr.TQR_PREC_FP32 if q["prec"] == "fp32r" else tqr.TQR_PREC_FP64))
     base = srv.stats()
     ids = [None] * len(reqs)
+    if dist is not None:
+        dist.barrier()
     t0 = time.perf_counter()
 
     def feeder():
@@ -1029,24 +1053,43 @@ def run_serve(args, w):
     th.join()
     infos = [srv.wait(r) for r in ids]
     t1 = time.perf_counter()
+    span = max_over_ranks(t1 - t0, dist, dev)
+    if dist is not None:
+        # per-request records (latency, status, class, backward error) to rank 0
+        recs = [(i["latency_ms"], i["status"], q["prec"], i["berr"], i["iters"]) for i, q in zip(infos, reqs)]
+        gathered = [None] * world
+        dist.all_gather_object(gathered, recs)
+        stats = srv.stats()
+        srv.close()
+        if rank != 0:
+            dist.destroy_process_group()
+            return
+        recs = [x for g in gathered for x in g]
+        infos = [dict(latency_ms=x[0], status=x[1], berr=x[3], iters=x[4]) for x in recs]
+        reqs = [dict(prec=x[2]) for x in recs]
+        t1 = t0 + span
     failures = {}
     for i, q in zip(infos, reqs):
         if i["status"] != 0:
             key = "%s status %d" % (q["prec"], i["status"])
             failures[key] = failures.get(key, 0) + 1
-    stats = srv.stats()
-    srv.close()
+    if dist is None:
+        stats = srv.stats()
+        srv.close()
     lat = {c: sorted(i["latency_ms"] for i, q in zip(infos, reqs) if q["prec"] == c) for c in ("fp64", "fp32r")}
     def pct(v, p):
         return v[min(len(v) - 1, int(p * (len(v) - 1) + 0.5))] if v else None
     allv = sorted(i["latency_ms"] for i in infos)
     bad = sum(1 for i in infos if i["status"] != 0)
     line = {"metric": "LS solves/s + p99 latency (served stream)", "value": len(reqs) / (t1 - t0), "unit": "solves/s",
-            "n_gpus": 1, "steps": 1, "warmup": 3, "ms_per_step": 1e3 * (t1 - t0), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64 / f32+f64 refined",
+            "n_gpus": world, "steps": 1, "warmup": 3, "ms_per_step": 1e3 * (t1 - t0), "higher_is_better": True,
+            "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
+            "dtype": {"mixed": "f64 / f32+f64 refined", "fp64": "f64", "fp32r": "f32+f64 refined"}[args.classes],
             "data": "synthetic: Poisson stream seed 0; matrix data from a %.1f GB pool" % (w["pool_bytes"] / 2**30),
-            "config": {"workload": "served LS stream %.0f req/s for %.1f s, %d requests, %d matrices, budget %d GB, %d slots"
-                       % (rate, window, len(reqs), len(mats), w["budget"] >> 30, w["slots"])},
+            "config": {"workload": "served LS stream %.0f req/s for %.1f s, %d requests, budget %d GB, %d slots, "
+                                   "classes %s" % (rate, window, len(reqs), w["budget"] >> 30, w["slots"], args.classes),
+                       "parallelism": ("requests routed over %d ranks (matrix affinity, least load), no data "
+                                       "collective" % world) if world > 1 else "single GPU"},
             "offered_per_s": len(reqs) / window, "completed": len(reqs) - bad, "failed": bad,
             "failures": failures, "slots": w["slots"], "grid_cap": args.grid_cap,
             "p50_ms": pct(allv, 0.5), "p99_ms": pct(allv, 0.99),
@@ -1054,11 +1097,13 @@ def run_serve(args, w):
             "reused_resident": stats["reused"] - base["reused"],
             "max_iters_fp32r": max([i["iters"] for i, q in zip(infos, reqs) if q["prec"] == "fp32r"] or [0]),
             "max_berr": max(i["berr"] for i in infos)}
-    if not args.no_cpu_baseline:
+    if not args.no_cpu_baseline and world == 1:
         cnt, tt, smp = oracle_kind_sample("serve", {"rate": rate, "window": window}, 8.0)
         line["cpu_baseline"] = {"value": cnt / tt, "unit": "solves/s", "cores": 1, "kind": "oracle",
                                 "sample": smp + ", %.1f s" % tt}
     print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
 
 
 def main():
@@ -1071,6 +1116,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end measurement")
     ap.add_argument("--no-ls", action="store_true", help="skip the least-squares comparison of the default line")
+    ap.add_argument("--classes", default="mixed", choices=["mixed", "fp64", "fp32r"],
+                    help="serve: precision classes of the stream (mixed 50/50, or all one class)")
     ap.add_argument("--tune-cache", default="", help="batch: autotuner table file to load before and save after")
     ap.add_argument("--variant", default="", choices=["", "flat", "pairs", "tree"],
                     help="override the factorization variant of a QR workload")
