@@ -2227,6 +2227,7 @@ template cudaError_t launch_pack_t<double>(const double*, long long, int, int, d
 template cudaError_t launch_unpack_t<double>(const double*, int, int, double*, long long, int, int, int,
                                              cudaStream_t);
 template cudaError_t launch_identity<double>(int, int, double*, int, int, int, int, cudaStream_t);
+template cudaError_t launch_identity<float>(int, int, float*, int, int, int, int, cudaStream_t);
 template cudaError_t launch_pack_batched<double>(const PackDesc*, int, cudaStream_t);
 template cudaError_t launch_unpack_batched<double>(const PackDesc*, int, cudaStream_t);
 template cudaError_t occupancy<float>(int, int*);

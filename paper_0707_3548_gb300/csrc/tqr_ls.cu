@@ -387,6 +387,8 @@ bool LsJob::init(int m_, int n_, int rhs_cap_, int nb_, int ib_, int prec_, int 
   o_b2 = o;    o += al(W.oT - W.oB);                       // as large as the first tile array
   o_ver2 = o;  o += al(sizeof(int) * static_cast<size_t>(I.p) * (I.q + I.qb) * I.NS);
   o_inst2 = o; o += al(2 * sizeof(Inst));
+  o_tctl = o;  o += al(sizeof(int) * trsv_ctl_ints(n, nb));
+  o_y = o;     o += al(sizeof(double) * nr);
   o_acopy = o;
   bytes = o;
   return true;
@@ -449,6 +451,57 @@ int LsJob::run_two(int mode_a, int mode_b, int nrhs_now, cudaStream_t st) {
                     : run_plan_multi<float>(two, 2, d_insts, d_ctl, occ, smem, st, grid_cap);
 }
 
+int LsJob::fast_ok(int nrhs) const { return esize == 4 && trsv_fits(nb, nrhs, 4) ? 1 : 0; }
+
+// R X = Y or R^T X = Y with the FP32 factor's R, one launch (fast_ok).  A
+// wait that runs out is recorded in the backward-error read-back area
+// (slot 4 rhs_cap + 1) and reported by finish.
+int LsJob::trsv(bool trans, const double* Y, long long ldy, double* X, long long ldx, int nrhs, cudaStream_t st) {
+  double* err = reinterpret_cast<double*>(ws + o_nrm) + 4 * rhs_cap + 1;
+  return launch_trsv<float>(trans, static_cast<const float*>(I.A), I.p, nb, n, nrhs, Y, ldy, X, ldx,
+                            reinterpret_cast<int*>(ws + o_tctl), wait_limit_ns(), err, st) == cudaSuccess
+             ? TQR_OK
+             : TQR_ERR_CUDA;
+}
+
+// The explicit thin Q1 (m x n, FP32 tiles): the identity's first n columns
+// through the factorization's Q (the M_FORM_Q task graph), once per solve.
+int LsJob::form_q1(cudaStream_t st) {
+  if (vws != nullptr) return TQR_OK;
+  Inst Iq = I;
+  Iq.mode = M_FORM_Q;
+  Iq.trsm = 0;
+  Iq.nrhs = n;
+  Iq.qb = I.q;
+  const size_t tiles = al(sizeof(float) * static_cast<size_t>(nb) * nb * I.p * I.q);
+  size_t o = tiles;
+  vo_ver = o;  o += al(sizeof(int) * static_cast<size_t>(I.p) * (2 * I.q) * I.NS);
+  vo_inst = o; o += al(sizeof(Inst));
+  vo_ctl = o;  o += al(ctl_bytes());
+  vo_part = o; o += al(sizeof(float) * kQ1SplitsCap * static_cast<size_t>(std::max(m, n)) * rhs_cap);
+  vbytes = o;
+  if (lib_malloc(reinterpret_cast<void**>(&vws), vbytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    vws = nullptr;
+    return TQR_ERR_NOMEM;
+  }
+  Iq.B = vws;
+  Iq.ver = reinterpret_cast<int*>(vws + vo_ver);
+  if (launch_identity<float>(m, n, static_cast<float*>(Iq.B), I.p, I.q, nb, device_sms(), st) != cudaSuccess)
+    return TQR_ERR_CUDA;
+  WsLayout W2 = {};
+  W2.oVer = vo_ver;
+  W2.oInst = vo_inst;
+  W2.oCtl = vo_ctl;
+  W2.bytes = vbytes;
+  return run_plan<float>(Iq, vws, W2, occ, smem, st, grid_cap);
+}
+
+void LsJob::free_q1(cudaStream_t st) {
+  if (vws) cudaFreeAsync(vws, st);
+  vws = nullptr;
+}
+
 // [U; V] = M^-1 [F; G] with M = [I, QR; (QR)^T, 0] from the factors in the
 // tiles: d = Q^T F and h = R^-T G (one launch), then V = R^-1 (d1 - h) and
 // U = Q [h; d2] (one launch) -- the correction of the augmented-system
@@ -458,6 +511,27 @@ int LsJob::run_two(int mode_a, int mode_b, int nrhs_now, cudaStream_t st) {
 // written, so F and G may be those buffers.
 int LsJob::precond(const double* F, long long ldf, const double* G, long long ldg, double* U, long long ldu,
                    double* V, long long ldv, int nrhs, cudaStream_t st) {
+  if (vws != nullptr) {
+    // explicit Q1: h = R^-T g, y = Q1^T f - h, V = R^-1 y, U = f - Q1 y
+    // (= Q [h; d2] with d2 = Q2^T f, since Q1 Q1^T + Q2 Q2^T = I)
+    double* Hh = reinterpret_cast<double*>(ws + o_h);
+    double* Yy = reinterpret_cast<double*>(ws + o_y);
+    float* Q1 = reinterpret_cast<float*>(vws);
+    float* part = reinterpret_cast<float*>(vws + vo_part);
+    const size_t nr = static_cast<size_t>(n) * nrhs;
+    int s = trsv(true, G, ldg, Hh, n, nrhs, st);
+    if (s == TQR_OK &&
+        launch_q1t(Q1, I.p, nb, m, n, nrhs, F, ldf, 1.0, part, kQ1SplitsCap, Yy, n, st) != cudaSuccess)
+      s = TQR_ERR_CUDA;
+    if (s != TQR_OK) return s;
+    axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Yy, n, -1.0, Hh, n, Yy, n);
+    if (cudaGetLastError() != cudaSuccess) return TQR_ERR_CUDA;
+    s = trsv(false, Yy, n, V, ldv, nrhs, st);
+    if (s == TQR_OK &&
+        launch_q1n(Q1, I.p, nb, m, n, nrhs, Yy, n, 1.0, F, ldf, part, kQ1SplitsCap, U, ldu, st) != cudaSuccess)
+      s = TQR_ERR_CUDA;
+    return s;
+  }
   double* D = reinterpret_cast<double*>(ws + o_d);
   double* H = reinterpret_cast<double*>(ws + o_h);
   double* Gv = reinterpret_cast<double*>(ws + o_g);
@@ -563,7 +637,10 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     if (cudaMemcpyAsync(hn.data(), bb.nrm, sizeof(double) * hn.size(), cudaMemcpyDeviceToHost, st) != cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
       fail(TQR_ERR_CUDA);
+    if (hn[4 * R + 1] != 0.0) fail(TQR_ERR_TIMEOUT);  // a triangular-solve wait ran out
   };
+  // the triangular-solve kernel's error slot starts clear
+  if (cudaMemsetAsync(bb.nrm + 4 * R + 1, 0, sizeof(double), st) != cudaSuccess) fail(TQR_ERR_CUDA);
   // hn[c] holds s ||A^T e|| with s = norm_scale(||A||_F) (exact power of
   // two), so the ratio is formed as s||A^T e|| / ((s ||A||) (||A|| ||x|| + ||b||))
   // -- every factor finite for any finite data
@@ -651,10 +728,16 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
       const double gs = gmax > 0 && std::isfinite(gmax) ? std::ldexp(1.0, -std::ilogb(gmax)) : 1.0;
       const double scale = gs * norm_scale(hn[4 * R]);
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, gs, bb.G, n, 0.0, nullptr, 0, Gv, n);
-      fail(pack_rhs(Gv, n, n, nrhs, st));
-      if (status == TQR_OK) fail(run_mode(M_TRSMT, 0, nrhs, st));
-      if (status == TQR_OK) fail(run_mode(M_TRSM, 0, nrhs, st));
-      fail(unpack_rhs(Gv, n, n, nrhs, st));
+      if (fast_ok(nrhs)) {
+        // R^-T then R^-1 by the triangular-solve kernel, in place
+        fail(trsv(true, Gv, n, Gv, n, nrhs, st));
+        if (status == TQR_OK) fail(trsv(false, Gv, n, Gv, n, nrhs, st));
+      } else {
+        fail(pack_rhs(Gv, n, n, nrhs, st));
+        if (status == TQR_OK) fail(run_mode(M_TRSMT, 0, nrhs, st));
+        if (status == TQR_OK) fail(run_mode(M_TRSM, 0, nrhs, st));
+        fail(unpack_rhs(Gv, n, n, nrhs, st));
+      }
       col_nrm2<<<nrhs, kLsThreads, 0, st>>>(Gv, n, n, dx2);
       axpby<<<ew_grid(nr), 256, 0, st>>>(n, nrhs, 1.0, Xw, n, 1.0 / scale, Gv, n, Xw, n);
       ++iters;
@@ -695,6 +778,9 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     int stall = 0;
     const bool aug = spread * 0x1p-24 < 0.02;
     if (aug && more()) path = TQR_LS_PATH_FP32_AUGMENTED;
+    // the refinements with Q apply it through the explicit thin Q1 when the
+    // few-right-hand-side kernels take this problem
+    if (more() && fast_ok(nrhs) && (aug || spread * 0x1p-24 < kGmresSpreadLimit)) fail(form_q1(st));
     while (aug && more()) {
       // f = b - r - A x = e - r;  g = -A^T r;  [dr; dx] = M^-1 [f; g]
       axpby<<<ew_grid(mr), 256, 0, st>>>(m, nrhs, 1.0, E, m, -1.0, Rr, m, F, m);
@@ -886,6 +972,7 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     // TQR_ERR_NOCONV; stagnation hands the problem to an FP64 solve
     if (status == TQR_OK && !(berr <= tol)) status = iters >= maxit ? TQR_ERR_NOCONV : kLsStalled;
   }
+  free_q1(st);
   if (X != nullptr &&
       copy_cols(X, sizeof(double) * ldx, Xw, sizeof(double) * n, sizeof(double) * n, nrhs,
                 cudaMemcpyDeviceToDevice, st) != cudaSuccess)

@@ -18,6 +18,29 @@ constexpr int kLsFp32Range = 1000;
 // up its steps) before maxit -- the caller solves in FP64 instead.  Internal.
 constexpr int kLsStalled = 1001;
 
+// ---- few-right-hand-side kernels of the refinement (tqr_lsvec.cu)
+constexpr int kMaxVecRhs = 16;
+size_t trsv_ctl_ints(int n, int nb);
+size_t trsv_smem(int nb, int nrhs, int esize);
+bool trsv_fits(int nb, int nrhs, int esize);
+// R X = Y (trans false) or R^T X = Y (trans true) with the R of the tiles;
+// ctl: trsv_ctl_ints(n, nb) ints of device memory (cleared here); a wait
+// that runs out writes TQR_ERR_TIMEOUT to *err_out (may be null).
+template <typename real>
+cudaError_t launch_trsv(bool trans, const real* tiles, int p, int nb, int n, int nrhs, const double* Y,
+                        long long ldy, double* X, long long ldx, int* ctl, long long limit_ns, double* err_out,
+                        cudaStream_t st);
+// D = Q1^T F (n x nrhs) and U = F - Q1 Y (m x nrhs) with the explicit thin
+// Q1 in FP32 tiles; inputs are multiplied by the scale (a power of two)
+// before rounding to FP32 and the results divided by it.  part: scratch of
+// at most splits_cap * max(m, n) * nrhs floats.
+cudaError_t launch_q1t(const float* Q, int p, int nb, int m, int n, int nrhs, const double* F, long long ldf,
+                       double fscale, float* part, int splits_cap, double* D, long long ldd, cudaStream_t st);
+cudaError_t launch_q1n(const float* Q, int p, int nb, int m, int n, int nrhs, const double* Yv, long long ldy,
+                       double yscale, const double* F, long long ldf, float* part, int splits_cap, double* U,
+                       long long ldu, cudaStream_t st);
+constexpr int kQ1SplitsCap = 64;
+
 struct LsScratch {
   double* part;  // nsplit * m * nrhs partial products
   int nsplit;
@@ -34,7 +57,18 @@ struct LsJob {
   // a second right-hand-side tile array, its counters, and room for two
   // instances: two independent graphs of the refinement step in one launch
   size_t o_b2 = 0, o_ver2 = 0, o_inst2 = 0;
+  size_t o_tctl = 0;  // control words of the triangular-solve kernel
+  size_t o_y = 0;     // n x rhs_cap scratch of the fast preconditioner
   size_t bytes = 0;  // workspace without the FP64 copy of A
+  // FP32 class, refinement with Q (augmented / GMRES-IR): the explicit thin
+  // Q1 in FP32 tiles, formed once from the factors, with its launch state
+  // and the GEMV scratch (allocated on first use, freed by finish)
+  char* vws = nullptr;
+  size_t vo_ver = 0, vo_inst = 0, vo_ctl = 0, vo_part = 0, vbytes = 0;
+  int fast_ok(int nrhs) const;  // the few-right-hand-side kernels apply
+  int form_q1(cudaStream_t st);
+  void free_q1(cudaStream_t st);
+  int trsv(bool trans, const double* Y, long long ldy, double* X, long long ldx, int nrhs, cudaStream_t st);
   char* ws = nullptr;
   double* Acopy = nullptr;
   bool factored = false;
