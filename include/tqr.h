@@ -51,7 +51,7 @@ enum {
   TQR_ERR_BUSY = 6,        /* batch / server: no free slot right now */
   TQR_ERR_UNSUPPORTED = 7, /* valid arguments outside what this build supports */
   TQR_ERR_TOO_LARGE = 8,   /* tqr_factor_noalloc: problem exceeds its static scratch */
-  TQR_ERR_NONFINITE = 9    /* least squares: A or B holds a NaN or an infinity */
+  TQR_ERR_NONFINITE = 9    /* an input matrix holds a NaN or an infinity */
 };
 
 enum { TQR_PREC_FP64 = 0, TQR_PREC_FP32 = 1 };
@@ -92,6 +92,10 @@ size_t tqr_work_size(int64_t m, int64_t n, int nb, int ib);
  * The result can only be used with the same nb, ib and T.  Rank-deficient
  * input is factored (zero columns give tau = 0).  The factorization is
  * deterministic: the task order on the GPU does not change a single bit.
+ * A NaN or an infinity in A is reported as TQR_ERR_NONFINITE -- by the call
+ * itself for host buffers, by tqr_stream_status for device buffers -- and
+ * the output is then undefined; the same holds for every factorization
+ * entry point below (tree, 2b x b, LU, allocation-free).
  */
 int tqr_factor(int64_t m, int64_t n, double* A, int64_t lda, int nb, int ib,
                double* T, void* stream);
@@ -557,7 +561,8 @@ int tqr_factor_noalloc(int64_t m, int64_t n, double* A, int64_t lda, int nb, int
 
 /*
  * Device status of the asynchronous calls made on `stream`: synchronizes the
- * stream and returns TQR_OK, TQR_ERR_TIMEOUT (a scheduler wait ran out; the
+ * stream and returns TQR_OK, TQR_ERR_NONFINITE (an input matrix held a NaN
+ * or an infinity), TQR_ERR_TIMEOUT (a scheduler wait ran out; the
  * affected output is undefined), TQR_ERR_UNSUPPORTED (a launch met a task
  * kind its kernel does not implement; output undefined) or TQR_ERR_CUDA.
  * Clears the recorded status.

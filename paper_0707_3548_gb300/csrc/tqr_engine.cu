@@ -1864,8 +1864,16 @@ __global__ void pack_kernel(const S* __restrict__ A, long long lda, int m, int n
     }
     const S* src = A + gi0 + gj * lda;
     D* dst = Ab + t * nb * static_cast<long long>(nb) + static_cast<long long>(c) * nb;
+    bool bad = false;
 #pragma unroll 4
-    for (int r = lane; r < nb; r += 32) dst[r] = r < valid ? static_cast<D>(src[r]) : D(0);
+    for (int r = lane; r < nb; r += 32) {
+      const S v = r < valid ? src[r] : S(0);
+      bad = bad || !isfinite(v);
+      dst[r] = static_cast<D>(v);
+    }
+    // a NaN or an infinity in the input: the sticky device status reports
+    // TQR_ERR_NONFINITE (9) to the call (host buffers) or tqr_stream_status
+    if (__any_sync(0xffffffffu, bad) && lane == 0) atomicCAS(&g_status, 0, 9);
   }
 }
 

@@ -194,3 +194,39 @@ def test_release_cached_memory_then_factor_again():
     hA = np.array(A, order="F", copy=True)
     hT = tqr.tqr_factor(hA, 128, 32)
     assert np.array_equal(hA, F1)
+
+
+def test_nonfinite_input_is_reported_by_every_factorization():
+    """A NaN or an infinity in A: host-buffer calls return TQR_ERR_NONFINITE,
+    device-buffer calls report it through tqr_stream_status (which clears
+    it), and a clean call afterwards reports nothing."""
+    torch = torch_cuda()
+    from paper_0707_3548_gb300.tqr import lib
+    A = inputs.normal_matrix(200, 150, 91)
+    bad_nan, bad_inf = A.copy(), A.copy()
+    bad_nan[17, 33] = np.nan
+    bad_inf[199, 149] = -np.inf
+    nb, ib = 64, 16
+    for bad in (bad_nan, bad_inf):
+        # host buffers: the call synchronizes and returns the status
+        T = np.zeros(tqr.tqr_t_size(200, 150, nb, ib) // 8)
+        h = np.asfortranarray(bad.copy())
+        rc = lib().tqr_factor(200, 150, h.ctypes.data, 200, nb, ib, T.ctypes.data, None)
+        assert rc == tqr.TQR_ERR_NONFINITE
+        # device buffers: asynchronous, reported by tqr_stream_status
+        calls = [
+            lambda d: tqr.tqr_factor(d, nb, ib, check=False),
+            lambda d: tqr.tqr_factor_pairs(d, nb, ib),
+            lambda d: tqr.tqr_factor_tree(d, nb, ib, 2),
+            lambda d: tqr.tqr_lu_factor(d, nb, ib),
+        ]
+        for call in calls:
+            call(to_dev(bad))
+            assert tqr.tqr_stream_status() == tqr.TQR_ERR_NONFINITE
+            assert tqr.tqr_stream_status() == tqr.TQR_OK          # cleared
+        dA = to_dev(bad)
+        Tn = torch.zeros(tqr.tqr_t_size(200, 150, nb, ib) // 8, dtype=torch.float64, device="cuda")
+        assert tqr.tqr_factor_noalloc(dA, nb, ib, Tn, check=False) == tqr.TQR_OK
+        assert tqr.tqr_stream_status() == tqr.TQR_ERR_NONFINITE
+    tqr.tqr_factor(to_dev(A), nb, ib)
+    assert tqr.tqr_stream_status() == tqr.TQR_OK
