@@ -38,8 +38,10 @@ if ROOT not in sys.path:
 WORKLOADS = {
     "qr8192": dict(m=8192, n=8192, nb=128, ib=16),
     "qr16384": dict(m=16384, n=16384, nb=128, ib=16),
-    "qr4096": dict(m=4096, n=4096, nb=128, ib=16),
-    "qr2048": dict(m=2048, n=2048, nb=128, ib=16),
+    # the small squares take the fastest tiles of the measured sweep (nb in
+    # {32 .. 256} x ib in {8 .. 64}): the panel chain, not the updates, bounds them
+    "qr4096": dict(m=4096, n=4096, nb=64, ib=8),
+    "qr2048": dict(m=2048, n=2048, nb=32, ib=8),
     "ts65536x2048": dict(m=65536, n=2048, nb=128, ib=16),
     # 2b x b bottoms (pairs of tile rows below the diagonal)
     "qr16384_pairs": dict(m=16384, n=16384, nb=128, ib=16, pairs=True),
