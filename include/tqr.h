@@ -416,13 +416,13 @@ int tqr_autotune(int64_t m, int64_t n, int* nb, int* ib);
  * chosen per size class by timing them on this GPU).
  *   tqr_autotune_run(m, n, stream): unless the class of m x n is already in
  *     the table, factors batches of copies of one representative matrix of
- *     the class (its geometric middle; enough copies for ~2e11 flops, 8 to
+ *     the class (its geometric middle; enough copies for ~1e11 flops, 8 to
  *     1024, so that the batch runs in the throughput regime of a large
  *     mixed batch) in one persistent launch each, for every candidate nb in
  *     {16, 32, 64, 96, 128, 192, 256} (up to the smallest that holds the
  *     matrix) and ib in {8, 16, 32} dividing nb; keeps the (nb, ib) with the
- *     least device time per matrix (best of two timed runs after one that
- *     builds the plan).  Allocates its matrices from the library's pool and
+ *     least device time per matrix (one timed run after one that builds the
+ *     plan).  Allocates its matrices from the library's pool and
  *     synchronizes the stream.  Returns 0, -i, TQR_ERR_NOMEM or a batch
  *     status.
  *   tqr_autotune_save(path) / tqr_autotune_load(path): the table as text,

@@ -103,10 +103,10 @@ extern "C" int tqr_autotune_run(int64_t m, int64_t n, void* stream) {
   const int64_t mr = mid(cls.first), nr = mid(cls.second);
   const double flops = mr >= nr ? 2.0 * mr * nr * nr - 2.0 * nr * nr * nr / 3.0
                                 : 2.0 * nr * mr * mr - 2.0 * mr * mr * mr / 3.0;
-  // enough copies for ~2e11 flops (8 .. 1024): a batch in the throughput
+  // enough copies for ~1e11 flops (8 .. 1024): a batch in the throughput
   // regime, as inside a large mixed batch -- a few copies of a large matrix
   // would measure its critical path instead and favour small tiles
-  const int count = static_cast<int>(std::max(8.0, std::min(1024.0, std::ceil(2e11 / std::max(flops, 1.0)))));
+  const int count = static_cast<int>(std::max(8.0, std::min(1024.0, std::ceil(1e11 / std::max(flops, 1.0)))));
   const size_t elems = static_cast<size_t>(mr) * nr;
   size_t tmax = 0;
   const auto cands = candidates(std::max(mr, nr));
@@ -136,7 +136,7 @@ extern "C" int tqr_autotune_run(int64_t m, int64_t n, void* stream) {
       d[a].ib = c.second;
     }
     float ms_best = INFINITY;
-    for (int rep = 0; rep < 3 && status == TQR_OK; ++rep) {  // the first builds the plan and graph
+    for (int rep = 0; rep < 2 && status == TQR_OK; ++rep) {  // the first builds the plan and graph
       tune_fill<<<1024, 256, 0, st>>>(A, static_cast<long long>(elems) * count);
       uint64_t ticket = 0;
       cudaEventRecord(e0, st);
