@@ -63,10 +63,14 @@ __global__ void __launch_bounds__(kLsThreads) gemm_nn_partial(const double* __re
       }
       __syncthreads();
       if (r < m) {
-        for (int jj = 0; jj < jw; ++jj) {
-          const double a = A[r + static_cast<long long>(jb + jj) * lda];
+        if (cw == 1) {  // one right-hand side: one FMA per element of A
+          for (int jj = 0; jj < jw; ++jj) acc[0] = fma(A[r + static_cast<long long>(jb + jj) * lda], xs[jj][0], acc[0]);
+        } else {
+          for (int jj = 0; jj < jw; ++jj) {
+            const double a = A[r + static_cast<long long>(jb + jj) * lda];
 #pragma unroll
-          for (int c = 0; c < kRhsChunk; ++c) acc[c] = fma(a, xs[jj][c], acc[c]);
+            for (int c = 0; c < kRhsChunk; ++c) acc[c] = fma(a, xs[jj][c], acc[c]);
+          }
         }
       }
     }
