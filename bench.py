@@ -882,12 +882,8 @@ def run_batch(args, w):
         t0 = time.perf_counter()
         if args.tune_cache and os.path.exists(args.tune_cache):
             tqr.tqr_autotune_load(args.tune_cache)
-        seen = set()
-        for m, n in shapes:
-            c = tqr.tqr_debug_autotune_class(m, n)
-            if c not in seen:
-                seen.add(c)
-                tqr.tqr_autotune_run(m, n)
+        # per-class measurements, then the tile policy measured on this batch
+        tqr.tqr_autotune_batch(shapes)
         if args.tune_cache:
             tqr.tqr_autotune_save(args.tune_cache)
         tune_s = time.perf_counter() - t0
@@ -961,7 +957,8 @@ def run_batch(args, w):
                        "parallelism": ("instances sharded over %d ranks by flops (greedy), no collective" % world)
                                       if world > 1 else "single GPU",
                        "tile_classes_rank0": classes,
-                       "autotune": "measured per size class (tqr_autotune_run), %.1f s" % tune_s
+                       "autotune": "measured per size class and per batch policy (tqr_autotune_batch), %.1f s"
+                                   % tune_s
                                    if rule_tiles is not None else "fixed by --nb/--ib"},
             "rule_tiles_value": flops / rule_sec / 1e12 if rule_sec else None,
             "first_submit_s_incl_plan": t_plan, "gpu_launches": 3 * args.steps, "cpu_baseline": cpu,

@@ -430,11 +430,23 @@ int tqr_autotune(int64_t m, int64_t n, int* nb, int* ib);
  *     merges, and rejects a malformed file as a whole (TQR_ERR_UNSUPPORTED,
  *     as for a file that cannot be opened).
  *   tqr_autotune_clear(): empties the table (every class back to the rule).
+ *   tqr_autotune_batch(count, ms, ns, stream): tunes for one batch of
+ *     shapes (ms[a] x ns[a], a < count): measures every class present with
+ *     tqr_autotune_run, then factors synthetic matrices of exactly these
+ *     shapes as one batch under five tile policies -- the fixed rule, the
+ *     rule with ib 8, the measured per-class table, that table with ib 16,
+ *     and the table for matrices up to 512 with the rule above -- and writes
+ *     the fastest policy's choice for each of the batch's classes into the
+ *     table (the rule is a candidate, so the batch never runs slower than
+ *     under the rule, up to timing noise).  Allocates the batch's matrices
+ *     from the library's pool; synchronizes.  Returns 0, -i, TQR_ERR_NOMEM
+ *     or a batch status.
  */
 int tqr_autotune_run(int64_t m, int64_t n, void* stream);
 int tqr_autotune_save(const char* path);
 int tqr_autotune_load(const char* path);
 int tqr_autotune_clear(void);
+int tqr_autotune_batch(int count, const int64_t* ms, const int64_t* ns, void* stream);
 
 /*
  * Factor `count` independent matrices in ONE persistent launch whose global

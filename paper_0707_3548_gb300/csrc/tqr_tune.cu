@@ -166,6 +166,129 @@ extern "C" int tqr_autotune_run(int64_t m, int64_t n, void* stream) {
   return TQR_OK;
 }
 
+// ---------------------------------------------------------------- batch-level tuning
+// Candidate tile policies for a whole batch, each a map from a matrix's size
+// class to (nb, ib): the fixed rule, the rule with ib 8, the per-class table
+// of tqr_autotune_run, that table with ib 16, and the table for matrices of
+// at most 512 rows and columns with the rule above.  The batch's own shapes
+// are factored under each, and the fastest policy's choices are written into
+// the class table.
+static void rule_tiles(int64_t m, int64_t n, int* nb, int* ib) {
+  const int64_t mx = std::max(m, n);
+  int b = 16;
+  while (b < 128 && b < mx) b *= 2;
+  *nb = b;
+  *ib = std::min(16, b);
+}
+
+extern "C" int tqr_autotune_batch(int count, const int64_t* ms, const int64_t* ns, void* stream) {
+  if (count < 1) return -1;
+  if (ms == nullptr) return -2;
+  if (ns == nullptr) return -3;
+  for (int a = 0; a < count; ++a)
+    if (ms[a] < 1 || ns[a] < 1 || ms[a] > (1 << 20) || ns[a] > (1 << 20)) return -2;
+  cudaStream_t st = static_cast<cudaStream_t>(stream);
+  // the per-class measurements first (each class once)
+  std::map<std::pair<int, int>, std::pair<int64_t, int64_t>> classes;
+  for (int a = 0; a < count; ++a) classes.emplace(tune_class(ms[a], ns[a]), std::make_pair(ms[a], ns[a]));
+  for (const auto& kv : classes) {
+    const int s = tqr_autotune_run(kv.second.first, kv.second.second, stream);
+    if (s != TQR_OK) return s;
+  }
+  std::map<std::pair<int, int>, TuneEntry> measured;
+  {
+    std::lock_guard<std::mutex> lk(g_tmu);
+    measured = g_table;
+  }
+  constexpr int kPolicies = 5;
+  auto policy = [&](int pol, int64_t m, int64_t n, int* nb, int* ib) {
+    rule_tiles(m, n, nb, ib);
+    if (pol == 1) {
+      *ib = std::min(8, *nb);
+      return;
+    }
+    if (pol == 0) return;
+    auto it = measured.find(tune_class(m, n));
+    if (it == measured.end()) return;
+    if (pol == 4 && std::max(m, n) > 512) return;
+    *nb = it->second.nb;
+    *ib = it->second.ib;
+    if (pol == 3 && *nb % 16 == 0) *ib = 16;
+  };
+  // one allocation for every matrix and the largest T of any policy
+  std::vector<size_t> aoff(count), toff(count);
+  size_t abytes = 0, tbytes = 0;
+  for (int a = 0; a < count; ++a) {
+    aoff[a] = abytes;
+    abytes += ((sizeof(double) * static_cast<size_t>(ms[a]) * ns[a]) + 255) & ~size_t(255);
+    size_t tmax = 0;
+    for (int pol = 0; pol < kPolicies; ++pol) {
+      int nb, ib;
+      policy(pol, ms[a], ns[a], &nb, &ib);
+      tmax = std::max(tmax, tqr_t_size(ms[a], ns[a], nb, ib));
+    }
+    toff[a] = tbytes;
+    tbytes += (tmax + 255) & ~size_t(255);
+  }
+  char* buf = nullptr;
+  if (lib_malloc(reinterpret_cast<void**>(&buf), abytes + tbytes, st) != cudaSuccess) {
+    cudaGetLastError();
+    return TQR_ERR_NOMEM;
+  }
+  cudaEvent_t e0, e1;
+  cudaEventCreate(&e0);
+  cudaEventCreate(&e1);
+  std::vector<tqr_desc> d(count);
+  int best = 0, status = TQR_OK;
+  float best_ms = INFINITY;
+  for (int pol = 0; pol < kPolicies && status == TQR_OK; ++pol) {
+    for (int a = 0; a < count; ++a) {
+      int nb, ib;
+      policy(pol, ms[a], ns[a], &nb, &ib);
+      d[a].m = ms[a];
+      d[a].n = ns[a];
+      d[a].A = reinterpret_cast<double*>(buf + aoff[a]);
+      d[a].lda = ms[a];
+      d[a].T = reinterpret_cast<double*>(buf + abytes + toff[a]);
+      d[a].nb = nb;
+      d[a].ib = ib;
+    }
+    float ms_best = INFINITY;
+    for (int rep = 0; rep < 2; ++rep) {  // the first builds the plan and graph
+      tune_fill<<<4096, 256, 0, st>>>(reinterpret_cast<double*>(buf), static_cast<long long>(abytes / 8));
+      uint64_t ticket = 0;
+      cudaEventRecord(e0, st);
+      int s = tqr_batch_submit(count, d.data(), &ticket, st);
+      if (s == TQR_OK) s = tqr_batch_wait(ticket, nullptr);
+      cudaEventRecord(e1, st);
+      if (s != TQR_OK || cudaEventSynchronize(e1) != cudaSuccess) {
+        status = s != TQR_OK ? s : TQR_ERR_CUDA;
+        break;
+      }
+      float t = 0.0f;
+      cudaEventElapsedTime(&t, e0, e1);
+      if (rep > 0) ms_best = t;
+    }
+    if (status == TQR_OK && ms_best < best_ms) {
+      best_ms = ms_best;
+      best = pol;
+    }
+  }
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  cudaFreeAsync(buf, st);
+  cudaStreamSynchronize(st);
+  if (status != TQR_OK) return status;
+  // the winning policy's choice for every class of the batch
+  std::lock_guard<std::mutex> lk(g_tmu);
+  for (const auto& kv : classes) {
+    int nb, ib;
+    policy(best, kv.second.first, kv.second.second, &nb, &ib);
+    g_table[kv.first] = {nb, ib, best_ms * 1e3 / count};
+  }
+  return TQR_OK;
+}
+
 extern "C" int tqr_autotune_save(const char* path) {
   if (path == nullptr) return -1;
   FILE* f = std::fopen(path, "w");

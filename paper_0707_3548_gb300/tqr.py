@@ -93,6 +93,7 @@ SIGNATURES = {
     "tqr_autotune_save": (_int, [ctypes.c_char_p]),
     "tqr_autotune_load": (_int, [ctypes.c_char_p]),
     "tqr_autotune_clear": (_int, []),
+    "tqr_autotune_batch": (_int, [_int, _vp, _vp, _vp]),
     "tqr_debug_autotune_class": (_int, [_i64, _i64, ctypes.POINTER(_int), ctypes.POINTER(_int)]),
     "tqr_debug_autotune_put": (_int, [_i64, _i64, _int, _int, _dbl]),
     "tqr_server_create": (_int, [_size, _int, _int, ctypes.POINTER(_vp)]),
@@ -382,6 +383,14 @@ def tqr_autotune(m, n):
 def tqr_autotune_run(m, n, stream=None):
     """Measure the size class of m x n on the device (no-op if tuned)."""
     _check("tqr_autotune_run", lib().tqr_autotune_run(m, n, _stream(True, stream)))
+
+
+def tqr_autotune_batch(shapes, stream=None):
+    """Tune the tile policy for a batch of (m, n) shapes on the device."""
+    ms = np.asarray([m for m, n in shapes], dtype=np.int64)
+    ns = np.asarray([n for m, n in shapes], dtype=np.int64)
+    _check("tqr_autotune_batch", lib().tqr_autotune_batch(len(shapes), ms.ctypes.data, ns.ctypes.data,
+                                                           _stream(True, stream)))
 
 
 def tqr_autotune_save(path):

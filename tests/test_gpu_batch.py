@@ -94,3 +94,33 @@ def test_measured_autotuner_picks_a_candidate_and_the_batch_uses_it(tmp_path):
             assert np.max(np.abs(F - f.F)) <= 1e-11 * np.abs(f.F).max()
     finally:
         tqr.tqr_autotune_clear()
+
+
+def test_batch_policy_tuner_writes_one_choice_per_class_and_the_batch_is_correct():
+    """tqr_autotune_batch measures the classes of a batch and five tile
+    policies on the batch's own shapes, then stores one (nb, ib) per class;
+    the batch factored with the library's choice matches factoring each
+    matrix alone and the oracle."""
+    torch_cuda()
+    tqr.tqr_autotune_clear()
+    try:
+        shapes = inputs.batch_shapes(24, seed=11, m_lo=40, m_hi=300, n_lo=8)
+        tqr.tqr_autotune_batch(shapes)
+        tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
+        by_class = {}
+        for (m, n), t in zip(shapes, tiles):
+            by_class.setdefault(tqr.tqr_debug_autotune_class(m, n), set()).add(t)
+        assert all(len(v) == 1 for v in by_class.values())
+        for nb, ib in tiles:
+            assert nb % 8 == 0 and nb % ib == 0
+        mats = inputs.batch_matrices(shapes, seed=11)
+        t, dev, Ts = _submit(mats, tiles)
+        rc, st = tqr.tqr_batch_wait(t, len(mats))
+        assert rc == 0 and not st.any()
+        for A, dA, (nb, ib) in zip(mats, dev, tiles):
+            F, _ = _alone(A, nb, ib)
+            assert np.array_equal(to_host(dA), F)
+            f = TL.tiled_qr(A, nb, ib)
+            assert np.max(np.abs(F - f.F)) <= 1e-11 * np.abs(f.F).max()
+    finally:
+        tqr.tqr_autotune_clear()
