@@ -333,7 +333,9 @@ int tqr_solve_ls(int64_t m, int64_t n, int64_t nrhs, const double* A, int64_t ld
  * iters: outer refinement steps; inner_iters: GMRES steps; berr: the final
  * backward error; berr_fp32: the one the FP32 refinement reached;
  * gmres_res: the relative residual the last GMRES cycle reached (max over
- * right-hand sides; 0 if GMRES did not run).
+ * right-hand sides; 0 if GMRES did not run); r_spread: max |r_ii| / min |r_ii|
+ * of the factor the refinement used (a lower bound on kappa(A) that selects
+ * the refinement form).
  * tqr_ls_last_info(&info) returns this for the calling thread's last
  * tqr_solve_ls or tqr_ls_solve (0, or -1 for a NULL pointer).
  */
@@ -347,7 +349,7 @@ enum {
 };
 typedef struct tqr_ls_info {
   int32_t path, iters, inner_iters, fp32_status;
-  double berr, berr_fp32, gmres_res;
+  double berr, berr_fp32, gmres_res, r_spread;
 } tqr_ls_info;
 int tqr_ls_last_info(tqr_ls_info* info);
 

@@ -123,17 +123,34 @@ __global__ void __launch_bounds__(kLsThreads) gemm_tn(const double* __restrict__
     double acc[kRhsChunk];
 #pragma unroll
     for (int c = 0; c < kRhsChunk; ++c) acc[c] = 0.0;
-    for (int r = lane; r < m; r += 32) {
-      const double av = a[r] * s;
+    if (cw == 1) {
+      // one right-hand side: no predicated FMAs (they would still take
+      // issue slots of the FP64 pipe), four independent partial sums
+      const double* rr = R + static_cast<long long>(c0) * ldr;
+      double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      int r = lane;
+      for (; r + 96 < m; r += 128) {
+        acc[0] = fma(a[r] * s, rr[r], acc[0]);
+        a1 = fma(a[r + 32] * s, rr[r + 32], a1);
+        a2 = fma(a[r + 64] * s, rr[r + 64], a2);
+        a3 = fma(a[r + 96] * s, rr[r + 96], a3);
+      }
+      for (; r < m; r += 32) acc[0] = fma(a[r] * s, rr[r], acc[0]);
+      acc[0] += (a1 + a2) + a3;
+    } else {
+      for (int r = lane; r < m; r += 32) {
+        const double av = a[r] * s;
 #pragma unroll
-      for (int c = 0; c < kRhsChunk; ++c)
-        if (c < cw) acc[c] = fma(av, R[r + static_cast<long long>(c0 + c) * ldr], acc[c]);
+        for (int c = 0; c < kRhsChunk; ++c)
+          if (c < cw) acc[c] = fma(av, R[r + static_cast<long long>(c0 + c) * ldr], acc[c]);
+      }
     }
 #pragma unroll
     for (int c = 0; c < kRhsChunk; ++c) {
+      if (c >= cw) break;  // uniform over the warp
       double v = acc[c];
       for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-      if (lane == 0 && c < cw) G[j + static_cast<long long>(c0 + c) * ldg] = alpha * v;
+      if (lane == 0) G[j + static_cast<long long>(c0 + c) * ldg] = alpha * v;
     }
   }
 }
@@ -987,6 +1004,7 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
     info->inner_iters = inner;
     info->berr = berr;
     info->gmres_res = gres;
+    info->r_spread = hn[4 * R + 3] / hn[4 * R + 2];
   }
   return status;
 }

@@ -78,96 +78,162 @@ __device__ bool wait_flag(const int* f, TrsvCtl* ctl, long long limit_ns, int* s
   return *s_ok != 0;
 }
 
+// One tile (nb x nb, column-major, 16-byte aligned) in 16-byte pieces: each
+// thread holds up to kTileChunks of them in registers, so the loads of the
+// next tile are in flight while the current one is used or a flag awaited.
+constexpr int kTileChunks = 16;
+
+template <typename real>
+__device__ __forceinline__ void tile_fetch(const real* tile, int nb, uint4 (&buf)[kTileChunks]) {
+  const int chunks = nb * nb * static_cast<int>(sizeof(real)) / 16;
+  const uint4* src = reinterpret_cast<const uint4*>(tile);
+#pragma unroll
+  for (int i = 0; i < kTileChunks; ++i) {
+    const int e = threadIdx.x + i * kVecThreads;
+    if (e < chunks) buf[i] = __ldcg(src + e);
+  }
+}
+
+// The fetched tile into shared memory with leading dimension ldt (nb + 1:
+// row and column walks across lanes both fall on distinct banks).
+template <typename real>
+__device__ __forceinline__ void tile_store(const uint4 (&buf)[kTileChunks], int nb, real* sT, int ldt) {
+  constexpr int per = 16 / static_cast<int>(sizeof(real));
+  const int chunks = nb * nb * static_cast<int>(sizeof(real)) / 16;
+#pragma unroll
+  for (int i = 0; i < kTileChunks; ++i) {
+    const int e = threadIdx.x + i * kVecThreads;
+    if (e < chunks) {
+      const real* v = reinterpret_cast<const real*>(&buf[i]);
+      const int lin = e * per, r = lin % nb, c = lin / nb;  // nb % per == 0: one column per piece
+#pragma unroll
+      for (int q = 0; q < per; ++q) sT[r + q + c * ldt] = v[q];
+    }
+  }
+}
+
 // R X = Y (TRANS false, rows solved from the last tile row up) or
 // R^T X = Y (TRANS true, from the first down).  R: the upper triangle of the
 // tiles (k, j), j >= k, of an n-column factorization (tile rows 0 .. qn-1,
 // qn = ceil(n / nb)), p tile rows in the BDL array.  Y, X: n x nrhs, FP64,
-// column-major; X may alias Y.  Dynamic shared memory: the diagonal tile
-// (nb x (nb + 1) reals) and two nb x nrhs work arrays.
+// column-major; X may alias Y.  Requires nb * nb * sizeof(real) <= 16
+// kTileChunks kVecThreads bytes and nb <= 128 (four rows per lane in the
+// substitution).  Dynamic shared memory: trsv_smem.
 template <typename real, bool TRANS>
 __global__ void __launch_bounds__(kVecThreads) trsv_kernel(const real* __restrict__ A, int p, int nb, int n,
                                                            int nrhs, const double* Y, long long ldy, double* X,
                                                            long long ldx, int* ctl_words, long long limit_ns,
                                                            double* err_out) {
   extern __shared__ __align__(16) unsigned char vec_smem[];
-  real* sD = reinterpret_cast<real*>(vec_smem);            // diagonal tile, ld nb + 1
-  const int ldd = nb + 1;
-  real* sC = sD + nb * ldd;                                // right-hand side, then solution (nb x nrhs)
-  real* sV = sC + nb * nrhs;                               // a published block (nb x nrhs)
+  const int ld = nb + 1;
+  real* sD = reinterpret_cast<real*>(vec_smem);  // diagonal tile
+  real* sT = sD + nb * ld;                        // off-diagonal tile
+  real* sC = sT + nb * ld;                        // right-hand side, then solution (nb x nrhs)
+  real* sV = sC + nb * nrhs;                      // a published block (nb x nrhs)
+  real* sP = sV + nb * nrhs;                      // partial sums (kVecThreads x nrhs)
+  real* sRd = sP + kVecThreads * nrhs;            // reciprocals of the diagonal
   __shared__ int s_row, s_ok;
   TrsvCtl* ctl = reinterpret_cast<TrsvCtl*>(ctl_words);
   int* flags = ctl_words + 4;
   const int qn = (n + nb - 1) / nb;
   const long long nb2 = static_cast<long long>(nb) * nb;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  constexpr int nwarps = kVecThreads / 32;
+  const int parts = kVecThreads / nb;             // threads per row (column) of a tile product
+  const int u = tid % nb, h = tid / nb;
+  uint4 buf[kTileChunks];
   for (;;) {
     if (tid == 0) s_row = ld_acquire_flag(&ctl->abort) != 0 ? qn : atomicAdd(&ctl->ticket, 1);
     __syncthreads();
     const int t = s_row;
     __syncthreads();
     if (t >= qn) return;
-    const int k = TRANS ? t : qn - 1 - t;                  // tile row solved by this ticket
+    const int k = TRANS ? t : qn - 1 - t;        // tile row solved by this ticket
     const int r0 = k * nb;
     const int rows = min(nb, n - r0);
-    // diagonal tile and the right-hand side
-    const real* Dk = A + (static_cast<long long>(k) + static_cast<long long>(k) * p) * nb2;
-    for (int e = tid; e < nb * nb; e += kVecThreads) sD[(e % nb) + (e / nb) * ldd] = Dk[e];
+    tile_fetch(A + (static_cast<long long>(k) + static_cast<long long>(k) * p) * nb2, nb, buf);
+    tile_store(buf, nb, sD, ld);
     for (int e = tid; e < nb * nrhs; e += kVecThreads) {
       const int r = e % nb, c = e / nb;
       sC[e] = r < rows ? static_cast<real>(Y[r0 + r + c * ldy]) : real(0);
     }
     __syncthreads();
+    for (int e = tid; e < rows; e += kVecThreads) sRd[e] = real(1) / sD[e + e * ld];
+    __syncthreads();
     // contributions of the rows solved before this one, in solve order
     const int nl = TRANS ? k : qn - 1 - k;
+    auto off_tile = [&](int l) {
+      return TRANS ? A + (static_cast<long long>(l) + static_cast<long long>(k) * p) * nb2   // tile (l, k)
+                   : A + (static_cast<long long>(k) + static_cast<long long>(l) * p) * nb2;  // tile (k, l)
+    };
+    if (nl > 0) tile_fetch(off_tile(TRANS ? 0 : qn - 1), nb, buf);
     for (int a = 0; a < nl; ++a) {
       const int l = TRANS ? a : qn - 1 - a;
       if (!wait_flag(&flags[l], ctl, limit_ns, &s_ok, err_out)) return;
+      tile_store(buf, nb, sT, ld);
+      if (a + 1 < nl) tile_fetch(off_tile(TRANS ? a + 1 : qn - 2 - a), nb, buf);
       const int lrows = min(nb, n - l * nb);
       for (int e = tid; e < nb * nrhs; e += kVecThreads) {
         const int r = e % nb, c = e / nb;
         sV[e] = r < lrows ? static_cast<real>(__ldcg(X + l * nb + r + c * ldx)) : real(0);
       }
       __syncthreads();
-      if (TRANS) {
-        // C(j) -= sum_r R(l, k)[r, j] V(r): tile (l, k), column j contiguous;
-        // one warp per column, lanes over r
-        const real* Tl = A + (static_cast<long long>(l) + static_cast<long long>(k) * p) * nb2;
-        for (int j = wid; j < nb; j += nwarps)
-          for (int c = 0; c < nrhs; ++c) {
-            real acc = real(0);
-            for (int r = lane; r < nb; r += 32) acc = fma(Tl[r + static_cast<long long>(j) * nb], sV[r + c * nb], acc);
-            for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-            if (lane == 0) sC[j + c * nb] -= acc;
-          }
-      } else {
-        // C(r) -= sum_j R(k, l)[r, j] V(j): tile (k, l), one thread per row
-        const real* Tl = A + (static_cast<long long>(k) + static_cast<long long>(l) * p) * nb2;
-        for (int e = tid; e < nb * nrhs; e += kVecThreads) {
-          const int r = e % nb, c = e / nb;
+      // R^T: C(u) -= sum_w T(w, u) V(w);  R: C(u) -= sum_w T(u, w) V(w);
+      // thread (u, h) sums its part of w
+      if (h < parts) {
+        const int w0 = h * nb / parts, w1 = (h + 1) * nb / parts;
+        for (int c = 0; c < nrhs; ++c) {
           real acc = real(0);
-          for (int j = 0; j < nb; ++j) acc = fma(Tl[r + static_cast<long long>(j) * nb], sV[j + c * nb], acc);
-          sC[e] -= acc;
+          const real* vv = sV + c * nb;
+          if (TRANS) {
+            for (int w = w0; w < w1; ++w) acc = fma(sT[w + u * ld], vv[w], acc);
+          } else {
+            for (int w = w0; w < w1; ++w) acc = fma(sT[u + w * ld], vv[w], acc);
+          }
+          sP[c * kVecThreads + h * nb + u] = acc;
         }
       }
       __syncthreads();
+      for (int e = tid; e < nb * nrhs; e += kVecThreads) {
+        const int r = e % nb, c = e / nb;
+        real acc = real(0);
+        for (int hh = 0; hh < parts; ++hh) acc += sP[c * kVecThreads + hh * nb + r];
+        sC[e] -= acc;
+      }
+      __syncthreads();
     }
-    // substitution with the diagonal triangle, one warp, column oriented:
-    // x_s = c_s / d_s, then c_t -= D(s, t) x_s (R^T) or D(t, s) x_s (R)
+    // substitution with the diagonal triangle in one warp, column oriented,
+    // the right-hand side in registers (lane owns rows lane + 32 j):
+    // x_s = c_s / d_s, then c_w -= D(s, w) x_s (R^T, w > s) or D(w, s) x_s (R, w < s)
     if (wid == 0) {
       for (int c = 0; c < nrhs; ++c) {
-        real* cc = sC + c * nb;
+        real cr[4];
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int w = lane + 32 * j;
+          cr[j] = w < rows ? sC[w + c * nb] : real(0);
+        }
         for (int step = 0; step < rows; ++step) {
           const int s = TRANS ? step : rows - 1 - step;
-          const real xs = cc[s] / sD[s + s * ldd];
-          __syncwarp();
-          if (TRANS) {
-            for (int u = s + 1 + lane; u < rows; u += 32) cc[u] = fma(-sD[s + u * ldd], xs, cc[u]);
-          } else {
-            for (int u = lane; u < s; u += 32) cc[u] = fma(-sD[u + s * ldd], xs, cc[u]);
+          const int owner = s & 31, js = s >> 5;
+          real mine = real(0);
+#pragma unroll
+          for (int j = 0; j < 4; ++j)
+            if (j == js) mine = cr[j];
+          const real xs = __shfl_sync(0xffffffffu, mine * sRd[s], owner);
+#pragma unroll
+          for (int j = 0; j < 4; ++j) {
+            const int w = lane + 32 * j;
+            if (w == s) {
+              cr[j] = xs;
+            } else if (w < rows && (TRANS ? w > s : w < s)) {
+              cr[j] = fma(-(TRANS ? sD[s + w * ld] : sD[w + s * ld]), xs, cr[j]);
+            }
           }
-          if (lane == 0) cc[s] = xs;
-          __syncwarp();
+        }
+#pragma unroll
+        for (int j = 0; j < 4; ++j) {
+          const int w = lane + 32 * j;
+          if (w < rows) sC[w + c * nb] = cr[j];
         }
       }
     }
@@ -231,15 +297,35 @@ __global__ void __launch_bounds__(kVecThreads) q1n_partial(const float* __restri
   }
   __syncthreads();
   const long long nb2 = static_cast<long long>(nb) * nb;
-  for (int r = threadIdx.x; r < nb; r += kVecThreads) {
-    float acc = 0.0f;
+  // threads (r, h): row r of the tile row, column quarter h of each tile;
+  // four independent sums keep several loads in flight per thread
+  const int parts = kVecThreads / nb;
+  const int r = threadIdx.x % nb, h = threadIdx.x / nb;
+  float* red = sy + (j1 - j0) * nb;               // parts x nb partial sums
+  float acc = 0.0f;
+  if (h < parts) {
+    float a1 = 0.0f, a2 = 0.0f, a3 = 0.0f;
+    const int c0 = h * nb / parts, c1 = (h + 1) * nb / parts;
     for (int jt = j0; jt < j1; ++jt) {
       const float* tl = Q + (static_cast<long long>(it) + static_cast<long long>(jt) * p) * nb2 + r;
       const float* yy = sy + (jt - j0) * nb;
-      for (int jj = 0; jj < nb; ++jj) acc = fmaf(tl[static_cast<long long>(jj) * nb], yy[jj], acc);
+      int jj = c0;
+      for (; jj + 3 < c1; jj += 4) {
+        acc = fmaf(__ldcg(tl + static_cast<long long>(jj) * nb), yy[jj], acc);
+        a1 = fmaf(__ldcg(tl + static_cast<long long>(jj + 1) * nb), yy[jj + 1], a1);
+        a2 = fmaf(__ldcg(tl + static_cast<long long>(jj + 2) * nb), yy[jj + 2], a2);
+        a3 = fmaf(__ldcg(tl + static_cast<long long>(jj + 3) * nb), yy[jj + 3], a3);
+      }
+      for (; jj < c1; ++jj) acc = fmaf(__ldcg(tl + static_cast<long long>(jj) * nb), yy[jj], acc);
     }
-    const int row = it * nb + r;
-    if (row < m) part[(static_cast<long long>(s) * gridDim.z + c) * m + row] = acc;
+    red[h * nb + r] = (acc + a1) + (a2 + a3);
+  }
+  __syncthreads();
+  if (threadIdx.x < nb) {
+    float sum = 0.0f;
+    for (int hh = 0; hh < parts; ++hh) sum += red[hh * nb + threadIdx.x];
+    const int row = it * nb + threadIdx.x;
+    if (row < m) part[(static_cast<long long>(s) * gridDim.z + c) * m + row] = sum;
   }
 }
 
@@ -263,10 +349,14 @@ __global__ void vec_combine(const float* __restrict__ part, int nsplit, int rows
 size_t trsv_ctl_ints(int n, int nb) { return 4 + static_cast<size_t>((n + nb - 1) / nb); }
 
 size_t trsv_smem(int nb, int nrhs, int esize) {
-  return static_cast<size_t>(esize) * (static_cast<size_t>(nb) * (nb + 1) + 2 * static_cast<size_t>(nb) * nrhs);
+  return static_cast<size_t>(esize) * (2 * static_cast<size_t>(nb) * (nb + 1) + 2 * static_cast<size_t>(nb) * nrhs +
+                                       static_cast<size_t>(kVecThreads) * nrhs + nb);
 }
 
-bool trsv_fits(int nb, int nrhs, int esize) { return nrhs <= kMaxVecRhs && trsv_smem(nb, nrhs, esize) <= 200 * 1024; }
+bool trsv_fits(int nb, int nrhs, int esize) {
+  return nrhs <= kMaxVecRhs && nb <= 128 && static_cast<size_t>(nb) * nb * esize <= 16u * kTileChunks * kVecThreads &&
+         trsv_smem(nb, nrhs, esize) <= 200 * 1024;
+}
 
 template <typename real>
 cudaError_t launch_trsv(bool trans, const real* tiles, int p, int nb, int n, int nrhs, const double* Y, long long ldy,
@@ -322,7 +412,7 @@ cudaError_t launch_q1n(const float* Q, int p, int nb, int m, int n, int nrhs, co
   int splits = std::min(std::min(q1_splits(p), qn), splits_cap);
   const int per = (qn + splits - 1) / splits;
   splits = (qn + per - 1) / per;
-  const size_t smem = sizeof(float) * static_cast<size_t>(per) * nb;
+  const size_t smem = sizeof(float) * (static_cast<size_t>(per) * nb + kVecThreads);
   cudaFuncSetAttribute(q1n_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
   q1n_partial<<<dim3(p, splits, nrhs), kVecThreads, smem, st>>>(Q, p, nb, m, n, Yv, ldy, static_cast<float>(yscale),
                                                                  per, part);

@@ -59,12 +59,12 @@ class TqrLsInfo(ctypes.Structure):
     """tqr_ls_info of include/tqr.h."""
     _fields_ = [("path", ctypes.c_int32), ("iters", ctypes.c_int32), ("inner_iters", ctypes.c_int32),
                 ("fp32_status", ctypes.c_int32), ("berr", ctypes.c_double), ("berr_fp32", ctypes.c_double),
-                ("gmres_res", ctypes.c_double)]
+                ("gmres_res", ctypes.c_double), ("r_spread", ctypes.c_double)]
 
     def as_dict(self):
         return dict(path=LS_PATH_NAMES.get(self.path, str(self.path)), iters=self.iters,
                     inner_iters=self.inner_iters, fp32_status=self.fp32_status, berr=self.berr,
-                    berr_fp32=self.berr_fp32, gmres_res=self.gmres_res)
+                    berr_fp32=self.berr_fp32, gmres_res=self.gmres_res, r_spread=self.r_spread)
 
 
 _i64 = ctypes.c_int64
