@@ -287,7 +287,7 @@ int tqr_lu_solve_pairs(int64_t n, int64_t nrhs, const double* A, int64_t lda, in
  *                           seems below 0.02 and it keeps converging); then
  *                           GMRES-IR on the same system, left-preconditioned
  *                           by the FP32 factors (Carson, Higham and Pranesh
- *                           2020), while kappa u_fp32 seems below 0.1 and
+ *                           2020), while kappa u_fp32 seems below 0.03 and
  *                           each GMRES cycle gets its residual below 0.1.
  *                           A problem none of them finishes -- or
  *                           whose ||A||_F lies outside [2^-40, 2^40] -- is

@@ -201,43 +201,52 @@ __global__ void __launch_bounds__(kVecThreads) trsv_kernel(const real* __restric
       }
       __syncthreads();
     }
-    // substitution with the diagonal triangle in one warp, column oriented,
-    // the right-hand side in registers (lane owns rows lane + 32 j):
-    // x_s = c_s / d_s, then c_w -= D(s, w) x_s (R^T, w > s) or D(w, s) x_s (R, w < s)
-    if (wid == 0) {
-      for (int c = 0; c < nrhs; ++c) {
-        real cr[4];
+    // substitution with the diagonal triangle in blocks of 32 rows: warp 0
+    // solves a block with the right-hand side and the block's triangle in
+    // registers (lane i owns row i of the block), then every thread folds
+    // the block's solution into the rows still to be solved.
+    // R^T (lower): x_s = c_s / d_s, c_i -= D(s, i) x_s for i > s;
+    // R (upper):   the same from the last row up, with D(i, s), i < s.
+    const int nblk = (rows + 31) / 32;
+    for (int bb = 0; bb < nblk; ++bb) {
+      const int b = TRANS ? bb : nblk - 1 - bb;
+      const int base = 32 * b, i = base + lane;
+      if (wid == 0) {
+        real Lrow[32];
 #pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int w = lane + 32 * j;
-          cr[j] = w < rows ? sC[w + c * nb] : real(0);
+        for (int t = 0; t < 32; ++t) {
+          const int col = base + t;
+          Lrow[t] = (i < rows && col < rows) ? (TRANS ? sD[col + i * ld] : sD[i + col * ld]) : real(0);
         }
-        for (int step = 0; step < rows; ++step) {
-          const int s = TRANS ? step : rows - 1 - step;
-          const int owner = s & 31, js = s >> 5;
-          real mine = real(0);
+        for (int c = 0; c < nrhs; ++c) {
+          real v = i < rows ? sC[i + c * nb] : real(0);
 #pragma unroll
-          for (int j = 0; j < 4; ++j)
-            if (j == js) mine = cr[j];
-          const real xs = __shfl_sync(0xffffffffu, mine * sRd[s], owner);
-#pragma unroll
-          for (int j = 0; j < 4; ++j) {
-            const int w = lane + 32 * j;
-            if (w == s) {
-              cr[j] = xs;
-            } else if (w < rows && (TRANS ? w > s : w < s)) {
-              cr[j] = fma(-(TRANS ? sD[s + w * ld] : sD[w + s * ld]), xs, cr[j]);
+          for (int tt = 0; tt < 32; ++tt) {
+            const int t = TRANS ? tt : 31 - tt;
+            if (base + t >= rows) continue;  // uniform over the warp
+            const real xs = __shfl_sync(0xffffffffu, v * sRd[base + t], t);
+            if (lane == t) {
+              v = xs;
+            } else if (TRANS ? lane > t : lane < t) {
+              v = fma(-Lrow[t], xs, v);
             }
           }
-        }
-#pragma unroll
-        for (int j = 0; j < 4; ++j) {
-          const int w = lane + 32 * j;
-          if (w < rows) sC[w + c * nb] = cr[j];
+          if (i < rows) sC[i + c * nb] = v;
         }
       }
+      __syncthreads();
+      // rows outside the block: R^T the rows after it, R the rows before it
+      const int o0 = TRANS ? base + 32 : 0, o1 = TRANS ? rows : base;
+      const int bw = min(32, rows - base);
+      for (int e = tid; e < (o1 - o0) * nrhs; e += kVecThreads) {
+        const int w = o0 + e % (o1 - o0), c = e / (o1 - o0);
+        real acc = real(0);
+        for (int t = 0; t < bw; ++t)
+          acc = fma(TRANS ? sD[(base + t) + w * ld] : sD[w + (base + t) * ld], sC[base + t + c * nb], acc);
+        sC[w + c * nb] -= acc;
+      }
+      __syncthreads();
     }
-    __syncthreads();
     for (int e = tid; e < rows * nrhs; e += kVecThreads) {
       const int r = e % rows, c = e / rows;
       X[r0 + r + c * ldx] = static_cast<double>(sC[r + c * nb]);
