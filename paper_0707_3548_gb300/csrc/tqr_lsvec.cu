@@ -21,6 +21,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <mutex>
 
 #include "tqr.h"
 #include "tqr_api_internal.h"
@@ -126,8 +127,8 @@ __global__ void __launch_bounds__(kVecThreads) trsv_kernel(const real* __restric
                                                            double* err_out) {
   extern __shared__ __align__(16) unsigned char vec_smem[];
   const int ld = nb + 1;
-  real* sD = reinterpret_cast<real*>(vec_smem);  // diagonal tile
-  real* sT = sD + nb * ld;                        // off-diagonal tile
+  real* sT = reinterpret_cast<real*>(vec_smem);  // off-diagonal tiles, then the diagonal one
+  real* sD = sT;
   real* sC = sT + nb * ld;                        // right-hand side, then solution (nb x nrhs)
   real* sV = sC + nb * nrhs;                      // a published block (nb x nrhs)
   real* sP = sV + nb * nrhs;                      // partial sums (kVecThreads x nrhs)
@@ -150,27 +151,25 @@ __global__ void __launch_bounds__(kVecThreads) trsv_kernel(const real* __restric
     const int k = TRANS ? t : qn - 1 - t;        // tile row solved by this ticket
     const int r0 = k * nb;
     const int rows = min(nb, n - r0);
-    tile_fetch(A + (static_cast<long long>(k) + static_cast<long long>(k) * p) * nb2, nb, buf);
-    tile_store(buf, nb, sD, ld);
+    const real* Dk = A + (static_cast<long long>(k) + static_cast<long long>(k) * p) * nb2;
     for (int e = tid; e < nb * nrhs; e += kVecThreads) {
       const int r = e % nb, c = e / nb;
       sC[e] = r < rows ? static_cast<real>(Y[r0 + r + c * ldy]) : real(0);
     }
-    __syncthreads();
-    for (int e = tid; e < rows; e += kVecThreads) sRd[e] = real(1) / sD[e + e * ld];
-    __syncthreads();
-    // contributions of the rows solved before this one, in solve order
+    // contributions of the rows solved before this one, in solve order; the
+    // next tile (the diagonal one after the last) is fetched while the
+    // current one is used
     const int nl = TRANS ? k : qn - 1 - k;
     auto off_tile = [&](int l) {
       return TRANS ? A + (static_cast<long long>(l) + static_cast<long long>(k) * p) * nb2   // tile (l, k)
                    : A + (static_cast<long long>(k) + static_cast<long long>(l) * p) * nb2;  // tile (k, l)
     };
-    if (nl > 0) tile_fetch(off_tile(TRANS ? 0 : qn - 1), nb, buf);
+    tile_fetch(nl > 0 ? off_tile(TRANS ? 0 : qn - 1) : Dk, nb, buf);
     for (int a = 0; a < nl; ++a) {
       const int l = TRANS ? a : qn - 1 - a;
       if (!wait_flag(&flags[l], ctl, limit_ns, &s_ok, err_out)) return;
       tile_store(buf, nb, sT, ld);
-      if (a + 1 < nl) tile_fetch(off_tile(TRANS ? a + 1 : qn - 2 - a), nb, buf);
+      tile_fetch(a + 1 < nl ? off_tile(TRANS ? a + 1 : qn - 2 - a) : Dk, nb, buf);
       const int lrows = min(nb, n - l * nb);
       for (int e = tid; e < nb * nrhs; e += kVecThreads) {
         const int r = e % nb, c = e / nb;
@@ -201,6 +200,11 @@ __global__ void __launch_bounds__(kVecThreads) trsv_kernel(const real* __restric
       }
       __syncthreads();
     }
+    __syncthreads();
+    tile_store(buf, nb, sD, ld);  // the diagonal tile
+    __syncthreads();
+    for (int e = tid; e < rows; e += kVecThreads) sRd[e] = real(1) / sD[e + e * ld];
+    __syncthreads();
     // substitution with the diagonal triangle in blocks of 32 rows: warp 0
     // solves a block with the right-hand side and the block's triangle in
     // registers (lane i owns row i of the block), then every thread folds
@@ -358,13 +362,40 @@ __global__ void vec_combine(const float* __restrict__ part, int nsplit, int rows
 size_t trsv_ctl_ints(int n, int nb) { return 4 + static_cast<size_t>((n + nb - 1) / nb); }
 
 size_t trsv_smem(int nb, int nrhs, int esize) {
-  return static_cast<size_t>(esize) * (2 * static_cast<size_t>(nb) * (nb + 1) + 2 * static_cast<size_t>(nb) * nrhs +
+  return static_cast<size_t>(esize) * (static_cast<size_t>(nb) * (nb + 1) + 2 * static_cast<size_t>(nb) * nrhs +
                                        static_cast<size_t>(kVecThreads) * nrhs + nb);
+}
+
+// The kernels' dynamic shared-memory limits are raised once per device
+// (under a lock), not at every launch: the request server launches them from
+// several host threads at once.
+constexpr int kVecSmemMax = 200 * 1024;
+static std::mutex g_vec_mu;
+static bool g_vec_ready[64];
+
+static cudaError_t vec_setup() {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= 64) return cudaErrorInvalidDevice;
+  std::lock_guard<std::mutex> lk(g_vec_mu);
+  if (g_vec_ready[dev]) return cudaSuccess;
+  cudaError_t e = cudaSuccess;
+  auto set = [&](const void* f) {
+    const cudaError_t r = cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, kVecSmemMax);
+    if (r != cudaSuccess && e == cudaSuccess) e = r;
+  };
+  set(reinterpret_cast<const void*>(trsv_kernel<float, true>));
+  set(reinterpret_cast<const void*>(trsv_kernel<float, false>));
+  set(reinterpret_cast<const void*>(trsv_kernel<double, true>));
+  set(reinterpret_cast<const void*>(trsv_kernel<double, false>));
+  set(reinterpret_cast<const void*>(q1t_partial));
+  set(reinterpret_cast<const void*>(q1n_partial));
+  if (e == cudaSuccess) g_vec_ready[dev] = true;
+  return e;
 }
 
 bool trsv_fits(int nb, int nrhs, int esize) {
   return nrhs <= kMaxVecRhs && nb <= 128 && static_cast<size_t>(nb) * nb * esize <= 16u * kTileChunks * kVecThreads &&
-         trsv_smem(nb, nrhs, esize) <= 200 * 1024;
+         trsv_smem(nb, nrhs, esize) <= static_cast<size_t>(kVecSmemMax);
 }
 
 template <typename real>
@@ -372,15 +403,18 @@ cudaError_t launch_trsv(bool trans, const real* tiles, int p, int nb, int n, int
                         double* X, long long ldx, int* ctl, long long limit_ns, double* err_out, cudaStream_t st) {
   const size_t smem = trsv_smem(nb, nrhs, sizeof(real));
   const int qn = (n + nb - 1) / nb;
-  const int grid = std::max(1, std::min(qn, 2 * device_sms()));
-  cudaError_t e = cudaMemsetAsync(ctl, 0, sizeof(int) * trsv_ctl_ints(n, nb), st);
+  // a few CTAs keep up with the wavefront of tile rows (each folds in the
+  // rows solved before its own while it waits); more would only hold SMs
+  // that concurrent work could use
+  const int grid = std::max(1, std::min(qn, 8));
+  cudaError_t e = vec_setup();
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(ctl, 0, sizeof(int) * trsv_ctl_ints(n, nb), st);
   if (e != cudaSuccess) return e;
   if (trans) {
-    cudaFuncSetAttribute(trsv_kernel<real, true>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     trsv_kernel<real, true><<<grid, kVecThreads, smem, st>>>(tiles, p, nb, n, nrhs, Y, ldy, X, ldx, ctl, limit_ns,
                                                              err_out);
   } else {
-    cudaFuncSetAttribute(trsv_kernel<real, false>, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
     trsv_kernel<real, false><<<grid, kVecThreads, smem, st>>>(tiles, p, nb, n, nrhs, Y, ldy, X, ldx, ctl, limit_ns,
                                                               err_out);
   }
@@ -405,7 +439,8 @@ cudaError_t launch_q1t(const float* Q, int p, int nb, int m, int n, int nrhs, co
   const int per = (p + splits - 1) / splits;
   splits = (p + per - 1) / per;
   const size_t smem = sizeof(float) * static_cast<size_t>(per) * nb;
-  cudaFuncSetAttribute(q1t_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  const cudaError_t e = vec_setup();
+  if (e != cudaSuccess) return e;
   q1t_partial<<<dim3(qn, splits, nrhs), kVecThreads, smem, st>>>(Q, p, nb, m, n, F, ldf, static_cast<float>(fscale),
                                                                   per, part);
   const long long total = static_cast<long long>(n) * nrhs;
@@ -422,7 +457,8 @@ cudaError_t launch_q1n(const float* Q, int p, int nb, int m, int n, int nrhs, co
   const int per = (qn + splits - 1) / splits;
   splits = (qn + per - 1) / per;
   const size_t smem = sizeof(float) * (static_cast<size_t>(per) * nb + kVecThreads);
-  cudaFuncSetAttribute(q1n_partial, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  const cudaError_t e = vec_setup();
+  if (e != cudaSuccess) return e;
   q1n_partial<<<dim3(p, splits, nrhs), kVecThreads, smem, st>>>(Q, p, nb, m, n, Yv, ldy, static_cast<float>(yscale),
                                                                  per, part);
   const long long total = static_cast<long long>(m) * nrhs;
