@@ -124,3 +124,25 @@ def test_batch_policy_tuner_writes_one_choice_per_class_and_the_batch_is_correct
             assert np.max(np.abs(F - f.F)) <= 1e-11 * np.abs(f.F).max()
     finally:
         tqr.tqr_autotune_clear()
+
+
+def test_batch_with_config_sized_matrices_up_to_2048():
+    """Matrices of the batch benchmark's size range (m up to 2048, n up to m)
+    in one launch with the library's tile choice: each equals factoring it
+    alone, and its R satisfies R^T R = A^T A to 10 n u of ||A||_F^2 (a
+    backward-stable factorization's bound, independent of conditioning)."""
+    torch_cuda()
+    shapes = [(2048, 2048), (2048, 1500), (1900, 37), (1024, 1024), (777, 500), (64, 32), (1300, 1299)]
+    mats = [inputs.normal_matrix(m, n, 300 + a) for a, (m, n) in enumerate(shapes)]
+    tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
+    t, dev, Ts = _submit(mats, tiles)
+    rc, st = tqr.tqr_batch_wait(t, len(mats))
+    assert rc == 0 and not st.any()
+    for A, dA, (nb, ib) in zip(mats, dev, tiles):
+        F = to_host(dA)
+        Fa, _ = _alone(A, nb, ib)
+        assert np.array_equal(F, Fa)
+        k = min(A.shape)
+        R = np.triu(F)[:k]
+        err = np.linalg.norm(R.T @ R - A.T @ A) / np.linalg.norm(A) ** 2
+        assert err <= 10 * max(A.shape) * 2.0 ** -53, err

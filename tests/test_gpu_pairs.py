@@ -97,6 +97,37 @@ def test_full_size_sampled_pairs():
     assert err <= 10 * n * U53
 
 
+def test_full_size_every_column_and_sampled_gram_entries():
+    """16384 x 16384, nb 128, ib 16 (the benchmark's launch), checked in
+    every block of R with identities that hold at any size: Q is orthogonal,
+    so ||R e_j|| = ||A e_j|| for every column j, and (R^T R)(i, j) =
+    (A^T A)(i, j) for every pair -- here 400 pairs drawn over the whole
+    matrix, interior and trailing blocks included -- within a few units of
+    FP64 rounding relative to the column norms (1e4 u; a wrong block would
+    be off by O(1))."""
+    torch = torch_cuda()
+    m = n = 16384
+    A = inputs.normal_matrix(m, n, 0)
+    dA = to_dev(A)
+    tqr.tqr_factor_pairs(dA, 128, 16)
+    torch.cuda.synchronize()
+    R = torch.triu(dA)
+    rn = torch.linalg.vector_norm(R, dim=0).cpu().numpy()
+    an = np.linalg.norm(A, axis=0)
+    assert np.max(np.abs(rn - an) / an) <= 1e4 * U53
+    g = inputs.rng(5)
+    ii = g.integers(0, n, 400)
+    jj = g.integers(0, n, 400)
+    Rc = R.cpu().numpy()
+    for i, j in zip(ii, jj):
+        rr = Rc[:, i] @ Rc[:, j]
+        aa = A[:, i] @ A[:, j]
+        assert abs(rr - aa) <= 1e4 * U53 * an[i] * an[j], (i, j, rr, aa)
+    # the stored factor: reflectors below the diagonal, R on and above; the
+    # returned R (upper part) has its own diagonal entries nonzero
+    assert np.all(np.abs(np.diag(Rc)) > 0)
+
+
 def test_pair_and_flat_plans_do_not_mix():
     """Both variants of one shape, alternately: each must run its own task
     list (the plan cache keys on the variant)."""
