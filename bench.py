@@ -1052,6 +1052,7 @@ def run_serve(args, w):
     th.join()
     infos = [srv.wait(r) for r in ids]
     t1 = time.perf_counter()
+    last_failure = srv.last_failure()
     span = max_over_ranks(t1 - t0, dist, dev)
     if dist is not None:
         # per-request records (latency, status, class, backward error) to rank 0
@@ -1090,7 +1091,8 @@ def run_serve(args, w):
                        "parallelism": ("requests routed over %d ranks (matrix affinity, least load), no data "
                                        "collective" % world) if world > 1 else "single GPU"},
             "offered_per_s": len(reqs) / window, "completed": len(reqs) - bad, "failed": bad,
-            "failures": failures, "slots": w["slots"], "grid_cap": args.grid_cap,
+            "failures": failures, "last_failure": last_failure or None, "slots": w["slots"],
+            "grid_cap": args.grid_cap,
             "p50_ms": pct(allv, 0.5), "p99_ms": pct(allv, 0.99),
             "classes": {c: {"count": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)} for c, v in lat.items()},
             "reused_resident": stats["reused"] - base["reused"],

@@ -142,6 +142,17 @@ int tqr_debug_autotune_put(int64_t m, int64_t n, int nb, int ib, double us);
 /* Last error message of this thread ("" if none). */
 const char* tqr_debug_last_error(void);
 
+/*
+ * Description of the server's latest failed request ("" if none): its id,
+ * matrix id, shape, class and status, and for a device wait that ran out
+ * in a task kernel, whether it was a dependency or a bulk-copy wait and the
+ * task (kind, k, i, j, s, l as in tqr_debug_plan) it was running.  Written
+ * into buf (len bytes, NUL-terminated, truncated to fit).  Returns 0, -1
+ * for a null server or -2 for a null or empty buffer.
+ */
+struct tqr_server;
+int tqr_debug_server_last_failure(struct tqr_server* server, char* buf, size_t len);
+
 #ifdef __cplusplus
 }
 #endif

@@ -510,7 +510,8 @@ WsLayout ws_layout(const Inst& I, int esize, bool with_t) {
 // Clears the counters and control block, uploads the instance and runs the
 // plan.  `I` must already hold the device pointers.
 template <typename real>
-int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st, int grid_cap) {
+int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st, int grid_cap,
+             double* err_out) {
   int status = TQR_OK;
   std::shared_ptr<DevPlan> plan = get_plan(I, sizeof(real), ctas_per_sm, &status, grid_cap);
   if (!plan) return status;
@@ -527,6 +528,7 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
   }
   cudaError_t e = launch_run<real>(plan->d_tasks, plan->ntasks, reinterpret_cast<const Inst*>(ws + W.oInst),
                                    ws + W.oCtl, wait_limit_ns(), plan->grid, smem, st, I.lu ? 1 : (I.pair ? 2 : 0));
+  if (e == cudaSuccess && err_out != nullptr) e = launch_fold_error(ws + W.oCtl, plan->d_tasks, plan->ntasks, err_out, st);
   if (ev.first) {
     cudaEventRecord(ev.second, st);
     std::lock_guard<std::mutex> lk(g_mu);
@@ -540,8 +542,8 @@ int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int sm
   return TQR_OK;
 }
 
-template int run_plan<double>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t, int);
-template int run_plan<float>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t, int);
+template int run_plan<double>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t, int, double*);
+template int run_plan<float>(const Inst&, char*, const WsLayout&, int, int, cudaStream_t, int, double*);
 
 // ---------------------------------------------------------------- several graphs, one launch
 // Independent task graphs of one factorization's operands (say Q^T f and a
@@ -553,7 +555,7 @@ static const size_t kMaxMultiPlans = 64;
 
 template <typename real>
 int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int ctas_per_sm, int smem,
-                   cudaStream_t st, int grid_cap) {
+                   cudaStream_t st, int grid_cap, double* err_out) {
   int dev = 0;
   cudaGetDevice(&dev);
   int policy, max_ctas;
@@ -634,6 +636,7 @@ int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int
   }
   cudaError_t e = launch_run<real>(plan->d_tasks, plan->ntasks, d_insts, d_ctl, wait_limit_ns(), plan->grid, smem,
                                    st, insts[0].lu ? 1 : (insts[0].pair ? 2 : 0));
+  if (e == cudaSuccess && err_out != nullptr) e = launch_fold_error(d_ctl, plan->d_tasks, plan->ntasks, err_out, st);
   if (ev.first) {
     cudaEventRecord(ev.second, st);
     std::lock_guard<std::mutex> lk(g_mu);
@@ -647,8 +650,8 @@ int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int
   return TQR_OK;
 }
 
-template int run_plan_multi<double>(const Inst*, int, Inst*, void*, int, int, cudaStream_t, int);
-template int run_plan_multi<float>(const Inst*, int, Inst*, void*, int, int, cudaStream_t, int);
+template int run_plan_multi<double>(const Inst*, int, Inst*, void*, int, int, cudaStream_t, int, double*);
+template int run_plan_multi<float>(const Inst*, int, Inst*, void*, int, int, cudaStream_t, int, double*);
 
 // ---------------------------------------------------------------- pointers
 int ptr_kind(const void* p) {

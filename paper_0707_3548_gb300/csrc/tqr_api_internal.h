@@ -26,16 +26,18 @@ bool choose_shape(int nb, int ib, int esize, int* cs, int* ctas_per_sm, int* sme
 Inst make_inst(int mode, int64_t m, int64_t n, int nb, int ib, int cs, int nrhs, int trsm);
 WsLayout ws_layout(const Inst& I, int esize, bool with_t);
 // grid_cap > 0 limits the persistent grid (concurrent launches share SMs).
+// err_out (device, 8 doubles, zeroed by the caller) receives the launch's
+// own error record (launch_fold_error), independent of other launches.
 template <typename real>
 int run_plan(const Inst& I, char* ws, const WsLayout& W, int ctas_per_sm, int smem, cudaStream_t st,
-             int grid_cap = 0);
+             int grid_cap = 0, double* err_out = nullptr);
 // Several instances' task graphs in one persistent launch.  insts[a].ver
 // must be disjoint counter regions (zeroed here), d_insts device room for
 // `count` instances, d_ctl the launch's control block (ctl_bytes()).  The
 // host array's Inst.vtab may be a device pointer (the host copy is rebuilt).
 template <typename real>
 int run_plan_multi(const Inst* insts, int count, Inst* d_insts, void* d_ctl, int ctas_per_sm, int smem,
-                   cudaStream_t st, int grid_cap = 0);
+                   cudaStream_t st, int grid_cap = 0, double* err_out = nullptr);
 // Stream-ordered allocation from the library's pool (keeps freed memory).
 cudaError_t lib_malloc(void** p, size_t bytes, cudaStream_t st);
 int release_memory();

@@ -789,6 +789,18 @@ __device__ __forceinline__ real* t2_ptr(const Inst& I, int i, int k) {
   return static_cast<real*>(I.T) + t2_offset(I.p, I.q, I.nb, I.ib, i, k);
 }
 
+// Rows of tile row i that lie inside the matrix (below them the tiles hold
+// zero padding, in A, in the right-hand sides and in the reflectors), rounded
+// up to a multiple of 4 (the FP32 micro-tiles' granularity).  The TS / SS
+// kernels take only these rows: the padding would add exact zeros to every
+// sum and leave itself unchanged.
+__device__ __forceinline__ int live_rows(const Inst& I, int i) {
+  const int v = I.m - i * I.nb;
+  if (v >= I.nb) return I.nb;
+  const int r = (v + 3) & ~3;
+  return r < I.nb ? r : I.nb;
+}
+
 // Width of slab s of tile column j.
 __device__ __forceinline__ int slab_width(const Inst& I, int j, int s) {
   int w = I.cs;
@@ -849,7 +861,7 @@ __device__ void exec_tsqrt(Ctx<real>& cx, const Inst& I, int k, int head, int i,
       Rb[r + c * ib] = (r <= c) ? ldg_cg(Rt + (l0 + r) + static_cast<long long>(l0 + c) * nb) : real(0);
     }
     bulk_cols(cx, cx.P, cx.ldP, Ai + static_cast<long long>(l0) * nb, nb, nb, ib);
-    const int nv = tt ? l0 + ib : nb;  // rows that can hold reflector entries
+    const int nv = tt ? l0 + ib : live_rows(I, i);  // rows that can hold reflector entries
     if (tt)
       for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
         const int r = e % nv, c = e / nv;
@@ -958,7 +970,7 @@ __device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int head, int i,
         const int r = e % ib, c = e / ib;
         cx.T[r + c * cx.ldT] = cx.Tst[l0 * ib + r + c * ib];
       }
-      const int nv = tt ? l0 + ib : nb;
+      const int nv = tt ? l0 + ib : live_rows(I, i);
       if (tt)
         for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
           const int r = e % nv, c = e / nv;
@@ -993,7 +1005,7 @@ __device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int head, int i,
       }
       load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
       load_block(cx.Top, ib, Ct + l0, nb, ib, w);
-      const int nv = tt ? l0 + ib : nb;
+      const int nv = tt ? l0 + ib : live_rows(I, i);
       if (tt)
         for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
           const int r = e % nv, c = e / nv;
@@ -1016,7 +1028,7 @@ __device__ void exec_ssrfb(Ctx<real>& cx, const Inst& I, int k, int head, int i,
     load_block(cx.T, cx.ldT, Tg + static_cast<long long>(l0) * ib, ib, ib, ib);
     load_block(cx.Top, ib, Ct + l0, nb, ib, w);
     bulk_cols(cx, cx.P, cx.ldP, Vt + static_cast<long long>(l0) * nb, nb, nb, ib);
-    const int nv = tt ? l0 + ib : nb;
+    const int nv = tt ? l0 + ib : live_rows(I, i);
     if (tt)
       for (int e = threadIdx.x; e < nv * ib; e += kThreads) {
         const int r = e % nv, c = e / nv;
@@ -1205,7 +1217,7 @@ __device__ void exec_trsmt_solve(Ctx<real>& cx, const Inst& I, int k, int j, int
 // storage tiles.  The panel and slabs are staged with rows*nb rows.
 template <typename real>
 __device__ void exec_tsqrt2(Ctx<real>& cx, const Inst& I, int k, int h, int rows) {
-  const int nb = I.nb, ib = I.ib, cs = I.cs, nv = rows * nb;
+  const int nb = I.nb, ib = I.ib, cs = I.cs, nv = (rows - 1) * nb + live_rows(I, h + rows - 1);
   real* Rt = tile_ptr<real>(I, k, k);
   real* Tg = t_ptr<real>(I, h, k);
   double* taus = cx.red + 2 * kThreads;
@@ -1248,7 +1260,7 @@ __device__ void exec_tsqrt2(Ctx<real>& cx, const Inst& I, int k, int h, int rows
 // transformations of TSQRT2(k, h, rows) (Q^T if trans, else Q).
 template <typename real>
 __device__ void exec_ssrfb2(Ctx<real>& cx, const Inst& I, int k, int h, int rows, int j, int s, bool trans) {
-  const int nb = I.nb, ib = I.ib, nv = rows * nb;
+  const int nb = I.nb, ib = I.ib, nv = (rows - 1) * nb + live_rows(I, h + rows - 1);
   const real* Tg = t_ptr<real>(I, h, k);
   const long long soff = static_cast<long long>(s) * I.cs * nb;
   real* Ct = tile_ptr<real>(I, k, j) + soff;
@@ -2014,6 +2026,32 @@ __global__ void identity_kernel(int m, int ncols, D* __restrict__ Ab, int p, int
 }
 
 __global__ void status_reset_kernel() { g_status = 0; }
+
+// A launch's error record into out[0..7] (code, where, and the failing
+// task's kind, k, i, j, s, l) unless out[0] already holds one.  Runs after
+// the launch on its stream, so the record belongs to that launch alone
+// (g_status is shared by every launch on the device).
+__global__ void fold_error_kernel(const Ctl* ctl, const TaskX* tasks, int ntasks, double* out) {
+  const int e = ctl->error;
+  if (e == 0 || out[0] != 0.0) return;
+  out[0] = e;
+  out[1] = ctl->err_where;
+  const int t = ctl->err_task;
+  if (t >= 0 && t < ntasks) {
+    const TaskX x = tasks[t];
+    out[2] = x.kind;
+    out[3] = x.k;
+    out[4] = x.i;
+    out[5] = x.j;
+    out[6] = x.s;
+    out[7] = x.l;
+  }
+}
+
+cudaError_t launch_fold_error(const void* ctl, const TaskX* tasks, int ntasks, double* out, cudaStream_t st) {
+  fold_error_kernel<<<1, 1, 0, st>>>(static_cast<const Ctl*>(ctl), tasks, ntasks, out);
+  return cudaGetLastError();
+}
 
 cudaError_t set_trace(void* buffer, long long capacity) {
   unsigned long long* b = static_cast<unsigned long long*>(buffer);

@@ -46,6 +46,11 @@ cudaError_t launch_unpack_batched(const PackDesc* d, int count, cudaStream_t st)
 
 // Copies the sticky device status to *status (synchronizing st) and clears it.
 cudaError_t read_status(int* status, cudaStream_t st);
+// After a task-kernel launch on st: its error record (control block `ctl`)
+// into out[0..7] = code, where (1 dependency wait, 2 bulk-copy wait, 3 task
+// kind), failing task's kind, k, i, j, s, l -- unless out[0] is already
+// nonzero.  out must start zeroed.
+cudaError_t launch_fold_error(const void* ctl, const TaskX* tasks, int ntasks, double* out, cudaStream_t st);
 size_t ctl_bytes();
 // FP64 FMA throughput probe (TFLOP/s).
 cudaError_t fp64_peak(double* tflops, cudaStream_t st);

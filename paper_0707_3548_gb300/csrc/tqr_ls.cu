@@ -407,7 +407,7 @@ bool LsJob::init(int m_, int n_, int rhs_cap_, int nb_, int ib_, int prec_, int 
   o_h = o;     o += al(sizeof(double) * nr);
   o_x = o;     o += al(sizeof(double) * nr);
   o_G = o;     o += al(sizeof(double) * nr);
-  o_nrm = o;   o += al(sizeof(double) * (4 * rhs_cap + 4));
+  o_nrm = o;   o += al(sizeof(double) * (4 * rhs_cap + 12));
   o_b2 = o;    o += al(W.oT - W.oB);                       // as large as the first tile array
   o_ver2 = o;  o += al(sizeof(int) * static_cast<size_t>(I.p) * (I.q + I.qb) * I.NS);
   o_inst2 = o; o += al(2 * sizeof(Inst));
@@ -419,6 +419,8 @@ bool LsJob::init(int m_, int n_, int rhs_cap_, int nb_, int ib_, int prec_, int 
 }
 
 size_t LsJob::bytes_with_acopy() const { return bytes + al(sizeof(double) * static_cast<size_t>(m) * n); }
+
+double* LsJob::err_rec() const { return reinterpret_cast<double*>(ws + o_nrm) + 4 * rhs_cap + 4; }
 
 void LsJob::bind(char* base, bool with_acopy) {
   ws = base;
@@ -435,8 +437,8 @@ int LsJob::run_mode(int mode, int trsm, int nrhs_now, cudaStream_t st) {
   I.trsm = trsm;
   I.nrhs = nrhs_now;
   I.qb = (nrhs_now + nb - 1) / nb;
-  return esize == 8 ? run_plan<double>(I, ws, W, occ, smem, st, grid_cap)
-                    : run_plan<float>(I, ws, W, occ, smem, st, grid_cap);
+  return esize == 8 ? run_plan<double>(I, ws, W, occ, smem, st, grid_cap, err_rec())
+                    : run_plan<float>(I, ws, W, occ, smem, st, grid_cap, err_rec());
 }
 
 int LsJob::pack_rhs(const double* src, long long lds, int rows, int nrhs, cudaStream_t st, void* tiles) {
@@ -471,8 +473,8 @@ int LsJob::run_two(int mode_a, int mode_b, int nrhs_now, cudaStream_t st) {
   two[1].ver = reinterpret_cast<int*>(ws + o_ver2);
   Inst* d_insts = reinterpret_cast<Inst*>(ws + o_inst2);
   void* d_ctl = ws + W.oCtl;
-  return esize == 8 ? run_plan_multi<double>(two, 2, d_insts, d_ctl, occ, smem, st, grid_cap)
-                    : run_plan_multi<float>(two, 2, d_insts, d_ctl, occ, smem, st, grid_cap);
+  return esize == 8 ? run_plan_multi<double>(two, 2, d_insts, d_ctl, occ, smem, st, grid_cap, err_rec())
+                    : run_plan_multi<float>(two, 2, d_insts, d_ctl, occ, smem, st, grid_cap, err_rec());
 }
 
 int LsJob::fast_ok(int nrhs) const { return esize == 4 && trsv_fits(nb, nrhs, 4) ? 1 : 0; }
@@ -518,7 +520,7 @@ int LsJob::form_q1(cudaStream_t st) {
   W2.oInst = vo_inst;
   W2.oCtl = vo_ctl;
   W2.bytes = vbytes;
-  return run_plan<float>(Iq, vws, W2, occ, smem, st, grid_cap);
+  return run_plan<float>(Iq, vws, W2, occ, smem, st, grid_cap, err_rec());
 }
 
 void LsJob::free_q1(cudaStream_t st) {
@@ -587,6 +589,8 @@ int LsJob::factor_solve(const double* A, long long lda, const double* B, long lo
   factored = false;
   double* nrm = reinterpret_cast<double*>(ws + o_nrm);
   double* colnrm = reinterpret_cast<double*>(ws + o_g);
+  std::fill(err_host, err_host + 8, 0.0);
+  if (cudaMemsetAsync(err_rec(), 0, 8 * sizeof(double), st) != cudaSuccess) return TQR_ERR_CUDA;
   if (fro_norm(A, lda, m, n, colnrm, nrm + 4 * rhs_cap, st) != cudaSuccess) return TQR_ERR_CUDA;
   if (esize == 4) {
     double h = 0.0;
@@ -626,6 +630,8 @@ int LsJob::factor_solve(const double* A, long long lda, const double* B, long lo
 
 // x0 from the resident factors: Q^T B and back substitution, one graph
 int LsJob::solve(const double* B, long long ldb, int nrhs, cudaStream_t st) {
+  std::fill(err_host, err_host + 8, 0.0);
+  if (cudaMemsetAsync(err_rec(), 0, 8 * sizeof(double), st) != cudaSuccess) return TQR_ERR_CUDA;
   int s = pack_rhs(B, ldb, m, nrhs, st);
   if (s == TQR_OK) s = run_mode(M_APPLY_QT, 1, nrhs, st);
   if (s == TQR_OK) s = unpack_rhs(reinterpret_cast<double*>(ws + o_x), n, n, nrhs, st);
@@ -647,10 +653,12 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
   bb.G = reinterpret_cast<double*>(ws + o_G);
   bb.nrm = reinterpret_cast<double*>(ws + o_nrm);
   // nrm layout (norms, not squares): [0,R) ||A^T e||, [R,2R) ||x||, [2R,3R) ||b||,
-  // [3R,4R) ||dx||, [4R] ||A||_F, [4R+2], [4R+3] min and max |r_ii|
+  // [3R,4R) ||dx||, [4R] ||A||_F, [4R+1] the triangular-solve kernel's
+  // error, [4R+2], [4R+3] min and max |r_ii|, [4R+4, 4R+12) the task-kernel
+  // launches' error record
   const int R = rhs_cap;
   double* dx2 = bb.nrm + 3 * R;
-  std::vector<double> hn(4 * R + 4);
+  std::vector<double> hn(4 * R + 12);
   int status = TQR_OK;
   int iters = 0, inner = 0, path = esize == 8 ? TQR_LS_PATH_FP64 : TQR_LS_PATH_FP32;
   double berr = INFINITY, gres = 0.0;
@@ -662,6 +670,10 @@ int LsJob::finish(const double* A, long long lda, const double* B, long long ldb
         cudaStreamSynchronize(st) != cudaSuccess)
       fail(TQR_ERR_CUDA);
     if (hn[4 * R + 1] != 0.0) fail(TQR_ERR_TIMEOUT);  // a triangular-solve wait ran out
+    if (hn[4 * R + 4] != 0.0) {                       // a task-kernel wait ran out
+      for (int a = 0; a < 8; ++a) err_host[a] = hn[4 * R + 4 + a];
+      fail(static_cast<int>(hn[4 * R + 4]));
+    }
   };
   // the triangular-solve kernel's error slot starts clear
   if (cudaMemsetAsync(bb.nrm + 4 * R + 1, 0, sizeof(double), st) != cudaSuccess) fail(TQR_ERR_CUDA);

@@ -72,6 +72,11 @@ struct LsJob {
   char* ws = nullptr;
   double* Acopy = nullptr;
   bool factored = false;
+  // the error record of this job's own task-kernel launches (device, 8
+  // doubles after the norms: code, where, task kind, k, i, j, s, l), cleared
+  // by factor_solve and solve and read by finish; err_host is finish's copy
+  double* err_rec() const;
+  double err_host[8] = {};
 
   // sizes for m x n with up to rhs_cap right-hand sides; false if the tile
   // shape is unsupported

@@ -22,7 +22,9 @@
 #include <list>
 #include <map>
 #include <memory>
+#include <cstdio>
 #include <mutex>
+#include <string>
 #include <thread>
 #include <vector>
 
@@ -86,6 +88,7 @@ struct tqr_server {
   std::vector<std::thread> workers;
   std::vector<double> lat_ms;  // completed requests
   int64_t completed = 0, reused = 0, failed = 0;
+  std::string last_failure;    // description of the latest failed request
 };
 
 namespace tqr {
@@ -180,11 +183,27 @@ static void run_request(tqr_server* S, Request& R, cudaStream_t st, std::unique_
   if (status == kLsStalled || status == kLsFp32Range) status = TQR_ERR_NOCONV;
   R.iters = R.info.iters;
   R.berr = R.info.berr;
-  int dev_status = TQR_OK;
-  if (read_status(&dev_status, st) != cudaSuccess && status == TQR_OK) status = TQR_ERR_CUDA;
-  if (dev_status != TQR_OK) status = dev_status;
+  // every launch of the request reported into its job's own error record
+  // (read by finish); the device-wide sticky status is not read here, since
+  // it mixes the concurrent requests' launches
   if (cudaStreamSynchronize(st) != cudaSuccess && status == TQR_OK) status = TQR_ERR_CUDA;
+  std::string why;
+  if (status != TQR_OK) {
+    char msg[256];
+    const double* e = E.job.err_host[0] != 0.0 ? E.job.err_host : E.job64.err_host;
+    int len = std::snprintf(msg, sizeof msg, "request %llu (matrix %llu, %lld x %lld, %lld rhs, %s): status %d",
+                            static_cast<unsigned long long>(R.rid), static_cast<unsigned long long>(R.matrix),
+                            static_cast<long long>(R.m), static_cast<long long>(R.n), static_cast<long long>(R.nrhs),
+                            R.prec == TQR_PREC_FP32 ? "fp32r" : "fp64", status);
+    if (e[0] != 0.0 && len > 0 && len < static_cast<int>(sizeof msg))
+      std::snprintf(msg + len, sizeof msg - len, "; task-kernel %s wait ran out in task kind %d (k %d i %d j %d s %d l %d)",
+                    e[1] == 2.0 ? "bulk-copy" : e[1] == 1.0 ? "dependency" : "other", static_cast<int>(e[2]),
+                    static_cast<int>(e[3]), static_cast<int>(e[4]), static_cast<int>(e[5]), static_cast<int>(e[6]),
+                    static_cast<int>(e[7]));
+    why = msg;
+  }
   lk.lock();
+  if (!why.empty()) S->last_failure = why;
   if (extra) {
     E.bytes += extra;
     S->in_use += extra;
@@ -458,6 +477,14 @@ int tqr_server_stats(tqr_server* S, double* out) {
   out[5] = static_cast<double>(S->failed);
   out[6] = static_cast<double>(S->pending.size());
   out[7] = static_cast<double>(S->cache.size());
+  return TQR_OK;
+}
+
+int tqr_debug_server_last_failure(tqr_server* S, char* buf, size_t len) {
+  if (S == nullptr) return -1;
+  if (buf == nullptr || len == 0) return -2;
+  std::lock_guard<std::mutex> lk(S->mu);
+  std::snprintf(buf, len, "%s", S->last_failure.c_str());
   return TQR_OK;
 }
 

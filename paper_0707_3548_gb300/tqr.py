@@ -138,6 +138,7 @@ SIGNATURES = {
     "tqr_debug_trace": (_int, [_vp, _i64]),
     "tqr_debug_set_shape": (_int, [_int, _int]),
     "tqr_debug_last_error": (ctypes.c_char_p, []),
+    "tqr_debug_server_last_failure": (_int, [_vp, ctypes.c_char_p, ctypes.c_size_t]),
 }
 
 
@@ -746,6 +747,12 @@ class Server:
         _check("tqr_server_stats", lib().tqr_server_stats(self.h, out.ctypes.data))
         keys = ("completed", "p50_ms", "p99_ms", "bytes_in_use", "reused", "failed", "queued", "resident")
         return dict(zip(keys, out.tolist()))
+
+    def last_failure(self):
+        """Description of the latest failed request ("" if none)."""
+        buf = ctypes.create_string_buffer(512)
+        _check("tqr_debug_server_last_failure", lib().tqr_debug_server_last_failure(self.h, buf, len(buf)))
+        return buf.value.decode()
 
     def close(self):
         if self.h:
