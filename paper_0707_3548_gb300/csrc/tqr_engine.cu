@@ -591,6 +591,24 @@ __device__ __forceinline__ Refl make_refl(double alpha, double xm, bool squared)
     f.tau = 0.0;
     f.beta = alpha;
     f.scal = 0.0;
+  } else if (squared && sizeof(real) == 4 && xm >= 0x1p-20 * (alpha * alpha)) {
+    // FP32 panels: with a = |alpha|, s = a^2 + xm and h = sqrt(s),
+    //   beta = -sign(alpha) h,  tau = 1 + a / h,  1/d = sign(alpha) (h - a) / xm,
+    // so the two long FP64 operations, 1/sqrt(s) and 1/xm, run side by side
+    // instead of a square root followed by a division (each costs hundreds of
+    // cycles on the panel's serial column chain).  h - a loses at most
+    // log2(4 a^2 / xm) <= 22 bits to cancellation, leaving 1/d far more
+    // accurate than the FP32 value it is rounded to; smaller xm takes the
+    // general formula below.
+    const double a = fabs(alpha);
+    const double sv = fma(a, a, xm);
+    const double r = rsqrt(sv);
+    const double q = 1.0 / xm;
+    const double h = sv * r;
+    f.beta = (alpha >= 0.0) ? -h : h;  // sign(0) = +1, also for -0.0
+    f.tau = fma(a, r, 1.0);
+    const double sc = (h - a) * q;
+    f.scal = (alpha >= 0.0) ? sc : -sc;
   } else if (squared) {
     const double h = sqrt(fma(alpha, alpha, xm));
     f.beta = (alpha >= 0.0) ? -h : h;  // sign(0) = +1, also for -0.0
@@ -610,11 +628,11 @@ __device__ __forceinline__ Refl make_refl(double alpha, double xm, bool squared)
 template <typename real, bool TS>
 __device__ __forceinline__ void publish_refl(double* red, int c, double alpha, double xn, bool squared) {
   const Refl f = make_refl<real>(alpha, xn, squared);
-  double* d = red + 4 * (c & 1);
+  double* d = red + 4 * (c % 3);
   d[0] = f.tau;
   d[1] = f.beta;
   d[2] = f.scal;
-  real* r = reinterpret_cast<real*>(red + 8) + 2 * (c & 1);
+  real* r = reinterpret_cast<real*>(red + 12) + 2 * (c % 3);
   r[0] = static_cast<real>(f.tau);
   r[1] = static_cast<real>(f.scal);
 }
@@ -662,9 +680,10 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
   }
   __syncthreads();
   for (int c = 0; c <= ib; ++c) {
-    // deferred writes of column c-1
-    if (wid == 0 && c > 0) {
-      const double* pf = red + 4 * ((c - 1) & 1);
+    // deferred writes of column c-1 (by the last warp: warp 0 carries the
+    // column chain)
+    if (wid == nwarps - 1 && c > 0) {
+      const double* pf = red + 4 * ((c - 1) % 3);
       real* pp = P + (c - 1) * ldP;
       const int r0p = TS ? 0 : c;
       const real sp = static_cast<real>(pf[2]);
@@ -680,10 +699,13 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
     if (c == ib) break;
     real* pc = P + c * ldP;
     const int r0 = TS ? 0 : c + 1;
-    const real* rf = reinterpret_cast<const real*>(red + 8) + 2 * (c & 1);
+    const real* rf = reinterpret_cast<const real*>(red + 12) + 2 * (c % 3);
     const real tau = rf[0];
     const real scal = rf[1];
-    for (int d = c + 1 + wid; d < ib; d += nwarps) {
+    // warp 0 updates column c + 1 and derives its reflector (the serial
+    // chain); warps 1 .. nwarps-1 update columns c + 2 .. ib-1 meanwhile
+    for (int d = wid == 0 ? c + 1 : c + 1 + wid; d < ib && (wid != 0 || d == c + 1);
+         d += (wid == 0 ? 1 : nwarps - 1)) {
       real* pd = P + d * ldP;
       if (tau != real(0)) {
         real acc = real(0);
