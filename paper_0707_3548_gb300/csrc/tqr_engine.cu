@@ -749,8 +749,7 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
 
 // Compact-WY T of the panel's reflectors (DLARFT, forward, columnwise):
 //   T(c,c) = tau_c,  T(0:c, c) = -tau_c T(0:c, 0:c) (V(:,0:c)^T v_c).
-// The Gram products Y(a,b) = v_a^T v_b (a < b) go to Y (ib x ib, ld ib); the
-// recurrence runs one row of T per lane (rows are independent).
+// The Gram products Y(a,b) = v_a^T v_b (a < b) go to Y (ib x ib, ld ib).
 template <typename real, bool TS>
 __device__ void form_t(const real* P, int ldP, int nr, int ib, const double* taus, real* Y, real* Tm,
                        int ldT) {
@@ -771,25 +770,39 @@ __device__ void form_t(const real* P, int ldP, int nr, int ib, const double* tau
     }
     Y[a + b * ib] = acc;
   }
-  __syncthreads();
-  if (tid < 32) {
-    for (int r = tid; r < ib; r += 32) {
-      for (int c = 0; c < ib; ++c) {
-        real v;
-        if (c < r) {
-          v = real(0);
-        } else if (c == r) {
-          v = static_cast<real>(taus[c]);
-        } else {
-          real acc = real(0);
-          for (int s = r; s < c; ++s) acc += Tm[r + s * ldT] * Y[s + c * ib];
-          v = -static_cast<real>(taus[c]) * acc;
-        }
-        Tm[r + c * ldT] = v;
-      }
-    }
+  // T by doubling diagonal blocks: with Q1 = I - V1 T11 V1^T and
+  // Q2 = I - V2 T22 V2^T, Q1 Q2 = I - V T V^T with T12 = -T11 (V1^T V2) T22.
+  // Blocks of size bs already hold their T; each level merges neighbours
+  // (block 2 may be short when ib is not a power of two), so the dependent
+  // chain is 2 (1 + 2 + 4 + ...) multiply-adds and one barrier pair per level
+  // instead of the column recurrence's ib (ib - 1) / 2 on one warp.
+  // W = Y12 T22 is kept in Y's unused lower triangle (W(a, b) at Y[b + a ib]).
+  for (int e = tid; e < ib * ib; e += kThreads) {
+    const int r = e % ib, c = e / ib;
+    Tm[r + c * ldT] = r == c ? static_cast<real>(taus[c]) : real(0);
   }
   __syncthreads();
+  for (int bs = 1; bs < ib; bs *= 2) {
+    const int span = (ib + 2 * bs - 1) / (2 * bs) * bs * bs;
+    for (int e = tid; e < span; e += kThreads) {
+      const int g0 = 2 * bs * (e / (bs * bs)), rem = e % (bs * bs);
+      const int a = g0 + rem % bs, b = g0 + bs + rem / bs;
+      if (b >= ib) continue;
+      real acc = real(0);
+      for (int t = g0 + bs; t <= b; ++t) acc = fma(Y[a + t * ib], Tm[t + b * ldT], acc);
+      Y[b + a * ib] = acc;
+    }
+    __syncthreads();
+    for (int e = tid; e < span; e += kThreads) {
+      const int g0 = 2 * bs * (e / (bs * bs)), rem = e % (bs * bs);
+      const int a = g0 + rem % bs, b = g0 + bs + rem / bs;
+      if (b >= ib) continue;
+      real acc = real(0);
+      for (int t = a; t < g0 + bs; ++t) acc = fma(Tm[a + t * ldT], Y[b + t * ib], acc);
+      Tm[a + b * ldT] = -acc;
+    }
+    __syncthreads();
+  }
 }
 
 // ---------------------------------------------------------------- tasks
