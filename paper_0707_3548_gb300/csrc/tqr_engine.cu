@@ -672,6 +672,26 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
     const double amax = __longlong_as_double(static_cast<long long>(s_amax));
     extreme = amax > 0x1p480 || (amax != 0.0 && amax < 0x1p-480);
   }
+  // FP32 panels keep each column's FP64 sum of squares of the rows the next
+  // reflectors see (TS: all rows of the bottom block; else the rows from the
+  // current step down) and downdate it as reflectors are applied: an
+  // orthogonal reflector keeps top^2 + ||x||^2, so the next column's
+  // measure costs two FMAs on the chain instead of a warp reduction.  Where
+  // more than 16 bits of a sum have cancelled since it was last formed
+  // directly, it is formed directly again (its error then stays far below
+  // FP32's unit roundoff, which bounds the reflectors' stored precision).
+  double* s2 = red + 32;       // running sums, ib <= 64
+  double* s2ref = red + 96;    // the sums when last formed directly
+  if constexpr (sizeof(real) == 4) {
+    for (int d = wid; d < ib; d += nwarps) {
+      bool sq;
+      const double v = warp_norm<real>(P + d * ldP, nr, false, &sq);
+      if (lane == 0) {
+        s2[d] = v;
+        s2ref[d] = v;
+      }
+    }
+  }
   // reflector of column 0
   if (wid == 0) {
     bool sq;
@@ -707,6 +727,7 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
     for (int d = wid == 0 ? c + 1 : c + 1 + wid; d < ib && (wid != 0 || d == c + 1);
          d += (wid == 0 ? 1 : nwarps - 1)) {
       real* pd = P + d * ldP;
+      real top_old = real(0), top_new = real(0);
       if (tau != real(0)) {
         real acc = real(0);
         if (!extreme) {
@@ -723,19 +744,51 @@ __device__ void panel_qr(real* P, int ldP, int nr, int ib, real* R, int ldr, dou
         const real wv = extreme ? tau * (acc + top) : tau * fma(scal, acc, top);
         const real coef = -(wv * scal);
         for (int r = r0 + lane; r < nr; r += 32) pd[r] = fma(coef, pc[r], pd[r]);
+        top_old = top;
+        top_new = top - wv;
         if (lane == 0) {
           if constexpr (TS)
-            R[c + d * ldr] = top - wv;
+            R[c + d * ldr] = top_new;
           else
-            pd[c] = top - wv;
+            pd[c] = top_new;
+        }
+      } else if (!TS) {
+        top_new = pd[c];
+      }
+      if constexpr (sizeof(real) == 4) {
+        // TS: ||x||^2 += top_old^2 - top_new^2; else the sum drops row c
+        if (lane == 0) {
+          const double to = top_old, tn = top_new;
+          s2[d] = TS ? fma(-tn, tn, fma(to, to, s2[d])) : fma(-tn, tn, s2[d]);
         }
       }
       if (d == c + 1) {
         // this warp owns the next column: its reflector, for step c + 1
         __syncwarp();
-        bool sq;
-        const double xn = TS ? warp_norm<real>(pd, nr, extreme, &sq)
-                             : warp_norm<real>(pd + c + 2, nr - c - 2, extreme, &sq);
+        bool sq = true;
+        double xn = 0.0;
+        bool direct = true;
+        if constexpr (sizeof(real) == 4) {
+          double xm = 0.0;
+          if (lane == 0) {
+            const double al = static_cast<double>(TS ? R[(c + 1) + (c + 1) * ldr] : pd[c + 1]);
+            xm = TS ? s2[d] : fma(-al, al, s2[d]);
+          }
+          xm = __shfl_sync(0xffffffffu, xm, 0);
+          direct = !(xm >= 0x1p-16 * s2ref[d]);
+          xn = xm;
+        }
+        if (direct) {
+          xn = TS ? warp_norm<real>(pd, nr, extreme, &sq) : warp_norm<real>(pd + c + 2, nr - c - 2, extreme, &sq);
+          if constexpr (sizeof(real) == 4) {
+            // the sums restart from the direct value
+            if (lane == 0) {
+              const double al = static_cast<double>(TS ? R[(c + 1) + (c + 1) * ldr] : pd[c + 1]);
+              s2[d] = TS ? xn : fma(al, al, xn);
+              s2ref[d] = s2[d];
+            }
+          }
+        }
         if (lane == 0) {
           const double alpha = static_cast<double>(TS ? R[(c + 1) + (c + 1) * ldr] : pd[c + 1]);
           publish_refl<real, TS>(red, c + 1, alpha, xn, sq);

@@ -63,6 +63,36 @@ def test_solve_fp32_refined_reaches_fp64_accuracy(kappa):
     assert LS.backward_error(A, to_host(X)[:, 0], b) <= 1e-12
 
 
+
+@pytest.mark.parametrize("case", ["dominant_top", "graded_columns", "gaussian"])
+def test_fp32_factor_is_accurate_at_fp32_level(case):
+    """The FP32 factorization alone (no refinement) must solve to a backward
+    error of a modest multiple of the FP32 unit roundoff, also where the
+    panel's running column sums cancel heavily: a matrix whose top block
+    dominates the rows below it (each reflector then takes almost all of its
+    column) and one whose columns span twelve orders of magnitude."""
+    torch_cuda()
+    g = np.random.default_rng(7)
+    m, n = 1200, 300
+    if case == "dominant_top":
+        A = np.zeros((m, n))
+        A[:n] = np.triu(g.standard_normal((n, n))) + 50.0 * np.eye(n)
+        A[n:] = 1e-4 * g.standard_normal((m - n, n))
+    elif case == "graded_columns":
+        A = g.standard_normal((m, n)) * np.logspace(-6, 6, n)[None, :]
+    else:
+        A = g.standard_normal((m, n))
+    A = np.asfortranarray(A)
+    b = A @ g.standard_normal(n) + 1e-3 * g.standard_normal(m)
+    X, it, berr, rc = tqr.tqr_solve_ls(to_dev(A), to_dev(b[:, None]), prec=tqr.TQR_PREC_FP32, tol=1e-12,
+                                       maxit=0, nb=64, ib=16, check=False)
+    assert it == 0
+    eta = LS.backward_error(A, to_host(X)[:, 0], b)
+    assert eta <= 50 * n * 2.0 ** -24, eta
+    X2, it2, berr2, rc2 = tqr.tqr_solve_ls(to_dev(A), to_dev(b[:, None]), prec=tqr.TQR_PREC_FP32, tol=1e-12,
+                                          maxit=40, nb=64, ib=16, check=False)
+    assert rc2 == tqr.TQR_OK and LS.backward_error(A, to_host(X2)[:, 0], b) <= 1e-12
+
 def test_solve_host_buffers():
     torch_cuda()
     A = inputs.normal_matrix(300, 100, 3)
