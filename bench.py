@@ -899,17 +899,21 @@ def run_batch(args, w):
         for a, b in zip(work, pristine):
             a.copy_(b)
 
-    def timed(tl, clk_sampler):
+    # 2b x b bottoms by default (as the single-matrix headline); --variant flat
+    # gives Algorithm 1's b x b tiles
+    pairs = args.variant != "flat"
+
+    def timed(tl, clk_sampler, pairs=pairs):
         Ts = [torch.zeros(tqr.tqr_t_size(m, n, nb, ib) // 8, dtype=torch.float64, device=dev)
               for (m, n), (nb, ib) in zip(shapes, tl)]
         t_plan = time.perf_counter()
         restore()
-        rc, st = tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tl), len(shapes))
+        rc, st = tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tl, pairs=pairs), len(shapes))
         t_plan = time.perf_counter() - t_plan
         assert rc == 0
         for _ in range(args.warmup - 1):
             restore()
-            tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tl), len(shapes))
+            tqr.tqr_batch_wait(tqr.tqr_batch_submit(work, Ts, tl, pairs=pairs), len(shapes))
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
@@ -921,7 +925,7 @@ def run_batch(args, w):
                 e0 = torch.cuda.Event(enable_timing=True)
                 e1 = torch.cuda.Event(enable_timing=True)
                 e0.record(stream)
-                t = tqr.tqr_batch_submit(work, Ts, tl)
+                t = tqr.tqr_batch_submit(work, Ts, tl, pairs=pairs)
                 e1.record(stream)
                 rc, st = tqr.tqr_batch_wait(t, len(shapes))
                 torch.cuda.synchronize()
@@ -934,6 +938,7 @@ def run_batch(args, w):
     rule_sec = None
     if rule_tiles is not None and rule_tiles != tiles:
         rule_sec, _, _ = timed(rule_tiles, ClockSampler(None))
+    bxb_sec = timed(tiles, ClockSampler(None), pairs=False)[0] if pairs else None
     sec, t_plan, clk = timed(tiles, ClockSampler(bus))
     if rank != 0:
         dist.destroy_process_group()
@@ -957,10 +962,12 @@ def run_batch(args, w):
                        "parallelism": ("instances sharded over %d ranks by flops (greedy), no collective" % world)
                                       if world > 1 else "single GPU",
                        "tile_classes_rank0": classes,
+                       "variant": "2b x b bottoms (tqr_batch_submit_pairs)" if pairs else "b x b tiles",
                        "autotune": "measured per size class and per batch policy (tqr_autotune_batch), %.1f s"
                                    % tune_s
                                    if rule_tiles is not None else "fixed by --nb/--ib"},
             "rule_tiles_value": flops / rule_sec / 1e12 if rule_sec else None,
+            "bxb_tiles_value": flops / bxb_sec / 1e12 if bxb_sec else None,
             "first_submit_s_incl_plan": t_plan, "gpu_launches": 3 * args.steps, "cpu_baseline": cpu,
             "clocks": clk.summary()}
     print(json.dumps(line), flush=True)

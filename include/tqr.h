@@ -465,6 +465,16 @@ int tqr_autotune_batch(int count, const int64_t* ms, const int64_t* ns, void* st
 int tqr_batch_submit(int count, const tqr_desc* descs, uint64_t* ticket, void* stream);
 
 /*
+ * tqr_batch_submit with 2b x b bottoms (the paper's non-square blocks, as
+ * tqr_factor_pairs): every matrix is factored with its tile rows below the
+ * diagonal taken in pairs.  Arguments, asynchrony, tickets and errors as
+ * tqr_batch_submit; results (A and the T layout) are identical to
+ * tqr_factor_pairs of each matrix alone with the same nb, ib, so Q is
+ * applied with tqr_apply_qt_pairs.
+ */
+int tqr_batch_submit_pairs(int count, const tqr_desc* descs, uint64_t* ticket, void* stream);
+
+/*
  * Non-blocking completion check.  *done = 1 when the batch has finished;
  * then status_per_item (may be NULL, else `count` ints) receives each
  * matrix's status and the ticket is consumed.  Returns the batch status

@@ -52,6 +52,7 @@ struct BatchPlan {
   std::vector<std::tuple<int64_t, int64_t, int, int>> shape;  // (m, n, nb, ib) per item
   int count = 0;
   int device = -1;
+  int pair = 0;                // 2b x b bottoms (tqr_batch_submit_pairs)
   int smem = 0, grid = 0, ntasks = 0;
   PlanStats stats;
   char* ws = nullptr;          // tiles + counters + control, device
@@ -93,10 +94,11 @@ static uint64_t g_next_ticket = 1;
 
 static size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
 
-static int build_batch_plan(const std::vector<std::tuple<int64_t, int64_t, int, int>>& shape,
+static int build_batch_plan(const std::vector<std::tuple<int64_t, int64_t, int, int>>& shape, int pair,
                             std::shared_ptr<BatchPlan>* out) {
   auto P = std::make_shared<BatchPlan>();
   P->shape = shape;
+  P->pair = pair;
   P->count = static_cast<int>(shape.size());
   cudaGetDevice(&P->device);
   std::vector<Inst> insts(shape.size());
@@ -108,10 +110,11 @@ static int build_batch_plan(const std::vector<std::tuple<int64_t, int64_t, int, 
     const int64_t m = std::get<0>(shape[a]), n = std::get<1>(shape[a]);
     const int nb = std::get<2>(shape[a]), ib = std::get<3>(shape[a]);
     int cs, occ, smem;
-    if (!choose_shape(nb, ib, 8, &cs, &occ, &smem)) return TQR_ERR_UNSUPPORTED;
+    if (!choose_shape(nb, ib, 8, &cs, &occ, &smem, pair ? 2 * nb : 0)) return TQR_ERR_UNSUPPORTED;
     max_smem = std::max(max_smem, smem);
     min_occ = std::min(min_occ, occ);
     insts[a] = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
+    insts[a].pair = pair;
     P->tile_off[a] = off;
     off += al256(sizeof(double) * static_cast<size_t>(insts[a].p) * insts[a].q * nb * nb);
   }
@@ -183,7 +186,7 @@ static int build_batch_plan(const std::vector<std::tuple<int64_t, int64_t, int, 
         cudaMemsetAsync(P->ws + P->ver_off, 0, P->ver_bytes, cap) != cudaSuccess ||
         launch_pack_batched<double>(P->d_pack, P->count, cap) != cudaSuccess ||
         (P->ntasks > 0 && launch_run<double>(P->d_tasks, P->ntasks, P->d_insts, P->ws + P->ctl_off, wait_limit_ns(),
-                                             P->grid, P->smem, cap) != cudaSuccess) ||
+                                             P->grid, P->smem, cap, P->pair ? 2 : 0) != cudaSuccess) ||
         launch_unpack_batched<double>(P->d_pack, P->count, cap) != cudaSuccess ||
         cudaMemcpyAsync(P->h_status, P->ws + P->ctl_off, sizeof(int) * 4, cudaMemcpyDeviceToHost, cap) !=
             cudaSuccess)
@@ -215,7 +218,7 @@ int tqr_autotune(int64_t m, int64_t n, int* nb, int* ib) {
   return TQR_OK;
 }
 
-int tqr_batch_submit(int count, const tqr_desc* d, uint64_t* ticket, void* stream) {
+static int batch_submit(int count, const tqr_desc* d, int pair, uint64_t* ticket, void* stream) {
   if (count < 1) return -1;
   if (d == nullptr) return -2;
   if (ticket == nullptr) return -3;
@@ -236,14 +239,14 @@ int tqr_batch_submit(int count, const tqr_desc* d, uint64_t* ticket, void* strea
   cudaGetDevice(&dev);
   std::shared_ptr<BatchPlan> P;
   for (size_t a = 0; a < g_bplans.size(); ++a)
-    if (g_bplans[a]->device == dev && g_bplans[a]->shape == shape) {
+    if (g_bplans[a]->device == dev && g_bplans[a]->pair == pair && g_bplans[a]->shape == shape) {
       P = g_bplans[a];
       g_bplans.erase(g_bplans.begin() + a);
       g_bplans.insert(g_bplans.begin(), P);
       break;
     }
   if (!P) {
-    const int s = build_batch_plan(shape, &P);
+    const int s = build_batch_plan(shape, pair, &P);
     if (s != TQR_OK) return s;
     g_bplans.insert(g_bplans.begin(), P);
     while (g_bplans.size() > kMaxBatchPlans) g_bplans.pop_back();
@@ -267,6 +270,14 @@ int tqr_batch_submit(int count, const tqr_desc* d, uint64_t* ticket, void* strea
   g_tickets[t] = Ticket{P, count, false, TQR_OK};
   *ticket = t;
   return TQR_OK;
+}
+
+int tqr_batch_submit(int count, const tqr_desc* d, uint64_t* ticket, void* stream) {
+  return batch_submit(count, d, 0, ticket, stream);
+}
+
+int tqr_batch_submit_pairs(int count, const tqr_desc* d, uint64_t* ticket, void* stream) {
+  return batch_submit(count, d, 1, ticket, stream);
 }
 
 static int poll_locked(uint64_t ticket, bool wait, int* done, int* status_per_item) {

@@ -109,6 +109,7 @@ SIGNATURES = {
     "tqr_server_stats": (_int, [_vp, _vp]),
     "tqr_server_destroy": (_int, [_vp]),
     "tqr_batch_submit": (_int, [_int, _vp, ctypes.POINTER(ctypes.c_uint64), _vp]),
+    "tqr_batch_submit_pairs": (_int, [_int, _vp, ctypes.POINTER(ctypes.c_uint64), _vp]),
     "tqr_batch_poll": (_int, [ctypes.c_uint64, ctypes.POINTER(_int), _vp]),
     "tqr_batch_wait": (_int, [ctypes.c_uint64, _vp]),
     "tqr_t_size_tree": (_size, [_i64, _i64, _int, _int]),
@@ -416,10 +417,10 @@ def tqr_debug_autotune_put(m, n, nb, ib, us=1.0):
     _check("tqr_debug_autotune_put", lib().tqr_debug_autotune_put(m, n, nb, ib, us))
 
 
-def tqr_batch_submit(mats, Ts, tiles=None, stream=None):
+def tqr_batch_submit(mats, Ts, tiles=None, stream=None, pairs=False):
     """Submit column-major CUDA float64 matrices (factored in place) with T
-    buffers; tiles: list of (nb, ib) or None for the autotuner.  Returns the
-    ticket."""
+    buffers; tiles: list of (nb, ib) or None for the autotuner; pairs: 2b x b
+    bottoms (tqr_batch_submit_pairs).  Returns the ticket."""
     n = len(mats)
     descs = (TqrDesc * n)()
     for a, (A, T) in enumerate(zip(mats, Ts)):
@@ -427,8 +428,8 @@ def tqr_batch_submit(mats, Ts, tiles=None, stream=None):
         nb, ib = tiles[a] if tiles is not None else (0, 0)
         descs[a] = TqrDesc(m, nn, pa, lda, _ptr(T), nb, ib)
     ticket = ctypes.c_uint64(0)
-    _check("tqr_batch_submit", lib().tqr_batch_submit(n, ctypes.cast(descs, _vp), ctypes.byref(ticket),
-                                                       _stream(True, stream)))
+    fn = "tqr_batch_submit_pairs" if pairs else "tqr_batch_submit"
+    _check(fn, getattr(lib(), fn)(n, ctypes.cast(descs, _vp), ctypes.byref(ticket), _stream(True, stream)))
     return ticket.value
 
 

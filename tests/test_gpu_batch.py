@@ -44,6 +44,30 @@ def test_batch_equals_factoring_each_alone():
         assert np.max(np.abs(to_host(dA) - f.F)) <= 1e-11 * max(1.0, np.abs(f.F).max())
 
 
+
+def test_pairs_batch_equals_factor_pairs_alone():
+    """tqr_batch_submit_pairs: every matrix as tqr_factor_pairs alone (same
+    bits, A and T), ragged shapes with odd and even tile-row counts, plus a
+    few against the 2b x b oracle."""
+    torch = torch_cuda()
+    shapes = inputs.batch_shapes(30, seed=5, m_lo=16, m_hi=900, n_lo=4)
+    mats = inputs.batch_matrices(shapes, seed=5)
+    tiles = [tqr.tqr_autotune(m, n) for m, n in shapes]
+    dev = [to_dev(A) for A in mats]
+    Ts = [torch.zeros(tqr.tqr_t_size(m, n, nb, ib) // 8, dtype=torch.float64, device="cuda")
+          for (m, n), (nb, ib) in zip(shapes, tiles)]
+    t = tqr.tqr_batch_submit(dev, Ts, tiles, pairs=True)
+    rc, st = tqr.tqr_batch_wait(t, len(mats))
+    assert rc == 0 and not st.any()
+    for A, dA, T, (nb, ib) in zip(mats, dev, Ts, tiles):
+        dB = to_dev(A)
+        Tr = tqr.tqr_factor_pairs(dB, nb, ib)
+        assert np.array_equal(to_host(dA), to_host(dB))
+        assert np.array_equal(T.cpu().numpy(), Tr.cpu().numpy())
+    for A, dA, (nb, ib) in list(zip(mats, dev, tiles))[:4]:
+        f = TL.tiled_qr_pairs(A, nb, ib)
+        assert np.max(np.abs(to_host(dA) - f.F)) <= 1e-11 * max(1.0, np.abs(f.F).max())
+
 def test_batch_graph_replay_with_new_data_and_poll():
     torch = torch_cuda()
     shapes = [(200, 120), (64, 64), (333, 17), (90, 90)]
