@@ -328,12 +328,16 @@ bool build_dag(const std::vector<Inst>& insts, const std::vector<TaskX>& seq, st
 // trace at nb = 128, ib = 16: update tasks run at ~60 GFLOP/s per CTA (two
 // per SM) after ~10 us of fixed cost (staging, descriptor, dependency
 // handshake), panels ~3.5 us per column.  Panels pay a per-column latency
-// (reductions and barriers).
+// (reductions and barriers): FP64 6.5 us, the device trace's TSQRT time per
+// column at nb = 128 (its FP64 chain shares the pipe with the co-resident
+// CTA's updates); against the earlier 2 us it orders panels earlier, which
+// measured +7 % at 4096^2, +2 % at 8192^2 and -1.7 % time for the FP64 least
+// squares at 16384 x 4096 (-1.5 % at 2048^2 with nb = 32, the rest unchanged).
 double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
   const double sm_rate = esize == 8 ? 1.19e12 / 152.0 : 2 * 60.0e9;
   const double rate = sm_rate / (ctas_per_sm > 0 ? ctas_per_sm : 1);
   const double nb = I.nb, ib = I.ib;
-  const double col_lat = esize == 8 ? 2.0e-6 : 3.5e-6, blk_lat = 1.0e-6;
+  const double col_lat = esize == 8 ? 6.5e-6 : 3.5e-6, blk_lat = 1.0e-6;
   const double fixed = esize == 8 ? 0.0 : 10.0e-6;
   double w = I.cs;
   if (t.j >= I.q) {
