@@ -261,6 +261,11 @@ static void worker(tqr_server* S) {
         (*it)->status = code;
         (*it)->t_start = (*it)->t_end = Clock::now();
         (*it)->done = true;
+        char msg[160];
+        std::snprintf(msg, sizeof msg, "request %llu (matrix %llu, %lld x %lld): refused at admission, status %d",
+                      static_cast<unsigned long long>((*it)->rid), static_cast<unsigned long long>((*it)->matrix),
+                      static_cast<long long>((*it)->m), static_cast<long long>((*it)->n), code);
+        S->last_failure = msg;
         S->completed++;
         S->failed++;
         S->pending.erase(it);

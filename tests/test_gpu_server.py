@@ -107,6 +107,8 @@ def test_request_larger_than_the_budget_is_refused():
             info = s.poll(rid)
             time.sleep(0.01)
         assert info is not None and info["status"] == tqr.TQR_ERR_NOMEM
+        why = s.last_failure()
+        assert "3000 x 1000" in why and "status %d" % tqr.TQR_ERR_NOMEM in why, why
         A = inputs.normal_matrix(300, 100, 92)
         B = inputs.normal_matrix(300, 2, 93)
         X = tqr.colmajor(torch.zeros((100, 2), dtype=torch.float64, device="cuda"))
