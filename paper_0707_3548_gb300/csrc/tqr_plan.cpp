@@ -338,6 +338,9 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
   const double rate = sm_rate / (ctas_per_sm > 0 ? ctas_per_sm : 1);
   const double nb = I.nb, ib = I.ib;
   const double col_lat = esize == 8 ? 6.5e-6 : 3.5e-6, blk_lat = 1.0e-6;
+  // LU panel columns (argmax, interchange, scale: no norm or reflector)
+  // keep the earlier 2 us calibration
+  const double lu_col = esize == 8 ? 2.0e-6 : 3.5e-6;
   const double fixed = esize == 8 ? 0.0 : 10.0e-6;
   double w = I.cs;
   if (t.j >= I.q) {
@@ -357,7 +360,7 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
       break;
     case K_TSTRF2:
       f = t.l * nb * nb * nb;
-      lat = 2.0 * nb * col_lat;
+      lat = 2.0 * nb * lu_col;
       break;
     case K_SSSSM2:
       f = (nb / ib) * (2.0 * t.l * nb * ib * w + ib * ib * w);
@@ -365,11 +368,11 @@ double task_cost(const Inst& I, const TaskX& t, int esize, int ctas_per_sm) {
       break;
     case K_GETRF:
       f = 2.0 * nb * nb * nb / 3.0;
-      lat = 2.0 * nb * col_lat;
+      lat = 2.0 * nb * lu_col;
       break;
     case K_TSTRF:
       f = nb * nb * nb;
-      lat = 2.0 * nb * col_lat;
+      lat = 2.0 * nb * lu_col;
       break;
     case K_GESSM:
       f = nb * nb * w;
