@@ -1063,7 +1063,8 @@ def run_serve(args, w):
     span = max_over_ranks(t1 - t0, dist, dev)
     if dist is not None:
         # per-request records (latency, status, class, backward error) to rank 0
-        recs = [(i["latency_ms"], i["status"], q["prec"], i["berr"], i["iters"]) for i, q in zip(infos, reqs)]
+        recs = [(i["latency_ms"], i["status"], q["prec"], i["berr"], i["iters"], q["m"], q["n"], i.get("reused", 0))
+                for i, q in zip(infos, reqs)]
         gathered = [None] * world
         dist.all_gather_object(gathered, recs)
         stats = srv.stats()
@@ -1072,8 +1073,8 @@ def run_serve(args, w):
             dist.destroy_process_group()
             return
         recs = [x for g in gathered for x in g]
-        infos = [dict(latency_ms=x[0], status=x[1], berr=x[3], iters=x[4]) for x in recs]
-        reqs = [dict(prec=x[2]) for x in recs]
+        infos = [dict(latency_ms=x[0], status=x[1], berr=x[3], iters=x[4], reused=x[7]) for x in recs]
+        reqs = [dict(prec=x[2], m=x[5], n=x[6]) for x in recs]
         t1 = t0 + span
     failures = {}
     for i, q in zip(infos, reqs):
@@ -1088,6 +1089,26 @@ def run_serve(args, w):
         return v[min(len(v) - 1, int(p * (len(v) - 1) + 0.5))] if v else None
     allv = sorted(i["latency_ms"] for i in infos)
     bad = sum(1 for i in infos if i["status"] != 0)
+    # what the slowest requests are: their sizes against the stream's (a tail
+    # of the largest factorizations is service time, one of small requests
+    # would be queueing)
+    work = sorted(2.0 * q["m"] * q["n"] ** 2 for q in reqs)
+    def work_rank(q):
+        import bisect
+        return bisect.bisect_left(work, 2.0 * q["m"] * q["n"] ** 2) / max(1, len(work) - 1)
+    thr = pct(allv, 0.99)
+    tail = [(i, q) for i, q in zip(infos, reqs) if thr is not None and i["latency_ms"] >= thr]
+    tail_info = None
+    if tail:
+        ranks = sorted(work_rank(q) for _, q in tail)
+        tail_info = {"requests": len(tail), "median_m": sorted(q["m"] for _, q in tail)[len(tail) // 2],
+                     "median_n": sorted(q["n"] for _, q in tail)[len(tail) // 2],
+                     "fresh_fraction": sum(1 for i, _ in tail if not i.get("reused")) / len(tail),
+                     "median_work_percentile": ranks[len(ranks) // 2]}
+    buckets = {}
+    for lo, hi in ((128, 512), (512, 2048), (2048, 8193)):
+        v = sorted(i["latency_ms"] for i, q in zip(infos, reqs) if lo <= q["m"] < hi)
+        buckets["m %d-%d" % (lo, hi - 1)] = {"count": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)}
     line = {"metric": "LS solves/s + p99 latency (served stream)", "value": len(reqs) / (t1 - t0), "unit": "solves/s",
             "n_gpus": world, "steps": 1, "warmup": 3, "ms_per_step": 1e3 * (t1 - t0), "higher_is_better": True,
             "scaling": "strong" if world > 1 else "weak", "vs_baseline": None,
@@ -1104,7 +1125,8 @@ def run_serve(args, w):
             "classes": {c: {"count": len(v), "p50_ms": pct(v, 0.5), "p99_ms": pct(v, 0.99)} for c, v in lat.items()},
             "reused_resident": stats["reused"] - base["reused"],
             "max_iters_fp32r": max([i["iters"] for i, q in zip(infos, reqs) if q["prec"] == "fp32r"] or [0]),
-            "max_berr": max(i["berr"] for i in infos)}
+            "max_berr": max(i["berr"] for i in infos),
+            "p99_tail": tail_info, "latency_by_m": buckets}
     if not args.no_cpu_baseline and world == 1:
         cnt, tt, smp = oracle_kind_sample("serve", {"rate": rate, "window": window}, 8.0)
         line["cpu_baseline"] = {"value": cnt / tt, "unit": "solves/s", "cores": 1, "kind": "oracle",

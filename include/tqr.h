@@ -493,7 +493,7 @@ int tqr_batch_wait(uint64_t ticket, int* status_per_item);
  * CUDA stream, admit a request as soon as a slot is free and the HBM budget
  * has room, so requests that arrive while others run start at once and their
  * task graphs overlap on the device (every persistent launch of a request is
- * capped at grid_cap CTAs; 0 = 2 * SMs * 2 / slots).  Factorizations stay
+ * capped at grid_cap CTAs; 0 = min(2 * SMs, 8 * SMs / slots)).  Factorizations stay
  * resident under the caller's matrix id (least recently used first out when
  * the budget is needed): a later request with the same id, size and
  * precision class skips the factorization (Q^T B and the back substitution
