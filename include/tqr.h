@@ -477,9 +477,11 @@ int tqr_batch_submit_pairs(int count, const tqr_desc* descs, uint64_t* ticket, v
 /*
  * Non-blocking completion check.  *done = 1 when the batch has finished;
  * then status_per_item (may be NULL, else `count` ints) receives each
- * matrix's status and the ticket is consumed.  Returns the batch status
- * (0, TQR_ERR_TIMEOUT, TQR_ERR_CUDA) once done, 0 while running, -1 for an
- * unknown ticket.
+ * matrix's status (TQR_ERR_NONFINITE for a matrix holding a NaN or an
+ * infinity, the others of the batch unaffected) and the ticket is consumed.
+ * Returns the batch status (0, TQR_ERR_TIMEOUT, TQR_ERR_CUDA, or
+ * TQR_ERR_NONFINITE if some matrix held one) once done, 0 while running, -1
+ * for an unknown ticket.
  */
 int tqr_batch_poll(uint64_t ticket, int* done, int* status_per_item);
 

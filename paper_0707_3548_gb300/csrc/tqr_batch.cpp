@@ -63,6 +63,8 @@ struct BatchPlan {
   Inst* h_insts = nullptr;     // pinned
   PackDesc* h_pack = nullptr;  // pinned
   int* h_status = nullptr;     // pinned
+  int* d_bad = nullptr;        // device: per-matrix non-finite flags
+  int* h_bad = nullptr;        // pinned copy of d_bad
   std::vector<size_t> tile_off, ctr_off;
   cudaGraphExec_t exec = nullptr;
   cudaEvent_t done = nullptr;
@@ -74,6 +76,8 @@ struct BatchPlan {
     if (d_insts) cudaFree(d_insts);
     if (d_pack) cudaFree(d_pack);
     if (d_tasks) cudaFree(d_tasks);
+    if (d_bad) cudaFree(d_bad);
+    if (h_bad) cudaFreeHost(h_bad);
     if (h_insts) cudaFreeHost(h_insts);
     if (h_pack) cudaFreeHost(h_pack);
     if (h_status) cudaFreeHost(h_status);
@@ -145,7 +149,9 @@ static int build_batch_plan(const std::vector<std::tuple<int64_t, int64_t, int, 
       cudaMalloc(&P->d_tasks, sizeof(TaskX) * std::max<size_t>(1, ordered.size())) != cudaSuccess ||
       cudaMallocHost(&P->h_insts, sizeof(Inst) * shape.size()) != cudaSuccess ||
       cudaMallocHost(&P->h_pack, sizeof(PackDesc) * shape.size()) != cudaSuccess ||
-      cudaMallocHost(&P->h_status, sizeof(int) * 4) != cudaSuccess) {
+      cudaMallocHost(&P->h_status, sizeof(int) * 4) != cudaSuccess ||
+      cudaMalloc(&P->d_bad, sizeof(int) * shape.size()) != cudaSuccess ||
+      cudaMallocHost(&P->h_bad, sizeof(int) * shape.size()) != cudaSuccess) {
     cudaGetLastError();
     return TQR_ERR_NOMEM;
   }
@@ -184,12 +190,14 @@ static int build_batch_plan(const std::vector<std::tuple<int64_t, int64_t, int, 
     if (cudaMemcpyAsync(P->d_insts, P->h_insts, sizeof(Inst) * n, cudaMemcpyHostToDevice, cap) != cudaSuccess ||
         cudaMemcpyAsync(P->d_pack, P->h_pack, sizeof(PackDesc) * n, cudaMemcpyHostToDevice, cap) != cudaSuccess ||
         cudaMemsetAsync(P->ws + P->ver_off, 0, P->ver_bytes, cap) != cudaSuccess ||
-        launch_pack_batched<double>(P->d_pack, P->count, cap) != cudaSuccess ||
+        cudaMemsetAsync(P->d_bad, 0, sizeof(int) * n, cap) != cudaSuccess ||
+        launch_pack_batched<double>(P->d_pack, P->count, cap, P->d_bad) != cudaSuccess ||
         (P->ntasks > 0 && launch_run<double>(P->d_tasks, P->ntasks, P->d_insts, P->ws + P->ctl_off, wait_limit_ns(),
                                              P->grid, P->smem, cap, P->pair ? 2 : 0) != cudaSuccess) ||
         launch_unpack_batched<double>(P->d_pack, P->count, cap) != cudaSuccess ||
         cudaMemcpyAsync(P->h_status, P->ws + P->ctl_off, sizeof(int) * 4, cudaMemcpyDeviceToHost, cap) !=
-            cudaSuccess)
+            cudaSuccess ||
+        cudaMemcpyAsync(P->h_bad, P->d_bad, sizeof(int) * n, cudaMemcpyDeviceToHost, cap) != cudaSuccess)
       status = TQR_ERR_CUDA;
     cudaError_t e = cudaStreamEndCapture(cap, &graph);
     if (e != cudaSuccess) status = TQR_ERR_CUDA;
@@ -300,9 +308,14 @@ static int poll_locked(uint64_t ticket, bool wait, int* done, int* status_per_it
     T.plan->busy = false;
   }
   if (done) *done = 1;
-  if (status_per_item)
-    for (int a = 0; a < T.count; ++a) status_per_item[a] = T.status;
-  const int s = T.status;
+  // a matrix with a NaN or an infinity reports TQR_ERR_NONFINITE (the others
+  // of the batch are unaffected: every matrix has its own tiles and DAG)
+  int s = T.status;
+  for (int a = 0; a < T.count; ++a) {
+    const int own = T.status != TQR_OK ? T.status : (T.plan->h_bad[a] != 0 ? TQR_ERR_NONFINITE : TQR_OK);
+    if (status_per_item) status_per_item[a] = own;
+    if (s == TQR_OK) s = own;
+  }
   g_tickets.erase(it);
   return s;
 }

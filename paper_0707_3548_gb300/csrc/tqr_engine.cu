@@ -2003,12 +2003,13 @@ __global__ void unpack_kernel(const S* __restrict__ Ab, int p, int nb, D* __rest
 // Batched pack/unpack: blockIdx.y (strided) picks the matrix, blockIdx.x
 // and the threads stride over its elements.
 template <typename D>
-__global__ void pack_batched_kernel(const PackDesc* __restrict__ descs, int count) {
+__global__ void pack_batched_kernel(const PackDesc* __restrict__ descs, int count, int* __restrict__ bad) {
   for (int b = blockIdx.y; b < count; b += gridDim.y) {
     const PackDesc d = descs[b];
     const long long nb2 = static_cast<long long>(d.nb) * d.nb;
     const long long total = nb2 * d.p * d.q;
     D* Ab = static_cast<D*>(d.Ab);
+    bool nonfinite = false;
     for (long long e = blockIdx.x * static_cast<long long>(blockDim.x) + threadIdx.x; e < total;
          e += static_cast<long long>(gridDim.x) * blockDim.x) {
       const long long tile = e / nb2;
@@ -2016,8 +2017,13 @@ __global__ void pack_batched_kernel(const PackDesc* __restrict__ descs, int coun
       const int r = rem % d.nb, c = rem / d.nb;
       const int ti = static_cast<int>(tile % d.p), tj = static_cast<int>(tile / d.p);
       const long long gi = static_cast<long long>(ti) * d.nb + r, gj = static_cast<long long>(tj) * d.nb + c;
-      Ab[e] = (gi < d.m && gj < d.n) ? static_cast<D>(d.A[gi + gj * d.lda]) : D(0);
+      const double v = (gi < d.m && gj < d.n) ? d.A[gi + gj * d.lda] : 0.0;
+      nonfinite = nonfinite || !isfinite(v);
+      Ab[e] = static_cast<D>(v);
     }
+    // a NaN or an infinity in matrix b: its status (the same value from
+    // every thread that saw one)
+    if (nonfinite && bad != nullptr) bad[b] = 9;  // TQR_ERR_NONFINITE
   }
 }
 
@@ -2211,10 +2217,10 @@ cudaError_t launch_identity(int m, int ncols, real* Ab, int p, int q, int nb, in
 }
 
 template <typename real>
-cudaError_t launch_pack_batched(const PackDesc* d, int count, cudaStream_t st) {
+cudaError_t launch_pack_batched(const PackDesc* d, int count, cudaStream_t st, int* bad) {
   if (count <= 0) return cudaSuccess;
   dim3 grid(8, count < 65535 ? count : 65535);
-  pack_batched_kernel<real><<<grid, 256, 0, st>>>(d, count);
+  pack_batched_kernel<real><<<grid, 256, 0, st>>>(d, count, bad);
   return cudaGetLastError();
 }
 
@@ -2362,7 +2368,7 @@ template cudaError_t launch_unpack_t<double>(const double*, int, int, double*, l
                                              cudaStream_t);
 template cudaError_t launch_identity<double>(int, int, double*, int, int, int, int, cudaStream_t);
 template cudaError_t launch_identity<float>(int, int, float*, int, int, int, int, cudaStream_t);
-template cudaError_t launch_pack_batched<double>(const PackDesc*, int, cudaStream_t);
+template cudaError_t launch_pack_batched<double>(const PackDesc*, int, cudaStream_t, int*);
 template cudaError_t launch_unpack_batched<double>(const PackDesc*, int, cudaStream_t);
 template cudaError_t occupancy<float>(int, int*);
 

@@ -39,8 +39,10 @@ struct PackDesc {
   void* Ab;       // its tiles in Block Data Layout
   int m, n, p, q, nb, pad;
 };
+// bad (device, count ints, zeroed by the caller; may be null): entry b is
+// set to TQR_ERR_NONFINITE when matrix b holds a NaN or an infinity.
 template <typename real>
-cudaError_t launch_pack_batched(const PackDesc* d, int count, cudaStream_t st);
+cudaError_t launch_pack_batched(const PackDesc* d, int count, cudaStream_t st, int* bad = nullptr);
 template <typename real>
 cudaError_t launch_unpack_batched(const PackDesc* d, int count, cudaStream_t st);
 

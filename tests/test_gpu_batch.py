@@ -68,6 +68,31 @@ def test_pairs_batch_equals_factor_pairs_alone():
         f = TL.tiled_qr_pairs(A, nb, ib)
         assert np.max(np.abs(to_host(dA) - f.F)) <= 1e-11 * max(1.0, np.abs(f.F).max())
 
+
+def test_batch_reports_nonfinite_per_matrix():
+    """A NaN in one matrix and an infinity in another: those two report
+    TQR_ERR_NONFINITE, the batch returns it, and every other matrix is
+    factored exactly as alone; a resubmission of the same shapes with finite
+    data (the graph replay) reports all clear."""
+    torch_cuda()
+    shapes = [(200, 120), (64, 64), (333, 17), (90, 90), (150, 150)]
+    tiles = [(64, 16), (32, 8), (32, 16), (32, 8), (64, 16)]
+    mats = [inputs.normal_matrix(m, n, 40 + a) for a, (m, n) in enumerate(shapes)]
+    mats[1][5, 7] = np.nan
+    mats[3][80, 2] = np.inf
+    t, dev, Ts = _submit(mats, tiles)
+    rc, st = tqr.tqr_batch_wait(t, len(mats))
+    assert rc == tqr.TQR_ERR_NONFINITE
+    assert list(st) == [0, tqr.TQR_ERR_NONFINITE, 0, tqr.TQR_ERR_NONFINITE, 0]
+    for a in (0, 2, 4):
+        F, Tr = _alone(mats[a], *tiles[a])
+        assert np.array_equal(to_host(dev[a]), F)
+        assert np.array_equal(Ts[a].cpu().numpy(), Tr)
+    clean = [inputs.normal_matrix(m, n, 60 + a) for a, (m, n) in enumerate(shapes)]
+    t, dev, Ts = _submit(clean, tiles)
+    rc, st = tqr.tqr_batch_wait(t, len(clean))
+    assert rc == 0 and not st.any()
+
 def test_batch_graph_replay_with_new_data_and_poll():
     torch = torch_cuda()
     shapes = [(200, 120), (64, 64), (333, 17), (90, 90)]
