@@ -118,6 +118,14 @@ __global__ void __launch_bounds__(kLsThreads) gemm_tn(const double* __restrict__
   if (j >= n) return;
   const double s = nA ? norm_scale(*nA) : 1.0;
   const double* a = A + static_cast<long long>(j) * lda;
+  // the scale is an exact power of two, so applying it once to a lane's sum
+  // gives the value of scaling every product (rounding commutes with it) up
+  // to products below FP64's normal range.  That form skips one FP64
+  // multiply per element, half of this kernel's FP64 instructions; it runs
+  // while s <= 2^200 (||A||_F >= 2^-200: the unscaled products are not the
+  // ones that underflow), and a lane whose unscaled sum overflows (or meets a
+  // NaN) takes the scaled loop instead.
+  const bool post = s <= 0x1p200;
   for (int c0 = 0; c0 < nrhs; c0 += kRhsChunk) {
     const int cw = min(kRhsChunk, nrhs - c0);
     double acc[kRhsChunk];
@@ -127,16 +135,31 @@ __global__ void __launch_bounds__(kLsThreads) gemm_tn(const double* __restrict__
       // one right-hand side: no predicated FMAs (they would still take
       // issue slots of the FP64 pipe), four independent partial sums
       const double* rr = R + static_cast<long long>(c0) * ldr;
-      double a1 = 0.0, a2 = 0.0, a3 = 0.0;
+      double a0 = 0.0, a1 = 0.0, a2 = 0.0, a3 = 0.0;
       int r = lane;
-      for (; r + 96 < m; r += 128) {
-        acc[0] = fma(a[r] * s, rr[r], acc[0]);
-        a1 = fma(a[r + 32] * s, rr[r + 32], a1);
-        a2 = fma(a[r + 64] * s, rr[r + 64], a2);
-        a3 = fma(a[r + 96] * s, rr[r + 96], a3);
+      if (post) {
+        for (; r + 96 < m; r += 128) {
+          a0 = fma(a[r], rr[r], a0);
+          a1 = fma(a[r + 32], rr[r + 32], a1);
+          a2 = fma(a[r + 64], rr[r + 64], a2);
+          a3 = fma(a[r + 96], rr[r + 96], a3);
+        }
+        for (; r < m; r += 32) a0 = fma(a[r], rr[r], a0);
       }
-      for (; r < m; r += 32) acc[0] = fma(a[r] * s, rr[r], acc[0]);
-      acc[0] += (a1 + a2) + a3;
+      double v = (a0 + ((a1 + a2) + a3)) * s;
+      if (!post || !isfinite(v)) {
+        a0 = a1 = a2 = a3 = 0.0;
+        r = lane;
+        for (; r + 96 < m; r += 128) {
+          a0 = fma(a[r] * s, rr[r], a0);
+          a1 = fma(a[r + 32] * s, rr[r + 32], a1);
+          a2 = fma(a[r + 64] * s, rr[r + 64], a2);
+          a3 = fma(a[r + 96] * s, rr[r + 96], a3);
+        }
+        for (; r < m; r += 32) a0 = fma(a[r] * s, rr[r], a0);
+        v = a0 + ((a1 + a2) + a3);
+      }
+      acc[0] = v;
     } else {
       for (int r = lane; r < m; r += 32) {
         const double av = a[r] * s;
