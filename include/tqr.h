@@ -481,7 +481,8 @@ int tqr_batch_submit_pairs(int count, const tqr_desc* descs, uint64_t* ticket, v
  * infinity, the others of the batch unaffected) and the ticket is consumed.
  * Returns the batch status (0, TQR_ERR_TIMEOUT, TQR_ERR_CUDA, or
  * TQR_ERR_NONFINITE if some matrix held one) once done, 0 while running, -1
- * for an unknown ticket.
+ * for an unknown ticket.  A finished batch keeps its statuses for its ticket
+ * even when a later submission of the same shapes reuses its plan.
  */
 int tqr_batch_poll(uint64_t ticket, int* done, int* status_per_item);
 

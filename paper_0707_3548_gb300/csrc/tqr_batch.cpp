@@ -92,11 +92,31 @@ struct Ticket {
   int count;
   bool finished;
   int status;
+  std::vector<int> item;  // per-matrix statuses, copied out when finished
 };
 static std::map<uint64_t, Ticket> g_tickets;
 static uint64_t g_next_ticket = 1;
 
 static size_t al256(size_t x) { return (x + 255) & ~static_cast<size_t>(255); }
+
+// Marks a ticket finished (its plan's launch done, or failed) and copies its
+// statuses out of the plan's read-back buffers, before a later submission of
+// the same plan can overwrite them.  Called with g_bmu held.
+static void finish_ticket(Ticket& T, cudaError_t e) {
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    T.status = TQR_ERR_CUDA;
+  } else {
+    T.status = T.plan->h_status[1] != 0 ? TQR_ERR_TIMEOUT : TQR_OK;
+  }
+  // a matrix with a NaN or an infinity reports TQR_ERR_NONFINITE (the others
+  // of the batch are unaffected: every matrix has its own tiles and DAG)
+  T.item.assign(T.count, TQR_OK);
+  for (int a = 0; a < T.count; ++a)
+    T.item[a] = T.status != TQR_OK ? T.status : (T.plan->h_bad[a] != 0 ? TQR_ERR_NONFINITE : TQR_OK);
+  T.finished = true;
+  T.plan->busy = false;
+}
 
 static int build_batch_plan(const std::vector<std::tuple<int64_t, int64_t, int, int>>& shape, int pair,
                             std::shared_ptr<BatchPlan>* out) {
@@ -260,8 +280,11 @@ static int batch_submit(int count, const tqr_desc* d, int pair, uint64_t* ticket
     while (g_bplans.size() > kMaxBatchPlans) g_bplans.pop_back();
   }
   if (P->busy) {
-    if (cudaEventQuery(P->done) == cudaErrorNotReady) return TQR_ERR_BUSY;
-    cudaGetLastError();
+    const cudaError_t q = cudaEventQuery(P->done);
+    if (q == cudaErrorNotReady) return TQR_ERR_BUSY;
+    // the previous batch on this plan finished unpolled: keep its statuses
+    for (auto& kv : g_tickets)
+      if (kv.second.plan == P && !kv.second.finished) finish_ticket(kv.second, q);
     P->busy = false;
   }
   for (int a = 0; a < count; ++a) {
@@ -275,7 +298,7 @@ static int batch_submit(int count, const tqr_desc* d, int pair, uint64_t* ticket
   }
   P->busy = true;
   const uint64_t t = g_next_ticket++;
-  g_tickets[t] = Ticket{P, count, false, TQR_OK};
+  g_tickets[t] = Ticket{P, count, false, TQR_OK, {}};
   *ticket = t;
   return TQR_OK;
 }
@@ -298,23 +321,13 @@ static int poll_locked(uint64_t ticket, bool wait, int* done, int* status_per_it
       if (done) *done = 0;
       return TQR_OK;
     }
-    if (e != cudaSuccess) {
-      cudaGetLastError();
-      T.status = TQR_ERR_CUDA;
-    } else {
-      T.status = T.plan->h_status[1] != 0 ? TQR_ERR_TIMEOUT : TQR_OK;
-    }
-    T.finished = true;
-    T.plan->busy = false;
+    finish_ticket(T, e);
   }
   if (done) *done = 1;
-  // a matrix with a NaN or an infinity reports TQR_ERR_NONFINITE (the others
-  // of the batch are unaffected: every matrix has its own tiles and DAG)
   int s = T.status;
   for (int a = 0; a < T.count; ++a) {
-    const int own = T.status != TQR_OK ? T.status : (T.plan->h_bad[a] != 0 ? TQR_ERR_NONFINITE : TQR_OK);
-    if (status_per_item) status_per_item[a] = own;
-    if (s == TQR_OK) s = own;
+    if (status_per_item) status_per_item[a] = T.item[a];
+    if (s == TQR_OK) s = T.item[a];
   }
   g_tickets.erase(it);
   return s;

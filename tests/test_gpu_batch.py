@@ -93,6 +93,28 @@ def test_batch_reports_nonfinite_per_matrix():
     rc, st = tqr.tqr_batch_wait(t, len(clean))
     assert rc == 0 and not st.any()
 
+
+def test_unpolled_ticket_keeps_its_statuses_when_the_plan_is_reused():
+    """A finished batch that was never polled, then a new submission of the
+    same shapes: the first ticket still reports its own per-matrix statuses
+    (here a NaN in matrix 2), the second its own."""
+    torch = torch_cuda()
+    shapes = [(120, 80), (77, 77), (210, 40)]
+    tiles = [(32, 8), (32, 8), (64, 16)]
+    first = [inputs.normal_matrix(m, n, 70 + a) for a, (m, n) in enumerate(shapes)]
+    first[2][3, 3] = np.nan
+    t1, dev1, Ts1 = _submit(first, tiles)
+    torch.cuda.synchronize()
+    second = [inputs.normal_matrix(m, n, 80 + a) for a, (m, n) in enumerate(shapes)]
+    t2, dev2, Ts2 = _submit(second, tiles)
+    rc2, st2 = tqr.tqr_batch_wait(t2, len(second))
+    rc1, st1 = tqr.tqr_batch_wait(t1, len(first))
+    assert rc1 == tqr.TQR_ERR_NONFINITE and list(st1) == [0, 0, tqr.TQR_ERR_NONFINITE]
+    assert rc2 == 0 and not st2.any()
+    for a in range(len(second)):
+        F, Tr = _alone(second[a], *tiles[a])
+        assert np.array_equal(to_host(dev2[a]), F)
+
 def test_batch_graph_replay_with_new_data_and_poll():
     torch = torch_cuda()
     shapes = [(200, 120), (64, 64), (333, 17), (90, 90)]
