@@ -576,28 +576,35 @@ bool order_bottom_level(const std::vector<Inst>& insts, const std::vector<TaskX>
   const std::vector<int64_t> base = counter_bases(insts);
   const int64_t nctr = base.back();
   const int64_t n = static_cast<int64_t>(seq.size());
+  // every task's rules once (the three passes below reuse them)
+  struct Rules {
+    Wait w[kMaxWaits];
+    Signal sg[kMaxSignals];
+    int8_t nw, nsig;
+  };
+  std::vector<Rules> rules(static_cast<size_t>(n));
   std::vector<int64_t> wptr(nctr + 1, 0);
-  Wait w[kMaxWaits];
-  Signal sg[kMaxSignals];
-  int nsig;
   for (int64_t t = 0; t < n; ++t) {
-    task_rules(insts[seq[t].inst], seq[t], w, sg, &nsig);
+    Rules& R = rules[t];
+    int nsig = 0;
+    R.nw = static_cast<int8_t>(task_rules(insts[seq[t].inst], seq[t], R.w, R.sg, &nsig));
+    R.nsig = static_cast<int8_t>(nsig);
     for (int a = 0; a < nsig; ++a)
-      for (int c = 0; c < sg[a].cnt; ++c) wptr[base[seq[t].inst] + sg[a].ctr + c + 1]++;
+      for (int c = 0; c < R.sg[a].cnt; ++c) wptr[base[seq[t].inst] + R.sg[a].ctr + c + 1]++;
   }
   for (int64_t c = 0; c < nctr; ++c) wptr[c + 1] += wptr[c];
   std::vector<int> writers(static_cast<size_t>(wptr[nctr]));
   {
     std::vector<int64_t> fill(wptr.begin(), wptr.end() - 1);
     for (int64_t t = 0; t < n; ++t) {
-      const int nw = task_rules(insts[seq[t].inst], seq[t], w, sg, &nsig);
-      for (int a = 0; a < nsig; ++a)
-        for (int c = 0; c < sg[a].cnt; ++c) {
-          const int ctr = sg[a].ctr + c;
+      const Rules& R = rules[t];
+      for (int a = 0; a < R.nsig; ++a)
+        for (int c = 0; c < R.sg[a].cnt; ++c) {
+          const int ctr = R.sg[a].ctr + c;
           const int64_t g = base[seq[t].inst] + ctr;
           int need = -1;
-          for (int b = 0; b < nw; ++b)
-            if (ctr >= w[b].ctr && ctr < w[b].ctr + w[b].cnt) need = w[b].ver;
+          for (int b = 0; b < R.nw; ++b)
+            if (ctr >= R.w[b].ctr && ctr < R.w[b].ctr + R.w[b].cnt) need = R.w[b].ver;
           if (need != fill[g] - wptr[g]) {
             if (err) *err = "rule mismatch in task " + std::to_string(t);
             return false;
@@ -614,16 +621,16 @@ bool order_bottom_level(const std::vector<Inst>& insts, const std::vector<TaskX>
     work += c;
     bl[t] = c + maxsucc[t];
     cp = std::max(cp, bl[t]);
-    const int nw = task_rules(I, seq[t], w, sg, &nsig);
-    for (int b = 0; b < nw; ++b) {
-      if (w[b].ver <= 0) continue;
-      for (int cc = 0; cc < w[b].cnt; ++cc) {
-        const int64_t g = base[seq[t].inst] + w[b].ctr + cc;
-        if (wptr[g + 1] - wptr[g] < w[b].ver) {
+    const Rules& R = rules[t];
+    for (int b = 0; b < R.nw; ++b) {
+      if (R.w[b].ver <= 0) continue;
+      for (int cc = 0; cc < R.w[b].cnt; ++cc) {
+        const int64_t g = base[seq[t].inst] + R.w[b].ctr + cc;
+        if (wptr[g + 1] - wptr[g] < R.w[b].ver) {
           if (err) *err = "rule error: missing writer for task " + std::to_string(t);
           return false;
         }
-        const int pw = writers[wptr[g] + w[b].ver - 1];
+        const int pw = writers[wptr[g] + R.w[b].ver - 1];
         if (pw >= t) {
           if (err) *err = "rule error: task depends on a later task";
           return false;
@@ -632,14 +639,13 @@ bool order_bottom_level(const std::vector<Inst>& insts, const std::vector<TaskX>
       }
     }
   }
-  std::vector<int> idx(static_cast<size_t>(n));
-  for (int64_t t = 0; t < n; ++t) idx[t] = static_cast<int>(t);
-  std::sort(idx.begin(), idx.end(), [&bl](int x, int y) {
-    if (bl[x] != bl[y]) return bl[x] > bl[y];
-    return x < y;
-  });
+  // decreasing bottom level, ties by sequential index (keys sorted in place:
+  // no indirection in the comparisons)
+  std::vector<std::pair<double, int>> key(static_cast<size_t>(n));
+  for (int64_t t = 0; t < n; ++t) key[t] = std::make_pair(-bl[t], static_cast<int>(t));
+  std::sort(key.begin(), key.end());
   ordered.resize(static_cast<size_t>(n));
-  for (int64_t a = 0; a < n; ++a) ordered[a] = seq[idx[a]];
+  for (int64_t a = 0; a < n; ++a) ordered[a] = seq[key[a].second];
   if (stats) {
     stats->policy = 2;
     stats->critical_path_s = cp;
