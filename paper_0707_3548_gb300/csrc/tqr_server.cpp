@@ -26,6 +26,7 @@
 #include <mutex>
 #include <string>
 #include <thread>
+#include <tuple>
 #include <vector>
 
 #include "tqr.h"
@@ -89,6 +90,10 @@ struct tqr_server {
   std::vector<double> lat_ms;  // completed requests
   int64_t completed = 0, reused = 0, failed = 0;
   std::string last_failure;    // description of the latest failed request
+  // sized least-squares jobs per (m, n, class): sizing picks the tile grid's
+  // tree domain by a critical-path estimate per candidate (tens of ms for the
+  // largest grids), done outside the lock the first time a shape arrives
+  std::map<std::tuple<int64_t, int64_t, int>, std::pair<bool, tqr::LsJob>> shapes;
 };
 
 namespace tqr {
@@ -243,6 +248,7 @@ static void worker(tqr_server* S) {
     std::shared_ptr<Request> R;
     std::shared_ptr<Entry> entry;
     bool fresh = false;
+    bool rescan = false;
     for (auto it = S->pending.begin(); it != S->pending.end() && !R; ++it) {
       std::shared_ptr<Entry> e = find_entry(S, **it);
       if (e) {
@@ -254,9 +260,25 @@ static void worker(tqr_server* S) {
       }
       // a new factorization; only the head of the queue may evict, so large
       // requests are not starved by smaller ones behind them
+      const auto key = std::make_tuple((*it)->m, (*it)->n, (*it)->prec);
+      auto sized = S->shapes.find(key);
+      if (sized == S->shapes.end()) {
+        // size this shape without holding the lock, then scan again (the
+        // queue may have changed meanwhile)
+        const int64_t m = (*it)->m, n = (*it)->n;
+        const int prec = (*it)->prec, cap = S->grid_cap;
+        lk.unlock();
+        int nb = 0, ib = 0;
+        autotune(m, n, &nb, &ib);
+        LsJob tmpl;
+        const bool ok = tmpl.init(static_cast<int>(m), static_cast<int>(n), 16, nb, ib, prec, cap);
+        lk.lock();
+        if (S->shapes.size() >= 4096) S->shapes.clear();
+        S->shapes.emplace(key, std::make_pair(ok, tmpl));
+        rescan = true;
+        break;
+      }
       auto job = std::make_shared<Entry>();
-      int nb = 0, ib = 0;
-      autotune((*it)->m, (*it)->n, &nb, &ib);
       auto refuse = [&](int code) {
         (*it)->status = code;
         (*it)->t_start = (*it)->t_end = Clock::now();
@@ -271,8 +293,8 @@ static void worker(tqr_server* S) {
         S->pending.erase(it);
         S->cv_done.notify_all();
       };
-      if (!job->job.init(static_cast<int>((*it)->m), static_cast<int>((*it)->n), 16, nb, ib, (*it)->prec,
-                         S->grid_cap)) {
+      job->job = sized->second.second;
+      if (!sized->second.first) {
         refuse(TQR_ERR_UNSUPPORTED);
         break;
       }
@@ -306,6 +328,7 @@ static void worker(tqr_server* S) {
       S->pending.erase(it);
       break;
     }
+    if (rescan) continue;
     if (R) {
       entry->busy = true;
       // move to the front of the LRU list
