@@ -14,6 +14,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <thread>
 #include <string>
 #include <tuple>
 #include <vector>
@@ -442,25 +443,38 @@ int choose_domain(int64_t m, int64_t n, int nb, int ib, int esize) {
   int cs, occ, smem;
   if (!choose_shape(nb, ib, esize, &cs, &occ, &smem)) return 0;
   const int workers = std::max(1, device_sms()) * occ;
-  int best_d = 0;
-  double best = INFINITY, flat = INFINITY;
-  for (int D : {0, 64, 32, 16, 8, 4, 2, 1}) {
+  auto estimate = [&](int D, double* cp, double* work) {
     Inst I = make_inst(M_FACTOR, m, n, nb, ib, cs, 0, 0);
-    if (D >= I.p) continue;
     I.D = D;
     if (D > 0) I.vtab = host_vtab(I);
-    double cp = 0, work = 0;
-    critical_path_estimate(I, esize, occ, &cp, &work);
-    const double est = std::max(cp, work / workers);
-    if (D == 0) {
-      flat = est;
-      // work-bound: a tree only adds work
-      if (cp <= work / workers) break;
-    }
-    if (est < best) {
-      best = est;
-      best_d = D;
-    }
+    critical_path_estimate(I, esize, occ, cp, work);
+  };
+  double cp0 = 0, work0 = 0;
+  estimate(0, &cp0, &work0);
+  const double flat = std::max(cp0, work0 / workers);
+  int best_d = 0;
+  double best = flat;
+  // work-bound: a tree only adds work; otherwise the tree candidates are
+  // estimated side by side (one host thread each: each is a pass over the
+  // task list, tens of ms in all for the largest grids)
+  if (cp0 > work0 / workers) {
+    std::vector<int> cands;
+    for (int D : {64, 32, 16, 8, 4, 2, 1})
+      if (D < p) cands.push_back(D);
+    std::vector<double> est(cands.size(), INFINITY);
+    std::vector<std::thread> th;
+    for (size_t a = 0; a < cands.size(); ++a)
+      th.emplace_back([&, a]() {
+        double cp = 0, work = 0;
+        estimate(cands[a], &cp, &work);
+        est[a] = std::max(cp, work / workers);
+      });
+    for (auto& t : th) t.join();
+    for (size_t a = 0; a < cands.size(); ++a)
+      if (est[a] < best) {
+        best = est[a];
+        best_d = cands[a];
+      }
   }
   if (best_d != 0 && !(best < 0.95 * flat)) best_d = 0;
   std::lock_guard<std::mutex> lk(mu);
